@@ -1,0 +1,247 @@
+"""FP64 CPU oracle of the DRTS time step (arXiv:1611.08536, Eq. 18-27).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product (the
+CUDA library and its binding) never does, and shares no code with it.
+
+The arithmetic lives in ``drts_oracle.c`` (plain C, FP64, no FMA
+contraction); this module only compiles it with gcc and marshals numpy arrays.
+
+Parity status of each function (pins are in ``tests/test_oracle_pins.py``):
+  * ``raw_stencil``   pinned: closed-form weights of Eq. 18/19, HG g=0, Eq. 24
+                      column sums.
+  * ``assemble``      pinned: column sums, mirror conservation, dense brute
+                      force on 4^3, ballistic translation, single-scatter line,
+                      irreducibility.
+  * ``column_info``   pinned: Fresnel normal incidence, total internal
+                      reflection, ledger closure.
+  * ``run``           pinned: conservation, pure decay, dense matrix powers.
+  * interface / edge folding geometry (Section 4.2 readings): parity
+    unpinned beyond the invariants above; the paper prints no numbers for it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "drts_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OPEN, MIRROR, FRESNEL = 0, 1, 2
+NDIR = 26
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP when available)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11",
+            _SRC, "-o", _LIB + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("h", ctypes.c_double),
+        ("n_media", ctypes.c_int32),
+        ("mu_s", ctypes.c_void_p), ("mu_a", ctypes.c_void_p),
+        ("g", ctypes.c_void_p), ("n", ctypes.c_void_p),
+        ("medium", ctypes.c_void_p),
+        ("n_outside", ctypes.c_double),
+        ("boundary", ctypes.c_int32),
+        ("det_face", ctypes.c_int32),
+        ("det_nu", ctypes.c_int32), ("det_nv", ctypes.c_int32),
+    ]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER(_Problem)
+            vp = ctypes.c_void_p
+            lib.orc_assemble.restype = vp
+            lib.orc_assemble.argtypes = [P, ctypes.c_int, ctypes.c_int]
+            lib.orc_csr_info.argtypes = [vp, vp, vp, vp]
+            lib.orc_csr_copy.argtypes = [vp, vp, vp, vp]
+            lib.orc_csr_free.argtypes = [vp]
+            lib.orc_column_info.argtypes = [P, vp, vp, vp, vp]
+            lib.orc_spmv.argtypes = [vp, vp, vp, ctypes.c_int]
+            lib.orc_run.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int32, vp, vp, ctypes.c_int64,
+                                    ctypes.c_int32, vp, vp, vp, vp, vp,
+                                    ctypes.c_int32, vp, vp, ctypes.c_int]
+            lib.orc_raw_stencil.argtypes = [P, ctypes.c_int, vp]
+            lib.orc_fresnel.restype = ctypes.c_double
+            lib.orc_fresnel.argtypes = [ctypes.c_double] * 3
+            lib.orc_direction.argtypes = [ctypes.c_int, vp]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Problem:
+    """Marshals a problem description (any object with the fields of
+    ``paper_1611_08536_gb300.inputs.Problem``) into the oracle's struct."""
+
+    def __init__(self, prob):
+        self.keep = [
+            np.ascontiguousarray([m[0] for m in prob.media], dtype=np.float64),
+            np.ascontiguousarray([m[1] for m in prob.media], dtype=np.float64),
+            np.ascontiguousarray([m[2] for m in prob.media], dtype=np.float64),
+            np.ascontiguousarray([m[3] for m in prob.media], dtype=np.float64),
+            np.ascontiguousarray(prob.medium_of_voxel, dtype=np.uint8).ravel(),
+        ]
+        nx, ny, nz = prob.shape
+        assert self.keep[4].size == nx * ny * nz
+        self.s = _Problem(nx, ny, nz, float(prob.voxel_mm), len(prob.media),
+                          _ptr(self.keep[0]), _ptr(self.keep[1]),
+                          _ptr(self.keep[2]), _ptr(self.keep[3]),
+                          _ptr(self.keep[4]), float(prob.n_outside),
+                          int(prob.boundary), int(prob.det_face),
+                          int(prob.det_nu), int(prob.det_nv))
+        self.shape = (nx, ny, nz)
+        self.n_states = nx * ny * nz * NDIR
+
+
+class CSR:
+    """Oracle CSR rows (canonical row order, ascending columns)."""
+
+    def __init__(self, row_ptr, col, val, row0):
+        self.row_ptr, self.col, self.val, self.row0 = row_ptr, col, val, row0
+        self._h = None
+
+    @property
+    def n_rows(self):
+        return self.row_ptr.size - 1
+
+    @property
+    def nnz(self):
+        return int(self.row_ptr[-1])
+
+    def __del__(self):
+        if self._h is not None and _lib is not None:
+            _lib.orc_csr_free(self._h)
+            self._h = None
+
+
+def assemble(prob, z0: int = 0, z1: int | None = None) -> CSR:
+    """Rows of A (Eq. 21-23) for voxel planes [z0, z1)."""
+    lib = _load()
+    P = prob if isinstance(prob, Problem) else Problem(prob)
+    if z1 is None:
+        z1 = P.shape[2]
+    h = lib.orc_assemble(ctypes.byref(P.s), int(z0), int(z1))
+    if not h:
+        raise ValueError("oracle: invalid problem or plane range")
+    n_rows, nnz, row0 = (np.zeros(1, np.int64) for _ in range(3))
+    lib.orc_csr_info(h, _ptr(n_rows), _ptr(nnz), _ptr(row0))
+    rp = np.empty(int(n_rows[0]) + 1, np.int64)
+    col = np.empty(int(nnz[0]), np.int32)
+    val = np.empty(int(nnz[0]), np.float64)
+    lib.orc_csr_copy(h, _ptr(rp), _ptr(col), _ptr(val))
+    c = CSR(rp, col, val, int(row0[0]))
+    c._h = h
+    return c
+
+
+def column_info(prob):
+    """Per-state absorb, exit_total, exit_det and detector patch (Eq. 8, 27)."""
+    lib = _load()
+    P = prob if isinstance(prob, Problem) else Problem(prob)
+    n = P.n_states
+    ab, ex, ed = (np.empty(n, np.float64) for _ in range(3))
+    patch = np.empty(n, np.int32)
+    if lib.orc_column_info(ctypes.byref(P.s), _ptr(ab), _ptr(ex), _ptr(ed),
+                           _ptr(patch)):
+        raise ValueError("oracle: invalid problem")
+    return ab, ex, ed, patch
+
+
+def spmv(csr: CSR, x: np.ndarray, n_threads: int = 0) -> np.ndarray:
+    """y = A x over the rows of ``csr`` (x in canonical state order)."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.empty(csr.n_rows, np.float64)
+    if csr._h is None:
+        raise ValueError("CSR not owned by the oracle")
+    lib.orc_spmv(csr._h, _ptr(x), _ptr(y), int(n_threads))
+    return y
+
+
+def run(prob, csr: CSR, n_steps: int, sources, x0=None, t_begin: int = 0,
+        colinfo=None, n_threads: int = 0):
+    """Run Eq. 26 for ``n_steps`` from ``x0`` (zeros by default).
+
+    ``sources`` = (state_idx int64[], weight float64[], t0, profile float64[]).
+    Returns (x, det[n_steps][n_patch], ledger[4] = {sum x, injected,
+    absorbed, exited}).
+    """
+    lib = _load()
+    P = prob if isinstance(prob, Problem) else Problem(prob)
+    if csr.row0 != 0 or csr.n_rows != P.n_states:
+        raise ValueError("run needs the full-grid CSR")
+    ab, ex, ed, patch = colinfo if colinfo is not None else column_info(P)
+    x = (np.zeros(P.n_states) if x0 is None
+         else np.array(x0, dtype=np.float64, copy=True))
+    st, w, t0, prof = sources
+    st = np.ascontiguousarray(st, dtype=np.int64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    prof = np.ascontiguousarray(prof, dtype=np.float64)
+    n_patch = max(int(patch.max()) + 1, 1)
+    det = np.zeros((n_steps, n_patch), np.float64)
+    ledger = np.zeros(4, np.float64)
+    rc = lib.orc_run(csr._h, _ptr(x), int(t_begin), int(n_steps), st.size,
+                     _ptr(st), _ptr(w), int(t0), prof.size, _ptr(prof),
+                     _ptr(ab), _ptr(ex), _ptr(ed), _ptr(patch), n_patch,
+                     _ptr(det), _ptr(ledger), int(n_threads))
+    if rc:
+        raise RuntimeError(f"oracle run failed ({rc})")
+    return x, det, ledger
+
+
+def raw_stencil(prob, k: int) -> np.ndarray:
+    """Unfolded W[n][o][m] of medium k, o = (oz+1)*9 + (oy+1)*3 + (ox+1)."""
+    lib = _load()
+    P = prob if isinstance(prob, Problem) else Problem(prob)
+    W = np.empty((NDIR, 27, NDIR), np.float64)
+    if lib.orc_raw_stencil(ctypes.byref(P.s), int(k), _ptr(W)):
+        raise ValueError("oracle: invalid problem")
+    return W
+
+
+def fresnel(cos_i: float, n1: float, n2: float) -> float:
+    return _load().orc_fresnel(float(cos_i), float(n1), float(n2))
+
+
+def direction(d: int):
+    out = np.zeros(3, np.int32)
+    _load().orc_direction(int(d), _ptr(out))
+    return tuple(int(v) for v in out)
+
+
+def max_threads() -> int:
+    lib = _load()
+    lib.orc_max_threads.restype = ctypes.c_int
+    return lib.orc_max_threads()

@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test names the passage it follows.  None of them compares the oracle with
+itself: they use closed forms (tests/golden/closed_forms.json), invariants of
+Eq. 23/24, special cases that reduce to exact translation or exponential
+decay, a brute-force dense transcription on 4^3 grids, and graph properties.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.sparse.csgraph import connected_components
+
+from paper_1611_08536_gb300 import inputs as I
+
+GOLD = {c["name"]: c["value"] for c in json.load(open(os.path.join(
+    os.path.dirname(__file__), "golden", "closed_forms.json")))["cases"]}
+
+
+def _prob(n, media, boundary=I.MIRROR, mov=None, h=0.1, n_out=1.0, det=(I.FACE_PZ, 2, 2)):
+    shape = (n, n, n) if isinstance(n, int) else n
+    if mov is None:
+        mov = np.zeros(shape[::-1], np.uint8)
+    return I.Problem(shape, h, list(media), mov, n_out, boundary, I.FP64, 1,
+                     det[0], det[1], det[2])
+
+
+def _oidx(ox, oy, oz):
+    return (oz + 1) * 9 + (oy + 1) * 3 + (ox + 1)
+
+
+def _sparse(c):
+    return sp.csr_matrix((c.val, c.col, c.row_ptr), shape=(c.n_rows, c.n_rows))
+
+
+D = I.direction_index
+
+# --------------------------------------------------------------------------
+# Eq. 18: unscattered weights, closed forms
+
+
+def test_axis_direction_single_target(oracle_mod):
+    W = oracle_mod.raw_stencil(_prob(4, [(0.0, 0.0, 0.0, 1.0)]), 0)
+    n = D(1, 0, 0)
+    nz = np.argwhere(W[n] > 0)
+    assert nz.tolist() == [[_oidx(1, 0, 0), n]]
+    assert W[n, _oidx(1, 0, 0), n] == GOLD["axis_unscattered_single_target"]
+
+
+def test_edge_direction_closed_form(oracle_mod):
+    W = oracle_mod.raw_stencil(_prob(4, [(0.0, 0.0, 0.0, 1.0)]), 0)
+    n = D(1, 1, 0)
+    got = {tuple(o): W[n, o[0], o[1]] for o in np.argwhere(W[n] > 0)}
+    assert set(got) == {(_oidx(1, 1, 0), n), (_oidx(1, 0, 0), n), (_oidx(0, 1, 0), n)}
+    assert got[(_oidx(1, 1, 0), n)] == pytest.approx(GOLD["edge_unscattered_diag"], rel=1e-14)
+    assert got[(_oidx(1, 0, 0), n)] == pytest.approx(GOLD["edge_unscattered_axis"], rel=1e-14)
+    assert got[(_oidx(0, 1, 0), n)] == pytest.approx(GOLD["edge_unscattered_axis"], rel=1e-14)
+
+
+def test_corner_direction_seven_targets(oracle_mod):
+    W = oracle_mod.raw_stencil(_prob(4, [(0.0, 0.0, 0.0, 1.0)]), 0)
+    n = D(1, 1, 1)
+    got = {o: W[n, o, n] for o in range(27) if W[n, o, n] > 0}
+    assert len(got) == 7 and _oidx(0, 0, 0) not in got      # origin is exactly 2dr away
+    assert got[_oidx(1, 1, 1)] == pytest.approx(GOLD["corner_unscattered_111"], rel=1e-14)
+    for o in [(1, 1, 0), (1, 0, 1), (0, 1, 1)]:
+        assert got[_oidx(*o)] == pytest.approx(GOLD["corner_unscattered_110"], rel=1e-14)
+    for o in [(1, 0, 0), (0, 1, 0), (0, 0, 1)]:
+        assert got[_oidx(*o)] == pytest.approx(GOLD["corner_unscattered_100"], rel=1e-14)
+
+
+def test_unscattered_survival_factor(oracle_mod):
+    # Eq. 9: the unscattered share is exp(-mu_s L) exp(-mu_a L), L = h
+    mu_s, mu_a, h = 3.0, 0.7, 0.1
+    W = oracle_mod.raw_stencil(_prob(4, [(mu_s, mu_a, 0.0, 1.0)], h=h), 0)
+    n = D(1, 0, 0)
+    scat = (1 - math.exp(-mu_s * h)) * math.exp(-mu_a * h) / 26 * (1 / 3)
+    # target (1,0,0) along +x gets the unscattered part plus 1/3 of the
+    # S->S scatter (segment AB collapses to B, Eq. 21)
+    expect = math.exp(-mu_s * h) * math.exp(-mu_a * h) + (1 - math.exp(-mu_s * h)) * \
+        math.exp(-mu_a * h) / 26
+    assert W[n, _oidx(1, 0, 0), n] == pytest.approx(expect, rel=1e-13)
+    assert scat > 0
+
+# --------------------------------------------------------------------------
+# Eq. 19: scattered weights, closed forms
+
+
+def test_opposite_scatter_three_points(oracle_mod):
+    mu_s, mu_a, h = 5.0, 0.0, 0.1
+    W = oracle_mod.raw_stencil(_prob(4, [(mu_s, mu_a, 0.0, 1.0)], h=h), 0)
+    n, m = D(1, 0, 0), D(-1, 0, 0)
+    frac = GOLD["hg_uniform_g0"] * (1 - math.exp(-mu_s * h))
+    got = {o: W[n, o, m] for o in range(27) if W[n, o, m] > 0}
+    assert set(got) == {_oidx(-1, 0, 0), _oidx(0, 0, 0), _oidx(1, 0, 0)}
+    for v in got.values():
+        assert v == pytest.approx(frac * GOLD["opposite_scatter_each_of_three"], rel=1e-13)
+
+
+def test_perpendicular_scatter_four_points(oracle_mod):
+    mu_s, mu_a, h = 5.0, 0.2, 0.1
+    W = oracle_mod.raw_stencil(_prob(4, [(mu_s, mu_a, 0.0, 1.0)], h=h), 0)
+    n, m = D(1, 0, 0), D(0, 1, 0)
+    frac = GOLD["hg_uniform_g0"] * (1 - math.exp(-mu_s * h)) * math.exp(-mu_a * h)
+    got = {o: W[n, o, m] for o in range(27) if W[n, o, m] > 0}
+    assert set(got) == {_oidx(1, 0, 0), _oidx(0, 1, 0), _oidx(0, 0, 0), _oidx(1, 1, 0)}
+    for o in [(1, 0, 0), (0, 1, 0)]:
+        assert got[_oidx(*o)] == pytest.approx(frac * GOLD["perpendicular_scatter_endpoint"], rel=1e-13)
+    for o in [(0, 0, 0), (1, 1, 0)]:
+        assert got[_oidx(*o)] == pytest.approx(frac * GOLD["perpendicular_scatter_midpoint"], rel=1e-13)
+
+
+def test_isotropic_kernel_uniform(oracle_mod):
+    # g = 0: every S -> S' pair carries 1/26 of the scattered fraction
+    mu_s, h = 2.0, 0.1
+    W = oracle_mod.raw_stencil(_prob(4, [(mu_s, 0.0, 0.0, 1.0)], h=h), 0)
+    for n in range(26):
+        per_m = W[n].sum(axis=0)
+        unsc = math.exp(-mu_s * h)
+        for m in range(26):
+            expect = GOLD["hg_uniform_g0"] * (1 - unsc) + (unsc if m == n else 0.0)
+            assert per_m[m] == pytest.approx(expect, rel=1e-13)
+
+
+def test_hg_forward_bias_monotone(oracle_mod):
+    # HG with g > 0 favours small deflections: scattered share decreases with angle
+    W = oracle_mod.raw_stencil(_prob(4, [(5.0, 0.0, 0.9, 1.0)]), 0)
+    n = D(0, 0, 1)
+    sv = np.array(I.direction_vector(n)) / 1.0
+    share = W[n].sum(axis=0)
+    share[n] -= math.exp(-0.5)
+    cos = [np.dot(sv, I.direction_vector(m)) / np.linalg.norm(I.direction_vector(m))
+           for m in range(26)]
+    order = np.argsort(cos)
+    s = share[order]
+    c = np.array(cos)[order]
+    for a in range(25):
+        if c[a + 1] > c[a] + 1e-12:
+            assert s[a + 1] > s[a]
+
+# --------------------------------------------------------------------------
+# Properties listed under Eq. 24
+
+
+@pytest.mark.parametrize("mu_s,mu_a,g", [(10.0, 0.01, 0.9), (3.0, 1.0, 0.0), (0.0, 0.5, 0.5)])
+def test_interior_column_sums_equal_absorption_survival(oracle_mod, mu_s, mu_a, g):
+    h = 0.1
+    prob = _prob(6, [(mu_s, mu_a, g, 1.4)], boundary=I.OPEN, h=h)
+    A = _sparse(oracle_mod.assemble(prob))
+    cs = np.asarray(A.sum(axis=0)).ravel().reshape(6, 6, 6, 26)
+    interior = cs[1:-1, 1:-1, 1:-1]
+    assert np.allclose(interior, math.exp(-mu_a * h), rtol=0, atol=1e-14)
+
+
+def test_diagonal_zero_and_unit_interval(oracle_mod):
+    prob = _prob(5, [(10.0, 0.01, 0.9, 1.4)], boundary=I.FRESNEL)
+    c = oracle_mod.assemble(prob)
+    A = _sparse(c)
+    # L = h: zero diagonal away from the edge (edge reflection can send a
+    # photon travelling along the face back into its own state)
+    assert np.all(A.diagonal().reshape(5, 5, 5, 26)[1:-1, 1:-1, 1:-1] == 0.0)
+    assert c.val.min() > 0.0 and c.val.max() <= 1.0
+
+
+def test_mirror_columns_sum_to_survival_everywhere(oracle_mod):
+    prob = _prob(4, [(7.0, 0.3, 0.8, 1.3)], boundary=I.MIRROR)
+    A = _sparse(oracle_mod.assemble(prob))
+    cs = np.asarray(A.sum(axis=0)).ravel()
+    assert np.allclose(cs, math.exp(-0.3 * 0.1), rtol=0, atol=1e-14)
+
+
+def test_irreducible_on_4cube(oracle_mod):
+    prob = _prob(4, [(5.0, 0.1, 0.7, 1.4)], boundary=I.MIRROR)
+    A = _sparse(oracle_mod.assemble(prob))
+    ncomp, _ = connected_components(A, directed=True, connection="strong")
+    assert ncomp == 1
+
+# --------------------------------------------------------------------------
+# Time stepping (Eq. 23, 26): conservation, decay, translation
+
+
+def _layers4(n=6, mu_a=0.0, mu_s=(8.0, 4.0), ns=(1.45, 1.37), boundary=I.MIRROR):
+    mov = np.zeros((n, n, n), np.uint8)
+    mov[n // 2:] = 1
+    media = [(mu_s[0], mu_a, 0.85, ns[0]), (mu_s[1], mu_a, 0.9, ns[1])]
+    return _prob(n, media, boundary=boundary, mov=mov)
+
+
+def test_energy_conservation_mirror_with_interface(oracle_mod):
+    prob = _layers4()
+    c = oracle_mod.assemble(prob)
+    src = (np.array([prob.state(2, 3, 0, D(0, 0, 1))]), np.ones(1), 0, np.ones(1))
+    for T in (1, 7, 40):
+        x, det, led = oracle_mod.run(prob, c, T, src)
+        assert abs(x.sum() - 1.0) < 1e-12
+        assert led[2] == 0.0 and led[3] == 0.0
+
+
+def test_pure_decay_without_scattering(oracle_mod):
+    mu_a, h = 0.8, 0.1
+    prob = _prob(5, [(0.0, mu_a, 0.9, 1.4)], boundary=I.MIRROR, h=h)
+    c = oracle_mod.assemble(prob)
+    rng = np.random.default_rng(0)
+    x0 = rng.random(prob.n_states)
+    for T in (1, 10, 33):
+        x, _, _ = oracle_mod.run(prob, c, T, (np.zeros(0, np.int64), np.zeros(0), 0, np.ones(1)), x0=x0)
+        assert x.sum() == pytest.approx(math.exp(-mu_a * h * T) * x0.sum(), rel=1e-12)
+
+
+def test_pure_decay_with_scattering_closed_box(oracle_mod):
+    mu_a, h = 0.5, 0.1
+    prob = _prob(4, [(6.0, mu_a, 0.6, 1.4)], boundary=I.MIRROR, h=h)
+    c = oracle_mod.assemble(prob)
+    src = (np.array([prob.state(1, 1, 1, 5)]), np.ones(1), 0, np.ones(1))
+    x, _, led = oracle_mod.run(prob, c, 25, src)
+    # x_1 = s(0); then 24 decays
+    assert x.sum() == pytest.approx(math.exp(-mu_a * h * 24), rel=1e-12)
+
+
+def test_ballistic_axis_translation_exact(oracle_mod):
+    prob = _prob((9, 4, 4), [(0.0, 0.0, 0.9, 1.0)], boundary=I.OPEN)
+    c = oracle_mod.assemble(prob)
+    src = (np.array([prob.state(0, 2, 1, D(1, 0, 0))]), np.ones(1), 0, np.ones(1))
+    for T in range(1, 10):
+        x, _, led = oracle_mod.run(prob, c, T, src)
+        where = np.flatnonzero(x)
+        assert where.tolist() == [prob.state(T - 1, 2, 1, D(1, 0, 0))]
+        assert x[where[0]] == 1.0
+    x, _, led = oracle_mod.run(prob, c, 10, src)
+    assert x.sum() == 0.0 and led[3] == 1.0        # left through the +x face
+
+
+def test_ballistic_diagonal_centroid(oracle_mod):
+    prob = _prob((12, 12, 3), [(0.0, 0.0, 0.9, 1.0)], boundary=I.OPEN)
+    c = oracle_mod.assemble(prob)
+    d = D(1, 1, 0)
+    src = (np.array([prob.state(1, 1, 1, d)]), np.ones(1), 0, np.ones(1))
+    step = GOLD["edge_unscattered_diag"] + GOLD["edge_unscattered_axis"]
+    for T in (2, 4, 6):
+        x, _, _ = oracle_mod.run(prob, c, T, src)
+        v = x.reshape(3, 12, 12, 26)[..., d]
+        assert v.sum() == pytest.approx(1.0, abs=1e-14)
+        zz, yy, xx = np.meshgrid(range(3), range(12), range(12), indexing="ij")
+        cx, cy = (v * xx).sum(), (v * yy).sum()
+        assert cx == pytest.approx(1 + (T - 1) * step, abs=1e-12)
+        assert cy == pytest.approx(1 + (T - 1) * step, abs=1e-12)
+
+
+def test_nonnegative_heterogeneous(oracle_mod):
+    prob, srcs = I.inclusions(10, n_rhs=2, seed=11, n_spheres=2)
+    c = oracle_mod.assemble(prob)
+    for s in srcs:
+        x, det, led = oracle_mod.run(prob, c, 30, s.as_tuple())
+        assert x.min() >= 0.0 and det.min() >= 0.0
+        assert led[0] + led[2] + led[3] == pytest.approx(led[1], rel=1e-13)
+
+
+def test_single_scatter_line(oracle_mod):
+    # Section 2 / Fig. 7: after one step, once-scattered photons in S' lie on
+    # voxels within 2dr of the segment AB
+    prob = _prob(7, [(8.0, 0.0, 0.0, 1.0)], boundary=I.OPEN)
+    c = oracle_mod.assemble(prob)
+    n = D(1, 0, 1)
+    i = np.array([3, 3, 3])
+    src = (np.array([prob.state(*i, n)]), np.ones(1), 0, np.ones(1))
+    x0, _, _ = oracle_mod.run(prob, c, 1, src)
+    x1 = oracle_mod.spmv(c, x0)
+    v = x1.reshape(7, 7, 7, 26)
+    Sn = np.array(I.direction_vector(n)) / math.sqrt(2)
+    for m in range(26):
+        if m == n:
+            continue
+        Sm = np.array(I.direction_vector(m), float)
+        Sm /= np.linalg.norm(Sm)
+        a, b = i + Sm, i + Sn
+        for z, y, xx in np.argwhere(v[..., m] > 0):
+            p = np.array([xx, y, z], float)
+            t = np.clip(np.dot(p - a, b - a) / max(np.dot(b - a, b - a), 1e-300), 0, 1)
+            assert np.linalg.norm(a + t * (b - a) - p) < 1.0
+        assert v[..., m].sum() > 0
+
+# --------------------------------------------------------------------------
+# Section 4.2: Fresnel reflection at the grid edge and at interfaces
+
+
+def test_fresnel_normal_incidence_at_edge(oracle_mod):
+    prob = _prob(4, [(0.0, 0.0, 0.9, 1.4)], boundary=I.FRESNEL, det=(I.FACE_PZ, 1, 1))
+    c = oracle_mod.assemble(prob)
+    s = prob.state(1, 2, 3, D(0, 0, 1))
+    x0 = np.zeros(prob.n_states)
+    x0[s] = 1.0
+    x, det, led = oracle_mod.run(prob, c, 1, (np.zeros(0, np.int64), np.zeros(0), 0, np.ones(1)), x0=x0)
+    R = GOLD["fresnel_normal_1p4_to_1"]
+    assert x[prob.state(1, 2, 3, D(0, 0, -1))] == pytest.approx(R, rel=1e-13)
+    assert det[0, 0] == pytest.approx(1 - R, rel=1e-13)
+    assert led[3] == pytest.approx(1 - R, rel=1e-13)
+    assert oracle_mod.fresnel(1.0, 1.4, 1.0) == pytest.approx(R, rel=1e-14)
+
+
+def test_total_internal_reflection_corner_direction(oracle_mod):
+    # 1.4 -> 1: critical angle 45.6 deg; lattice corner directions meet a face at 54.7 deg
+    prob = _prob(4, [(0.0, 0.0, 0.9, 1.4)], boundary=I.FRESNEL)
+    ab, ex, ed, patch = oracle_mod.column_info(prob)
+    assert ex[prob.state(1, 2, 3, D(1, 1, 1))] == 0.0
+    assert ex[prob.state(1, 2, 3, D(0, 0, 1))] == pytest.approx(1 - GOLD["fresnel_normal_1p4_to_1"], rel=1e-13)
+    assert oracle_mod.fresnel(1 / math.sqrt(3), 1.4, 1.0) == 1.0
+
+
+def test_interface_transmission_normal_incidence(oracle_mod):
+    # axis photon crossing from n=1.37 (L = h) into n=1.45 at normal incidence
+    prob = _prob((3, 3, 6), [(0.0, 0.0, 0.9, 1.37), (0.0, 0.0, 0.9, 1.45)],
+                 boundary=I.MIRROR,
+                 mov=np.repeat(np.array([0, 0, 0, 1, 1, 1], np.uint8), 9).reshape(6, 3, 3))
+    c = oracle_mod.assemble(prob)
+    x0 = np.zeros(prob.n_states)
+    x0[prob.state(1, 1, 2, D(0, 0, 1))] = 1.0
+    x1 = oracle_mod.spmv(c, x0)
+    R = GOLD["fresnel_normal_1p45_to_1p37"]
+    assert x1[prob.state(1, 1, 3, D(0, 0, 1))] == pytest.approx(1 - R, rel=1e-12)
+    assert x1[prob.state(1, 1, 2, D(0, 0, -1))] == pytest.approx(R, rel=1e-12)
+    assert x1.sum() == pytest.approx(1.0, abs=1e-15)
+
+
+def test_ledger_closure_fresnel(oracle_mod):
+    prob, src = I.fresnel_cube(8)
+    c = oracle_mod.assemble(prob)
+    x, det, led = oracle_mod.run(prob, c, 60, src.as_tuple())
+    assert led[0] + led[2] + led[3] == pytest.approx(led[1], rel=1e-13)
+    # detector face exit is part of all exits
+    assert 0 < det.sum() < led[3]
+
+# --------------------------------------------------------------------------
+# Dense brute force on 4^3 (1,664 states) against an independent transcription
+
+
+@pytest.mark.parametrize("case", ["fresnel", "open_layers", "mirror_aniso"])
+def test_dense_bruteforce_4cube(oracle_mod, case):
+    from tests.dense_transcription import dense_matrix
+    if case == "fresnel":
+        prob = _prob(4, [(10.0, 0.01, 0.9, 1.4)], boundary=I.FRESNEL)
+    elif case == "open_layers":
+        mov = np.zeros((4, 4, 4), np.uint8)
+        mov[2:] = 1
+        mov[:, 0, 0] = 2
+        prob = _prob(4, [(8.0, 0.1, 0.85, 1.45), (4.0, 0.02, 0.9, 1.37),
+                         (2.0, 0.05, 0.7, 1.37)], boundary=I.OPEN, mov=mov)
+    else:
+        mov = np.zeros((4, 4, 4), np.uint8)
+        mov[1:3, 1:3, 1:3] = 1
+        prob = _prob(4, [(6.0, 0.3, 0.95, 1.4), (12.0, 0.0, 0.5, 1.33)],
+                     boundary=I.MIRROR, mov=mov)
+    Ad = dense_matrix(prob)
+    c = oracle_mod.assemble(prob)
+    Ao = _sparse(c).toarray()
+    assert np.array_equal(Ad > 0, Ao > 0)                     # same structure
+    assert np.allclose(Ad, Ao, rtol=1e-12, atol=1e-17)
+    rng = np.random.default_rng(1)
+    x0 = rng.random(prob.n_states)
+    for T in (1, 5, 50):
+        xd = np.linalg.matrix_power(Ad, T) @ x0
+        xo, _, _ = oracle_mod.run(prob, c, T, (np.zeros(0, np.int64), np.zeros(0), 0, np.ones(1)), x0=x0)
+        assert np.abs(xd - xo).sum() <= 1e-12 * np.abs(xd).sum()
+
+
+def test_slab_assembly_matches_full(oracle_mod):
+    prob, _ = I.three_layers(12)
+    full = oracle_mod.assemble(prob)
+    part = oracle_mod.assemble(prob, 3, 7)
+    r0 = part.row0
+    rp = full.row_ptr[r0:r0 + part.n_rows + 1]
+    assert np.array_equal(rp - rp[0], part.row_ptr)
+    assert np.array_equal(full.col[rp[0]:rp[-1]], part.col)
+    assert np.array_equal(full.val[rp[0]:rp[-1]], part.val)
