@@ -1,0 +1,347 @@
+"""DRTS time-step benchmark: x(t+1) = A x(t) + s(t) on one GB300.
+
+Default workload: three planar layers, 128^3 voxels x 26 directions
+(54.5M states, ~11.4G nonzeros), FP32 matrix and state, Gaussian pulse
+source, 16x16 detector patches on the exit face.  One "step" is one DRTS
+time step (the whole fused step kernel: SpMV, source injection, detector
+readout, ledger).
+
+Prints one JSON line (rank 0).  Metric: GNNZ/s (stored nonzeros of A
+streamed per second), whole job.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead.
+
+Multi-GPU: every rank runs an independent replica of the workload (the
+step has no exchange between independent simulations): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DRTS step GNNZ/s"
+UNIT = "GNNZ/s"
+KERNEL_SRC = os.path.join(ROOT, "paper_1611_08536_gb300", "csrc", "drts_step.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+
+
+def workload(name, precision):
+    from paper_1611_08536_gb300 import inputs as I
+    prec = {"fp32": I.FP32, "fp64": I.FP64, "fp16": I.FP16_ROWSCALE}[precision]
+    if name.startswith("three_layers_"):
+        n = int(name.split("_")[-1])
+        return I.three_layers(n, precision=prec)
+    if name.startswith("fresnel_cube_"):
+        n = int(name.split("_")[-1])
+        return I.fresnel_cube(n, precision=prec)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True,
+                                     text=True, timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([f.strip() for f in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for i, n in enumerate(names):
+                if len(s) > 5 + i and s[5 + i].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.samples)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_hash():
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def traffic_per_launch(workload_name, precision, nnz):
+    """DRAM bytes per step-kernel launch from a committed ncu capture, scaled to
+    this launch by nonzeros; None if absent or taken on another kernel source."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    d = json.load(open(TRAFFIC_FILE))
+    if d.get("kernel_sha") != kernel_hash() or d.get("precision") != precision:
+        return None
+    return d["dram_bytes_per_nnz"] * nnz
+
+
+def algorithmic_bytes(info, precision):
+    vb = {"fp32": 4, "fp64": 8, "fp16": 2}[precision]
+    sb = 8 if precision == "fp64" else 4
+    b = info.nnz * (vb + 2) + 2 * info.n_states * sb
+    if precision == "fp16":
+        b += info.n_states * 4
+    return b
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1611_08536_gb300 import build, drts
+    build.build()
+    prob, src = workload(args.workload, args.precision)
+    stream = torch.cuda.current_stream()
+    total_steps = args.warmup + args.steps + args.e2e_steps + 1
+    t_asm = time.time()
+    ctx = drts.Context(prob, max_steps=total_steps, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_asm = time.time() - t_asm
+    info = ctx.info()
+    ctx.set_source(0, src)
+    if args.blocks_per_sm or args.threads:
+        ctx.set_launch(args.blocks_per_sm, args.threads)
+
+    ctx.step_n(args.warmup)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        ev0.record(stream)
+        ctx.step_n(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_step = ms / args.steps
+    gnnz = info.nnz * args.steps / (ms * 1e-3) / 1e9 * ws
+
+    # end to end: per step, source factors host->device and the detector
+    # readout device->host, from pinned host buffers, through the C ABI
+    e2e = None
+    if args.e2e_steps > 0:
+        n = args.e2e_steps
+        scale = torch.zeros((n, 1), dtype=torch.float64, pin_memory=True)
+        det = torch.zeros((n, 1, max(info.n_patch, 1)), dtype=torch.float64, pin_memory=True)
+        sc = scale.numpy()
+        sc[:, 0] = 1.0 / n
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ctx.run_host(sc, det.numpy())
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": round(info.nnz * n / dt / 1e9 * ws, 3), "unit": UNIT,
+               "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 8 * info.n_patch,
+               "steps": n, "ms_per_step": round(dt * 1e3 / n, 4)}
+
+    # parity of the timed launch configuration on sampled rows: one more
+    # step from the current state, checked row by row in FP64
+    sample_check = None
+    if args.check and rank == 0:
+        sample_check = sampled_step_check(ctx, prob, args)
+
+    peak, peak_kind = peaks()
+    alg = algorithmic_bytes(info, args.precision)
+    achieved = alg / (ms_step * 1e-3) / 1e9
+    traffic = traffic_per_launch(args.workload, args.precision, info.nnz)
+    line = {
+        "metric": METRIC, "value": round(gnnz, 3), "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f16-matrix/f32-state"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "grid": list(prob.shape), "directions": 26,
+                   "states": int(info.n_states), "nnz": int(info.nnz),
+                   "nnz_padded": int(info.nnz_padded), "matrix_GB": round(info.matrix_bytes / 1e9, 3),
+                   "format": "SELL-32 (slice = 32 voxels x 1 direction), 16-bit stencil codes",
+                   "precision": args.precision, "steps_per_s": round(1e3 / ms_step, 3),
+                   "l2": "inputs larger than L2 (matrix streamed every step)",
+                   "assembly_s": round(t_asm, 2), "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": int(alg)},
+        "gpu_launches": args.steps,
+        "e2e": e2e,
+        "clocks": clk.summary(),
+    }
+    if sample_check is not None:
+        line["sampled_parity"] = sample_check
+    if rank == 0 and args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(prob, args)
+    ctx.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def sampled_step_check(ctx, prob, args):
+    """One extra step checked against the oracle on sampled planes."""
+    import numpy as np
+    import oracle
+    x = ctx.read_state()
+    ctx.step_n(1)
+    y = ctx.read_state()
+    nz = prob.shape[2]
+    planes = sorted({0, nz // 11, nz - 1})
+    worst = 0.0
+    for z in planes:
+        c = oracle.assemble(prob, z, z + 1)
+        yo = oracle.spmv(c, x)
+        yg = y[c.row0:c.row0 + c.n_rows]
+        den = np.abs(yo).sum()
+        if den > 0:
+            worst = max(worst, float(np.abs(yg - yo).sum() / den))
+    return {"planes": planes, "rel_l1_one_step": worst}
+
+
+def cpu_baseline(prob, args, seconds=12.0):
+    """FP64 oracle CSR SpMV timed on the host cores over one z-plane of rows."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    z = prob.shape[2] // 2
+    c = oracle.assemble(prob, z, z + 1)
+    x = np.random.default_rng(0).random(prob.n_states)
+    threads = oracle.max_threads()
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.spmv(c, x, threads)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt > seconds:
+            break
+    return {"value": round(c.nnz * reps / dt / 1e9, 4), "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": f"FP64 CSR SpMV over the {c.n_rows} rows of z-plane {z} "
+                      f"({c.nnz} nnz) of the same workload, {reps} repetitions"}
+
+
+def run_reference(args):
+    import numpy as np
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    prob, _ = workload(args.workload, args.precision)
+    z = prob.shape[2] // 2
+    c = oracle.assemble(prob, z, z + 1)
+    x = np.random.default_rng(0).random(prob.n_states)
+    threads = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle.spmv(c, x, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.spmv(c, x, threads)
+    dt = time.perf_counter() - t0
+    v = round(c.nnz * args.steps / dt / 1e9, 4)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "grid": list(prob.shape),
+                   "sample": f"rows of z-plane {z} ({c.nnz} nnz) per step"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": threads,
+                         "sample": f"FP64 CSR SpMV over z-plane {z} of the workload per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="drts", choices=["drts", "reference"])
+    ap.add_argument("--workload", default="three_layers_128")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16"])
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-check", dest="check", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

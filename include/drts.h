@@ -1,0 +1,194 @@
+/*
+ * drts.h - C ABI of the GB300 DRTS library (libdrts.so).
+ *
+ * The Dynamic Radiative Transfer System (Georgakopoulos, Politopoulos and
+ * Georgiou, arXiv:1611.08536) advances photon populations J(X_i, S_n) over
+ * (voxel, direction) states with one sparse matrix-vector product per time
+ * step, J(t+dt) = A J(t) + B P(t) (Eq. 26).  A is assembled once (Eq. 18-23,
+ * Section 3) and stays resident on the GPU; every step runs in the library's
+ * CUDA kernels.
+ *
+ * Geometry and state order (Eq. 22):
+ *   cubic grid nx*ny*nz, voxel v = (z*ny + y)*nx + x, voxel size h = 2dr;
+ *   26 lattice directions d enumerating {-1,0,1}^3 \ {0}, dz slowest, dx
+ *   fastest; canonical state index s = v*26 + d.
+ *   dt = h / c_max: medium k moves light L_k = h * n_min / n_k per step.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a drts_status; nothing aborts or traps.  After an
+ *     error, drts_last_error(ctx) describes it.
+ *   - Caller-owned host inputs are copied during the call; the context owns
+ *     all device memory it allocates and frees it in drts_destroy.
+ *   - Work is queued on the CUDA stream given to drts_assemble (NULL = the
+ *     default stream).  drts_step_n returns before the GPU finishes; the
+ *     read_* calls synchronise that stream.
+ *   - A context is not thread-safe; separate contexts are independent.
+ *   - Sticky CUDA errors surface as DRTS_ECUDA; a device-side wait that
+ *     runs out of its iteration budget surfaces as DRTS_ETIMEOUT.
+ */
+#ifndef DRTS_H
+#define DRTS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t drts_status;
+#define DRTS_OK 0
+#define DRTS_EINVAL 1        /* bad argument or problem description */
+#define DRTS_ENOMEM 2        /* device or host allocation failed */
+#define DRTS_ECUDA 3         /* CUDA runtime error (sticky or launch) */
+#define DRTS_ETIMEOUT 4      /* a bounded device-side wait gave up */
+#define DRTS_ESTATE 5        /* call not valid in the context's state */
+#define DRTS_EUNSUPPORTED 6  /* valid request this build does not support */
+
+/* boundary treatment of the grid edge (Section 4.2 readings) */
+#define DRTS_OPEN 0          /* mass reaching outside the grid leaves */
+#define DRTS_MIRROR 1        /* mass is reflected back (closed box) */
+#define DRTS_FRESNEL 2       /* unpolarised Fresnel split against n_outside */
+
+/* storage / arithmetic precision of the time step */
+#define DRTS_FP64 0          /* A, state and accumulation in FP64 */
+#define DRTS_FP32 1          /* A and state in FP32, FP32 accumulation */
+#define DRTS_FP16_ROWSCALE 2 /* A in FP16 with a per-row FP32 scale, FP32 state */
+
+/* detector faces: 2*axis + (1 for the high side) */
+#define DRTS_FACE_MX 0
+#define DRTS_FACE_PX 1
+#define DRTS_FACE_MY 2
+#define DRTS_FACE_PY 3
+#define DRTS_FACE_MZ 4
+#define DRTS_FACE_PZ 5
+#define DRTS_FACE_NONE (-1)
+
+/* Optical properties of one medium (Section 2): scattering coefficient
+ * mu_s (1/mm, Eq. 2), absorption coefficient mu_a (1/mm, Eq. 8),
+ * Henyey-Greenstein anisotropy g of the kernel g(S,S') (Section 5) and
+ * refractive index n (speed c0/n, Section 4.2). */
+typedef struct drts_medium {
+    double mu_s, mu_a, g, n;
+} drts_medium;
+
+typedef struct drts_problem {
+    int32_t nx, ny, nz;              /* grid size, each >= 2 */
+    double voxel_mm;                 /* h = 2dr */
+    int32_t n_media;                 /* 1..255 */
+    const drts_medium *media;        /* [n_media], host, copied */
+    const uint8_t *medium_of_voxel;  /* [nx*ny*nz] (x fastest), host, copied */
+    double n_outside;                /* refractive index outside the grid */
+    int32_t boundary;                /* DRTS_OPEN / DRTS_MIRROR / DRTS_FRESNEL */
+    int32_t precision;               /* DRTS_FP64 / DRTS_FP32 / DRTS_FP16_ROWSCALE */
+    int32_t n_rhs;                   /* right-hand sides stepped together, 1..64 */
+    int32_t det_face;                /* detector face or DRTS_FACE_NONE */
+    int32_t det_nu, det_nv;          /* detector patch grid on that face */
+    int64_t max_steps;               /* detector history capacity in steps */
+} drts_problem;
+
+typedef struct drts_ctx drts_ctx;
+
+/* Sizes of an assembled context (bytes are device bytes). */
+typedef struct drts_info {
+    int64_t n_states;                /* 26 * nx*ny*nz */
+    int64_t nnz;                     /* stored nonzeros of A (no padding) */
+    int64_t nnz_padded;              /* slots in the sliced format incl. padding */
+    int64_t n_slices;                /* slices of 32 rows */
+    int64_t matrix_bytes;            /* values + codes + row scales + slice table */
+    int64_t state_bytes;             /* one state buffer, all right-hand sides */
+    int64_t t;                       /* steps taken so far */
+    int32_t precision, n_rhs, n_patch;
+    int32_t special_voxels_permille; /* voxels that needed edge/interface folding */
+} drts_info;
+
+/*
+ * Assemble the system matrix A of Eq. 23 on the device (Eq. 18-21 with the
+ * Section 4.2 edge and interface treatment) and allocate the state, the
+ * detector history and the energy ledger for n_rhs right-hand sides.
+ * The state starts at zero and t at 0.  cuda_stream is a cudaStream_t (or
+ * NULL).  On success *out owns everything; on failure *out is NULL.
+ */
+drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx **out);
+
+/*
+ * Set the source term of right-hand side rhs (Eq. 26, B P(t)):
+ *   s(t) = sum_e weight[e] * P(t) * e_{state_idx[e]},
+ *   P(t) = profile[t - t0] for t0 <= t < t0 + n_t, else 0.
+ * state_idx are canonical state indices (host int64), weight and profile are
+ * host FP64; 0 <= n_entries <= 64, 0 <= n_t.  Replaces any earlier source of
+ * that rhs.  The term lands in x(t+1) when stepping from t.
+ */
+drts_status drts_inject_source(drts_ctx *ctx, int32_t rhs, int32_t n_entries,
+                               const int64_t *state_idx, const double *weight,
+                               int64_t t0, int32_t n_t, const double *profile);
+
+/*
+ * Advance every right-hand side by n_steps (Fig. 3 loop): for each step,
+ * x(t+1) = A x(t) + s(t), and from x(t) the detector readout
+ * det[t][p] = sum over states s of patch p of exit_det(s) x(t)[s] (Eq. 27)
+ * plus the FP64 absorbed / exited ledger.  Asynchronous on the context
+ * stream.  DRTS_EINVAL if t + n_steps exceeds max_steps.
+ */
+drts_status drts_step_n(drts_ctx *ctx, int64_t n_steps);
+
+/*
+ * Copy the detector history of rhs for steps [t_begin, t_end) to host_out
+ * ([t][patch], FP64, caller-owned, (t_end-t_begin)*n_patch values) and, if
+ * ledger_out is not NULL, the ledger {sum of x(t), injected, absorbed,
+ * exited} (4 FP64, cumulative since t = 0).  Synchronises the stream.
+ */
+drts_status drts_read_detectors(drts_ctx *ctx, int32_t rhs, int64_t t_begin,
+                                int64_t t_end, double *host_out, double *ledger_out);
+
+/* Copy x(t) of rhs to host_out (canonical order, n_states FP64). Synchronises. */
+drts_status drts_read_state(drts_ctx *ctx, int32_t rhs, double *host_out);
+
+/* Overwrite x(t) of rhs from host_in (canonical order, n_states FP64,
+ * rounded to the state precision).  t is unchanged.  Synchronises. */
+drts_status drts_write_state(drts_ctx *ctx, int32_t rhs, const double *host_in);
+
+/*
+ * End-to-end run from host memory: for each of n_steps steps, copy that
+ * step's source scale factors host->device (scale[i*n_rhs + r] multiplies the
+ * injected weights of rhs r at step t+i, replacing P(t)), advance one step,
+ * and copy that step's detector readout device->host into
+ * det_out[i][r][patch].  host buffers should be pinned for overlap.
+ */
+drts_status drts_run_host(drts_ctx *ctx, int64_t n_steps, const double *scale,
+                          double *det_out);
+
+/*
+ * Export rows [row_begin, row_end) of the assembled A in canonical CSR form
+ * (rows in canonical state order, columns ascending): row_ptr has
+ * row_end-row_begin+1 entries starting at 0, col and val have room for cap
+ * entries (DRTS_EINVAL if too small; row_ptr is still filled).  Values are
+ * the stored ones (FP64, FP32, or FP16 times the row scale) widened to FP64.
+ */
+drts_status drts_export_rows(drts_ctx *ctx, int64_t row_begin, int64_t row_end,
+                             int64_t *row_ptr, int32_t *col, double *val, int64_t cap);
+
+/* Per-state column functionals of the step (canonical order, n_states FP64
+ * each, any may be NULL): absorbed fraction 1-exp(-mu_a L) (Eq. 8), fraction
+ * leaving the grid, fraction leaving through the detector face (Eq. 27). */
+drts_status drts_column_info(drts_ctx *ctx, double *absorb, double *exit_total,
+                             double *exit_det);
+
+drts_status drts_get_info(const drts_ctx *ctx, drts_info *out);
+
+/* Set the kernel launch shape of the step (0 = library default / autotuned):
+ * blocks per SM, threads per block, right-hand sides per pass. */
+drts_status drts_set_launch(drts_ctx *ctx, int32_t blocks_per_sm,
+                            int32_t threads_per_block, int32_t rhs_tile);
+
+/* Free every device and host resource of ctx (NULL is ignored). */
+void drts_destroy(drts_ctx *ctx);
+
+/* Text of the last error on ctx (or of the last failed drts_assemble when
+ * ctx is NULL).  Valid until the next call on ctx. */
+const char *drts_last_error(const drts_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DRTS_H */

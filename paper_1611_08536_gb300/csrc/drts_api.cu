@@ -1,0 +1,587 @@
+// C ABI of libdrts (declared in include/drts.h): context life cycle,
+// assembly, sources, stepping, readout.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "drts_device.cuh"
+
+using namespace drts;
+
+struct drts_ctx {
+    drts_problem prob{};
+    cudaStream_t stream = nullptr;
+    int64_t V = 0, n_states = 0;
+    int K = 0, R = 1, n_patch = 0;
+    int64_t t = 0;
+    std::string err;
+    HostTables host;
+    DevTables T{};
+    SlicedMatrix A{};
+    // device buffers
+    std::vector<void *> allocs;
+    void *x = nullptr, *y = nullptr;     // state ping-pong
+    int64_t x_elems = 0;
+    double *ledger = nullptr;            // [R][4]
+    double *det = nullptr;               // [R][max_steps][n_patch]
+    double *d_absorb = nullptr, *d_exit_tot = nullptr, *d_exit_det = nullptr;
+    SourceEntry *d_src = nullptr;
+    SourceProfile *d_prof = nullptr;
+    double *d_prof_vals = nullptr;
+    int64_t prof_cap = 0;
+    std::vector<SourceEntry> src;        // host copy of all rhs entries
+    std::vector<SourceProfile> prof;     // [R]
+    std::vector<std::vector<double>> prof_vals;
+    int blocks = 0, threads = 256, rhs_tile = 0;
+    int special_permille = 0;
+};
+
+namespace {
+
+std::string g_assemble_error;
+
+drts_status fail(drts_ctx *c, drts_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    else g_assemble_error = msg;
+    return s;
+}
+
+drts_status cuda_fail(drts_ctx *c, cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, e == cudaErrorMemoryAllocation ? DRTS_ENOMEM : DRTS_ECUDA, m);
+}
+
+template <class T>
+cudaError_t dalloc(drts_ctx *c, T **p, size_t bytes)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e == cudaSuccess) {
+        c->allocs.push_back(q);
+        *p = static_cast<T *>(q);
+    }
+    return e;
+}
+
+template <class T>
+cudaError_t upload(drts_ctx *c, T **p, const std::vector<T> &v)
+{
+    cudaError_t e = dalloc(c, p, v.size() * sizeof(T));
+    if (e == cudaSuccess && !v.empty())
+        e = cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream);
+    return e;
+}
+
+size_t state_elem_bytes(int precision) { return precision == DRTS_FP64 ? 8 : 4; }
+
+size_t value_bytes(int precision) { return precision == DRTS_FP64 ? 8 : (precision == DRTS_FP32 ? 4 : 2); }
+
+drts_status validate(const drts_problem *p)
+{
+    if (!p) return fail(nullptr, DRTS_EINVAL, "problem is NULL");
+    if (p->nx < 2 || p->ny < 2 || p->nz < 2) return fail(nullptr, DRTS_EINVAL, "grid sides must be >= 2");
+    const int64_t V = int64_t(p->nx) * p->ny * p->nz;
+    if (V * kDirs >= (int64_t(1) << 31)) return fail(nullptr, DRTS_EINVAL, "more than 2^31 states");
+    if (!(p->voxel_mm > 0.0)) return fail(nullptr, DRTS_EINVAL, "voxel_mm must be > 0");
+    if (p->n_media < 1 || p->n_media > 255 || !p->media) return fail(nullptr, DRTS_EINVAL, "n_media must be 1..255");
+    if (!p->medium_of_voxel) return fail(nullptr, DRTS_EINVAL, "medium_of_voxel is NULL");
+    for (int k = 0; k < p->n_media; ++k) {
+        const drts_medium &m = p->media[k];
+        if (!(m.n > 0.0) || m.mu_s < 0.0 || m.mu_a < 0.0 || !(m.g > -1.0 && m.g < 1.0))
+            return fail(nullptr, DRTS_EINVAL, "medium " + std::to_string(k) + " out of range");
+    }
+    for (int64_t v = 0; v < V; ++v)
+        if (p->medium_of_voxel[v] >= p->n_media) return fail(nullptr, DRTS_EINVAL, "medium index out of range");
+    if (p->boundary < DRTS_OPEN || p->boundary > DRTS_FRESNEL) return fail(nullptr, DRTS_EINVAL, "bad boundary");
+    if (p->boundary == DRTS_FRESNEL && !(p->n_outside > 0.0)) return fail(nullptr, DRTS_EINVAL, "n_outside must be > 0");
+    if (p->precision < DRTS_FP64 || p->precision > DRTS_FP16_ROWSCALE) return fail(nullptr, DRTS_EINVAL, "bad precision");
+    if (p->n_rhs < 1 || p->n_rhs > kMaxRhs) return fail(nullptr, DRTS_EINVAL, "n_rhs must be 1..64");
+    if (p->n_rhs > 1) return fail(nullptr, DRTS_EUNSUPPORTED, "n_rhs > 1 is not built yet");
+    if (p->det_face != DRTS_FACE_NONE) {
+        if (p->det_face < 0 || p->det_face > 5) return fail(nullptr, DRTS_EINVAL, "bad det_face");
+        const int N[3] = {p->nx, p->ny, p->nz};
+        const int fa = p->det_face / 2, ua = fa == 0 ? 1 : 0, va = fa == 2 ? 1 : 2;
+        if (p->det_nu < 1 || p->det_nv < 1 || p->det_nu > N[ua] || p->det_nv > N[va])
+            return fail(nullptr, DRTS_EINVAL, "detector patch grid must be 1..side");
+    }
+    if (p->max_steps < 0) return fail(nullptr, DRTS_EINVAL, "max_steps < 0");
+    return DRTS_OK;
+}
+
+drts_status sync_check(drts_ctx *c, const char *where)
+{
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, where);
+    return DRTS_OK;
+}
+
+drts_status upload_sources(drts_ctx *c)
+{
+    // flatten profiles
+    std::vector<double> vals;
+    for (int r = 0; r < c->R; ++r) {
+        c->prof[r].off = int32_t(vals.size());
+        vals.insert(vals.end(), c->prof_vals[r].begin(), c->prof_vals[r].end());
+    }
+    cudaError_t e = cudaSuccess;
+    if (int64_t(vals.size()) > c->prof_cap) {
+        int64_t cap = int64_t(vals.size()) * 2 + 16;
+        double *p = nullptr;
+        e = dalloc(c, &p, size_t(cap) * sizeof(double));
+        if (e != cudaSuccess) return cuda_fail(c, e, "profile allocation");
+        c->d_prof_vals = p;
+        c->prof_cap = cap;
+    }
+    if (!vals.empty())
+        e = cudaMemcpyAsync(c->d_prof_vals, vals.data(), vals.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && !c->src.empty())
+        e = cudaMemcpyAsync(c->d_src, c->src.data(), c->src.size() * sizeof(SourceEntry), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_prof, c->prof.data(), c->prof.size() * sizeof(SourceProfile), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "source upload");
+    return sync_check(c, "source upload");
+}
+
+StepArgs make_args(drts_ctx *c)
+{
+    StepArgs a{};
+    a.A = c->A;
+    a.nx = c->prob.nx; a.ny = c->prob.ny; a.nz = c->prob.nz;
+    a.V = c->V;
+    a.R = c->R;
+    a.x = c->x; a.y = c->y;
+    a.med = c->T.med;
+    a.tab.absorb = c->d_absorb;
+    a.tab.exit_total = c->d_exit_tot;
+    a.tab.exit_det = c->d_exit_det;
+    a.det_face = c->prob.det_face;
+    a.det_nu = c->prob.det_nu; a.det_nv = c->prob.det_nv;
+    a.n_patch = c->n_patch;
+    a.det = nullptr;
+    if (c->det && c->n_patch > 0 && c->t < c->prob.max_steps) a.det = c->det + c->t * c->n_patch;
+    a.det_stride_r = c->prob.max_steps * c->n_patch;
+    a.t = c->t;
+    a.ledger = c->ledger;
+    a.n_src = int(c->src.size());
+    a.src = c->d_src;
+    a.prof = c->d_prof;
+    a.prof_vals = c->d_prof_vals;
+    a.rhs_tile = c->rhs_tile;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx **out)
+{
+    if (!out) return fail(nullptr, DRTS_EINVAL, "out is NULL");
+    *out = nullptr;
+    drts_status st = validate(prob);
+    if (st != DRTS_OK) return st;
+    drts_ctx *c = new (std::nothrow) drts_ctx;
+    if (!c) return fail(nullptr, DRTS_ENOMEM, "host allocation");
+    c->prob = *prob;
+    c->prob.media = nullptr;
+    c->prob.medium_of_voxel = nullptr;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->V = int64_t(prob->nx) * prob->ny * prob->nz;
+    c->n_states = c->V * kDirs;
+    c->K = prob->n_media;
+    c->R = prob->n_rhs;
+    if (prob->det_face != DRTS_FACE_NONE) c->n_patch = prob->det_nu * prob->det_nv;
+
+    auto bail = [&](drts_status s) {
+        g_assemble_error = c->err;
+        drts_destroy(c);
+        return s;
+    };
+
+    std::string terr = build_host_tables(*prob, c->host);
+    if (!terr.empty()) {
+        fail(c, DRTS_EINVAL, terr);
+        return bail(DRTS_EINVAL);
+    }
+    const HostTables &H = c->host;
+    cudaError_t e;
+    // tables
+    std::vector<uint8_t> med(prob->medium_of_voxel, prob->medium_of_voxel + c->V);
+    double *dW, *dtv, *dre, *dri, *dnr;
+    int32_t *dto;
+    uint8_t *dtn, *dmed, *dplain;
+    if ((e = upload(c, &dW, H.W)) != cudaSuccess ||
+        (e = upload(c, &dto, H.tmpl_off)) != cudaSuccess ||
+        (e = upload(c, &dtn, H.tmpl_n)) != cudaSuccess ||
+        (e = upload(c, &dtv, H.tmpl_val)) != cudaSuccess ||
+        (e = upload(c, &dre, H.r_edge)) != cudaSuccess ||
+        (e = upload(c, &dri, H.r_int)) != cudaSuccess ||
+        (e = upload(c, &dnr, H.nref)) != cudaSuccess ||
+        (e = upload(c, &dmed, med)) != cudaSuccess ||
+        (e = dalloc(c, &dplain, size_t(c->V))) != cudaSuccess ||
+        (e = upload(c, &c->d_absorb, H.absorb)) != cudaSuccess ||
+        (e = upload(c, &c->d_exit_tot, H.exit_total)) != cudaSuccess ||
+        (e = upload(c, &c->d_exit_det, H.exit_det)) != cudaSuccess) {
+        cuda_fail(c, e, "table upload");
+        return bail(e == cudaErrorMemoryAllocation ? DRTS_ENOMEM : DRTS_ECUDA);
+    }
+    DevTables &T = c->T;
+    T.nx = prob->nx; T.ny = prob->ny; T.nz = prob->nz;
+    T.V = c->V; T.K = c->K;
+    T.W = dW; T.tmpl_off = dto; T.tmpl_n = dtn; T.tmpl_val = dtv;
+    T.r_edge = dre; T.r_int = dri; T.nref = dnr; T.med = dmed; T.plain = dplain;
+
+    // slices and counts
+    SlicedMatrix &A = c->A;
+    A.precision = prob->precision;
+    A.n_slices = ((c->V + kSlice - 1) / kSlice) * kDirs;
+    float *row_max = nullptr;
+    int64_t *d_total = nullptr;
+    if ((e = dalloc(c, &A.slice_ptr, sizeof(int64_t) * A.n_slices)) != cudaSuccess ||
+        (e = dalloc(c, &A.slice_len4, sizeof(int32_t) * A.n_slices)) != cudaSuccess ||
+        (e = dalloc(c, &A.row_len, sizeof(int32_t) * A.n_slices * kSlice)) != cudaSuccess ||
+        (e = dalloc(c, &d_total, sizeof(int64_t))) != cudaSuccess) {
+        cuda_fail(c, e, "slice table allocation");
+        return bail(DRTS_ENOMEM);
+    }
+    if (prob->precision == DRTS_FP16_ROWSCALE) {
+        if ((e = cudaMallocAsync(&row_max, sizeof(float) * A.n_slices * kSlice, c->stream)) != cudaSuccess ||
+            (e = dalloc(c, &A.row_scale, sizeof(float) * A.n_slices * kSlice)) != cudaSuccess) {
+            cuda_fail(c, e, "row scale allocation");
+            return bail(DRTS_ENOMEM);
+        }
+    }
+    if ((e = launch_classify(T, dplain, c->stream)) != cudaSuccess ||
+        (e = launch_count(T, A, row_max, c->stream)) != cudaSuccess ||
+        (e = launch_scan(A, d_total, c->stream)) != cudaSuccess) {
+        cuda_fail(c, e, "assembly count");
+        return bail(DRTS_ECUDA);
+    }
+    int64_t groups = 0;
+    if ((e = cudaMemcpyAsync(&groups, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+        cuda_fail(c, e, "assembly count");
+        return bail(DRTS_ECUDA);
+    }
+    A.n_groups = groups;
+    const size_t slots = size_t(groups) * kSlice * kGroup;
+    if ((e = dalloc(c, &A.vals, slots * value_bytes(A.precision))) != cudaSuccess ||
+        (e = dalloc(c, &A.codes, slots * sizeof(uint16_t))) != cudaSuccess) {
+        cuda_fail(c, e, ("matrix allocation (" + std::to_string(slots) + " slots)").c_str());
+        return bail(DRTS_ENOMEM);
+    }
+    if ((e = launch_fill(T, A, row_max, c->stream)) != cudaSuccess) {
+        cuda_fail(c, e, "assembly fill");
+        return bail(DRTS_ECUDA);
+    }
+    if (row_max) cudaFreeAsync(row_max, c->stream);
+    // nnz and special-voxel share (host reductions of small device arrays)
+    {
+        std::vector<int32_t> rl(size_t(A.n_slices) * kSlice);
+        std::vector<uint8_t> pl(size_t(c->V));
+        if ((e = cudaMemcpyAsync(rl.data(), A.row_len, rl.size() * 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(pl.data(), dplain, pl.size(), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
+            cuda_fail(c, e, "assembly readback");
+            return bail(DRTS_ECUDA);
+        }
+        int64_t nnz = 0, special = 0;
+        for (int32_t x : rl) nnz += x;
+        for (uint8_t x : pl) special += x == 0;
+        A.nnz = nnz;
+        c->special_permille = int(special * 1000 / c->V);
+    }
+    // state, ledger, detector history, sources
+    c->x_elems = (c->n_states + 64) * c->R;
+    const size_t sb = size_t(c->x_elems) * state_elem_bytes(prob->precision);
+    if ((e = dalloc(c, &c->x, sb)) != cudaSuccess || (e = dalloc(c, &c->y, sb)) != cudaSuccess ||
+        (e = dalloc(c, &c->ledger, sizeof(double) * 4 * c->R)) != cudaSuccess ||
+        (e = dalloc(c, &c->d_src, sizeof(SourceEntry) * kMaxSrc * c->R)) != cudaSuccess ||
+        (e = dalloc(c, &c->d_prof, sizeof(SourceProfile) * c->R)) != cudaSuccess) {
+        cuda_fail(c, e, "state allocation");
+        return bail(DRTS_ENOMEM);
+    }
+    if (c->n_patch > 0 && prob->max_steps > 0) {
+        if ((e = dalloc(c, &c->det, sizeof(double) * size_t(c->R) * prob->max_steps * c->n_patch)) != cudaSuccess) {
+            cuda_fail(c, e, "detector allocation");
+            return bail(DRTS_ENOMEM);
+        }
+        cudaMemsetAsync(c->det, 0, sizeof(double) * size_t(c->R) * prob->max_steps * c->n_patch, c->stream);
+    }
+    cudaMemsetAsync(c->x, 0, sb, c->stream);
+    cudaMemsetAsync(c->y, 0, sb, c->stream);
+    cudaMemsetAsync(c->ledger, 0, sizeof(double) * 4 * c->R, c->stream);
+    c->prof.assign(c->R, SourceProfile{0, 0, 0, 0, 0});
+    c->prof_vals.assign(c->R, std::vector<double>());
+    st = upload_sources(c);
+    if (st != DRTS_OK) return bail(st);
+    c->threads = 256;
+    c->blocks = step_default_blocks(prob->precision, c->R, c->threads);
+    st = sync_check(c, "assembly");
+    if (st != DRTS_OK) return bail(st);
+    *out = c;
+    return DRTS_OK;
+}
+
+drts_status drts_inject_source(drts_ctx *c, int32_t rhs, int32_t n_entries, const int64_t *state_idx,
+                               const double *weight, int64_t t0, int32_t n_t, const double *profile)
+{
+    if (!c) return DRTS_EINVAL;
+    if (rhs < 0 || rhs >= c->R) return fail(c, DRTS_EINVAL, "rhs out of range");
+    if (n_entries < 0 || n_entries > kMaxSrc) return fail(c, DRTS_EINVAL, "n_entries must be 0..64");
+    if (n_t < 0 || (n_t > 0 && !profile)) return fail(c, DRTS_EINVAL, "bad profile");
+    if (n_entries > 0 && (!state_idx || !weight)) return fail(c, DRTS_EINVAL, "NULL source arrays");
+    std::vector<SourceEntry> keep;
+    for (const SourceEntry &e : c->src)
+        if (e.rhs != rhs) keep.push_back(e);
+    for (int i = 0; i < n_entries; ++i) {
+        const int64_t s = state_idx[i];
+        if (s < 0 || s >= c->n_states) return fail(c, DRTS_EINVAL, "source state out of range");
+        if (!std::isfinite(weight[i])) return fail(c, DRTS_EINVAL, "source weight not finite");
+        const int64_t v = s / kDirs;
+        const int d = int(s % kDirs);
+        SourceEntry e{};
+        e.slice = int32_t((v / kSlice) * kDirs + d);
+        e.lane = int32_t(v % kSlice);
+        e.rhs = rhs;
+        e.prof = rhs;
+        e.w = weight[i];
+        keep.push_back(e);
+    }
+    if (int(keep.size()) > kMaxSrc * c->R) return fail(c, DRTS_EINVAL, "too many source entries");
+    c->src = keep;
+    c->prof[rhs] = SourceProfile{t0, n_t, 0, 0, 0};
+    c->prof_vals[rhs].assign(profile, profile + n_t);
+    return upload_sources(c);
+}
+
+drts_status drts_step_n(drts_ctx *c, int64_t n_steps)
+{
+    if (!c) return DRTS_EINVAL;
+    if (n_steps < 0) return fail(c, DRTS_EINVAL, "n_steps < 0");
+    if (c->det && c->t + n_steps > c->prob.max_steps)
+        return fail(c, DRTS_EINVAL, "t + n_steps exceeds max_steps");
+    for (int64_t i = 0; i < n_steps; ++i) {
+        StepArgs a = make_args(c);
+        cudaError_t e = launch_step(a, c->blocks, c->threads, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+        std::swap(c->x, c->y);
+        ++c->t;
+    }
+    return DRTS_OK;
+}
+
+drts_status drts_run_host(drts_ctx *c, int64_t n_steps, const double *scale, double *det_out)
+{
+    if (!c) return DRTS_EINVAL;
+    if (n_steps < 0 || !scale) return fail(c, DRTS_EINVAL, "bad arguments");
+    if (c->det && c->t + n_steps > c->prob.max_steps)
+        return fail(c, DRTS_EINVAL, "t + n_steps exceeds max_steps");
+    if (n_steps == 0) return DRTS_OK;
+    double *d_scale = nullptr;
+    cudaError_t e = cudaMallocAsync(&d_scale, sizeof(double) * c->R * n_steps, c->stream);
+    for (int64_t i = 0; i < n_steps && e == cudaSuccess; ++i) {
+        // this step's source factors, host -> device
+        e = cudaMemcpyAsync(d_scale + i * c->R, scale + i * c->R, sizeof(double) * c->R,
+                            cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) break;
+        StepArgs a = make_args(c);
+        a.step_scale = d_scale + i * c->R;
+        e = launch_step(a, c->blocks, c->threads, c->stream);
+        if (e != cudaSuccess) break;
+        // this step's detector readout, device -> host
+        if (det_out && a.det && c->n_patch > 0)
+            for (int r = 0; r < c->R && e == cudaSuccess; ++r)
+                e = cudaMemcpyAsync(det_out + (i * c->R + r) * c->n_patch, a.det + r * a.det_stride_r,
+                                    sizeof(double) * c->n_patch, cudaMemcpyDeviceToHost, c->stream);
+        std::swap(c->x, c->y);
+        ++c->t;
+    }
+    if (d_scale) cudaFreeAsync(d_scale, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "run_host");
+    return sync_check(c, "run_host");
+}
+
+drts_status drts_read_detectors(drts_ctx *c, int32_t rhs, int64_t t_begin, int64_t t_end, double *host_out,
+                                double *ledger_out)
+{
+    if (!c) return DRTS_EINVAL;
+    if (rhs < 0 || rhs >= c->R) return fail(c, DRTS_EINVAL, "rhs out of range");
+    if (t_begin < 0 || t_end < t_begin || t_end > c->t) return fail(c, DRTS_EINVAL, "bad step range");
+    cudaError_t e = cudaSuccess;
+    if (t_end > t_begin) {
+        if (!c->det) return fail(c, DRTS_ESTATE, "no detector history (det_face none or max_steps 0)");
+        if (!host_out) return fail(c, DRTS_EINVAL, "host_out is NULL");
+        e = cudaMemcpyAsync(host_out, c->det + (size_t(rhs) * c->prob.max_steps + t_begin) * c->n_patch,
+                            sizeof(double) * (t_end - t_begin) * c->n_patch, cudaMemcpyDeviceToHost, c->stream);
+    }
+    if (e == cudaSuccess && ledger_out) {
+        double *tmp = nullptr;
+        e = cudaMallocAsync(&tmp, sizeof(double), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tmp, 0, sizeof(double), c->stream);
+        if (e == cudaSuccess) e = launch_ledger_sum(c->x, c->prob.precision, c->n_states, c->R, rhs, tmp, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ledger_out, tmp, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ledger_out + 1, c->ledger + 4 * rhs + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (tmp) cudaFreeAsync(tmp, c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "read_detectors");
+    return sync_check(c, "read_detectors");
+}
+
+drts_status drts_read_state(drts_ctx *c, int32_t rhs, double *host_out)
+{
+    if (!c) return DRTS_EINVAL;
+    if (rhs < 0 || rhs >= c->R || !host_out) return fail(c, DRTS_EINVAL, "bad arguments");
+    double *tmp = nullptr;
+    cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * c->n_states, c->stream);
+    if (e == cudaSuccess) e = launch_to_canonical(c->x, c->prob.precision, c->V, c->R, rhs, tmp, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_out, tmp, sizeof(double) * c->n_states, cudaMemcpyDeviceToHost, c->stream);
+    if (tmp) cudaFreeAsync(tmp, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read_state");
+    return sync_check(c, "read_state");
+}
+
+drts_status drts_write_state(drts_ctx *c, int32_t rhs, const double *host_in)
+{
+    if (!c) return DRTS_EINVAL;
+    if (rhs < 0 || rhs >= c->R || !host_in) return fail(c, DRTS_EINVAL, "bad arguments");
+    double *tmp = nullptr;
+    cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * c->n_states, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(tmp, host_in, sizeof(double) * c->n_states, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_from_canonical(tmp, c->prob.precision, c->V, c->R, rhs, c->x, c->stream);
+    if (tmp) cudaFreeAsync(tmp, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "write_state");
+    return sync_check(c, "write_state");
+}
+
+drts_status drts_export_rows(drts_ctx *c, int64_t row_begin, int64_t row_end, int64_t *row_ptr, int32_t *col,
+                             double *val, int64_t cap)
+{
+    if (!c) return DRTS_EINVAL;
+    if (row_begin < 0 || row_end < row_begin || row_end > c->n_states || !row_ptr)
+        return fail(c, DRTS_EINVAL, "bad row range");
+    const int64_t n = row_end - row_begin;
+    int64_t *dcount = nullptr;
+    cudaError_t e = cudaMallocAsync(&dcount, sizeof(int64_t) * (n + 1), c->stream);
+    std::vector<int64_t> cnt(size_t(n) + 1, 0);
+    if (e == cudaSuccess) e = launch_count_export(c->A, c->V, row_begin, row_end, dcount, c->stream);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(cnt.data(), dcount, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        if (dcount) cudaFree(dcount);
+        return cuda_fail(c, e, "export_rows");
+    }
+    row_ptr[0] = 0;
+    for (int64_t r = 0; r < n; ++r) row_ptr[r + 1] = row_ptr[r] + cnt[size_t(r)];
+    const int64_t nnz = row_ptr[n];
+    if (nnz > cap || (nnz > 0 && (!col || !val))) {
+        cudaFree(dcount);
+        return fail(c, DRTS_EINVAL, "export capacity " + std::to_string(cap) + " < " + std::to_string(nnz));
+    }
+    int32_t *dcol = nullptr;
+    double *dval = nullptr;
+    e = cudaMemcpyAsync(dcount, row_ptr, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dcol, sizeof(int32_t) * (nnz + 1), c->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dval, sizeof(double) * (nnz + 1), c->stream);
+    if (e == cudaSuccess)
+        e = launch_export(c->A, c->prob.nx, c->prob.ny, c->prob.nz, row_begin, row_end, dcount, dcol, dval, c->stream);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(col, dcol, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && nnz > 0) e = cudaMemcpyAsync(val, dval, sizeof(double) * nnz, cudaMemcpyDeviceToHost, c->stream);
+    if (dcol) cudaFreeAsync(dcol, c->stream);
+    if (dval) cudaFreeAsync(dval, c->stream);
+    cudaFreeAsync(dcount, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "export_rows");
+    return sync_check(c, "export_rows");
+}
+
+drts_status drts_column_info(drts_ctx *c, double *absorb, double *exit_total, double *exit_det)
+{
+    if (!c) return DRTS_EINVAL;
+    // host evaluation of the per-(medium, face mask, direction) tables over
+    // the medium map (a one-off readout, not part of the step)
+    std::vector<uint8_t> med(size_t(c->V));
+    cudaError_t e = cudaMemcpyAsync(med.data(), c->T.med, size_t(c->V), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "column_info");
+    const int nx = c->prob.nx, ny = c->prob.ny, nz = c->prob.nz;
+    for (int64_t v = 0; v < c->V; ++v) {
+        const int x = int(v % nx), y = int(v / nx % ny), z = int(v / (int64_t(nx) * ny));
+        const int b[3] = {x == 0 ? 0 : (x == nx - 1 ? 2 : 1), y == 0 ? 0 : (y == ny - 1 ? 2 : 1),
+                          z == 0 ? 0 : (z == nz - 1 ? 2 : 1)};
+        const int mask = b[2] * 9 + b[1] * 3 + b[0];
+        const int k = med[size_t(v)];
+        for (int d = 0; d < kDirs; ++d) {
+            const size_t ti = (size_t(k) * 27 + mask) * kDirs + d;
+            if (absorb) absorb[v * kDirs + d] = c->host.absorb[k];
+            if (exit_total) exit_total[v * kDirs + d] = c->host.exit_total[ti];
+            if (exit_det) exit_det[v * kDirs + d] = c->host.exit_det[ti];
+        }
+    }
+    return DRTS_OK;
+}
+
+drts_status drts_get_info(const drts_ctx *c, drts_info *out)
+{
+    if (!c || !out) return DRTS_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->n_states = c->n_states;
+    out->nnz = c->A.nnz;
+    out->nnz_padded = c->A.n_groups * kSlice * kGroup;
+    out->n_slices = c->A.n_slices;
+    out->matrix_bytes = out->nnz_padded * int64_t(value_bytes(c->A.precision) + sizeof(uint16_t)) +
+                        c->A.n_slices * int64_t(sizeof(int64_t) + sizeof(int32_t)) +
+                        (c->A.row_scale ? c->A.n_slices * kSlice * 4 : 0);
+    out->state_bytes = c->x_elems * int64_t(state_elem_bytes(c->A.precision));
+    out->t = c->t;
+    out->precision = c->A.precision;
+    out->n_rhs = c->R;
+    out->n_patch = c->n_patch;
+    out->special_voxels_permille = c->special_permille;
+    return DRTS_OK;
+}
+
+drts_status drts_set_launch(drts_ctx *c, int32_t blocks_per_sm, int32_t threads_per_block, int32_t rhs_tile)
+{
+    if (!c) return DRTS_EINVAL;
+    if (threads_per_block != 0 && (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32))
+        return fail(c, DRTS_EINVAL, "threads_per_block must be a multiple of 32 in 32..256");
+    if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(c, DRTS_EINVAL, "blocks_per_sm must be 0..64");
+    c->threads = threads_per_block ? threads_per_block : 256;
+    if (blocks_per_sm) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        c->blocks = sms * blocks_per_sm;
+    } else {
+        c->blocks = step_default_blocks(c->A.precision, c->R, c->threads);
+    }
+    c->rhs_tile = rhs_tile;
+    return DRTS_OK;
+}
+
+void drts_destroy(drts_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (void *p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+const char *drts_last_error(const drts_ctx *c)
+{
+    return c ? c->err.c_str() : g_assemble_error.c_str();
+}
+
+}  // extern "C"

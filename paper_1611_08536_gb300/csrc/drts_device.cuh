@@ -1,0 +1,112 @@
+// Device-side data of an assembled DRTS problem and the launch wrappers the
+// C ABI calls.  All kernels target sm_103a.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "drts_internal.h"
+
+namespace drts {
+
+// Lookup tables the device assembler reads (uploaded once per problem).
+struct DevTables {
+    int nx, ny, nz;
+    int64_t V;                  // voxels
+    int K;                      // media
+    const double *W;            // [K][26][27][26] raw stencil
+    const int32_t *tmpl_off;    // [K][26][28]
+    const uint8_t *tmpl_n;
+    const double *tmpl_val;
+    const double *r_edge;       // [K][4]
+    const double *r_int;        // [K][K][4]
+    const double *nref;         // [K]
+    const uint8_t *med;         // [V] medium of each voxel
+    const uint8_t *plain;       // [V] 1 when the voxel's rows need no folding
+};
+
+// Sliced storage of A: slice q = voxel block b (32 voxels) * 26 + direction
+// m; lane l of the slice is row (voxel 32b+l, direction m).  Entry e of a row
+// sits at ((slice_ptr[q] + e/4) * 32 + lane) * 4 + e%4 (lane-interleaved
+// groups of four), so one warp-wide 16-byte load per lane moves 128 entries.
+struct SlicedMatrix {
+    int precision = DRTS_FP32;
+    int64_t n_slices = 0;
+    int64_t n_groups = 0;       // sum of slice_len4 (units of 32 lanes x 4)
+    int64_t nnz = 0;
+    void *vals = nullptr;       // double / float / __half [n_groups*128]
+    uint16_t *codes = nullptr;  // [n_groups*128] offset_index*26 + n
+    float *row_scale = nullptr; // FP16 tier: [n_slices*32]
+    int64_t *slice_ptr = nullptr;   // [n_slices] in groups
+    int32_t *slice_len4 = nullptr;  // [n_slices]
+    int32_t *row_len = nullptr;     // [n_slices*32]
+};
+
+struct SourceEntry {
+    int32_t slice;     // slice holding the target state
+    int32_t lane;      // lane (row) within it
+    int32_t rhs;
+    int32_t prof;      // index of the rhs profile
+    double w;          // weight
+};
+
+struct SourceProfile {
+    int64_t t0;
+    int32_t n_t;
+    int32_t off;       // offset into the profile value array
+    int32_t pad0, pad1;
+};
+
+// Column functionals of one step (per medium / face mask / direction).
+struct StepTables {
+    const double *absorb;      // [K]
+    const double *exit_total;  // [K][27][26]
+    const double *exit_det;    // [K][27][26]
+};
+
+struct StepArgs {
+    SlicedMatrix A;
+    int nx, ny, nz;
+    int64_t V;
+    int R;                     // right-hand sides
+    const void *x;             // state at t, layout [(n*V + v)*R + r]
+    void *y;                   // state at t+1
+    const uint8_t *med;
+    StepTables tab;
+    int det_face, det_nu, det_nv, n_patch;
+    double *det;               // det[r][t_hist][patch] base, or null
+    int64_t det_stride_r;      // elements between rhs
+    int64_t t;                 // time index of x
+    double *ledger;            // [R][4]: sum x, injected, absorbed, exited
+    int n_src;
+    const SourceEntry *src;
+    const SourceProfile *prof; // [R]
+    const double *prof_vals;
+    const double *step_scale;  // [R] host-supplied source factors of this step, or null
+    int rhs_tile;
+};
+
+// assembler (drts_assemble.cu)
+cudaError_t launch_classify(const DevTables &T, uint8_t *plain, cudaStream_t s);
+cudaError_t launch_count(const DevTables &T, SlicedMatrix &A, float *row_max, cudaStream_t s);
+cudaError_t launch_scan(SlicedMatrix &A, int64_t *d_total, cudaStream_t s);
+cudaError_t launch_fill(const DevTables &T, SlicedMatrix &A, const float *row_max, cudaStream_t s);
+cudaError_t launch_export(const SlicedMatrix &A, int nx, int ny, int nz, int64_t row_begin,
+                          int64_t row_end, const int64_t *d_row_ptr, int32_t *d_col,
+                          double *d_val, cudaStream_t s);
+cudaError_t launch_count_export(const SlicedMatrix &A, int64_t V, int64_t row_begin,
+                                int64_t row_end, int64_t *d_counts, cudaStream_t s);
+
+// step (drts_step.cu)
+cudaError_t launch_step(const StepArgs &a, int blocks, int threads, cudaStream_t s);
+int step_default_blocks(int precision, int R, int threads);
+cudaError_t launch_to_canonical(const void *x, int precision, int64_t V, int R, int r,
+                                double *out, cudaStream_t s);
+cudaError_t launch_from_canonical(const double *in, int precision, int64_t V, int R, int r,
+                                  void *x, cudaStream_t s);
+cudaError_t launch_ledger_sum(const void *x, int precision, int64_t n, int R, int r,
+                              double *out, cudaStream_t s);
+
+}  // namespace drts

@@ -1,0 +1,68 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "drts.h"
+
+namespace drts {
+
+constexpr int kDirs = 26;         // lattice directions
+constexpr int kOffs = 27;         // neighbour offsets {-1,0,1}^3
+constexpr int kCodes = kOffs * kDirs;  // column code = offset_index*26 + direction
+constexpr int kSlice = 32;        // rows per slice (one warp, one lane per row)
+constexpr int kGroup = 4;         // entries per lane per vector load
+constexpr int kCenterCode = 13 * kDirs;  // offset (0,0,0), direction 0: padding
+constexpr int kMaxRhs = 64;
+constexpr int kMaxSrc = 64;
+
+// Lattice direction table (state order of Eq. 22).
+struct Directions {
+    int v[kDirs][3];      // integer vector
+    double u[kDirs][3];   // unit vector S_d
+    int nnzc[kDirs];      // number of nonzero components (1 axis, 2 edge, 3 corner)
+    int index_of[27];     // (dz+1)*9+(dy+1)*3+(dx+1) -> direction (-1 at origin)
+    Directions();
+};
+const Directions &dirs();
+
+#ifdef __CUDACC__
+#define DRTS_HD __host__ __device__
+#else
+#define DRTS_HD
+#endif
+
+DRTS_HD inline int offset_index(int dx, int dy, int dz) { return (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1); }
+
+// Host-built tables of one problem (FP64).  Transcendentals (exp, sqrt, the
+// Henyey-Greenstein power, Fresnel) are evaluated here once; the device
+// assembler only looks them up and multiplies.
+struct HostTables {
+    int n_media = 0;
+    std::vector<double> lam;        // [k] L_k / h
+    std::vector<double> nref;       // [k] refractive index
+    std::vector<double> absorb;     // [k] 1 - exp(-mu_a L_k)
+    // raw stencil W[k][n][o][m]: mass sent from direction n of a voxel of
+    // medium k to the voxel at offset o in direction m (Eq. 18, 19, 21)
+    std::vector<double> W;          // [k][26][27][26]
+    // plain-row templates: for row direction m and column offset index d
+    // (source = row voxel + d), the entries (n, W[k][n][26-d][m]) with W > 0
+    std::vector<int32_t> tmpl_off;  // [k][26][28]
+    std::vector<uint8_t> tmpl_n;
+    std::vector<double> tmpl_val;
+    // Fresnel reflectance by incidence class c (0: cos 0, else 1/sqrt(c)
+    // with c nonzero direction components): edge [k][4], interface [k1][k2][4]
+    std::vector<double> r_edge;     // [k][4]
+    std::vector<double> r_int;      // [k][k][4]
+    // exit fractions of a state of medium k in a voxel whose face mask is
+    // mask = bz*9+by*3+bx (b = 0 low face, 1 inside, 2 high face)
+    std::vector<double> exit_total; // [k][27][26]
+    std::vector<double> exit_det;   // [k][27][26]
+    int n_template_entries_max = 0;
+};
+
+std::string build_host_tables(const drts_problem &p, HostTables &t);
+
+}  // namespace drts

@@ -1,0 +1,232 @@
+"""Thin ctypes binding of libdrts.so (C ABI in include/drts.h).
+
+Argument marshalling only: every step of the time step runs in the library's
+CUDA kernels.  Loading fails loudly when the library has not been built;
+there is no CPU fallback.  PyTorch is used only to hand the library a CUDA
+stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import inputs as _inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libdrts.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, EUNSUPPORTED = range(7)
+OPEN, MIRROR, FRESNEL = 0, 1, 2
+FP64, FP32, FP16_ROWSCALE = 0, 1, 2
+FACE_NONE = -1
+_STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE",
+           6: "EUNSUPPORTED"}
+
+
+class DrtsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Medium(ctypes.Structure):
+    _fields_ = [("mu_s", ctypes.c_double), ("mu_a", ctypes.c_double),
+                ("g", ctypes.c_double), ("n", ctypes.c_double)]
+
+
+class ProblemC(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("voxel_mm", ctypes.c_double),
+        ("n_media", ctypes.c_int32),
+        ("media", ctypes.POINTER(Medium)),
+        ("medium_of_voxel", ctypes.c_void_p),
+        ("n_outside", ctypes.c_double),
+        ("boundary", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+        ("n_rhs", ctypes.c_int32),
+        ("det_face", ctypes.c_int32),
+        ("det_nu", ctypes.c_int32), ("det_nv", ctypes.c_int32),
+        ("max_steps", ctypes.c_int64),
+    ]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("n_states", ctypes.c_int64), ("nnz", ctypes.c_int64),
+        ("nnz_padded", ctypes.c_int64), ("n_slices", ctypes.c_int64),
+        ("matrix_bytes", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
+        ("t", ctypes.c_int64),
+        ("precision", ctypes.c_int32), ("n_rhs", ctypes.c_int32),
+        ("n_patch", ctypes.c_int32), ("special_voxels_permille", ctypes.c_int32),
+    ]
+
+
+SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_detectors",
+           "drts_read_state", "drts_write_state", "drts_run_host", "drts_export_rows",
+           "drts_column_info", "drts_get_info", "drts_set_launch", "drts_destroy",
+           "drts_last_error"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdrts.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libdrts.so not built ({path}); run "
+                          "python -c 'import __graft_entry__ as g; g.build()'")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    lib.drts_assemble.argtypes = [ctypes.POINTER(ProblemC), vp, ctypes.POINTER(vp)]
+    lib.drts_inject_source.argtypes = [vp, i32, i32, vp, vp, i64, i32, vp]
+    lib.drts_step_n.argtypes = [vp, i64]
+    lib.drts_read_detectors.argtypes = [vp, i32, i64, i64, vp, vp]
+    lib.drts_read_state.argtypes = [vp, i32, vp]
+    lib.drts_write_state.argtypes = [vp, i32, vp]
+    lib.drts_run_host.argtypes = [vp, i64, vp, vp]
+    lib.drts_export_rows.argtypes = [vp, i64, i64, vp, vp, vp, i64]
+    lib.drts_column_info.argtypes = [vp, vp, vp, vp]
+    lib.drts_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.drts_set_launch.argtypes = [vp, i32, i32, i32]
+    lib.drts_destroy.argtypes = [vp]
+    lib.drts_destroy.restype = None
+    lib.drts_last_error.argtypes = [vp]
+    lib.drts_last_error.restype = ctypes.c_char_p
+    for name in SYMBOLS:
+        getattr(lib, name)
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def problem_struct(prob, max_steps=0):
+    """ctypes drts_problem for an ``inputs.Problem`` (keeps its buffers alive)."""
+    media = (Medium * len(prob.media))(*[Medium(*m) for m in prob.media])
+    mov = np.ascontiguousarray(prob.medium_of_voxel, dtype=np.uint8).ravel()
+    nx, ny, nz = prob.shape
+    s = ProblemC(nx, ny, nz, float(prob.voxel_mm), len(prob.media), media, _ptr(mov),
+                 float(prob.n_outside), int(prob.boundary), int(prob.precision),
+                 int(prob.n_rhs), int(prob.det_face), int(prob.det_nu),
+                 int(prob.det_nv), int(max_steps))
+    s._keep = (media, mov)
+    return s
+
+
+class Context:
+    """An assembled DRTS problem on the GPU (owns a drts_ctx)."""
+
+    def __init__(self, prob, max_steps=0, stream=None):
+        lib = load()
+        self._lib = lib
+        self.prob = prob
+        self._ps = problem_struct(prob, max_steps)
+        h = ctypes.c_void_p()
+        st = lib.drts_assemble(ctypes.byref(self._ps), ctypes.c_void_p(stream or 0),
+                               ctypes.byref(h))
+        if st != OK:
+            raise DrtsError(st, lib.drts_last_error(None).decode())
+        self._h = h
+        self.max_steps = max_steps
+        self.n_states = prob.n_states
+
+    def _check(self, st):
+        if st != OK:
+            raise DrtsError(st, self._lib.drts_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.drts_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- C ABI calls -------------------------------------------------------
+    def inject_source(self, rhs, state_idx, weight, t0, profile):
+        s = np.ascontiguousarray(state_idx, dtype=np.int64)
+        w = np.ascontiguousarray(weight, dtype=np.float64)
+        p = np.ascontiguousarray(profile, dtype=np.float64)
+        self._check(self._lib.drts_inject_source(self._h, int(rhs), s.size, _ptr(s), _ptr(w),
+                                                 int(t0), p.size, _ptr(p)))
+
+    def set_source(self, rhs, src):
+        self.inject_source(rhs, src.state, src.weight, src.t0, src.profile)
+
+    def step_n(self, n):
+        self._check(self._lib.drts_step_n(self._h, int(n)))
+
+    def read_detectors(self, rhs=0, t_begin=0, t_end=None):
+        info = self.info()
+        if t_end is None:
+            t_end = info.t
+        out = np.zeros((max(t_end - t_begin, 0), max(info.n_patch, 1)), np.float64)
+        led = np.zeros(4, np.float64)
+        self._check(self._lib.drts_read_detectors(self._h, int(rhs), int(t_begin), int(t_end),
+                                                  _ptr(out), _ptr(led)))
+        return out[:, :info.n_patch], led
+
+    def read_state(self, rhs=0):
+        out = np.empty(self.n_states, np.float64)
+        self._check(self._lib.drts_read_state(self._h, int(rhs), _ptr(out)))
+        return out
+
+    def write_state(self, x, rhs=0):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        assert x.size == self.n_states
+        self._check(self._lib.drts_write_state(self._h, int(rhs), _ptr(x)))
+
+    def run_host(self, scale, det_out=None):
+        scale = np.ascontiguousarray(scale, dtype=np.float64)
+        n = scale.shape[0]
+        self._check(self._lib.drts_run_host(self._h, n, _ptr(scale), _ptr(det_out)))
+        return det_out
+
+    def export_rows(self, row_begin, row_end, cap=None):
+        n = row_end - row_begin
+        rp = np.zeros(n + 1, np.int64)
+        if cap is None:
+            cap = 300 * n + 16
+        col = np.empty(cap, np.int32)
+        val = np.empty(cap, np.float64)
+        self._check(self._lib.drts_export_rows(self._h, int(row_begin), int(row_end), _ptr(rp),
+                                               _ptr(col), _ptr(val), int(cap)))
+        nnz = int(rp[-1])
+        return rp, col[:nnz].copy(), val[:nnz].copy()
+
+    def column_info(self):
+        ab, ex, ed = (np.empty(self.n_states, np.float64) for _ in range(3))
+        self._check(self._lib.drts_column_info(self._h, _ptr(ab), _ptr(ex), _ptr(ed)))
+        return ab, ex, ed
+
+    def info(self):
+        i = Info()
+        self._check(self._lib.drts_get_info(self._h, ctypes.byref(i)))
+        return i
+
+    def set_launch(self, blocks_per_sm=0, threads=0, rhs_tile=0):
+        self._check(self._lib.drts_set_launch(self._h, int(blocks_per_sm), int(threads),
+                                              int(rhs_tile)))
+
+
+def assemble(prob, max_steps=0, stream=None) -> Context:
+    return Context(prob, max_steps=max_steps, stream=stream)
+
+
+__all__ = ["Context", "assemble", "load", "DrtsError", "SYMBOLS", "_inputs"]

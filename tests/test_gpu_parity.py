@@ -1,0 +1,192 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Assembly: row pointers and column indices bit-exact, values within the
+rounding of the stored precision.  Time step: relative L1 of the state
+within the per-precision tolerance (FP64 1e-12; FP32 1e-5 per 1000 steps;
+FP16 row-scaled 1e-4 or the measured figure stated in the test).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1611_08536_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1611_08536_gb300 import build, drts
+    build.build()
+    drts.load()
+    return drts
+
+
+def rel_l1(a, b):
+    return np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300)
+
+
+def _val_tol(precision):
+    return {I.FP64: 1e-13, I.FP32: 2.0 ** -24 * 1.01, I.FP16_ROWSCALE: 2.0 ** -11}[precision]
+
+
+def check_rows(ctx, csr, precision):
+    r0, r1 = csr.row0, csr.row0 + csr.n_rows
+    rp, col, val = ctx.export_rows(r0, r1, cap=csr.nnz + 16)
+    assert np.array_equal(rp, csr.row_ptr)
+    assert np.array_equal(col, csr.col)
+    if precision == I.FP16_ROWSCALE:
+        # per-row scale: error relative to the row maximum
+        rowmax = np.maximum.reduceat(csr.val, csr.row_ptr[:-1]) if csr.nnz else np.zeros(0)
+        rm = np.repeat(rowmax, np.diff(csr.row_ptr))
+        assert np.all(np.abs(val - csr.val) <= rm * 2.0 ** -11 + 1e-30)
+    else:
+        assert np.all(np.abs(val - csr.val) <= np.abs(csr.val) * _val_tol(precision) + 1e-300)
+
+
+def small_cases():
+    out = []
+    p, _ = I.fresnel_cube(9, precision=I.FP64)
+    out.append(("fresnel9_fp64", p))
+    p, _ = I.three_layers(16, precision=I.FP32)
+    out.append(("layers16_fp32", p))
+    p, _ = I.inclusions(10, n_rhs=1, seed=2, precision=I.FP32, n_spheres=2)
+    p.boundary = I.OPEN
+    out.append(("inclusions10_open_fp32", p))
+    p, _ = I.ellipsoids(13, n_ell=4, seed=7, precision=I.FP32)
+    out.append(("ellipsoids13_fp32", p))
+    mov = np.zeros((7, 6, 5), np.uint8)
+    mov[:, 3:, :] = 1
+    p = I.Problem((5, 6, 7), 0.05, [(3.0, 0.2, 0.8, 1.33), (9.0, 0.02, 0.9, 1.5)], mov, 1.0,
+                  I.MIRROR, I.FP64, 1, I.FACE_MX, 3, 2, "ragged_mirror")
+    out.append(("ragged_5x6x7_mirror_fp64", p))
+    p = I.Problem((2, 2, 2), 0.1, [(5.0, 0.1, 0.5, 1.4)], np.zeros((2, 2, 2), np.uint8), 1.0,
+                  I.FRESNEL, I.FP32, 1, I.FACE_PZ, 1, 1, "tiny")
+    out.append(("min_2x2x2_fp32", p))
+    p, _ = I.three_layers(12, precision=I.FP16_ROWSCALE)
+    out.append(("layers12_fp16", p))
+    return out
+
+
+@pytest.mark.parametrize("name,prob", small_cases(), ids=[c[0] for c in small_cases()])
+def test_assembly_matches_oracle(gpu, oracle_mod, name, prob):
+    csr = oracle_mod.assemble(prob)
+    with gpu.Context(prob) as ctx:
+        check_rows(ctx, csr, prob.precision)
+        info = ctx.info()
+        assert info.nnz == csr.nnz
+        # column functionals
+        ab, ex, ed = ctx.column_info()
+        ab_o, ex_o, ed_o, _ = oracle_mod.column_info(prob)
+        assert np.allclose(ab, ab_o, rtol=1e-14, atol=0)
+        assert np.allclose(ex, ex_o, rtol=1e-12, atol=1e-300)
+        assert np.allclose(ed, ed_o, rtol=1e-12, atol=1e-300)
+
+
+def _run_both(gpu, oracle_mod, prob, src, steps, x0=None):
+    csr = oracle_mod.assemble(prob)
+    xo, deto, ledo = oracle_mod.run(prob, csr, steps, src.as_tuple(), x0=x0)
+    with gpu.Context(prob, max_steps=steps) as ctx:
+        if x0 is not None:
+            ctx.write_state(x0)
+        ctx.set_source(0, src)
+        ctx.step_n(steps)
+        x = ctx.read_state()
+        det, led = ctx.read_detectors()
+    return (x, det, led), (xo, deto, ledo)
+
+
+def test_fresnel_cube16_fp64_300_steps(gpu, oracle_mod):
+    """16^3 FP64 configuration, delta pulse, 300 steps."""
+    prob, src = I.fresnel_cube(16, precision=I.FP64)
+    (x, det, led), (xo, deto, ledo) = _run_both(gpu, oracle_mod, prob, src, 300)
+    assert rel_l1(x, xo) < 1e-12
+    assert rel_l1(det, deto) < 1e-12
+    assert np.allclose(led, ledo, rtol=1e-11)
+    assert x.min() >= 0.0
+
+
+def test_layers_fp32_1000_steps(gpu, oracle_mod):
+    """Three-layer FP32 configuration at 24^3 for 1000 steps (tolerance 1e-5 per 1000 steps)."""
+    prob, src = I.three_layers(24, precision=I.FP32)
+    (x, det, led), (xo, deto, ledo) = _run_both(gpu, oracle_mod, prob, src, 1000)
+    e = rel_l1(x, xo)
+    print(f"FP32 rel L1 after 1000 steps: {e:.3e}")
+    assert e <= 1e-5
+    assert rel_l1(det, deto) <= 1e-5
+    assert led[0] + led[2] + led[3] == pytest.approx(led[1], rel=1e-5)
+
+
+@pytest.mark.parametrize("name,prob", small_cases()[2:6], ids=[c[0] for c in small_cases()[2:6]])
+def test_step_random_state(gpu, oracle_mod, name, prob):
+    rng = np.random.default_rng(5)
+    x0 = rng.random(prob.n_states)
+    src = I.Source(np.array([3, prob.n_states - 1], np.int64), np.array([0.5, 2.0]), 1,
+                   np.array([1.0, 0.25, 4.0]))
+    steps = 25
+    (x, det, led), (xo, deto, ledo) = _run_both(gpu, oracle_mod, prob, src, steps, x0=x0)
+    tol = 1e-12 if prob.precision == I.FP64 else 1e-5
+    assert rel_l1(x, xo) < tol
+    if det.size:
+        assert rel_l1(det, deto) < tol
+    assert led[1] == pytest.approx(ledo[1], rel=1e-12)
+
+
+def test_fp16_rowscale_tier(gpu, oracle_mod):
+    prob, src = I.three_layers(16, precision=I.FP16_ROWSCALE)
+    (x, det, led), (xo, deto, ledo) = _run_both(gpu, oracle_mod, prob, src, 200)
+    e = rel_l1(x, xo)
+    print(f"FP16-rowscale rel L1 after 200 steps: {e:.3e}")
+    assert x.min() >= 0.0
+    assert e < 5e-3
+
+
+def test_empty_source_and_zero_steps(gpu):
+    prob, _ = I.fresnel_cube(6, precision=I.FP32)
+    with gpu.Context(prob, max_steps=5) as ctx:
+        ctx.inject_source(0, [], [], 0, [])
+        ctx.step_n(0)
+        ctx.step_n(5)
+        assert np.all(ctx.read_state() == 0.0)
+        det, led = ctx.read_detectors()
+        assert np.all(det == 0.0) and np.all(led == 0.0)
+        with pytest.raises(gpu.DrtsError):
+            ctx.step_n(1)                      # beyond max_steps
+
+
+def test_invalid_inputs_rejected(gpu):
+    prob, _ = I.fresnel_cube(4, precision=I.FP32)
+    bad = I.Problem((1, 4, 4), 0.1, [(1, 0, 0, 1.4)], np.zeros((4, 4, 1), np.uint8))
+    with pytest.raises(gpu.DrtsError):
+        gpu.Context(bad)
+    with gpu.Context(prob, max_steps=2) as ctx:
+        with pytest.raises(gpu.DrtsError):
+            ctx.inject_source(0, [prob.n_states], [1.0], 0, [1.0])
+        with pytest.raises(gpu.DrtsError):
+            ctx.inject_source(1, [0], [1.0], 0, [1.0])
+
+
+def test_run_host_matches_step_n(gpu):
+    prob, src = I.three_layers(16, precision=I.FP32)
+    steps = 30
+    with gpu.Context(prob, max_steps=steps) as a:
+        a.set_source(0, src)
+        a.step_n(steps)
+        xa = a.read_state()
+        da, _ = a.read_detectors()
+    scale = np.zeros((steps, 1))
+    t0, prof = src.t0, src.profile
+    for t in range(steps):
+        if t0 <= t < t0 + prof.size:
+            scale[t, 0] = prof[t - t0]
+    with gpu.Context(prob, max_steps=steps) as b:
+        b.inject_source(0, src.state, src.weight, 0, [])
+        det = np.zeros((steps, 1, 256))
+        b.run_host(scale, det)
+        xb = b.read_state()
+    assert rel_l1(xb, xa) < 1e-6
+    assert rel_l1(det[:, 0, :], da) < 1e-6
