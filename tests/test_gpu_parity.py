@@ -136,13 +136,15 @@ def test_step_random_state(gpu, oracle_mod, name, prob):
     assert led[1] == pytest.approx(ledo[1], rel=1e-12)
 
 
+@pytest.mark.xfail(strict=False, reason="FP16 rounding of A drifts the solution; "
+                   "column-compensated rounding is not built yet")
 def test_fp16_rowscale_tier(gpu, oracle_mod):
     prob, src = I.three_layers(16, precision=I.FP16_ROWSCALE)
     (x, det, led), (xo, deto, ledo) = _run_both(gpu, oracle_mod, prob, src, 200)
     e = rel_l1(x, xo)
     print(f"FP16-rowscale rel L1 after 200 steps: {e:.3e}")
     assert x.min() >= 0.0
-    assert e < 5e-3
+    assert e < 1e-4
 
 
 def test_empty_source_and_zero_steps(gpu):
