@@ -181,6 +181,29 @@ drts_status drts_get_info(const drts_ctx *ctx, drts_info *out);
 drts_status drts_set_launch(drts_ctx *ctx, int32_t blocks_per_sm,
                             int32_t threads_per_block, int32_t rhs_tile);
 
+/*
+ * Sum of x(t) of right-hand side rhs (the "sum of x" term of the ledger that
+ * drts_read_detectors returns), written to out_device: one FP64 value in
+ * device memory the caller owns.  The paper has no counterpart to this call;
+ * it exists for callers that cannot allocate device memory when they need the
+ * sum: work being recorded into a CUDA graph or stream capture (allocation
+ * is not allowed there), real-time loops that must not wait on the
+ * allocator, and processes whose device memory belongs to another runtime's
+ * pool.  It allocates nothing: its per-block partial sums live in a static
+ * device array of 4096 doubles (32 KiB) that every GPU which loads the
+ * library keeps until the process exits.
+ *   - Limit: at most 268,435,456 states (4096 blocks of 65,536); larger state
+ *     vectors are rejected with DRTS_EINVAL.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the array.  Calls on one stream are ordered; calls
+ *     whose kernels overlap on the GPU (other streams, other contexts on the
+ *     same device) race on it and may return wrong sums.
+ *   - Asynchronous on the context stream; the result is deterministic (fixed
+ *     reduction order) and equals the ledger's sum up to rounding order.
+ */
+drts_status drts_state_sum_noalloc(drts_ctx *ctx, int32_t rhs, double *out_device);
+
 /* Free every device and host resource of ctx (NULL is ignored). */
 void drts_destroy(drts_ctx *ctx);
 

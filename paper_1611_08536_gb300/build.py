@@ -23,6 +23,7 @@ SOURCES = {
     "drts_assemble.cu": ["--fmad=false"],   # fixed-order FP64 table products
     "drts_step.cu": [],
     "drts_api.cu": [],
+    "drts_noalloc.cu": [],
 }
 
 

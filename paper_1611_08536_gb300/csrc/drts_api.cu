@@ -570,6 +570,20 @@ drts_status drts_set_launch(drts_ctx *c, int32_t blocks_per_sm, int32_t threads_
     return DRTS_OK;
 }
 
+drts_status drts_state_sum_noalloc(drts_ctx *c, int32_t rhs, double *out_device)
+{
+    if (!c) return DRTS_EINVAL;
+    if (rhs < 0 || rhs >= c->R || !out_device) return fail(c, DRTS_EINVAL, "bad arguments");
+    if (c->n_states > noalloc_max_states())
+        return fail(c, DRTS_EINVAL, "state vector of " + std::to_string(c->n_states) +
+                                        " states exceeds the static scratch limit of " +
+                                        std::to_string(noalloc_max_states()));
+    cudaError_t e = launch_state_sum_noalloc(c->x, c->prob.precision, c->n_states, c->R, rhs, out_device,
+                                             c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "state_sum_noalloc");
+    return DRTS_OK;
+}
+
 void drts_destroy(drts_ctx *c)
 {
     if (!c) return;

@@ -109,4 +109,9 @@ cudaError_t launch_from_canonical(const double *in, int precision, int64_t V, in
 cudaError_t launch_ledger_sum(const void *x, int precision, int64_t n, int R, int r,
                               double *out, cudaStream_t s);
 
+// no-allocation state sum (drts_noalloc.cu)
+int64_t noalloc_max_states();
+cudaError_t launch_state_sum_noalloc(const void *x, int precision, int64_t n, int R, int r,
+                                     double *out, cudaStream_t s);
+
 }  // namespace drts

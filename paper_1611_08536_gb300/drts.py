@@ -67,7 +67,7 @@ class Info(ctypes.Structure):
 SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_detectors",
            "drts_read_state", "drts_write_state", "drts_run_host", "drts_export_rows",
            "drts_column_info", "drts_get_info", "drts_set_launch", "drts_destroy",
-           "drts_last_error"]
+           "drts_last_error", "drts_state_sum_noalloc"]
 
 _lib = None
 
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
     lib.drts_column_info.argtypes = [vp, vp, vp, vp]
     lib.drts_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.drts_set_launch.argtypes = [vp, i32, i32, i32]
+    lib.drts_state_sum_noalloc.argtypes = [vp, i32, vp]
     lib.drts_destroy.argtypes = [vp]
     lib.drts_destroy.restype = None
     lib.drts_last_error.argtypes = [vp]
@@ -214,6 +215,13 @@ class Context:
         ab, ex, ed = (np.empty(self.n_states, np.float64) for _ in range(3))
         self._check(self._lib.drts_column_info(self._h, _ptr(ab), _ptr(ex), _ptr(ed)))
         return ab, ex, ed
+
+    def state_sum_noalloc(self, out_device_ptr, rhs=0):
+        """Sum of x(t) into caller-owned device memory (one FP64 at
+        ``out_device_ptr``), without any device allocation; asynchronous on
+        the context stream."""
+        self._check(self._lib.drts_state_sum_noalloc(self._h, int(rhs),
+                                                     ctypes.c_void_p(int(out_device_ptr))))
 
     def info(self):
         i = Info()
