@@ -154,8 +154,11 @@ def run_gpu(args):
     t_asm = time.time() - t_asm
     info = ctx.info()
     ctx.set_source(0, src)
-    if args.blocks_per_sm or args.threads:
-        ctx.set_launch(args.blocks_per_sm, args.threads)
+    tune = None
+    if args.blocks_per_sm or args.threads or args.variant >= 0:
+        ctx.set_launch(args.blocks_per_sm, args.threads, 0, args.variant)
+    elif args.autotune:
+        tune = ctx.autotune(args.autotune)
 
     ctx.step_n(args.warmup)
     torch.cuda.synchronize()
@@ -225,7 +228,8 @@ def run_gpu(args):
                    "format": "SELL-32 (slice = 32 voxels x 1 direction), 16-bit stencil codes",
                    "precision": args.precision, "steps_per_s": round(1e3 / ms_step, 3),
                    "l2": "inputs larger than L2 (matrix streamed every step)",
-                   "assembly_s": round(t_asm, 2), "parallelism": f"replicas x{ws}"},
+                   "assembly_s": round(t_asm, 2), "parallelism": f"replicas x{ws}",
+                   "launch": tune},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "peak_kind": peak_kind,
@@ -332,6 +336,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
+    ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--autotune", type=int, default=2, help="timed steps per candidate (0 = off)")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-check", dest="check", action="store_false")
     args = ap.parse_args()

@@ -176,10 +176,53 @@ drts_status drts_column_info(drts_ctx *ctx, double *absorb, double *exit_total,
 
 drts_status drts_get_info(const drts_ctx *ctx, drts_info *out);
 
-/* Set the kernel launch shape of the step (0 = library default / autotuned):
- * blocks per SM, threads per block, right-hand sides per pass. */
+/* Set the launch shape of the step kernel (0 = library default): blocks per
+ * SM (must fit), threads per block (multiple of 32, <= 256), right-hand sides
+ * per pass of the batched step, and the kernel variant (-1 keeps the current
+ * one; 0-2 = matrix streamed into registers with 1-3 groups prefetched, 3-6 =
+ * matrix streamed into shared-memory stages by bulk async copies, stage
+ * shapes (groups, stages) = (8,3), (4,3), (4,4), (2,6)).  All variants
+ * compute the same step; they differ only in speed.  DRTS_EINVAL if the
+ * shape does not fit on an SM. */
 drts_status drts_set_launch(drts_ctx *ctx, int32_t blocks_per_sm,
-                            int32_t threads_per_block, int32_t rhs_tile);
+                            int32_t threads_per_block, int32_t rhs_tile,
+                            int32_t variant);
+
+/* Result of drts_autotune. */
+typedef struct drts_tune_result {
+    int32_t variant, threads, blocks_per_sm, rhs_tile;
+    double ms_per_step;              /* measured time of the chosen launch */
+    int32_t candidates;              /* launches timed (0 when from the cache) */
+    int32_t from_cache;
+} drts_tune_result;
+
+/*
+ * Pick the fastest launch of the step for this context by timing every
+ * variant, block size and blocks-per-SM choice that fits (trial_steps timed
+ * launches each, CUDA events on the context stream) and apply it.  The state,
+ * t, detectors and ledger are left unchanged (the trial steps write the spare
+ * state buffer and a scratch ledger).  Results are cached per (grid,
+ * precision, rhs, SM count, nnz) in the process and, when the environment
+ * variable DRTS_TUNE_CACHE names a file, appended to it and read back by later
+ * processes.  Synchronises.  out may be NULL.
+ */
+drts_status drts_autotune(drts_ctx *ctx, int32_t trial_steps, drts_tune_result *out);
+
+/*
+ * Host-side fault injection for testing the failure paths (no GPU fault is
+ * ever caused).  kind:
+ *   DRTS_FAULT_NONE        clear everything below;
+ *   DRTS_FAULT_SKIP_COPY   the bulk-copy step variants never issue copy number
+ *                          arg of the first warp, so that warp's bounded wait
+ *                          runs out; the step then reports DRTS_ETIMEOUT at the
+ *                          next synchronising call and the context stays usable;
+ *   DRTS_FAULT_SPIN_LIMIT  polls before a device-side wait gives up (arg,
+ *                          1..2^30; default 2^22).
+ */
+#define DRTS_FAULT_NONE 0
+#define DRTS_FAULT_SKIP_COPY 1
+#define DRTS_FAULT_SPIN_LIMIT 2
+drts_status drts_set_fault(drts_ctx *ctx, int32_t kind, int64_t arg);
 
 /*
  * Sum of x(t) of right-hand side rhs (the "sum of x" term of the ledger that

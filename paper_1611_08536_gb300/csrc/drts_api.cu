@@ -4,8 +4,13 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -37,7 +42,10 @@ struct drts_ctx {
     std::vector<SourceEntry> src;        // host copy of all rhs entries
     std::vector<SourceProfile> prof;     // [R]
     std::vector<std::vector<double>> prof_vals;
-    int blocks = 0, threads = 256, rhs_tile = 0;
+    int blocks = 0, threads = 256, rhs_tile = 0, variant = 0;
+    int *d_err = nullptr;                // device error word of bounded waits
+    uint32_t spin_limit = 1u << 22;
+    int64_t fault_skip_chunk = -1;
     int special_permille = 0;
 };
 
@@ -119,6 +127,15 @@ drts_status sync_check(drts_ctx *c, const char *where)
 {
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, where);
+    if (c->d_err) {
+        int err = 0;
+        e = cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, where);
+        if (err) {
+            cudaMemset(c->d_err, 0, sizeof(int));
+            return fail(c, DRTS_ETIMEOUT, std::string(where) + ": a bounded device-side wait gave up");
+        }
+    }
     return DRTS_OK;
 }
 
@@ -174,6 +191,9 @@ StepArgs make_args(drts_ctx *c)
     a.prof = c->d_prof;
     a.prof_vals = c->d_prof_vals;
     a.rhs_tile = c->rhs_tile;
+    a.err = c->d_err;
+    a.spin_limit = c->spin_limit;
+    a.fault_skip_chunk = c->fault_skip_chunk;
     return a;
 }
 
@@ -304,7 +324,8 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     if ((e = dalloc(c, &c->x, sb)) != cudaSuccess || (e = dalloc(c, &c->y, sb)) != cudaSuccess ||
         (e = dalloc(c, &c->ledger, sizeof(double) * 4 * c->R)) != cudaSuccess ||
         (e = dalloc(c, &c->d_src, sizeof(SourceEntry) * kMaxSrc * c->R)) != cudaSuccess ||
-        (e = dalloc(c, &c->d_prof, sizeof(SourceProfile) * c->R)) != cudaSuccess) {
+        (e = dalloc(c, &c->d_prof, sizeof(SourceProfile) * c->R)) != cudaSuccess ||
+        (e = dalloc(c, &c->d_err, sizeof(int))) != cudaSuccess) {
         cuda_fail(c, e, "state allocation");
         return bail(DRTS_ENOMEM);
     }
@@ -318,12 +339,18 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     cudaMemsetAsync(c->x, 0, sb, c->stream);
     cudaMemsetAsync(c->y, 0, sb, c->stream);
     cudaMemsetAsync(c->ledger, 0, sizeof(double) * 4 * c->R, c->stream);
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     c->prof.assign(c->R, SourceProfile{0, 0, 0, 0, 0});
     c->prof_vals.assign(c->R, std::vector<double>());
     st = upload_sources(c);
     if (st != DRTS_OK) return bail(st);
     c->threads = 256;
-    c->blocks = step_default_blocks(prob->precision, c->R, c->threads);
+    c->variant = 0;
+    c->blocks = step_default_blocks(prob->precision, c->R, c->threads, c->variant);
+    if (c->blocks < 1) {
+        fail(c, DRTS_ECUDA, "step kernel does not fit on an SM");
+        return bail(DRTS_ECUDA);
+    }
     st = sync_check(c, "assembly");
     if (st != DRTS_OK) return bail(st);
     *out = c;
@@ -370,7 +397,7 @@ drts_status drts_step_n(drts_ctx *c, int64_t n_steps)
         return fail(c, DRTS_EINVAL, "t + n_steps exceeds max_steps");
     for (int64_t i = 0; i < n_steps; ++i) {
         StepArgs a = make_args(c);
-        cudaError_t e = launch_step(a, c->blocks, c->threads, c->stream);
+        cudaError_t e = launch_step(a, c->variant, c->blocks, c->threads, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
         std::swap(c->x, c->y);
         ++c->t;
@@ -394,7 +421,7 @@ drts_status drts_run_host(drts_ctx *c, int64_t n_steps, const double *scale, dou
         if (e != cudaSuccess) break;
         StepArgs a = make_args(c);
         a.step_scale = d_scale + i * c->R;
-        e = launch_step(a, c->blocks, c->threads, c->stream);
+        e = launch_step(a, c->variant, c->blocks, c->threads, c->stream);
         if (e != cudaSuccess) break;
         // this step's detector readout, device -> host
         if (det_out && a.det && c->n_patch > 0)
@@ -551,23 +578,172 @@ drts_status drts_get_info(const drts_ctx *c, drts_info *out)
     return DRTS_OK;
 }
 
-drts_status drts_set_launch(drts_ctx *c, int32_t blocks_per_sm, int32_t threads_per_block, int32_t rhs_tile)
+drts_status drts_set_launch(drts_ctx *c, int32_t blocks_per_sm, int32_t threads_per_block, int32_t rhs_tile,
+                            int32_t variant)
 {
     if (!c) return DRTS_EINVAL;
     if (threads_per_block != 0 && (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32))
         return fail(c, DRTS_EINVAL, "threads_per_block must be a multiple of 32 in 32..256");
     if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(c, DRTS_EINVAL, "blocks_per_sm must be 0..64");
-    c->threads = threads_per_block ? threads_per_block : 256;
-    if (blocks_per_sm) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        c->blocks = sms * blocks_per_sm;
-    } else {
-        c->blocks = step_default_blocks(c->A.precision, c->R, c->threads);
-    }
+    if (variant < -1 || variant >= kStepVariants) return fail(c, DRTS_EINVAL, "unknown step variant");
+    const int threads = threads_per_block ? threads_per_block : 256;
+    const int var = variant < 0 ? c->variant : variant;
+    const int fit = step_default_blocks(c->A.precision, c->R, threads, var);
+    if (fit < 1) return fail(c, DRTS_EINVAL, "launch shape does not fit on an SM");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (blocks_per_sm && sms * blocks_per_sm > fit)
+        return fail(c, DRTS_EINVAL, "more blocks per SM than fit (" + std::to_string(fit / sms) + ")");
+    c->threads = threads;
+    c->variant = var;
+    c->blocks = blocks_per_sm ? sms * blocks_per_sm : fit;
     c->rhs_tile = rhs_tile;
     return DRTS_OK;
+}
+
+namespace {
+
+// Autotuner cache: (grid, precision, rhs, SM count, nnz) -> best launch.
+std::mutex g_tune_mu;
+std::map<std::string, drts_tune_result> g_tune_cache;
+
+std::string tune_key(const drts_ctx *c, int sms)
+{
+    std::ostringstream k;
+    k << c->prob.nx << 'x' << c->prob.ny << 'x' << c->prob.nz << ":p" << c->prob.precision << ":r" << c->R
+      << ":sm" << sms << ":nnz" << c->A.nnz;
+    return k.str();
+}
+
+void tune_file_load(const char *path)
+{
+    std::ifstream f(path);
+    std::string key;
+    drts_tune_result r{};
+    while (f >> key >> r.variant >> r.threads >> r.blocks_per_sm >> r.rhs_tile >> r.ms_per_step) {
+        r.candidates = 0;
+        r.from_cache = 1;
+        g_tune_cache[key] = r;
+    }
+}
+
+void tune_file_store(const char *path, const std::string &key, const drts_tune_result &r)
+{
+    std::ofstream f(path, std::ios::app);
+    f << key << ' ' << r.variant << ' ' << r.threads << ' ' << r.blocks_per_sm << ' ' << r.rhs_tile << ' '
+      << r.ms_per_step << '\n';
+}
+
+}  // namespace
+
+drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *out)
+{
+    if (!c) return DRTS_EINVAL;
+    if (trial_steps < 1 || trial_steps > 1000) return fail(c, DRTS_EINVAL, "trial_steps must be 1..1000");
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const std::string key = tune_key(c, sms);
+    const char *cache_path = std::getenv("DRTS_TUNE_CACHE");
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        if (cache_path && g_tune_cache.empty()) tune_file_load(cache_path);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            const drts_tune_result &r = it->second;
+            drts_status st = drts_set_launch(c, r.blocks_per_sm, r.threads, r.rhs_tile, r.variant);
+            if (st == DRTS_OK) {
+                if (out) {
+                    *out = r;
+                    out->from_cache = 1;
+                }
+                return DRTS_OK;
+            }
+        }
+    }
+    // time every candidate on the current state without advancing it: the
+    // step writes y from x (no swap), with no detector and a scratch ledger
+    double *scratch_ledger = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&scratch_ledger, sizeof(double) * 4 * c->R);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    drts_tune_result best{};
+    best.ms_per_step = 1e30;
+    int tried = 0;
+    for (int var = 0; var < kStepVariants && e == cudaSuccess; ++var)
+        for (int threads : {256, 128}) {
+            const int fit = step_default_blocks(c->A.precision, c->R, threads, var);
+            if (fit < 1) continue;
+            const int fit_per_sm = fit / sms;
+            for (int bps : {fit_per_sm, fit_per_sm / 2}) {
+                if (bps < 1 || (bps == fit_per_sm / 2 && bps == fit_per_sm)) continue;
+                StepArgs a = make_args(c);
+                a.det = nullptr;
+                a.ledger = scratch_ledger;
+                a.n_src = 0;
+                const int blocks = bps * sms;
+                e = launch_step(a, var, blocks, threads, c->stream);          // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+                for (int i = 0; i < trial_steps && e == cudaSuccess; ++i)
+                    e = launch_step(a, var, blocks, threads, c->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) break;
+                ++tried;
+                const double per = double(ms) / trial_steps;
+                if (per < best.ms_per_step) {
+                    best.ms_per_step = per;
+                    best.variant = var;
+                    best.threads = threads;
+                    best.blocks_per_sm = bps;
+                    best.rhs_tile = c->rhs_tile;
+                }
+            }
+        }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (scratch_ledger) cudaFree(scratch_ledger);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+    drts_status st = sync_check(c, "autotune");
+    if (st != DRTS_OK) return st;
+    if (tried == 0) return fail(c, DRTS_ECUDA, "autotune: no candidate fits");
+    best.candidates = tried;
+    best.from_cache = 0;
+    st = drts_set_launch(c, best.blocks_per_sm, best.threads, best.rhs_tile, best.variant);
+    if (st != DRTS_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+        if (cache_path) tune_file_store(cache_path, key, best);
+    }
+    if (out) *out = best;
+    return DRTS_OK;
+}
+
+drts_status drts_set_fault(drts_ctx *c, int32_t kind, int64_t arg)
+{
+    if (!c) return DRTS_EINVAL;
+    switch (kind) {
+    case DRTS_FAULT_NONE:
+        c->fault_skip_chunk = -1;
+        c->spin_limit = 1u << 22;
+        return DRTS_OK;
+    case DRTS_FAULT_SKIP_COPY:
+        if (arg < 0) return fail(c, DRTS_EINVAL, "chunk index must be >= 0");
+        if (c->variant < 3) return fail(c, DRTS_ESTATE, "the registers variants have no copies to skip");
+        c->fault_skip_chunk = arg;
+        return DRTS_OK;
+    case DRTS_FAULT_SPIN_LIMIT:
+        if (arg < 1 || arg > (int64_t(1) << 30)) return fail(c, DRTS_EINVAL, "spin limit must be 1..2^30");
+        c->spin_limit = uint32_t(arg);
+        return DRTS_OK;
+    default:
+        return fail(c, DRTS_EINVAL, "unknown fault kind");
+    }
 }
 
 drts_status drts_state_sum_noalloc(drts_ctx *c, int32_t rhs, double *out_device)

@@ -86,6 +86,9 @@ struct StepArgs {
     const double *prof_vals;
     const double *step_scale;  // [R] host-supplied source factors of this step, or null
     int rhs_tile;
+    int *err;                  // set to 1 when a bounded device wait gives up
+    uint32_t spin_limit;       // polls before a device wait gives up
+    int64_t fault_skip_chunk;  // tests only: chunk warp 0 never copies (-1 none)
 };
 
 // assembler (drts_assemble.cu)
@@ -100,8 +103,11 @@ cudaError_t launch_count_export(const SlicedMatrix &A, int64_t V, int64_t row_be
                                 int64_t row_end, int64_t *d_counts, cudaStream_t s);
 
 // step (drts_step.cu)
-cudaError_t launch_step(const StepArgs &a, int blocks, int threads, cudaStream_t s);
-int step_default_blocks(int precision, int R, int threads);
+// variant: 0-2 registers path (prefetch depth 1-3), 3-6 bulk-copy paths
+// (shared-memory stages of (G, S) = (8,3), (4,3), (4,4), (2,6))
+cudaError_t launch_step(const StepArgs &a, int variant, int blocks, int threads, cudaStream_t s);
+int step_default_blocks(int precision, int R, int threads, int variant);
+constexpr int kStepVariants = 7;
 cudaError_t launch_to_canonical(const void *x, int precision, int64_t V, int R, int r,
                                 double *out, cudaStream_t s);
 cudaError_t launch_from_canonical(const double *in, int precision, int64_t V, int R, int r,

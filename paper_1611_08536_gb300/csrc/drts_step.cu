@@ -37,6 +37,30 @@ __device__ __forceinline__ void load4(const __half *p, float v[4])
     const float2 fa = __half22float2(a), fb = __half22float2(b);
     v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
 }
+__device__ __forceinline__ void load4_smem(const float *p, float v[4])
+{
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void load4_smem(const double *p, double v[4])
+{
+    const double2 a = reinterpret_cast<const double2 *>(p)[0];
+    const double2 b = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void load4_smem(const __half *p, float v[4])
+{
+    const uint2 t = *reinterpret_cast<const uint2 *>(p);
+    const float2 fa = __half22float2(*reinterpret_cast<const __half2 *>(&t.x));
+    const float2 fb = __half22float2(*reinterpret_cast<const __half2 *>(&t.y));
+    v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
+}
+__device__ __forceinline__ void load_codes_smem(const uint16_t *p, int c[4])
+{
+    const uint2 t = *reinterpret_cast<const uint2 *>(p);
+    c[0] = int(t.x & 0xffffu); c[1] = int(t.x >> 16);
+    c[2] = int(t.y & 0xffffu); c[3] = int(t.y >> 16);
+}
 __device__ __forceinline__ void load_codes(const uint16_t *p, int c[4])
 {
     const uint2 t = __ldcs(reinterpret_cast<const uint2 *>(p));
@@ -52,107 +76,378 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// VT: stored value type; XT: state type; AT: accumulation type
-template <class VT, class XT, class AT>
-__global__ void __launch_bounds__(256) step_kernel(StepArgs a)
-{
-    __shared__ int32_t s_delta[kCodes];
-    __shared__ double s_ledger[2];
-    __shared__ SourceEntry s_src[kMaxSrc];
-    __shared__ double s_src_val[kMaxSrc];
+// Compensated accumulator: FP32 rows sum ~200 products, and plain FP32
+// accumulation drifts the solution by a few 1e-6 per 1000 steps.  Products are
+// summed pairwise inside a group of four and the group sums are added with
+// Kahan compensation.  FP64 rows accumulate plainly.
+template <class AT>
+struct Acc {
+    AT s = 0, c = 0;
+    __device__ __forceinline__ void add(AT v)
+    {
+        const AT y = v - c;
+        const AT t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ AT value() const { return s; }
+};
+template <>
+struct Acc<double> {
+    double s = 0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
 
-    const int64_t V = a.V;
+// Group data held in registers: four values (widened to AT) and four codes.
+template <class AT>
+struct Group {
+    AT w[4];
+    int c[4];
+};
+
+template <class VT, class AT>
+__device__ __forceinline__ void load_group(const VT *vals, const uint16_t *codes, int64_t idx, Group<AT> &g)
+{
+    load4(vals + idx, g.w);
+    load_codes(codes + idx, g.c);
+}
+
+// Dot product of one row with x, streaming the row's groups with D groups
+// prefetched ahead so that D matrix loads per lane are in flight while the
+// current group's x gathers run.
+template <class VT, class XT, class AT, int D>
+__device__ __forceinline__ AT row_dot(const VT *__restrict__ vals, const uint16_t *__restrict__ codes,
+                                      int64_t base, int len4, const XT *__restrict__ x, int64_t v,
+                                      const int32_t *s_delta)
+{
+    Group<AT> buf[D];
+#pragma unroll
+    for (int s = 0; s < D; ++s)
+        if (s < len4) load_group(vals, codes, base + int64_t(s) * (kSlice * kGroup), buf[s]);
+    Acc<AT> acc;
+    for (int g0 = 0; g0 < len4; g0 += D) {
+#pragma unroll
+        for (int s = 0; s < D; ++s) {
+            const int g = g0 + s;
+            if (g < len4) {
+                const Group<AT> cur = buf[s];
+                if (g + D < len4) load_group(vals, codes, base + int64_t(g + D) * (kSlice * kGroup), buf[s]);
+                const AT p0 = cur.w[0] * AT(__ldg(x + (v + s_delta[cur.c[0]])));
+                const AT p1 = cur.w[1] * AT(__ldg(x + (v + s_delta[cur.c[1]])));
+                const AT p2 = cur.w[2] * AT(__ldg(x + (v + s_delta[cur.c[2]])));
+                const AT p3 = cur.w[3] * AT(__ldg(x + (v + s_delta[cur.c[3]])));
+                acc.add((p0 + p1) + (p2 + p3));
+            }
+        }
+    }
+    return acc.value();
+}
+
+// Shared per-block data of a step: the code -> state-offset table, the
+// block's ledger partials and this step's source values.
+struct StepShared {
+    int32_t delta[kCodes];
+    double ledger[2];
+    SourceEntry src[kMaxSrc];
+    double src_val[kMaxSrc];
+};
+
+__device__ __forceinline__ void step_prologue(const StepArgs &a, StepShared &sh)
+{
     for (int c = threadIdx.x; c < kCodes; c += blockDim.x) {
         const int d = c / kDirs, n = c % kDirs;
-        s_delta[c] = int32_t(n * V + (int64_t(d / 9 - 1) * a.ny + (d / 3 % 3 - 1)) * a.nx + (d % 3 - 1));
+        sh.delta[c] = int32_t(n * a.V + (int64_t(d / 9 - 1) * a.ny + (d / 3 % 3 - 1)) * a.nx + (d % 3 - 1));
     }
-    if (threadIdx.x < 2) s_ledger[threadIdx.x] = 0.0;
+    if (threadIdx.x < 2) sh.ledger[threadIdx.x] = 0.0;
     for (int e = threadIdx.x; e < a.n_src; e += blockDim.x) {
-        s_src[e] = a.src[e];
+        sh.src[e] = a.src[e];
         const SourceProfile &p = a.prof[a.src[e].prof];
         double val = 0.0;
         if (a.step_scale) val = a.src[e].w * a.step_scale[a.src[e].rhs];
         else if (a.t >= p.t0 && a.t < p.t0 + p.n_t) val = a.src[e].w * a.prof_vals[p.off + (a.t - p.t0)];
-        s_src_val[e] = val;
+        sh.src_val[e] = val;
     }
     __syncthreads();
+}
 
+// Finish row (voxel v, direction m) of slice q: row scale, source term, store,
+// and the column functionals of x(t) for the same state (Eq. 27, ledger).
+template <class XT, class AT>
+__device__ __forceinline__ void row_epilogue(const StepArgs &a, const StepShared &sh, int64_t q, int lane,
+                                             int64_t v, int m, AT acc, AT &ab_lane, AT &ex_lane)
+{
+    if (a.A.row_scale) acc *= AT(a.A.row_scale[q * kSlice + lane]);
+    if (v >= a.V) return;
+    const XT *x = static_cast<const XT *>(a.x);
+    XT *y = static_cast<XT *>(a.y);
+    const int64_t row = int64_t(m) * a.V + v;
+    for (int e = 0; e < a.n_src; ++e)
+        if (sh.src[e].slice == q && sh.src[e].lane == lane) acc += AT(sh.src_val[e]);
+    y[row] = XT(acc);
+    const AT xs = AT(x[row]);
+    const int k = a.med[v];
+    ab_lane += AT(a.tab.absorb[k]) * xs;
+    const int nxy = a.nx * a.ny;
+    const int xx = int(v % a.nx), yy = int(v / a.nx % a.ny), zz = int(v / nxy);
+    const int bx = xx == 0 ? 0 : (xx == a.nx - 1 ? 2 : 1);
+    const int by = yy == 0 ? 0 : (yy == a.ny - 1 ? 2 : 1);
+    const int bz = zz == 0 ? 0 : (zz == a.nz - 1 ? 2 : 1);
+    const int mask = bz * 9 + by * 3 + bx;
+    if (mask == 13) return;
+    const int ti = (k * 27 + mask) * kDirs + m;
+    ex_lane += AT(a.tab.exit_total[ti]) * xs;
+    const double ed = a.tab.exit_det[ti];
+    if (ed > 0.0 && a.det) {
+        // patch coordinates (u, v) = the two other axes in x, y, z order
+        const int fa = a.det_face >> 1;
+        const int cu = fa == 0 ? yy : xx, nu = fa == 0 ? a.ny : a.nx;
+        const int cv = fa == 2 ? yy : zz, nv = fa == 2 ? a.ny : a.nz;
+        const int p = int(int64_t(cv) * a.det_nv / nv) * a.det_nu + int(int64_t(cu) * a.det_nu / nu);
+        atomicAdd(a.det + p, ed * double(xs));
+    }
+}
+
+template <class AT>
+__device__ __forceinline__ void step_finish(const StepArgs &a, StepShared &sh, AT ab_lane, AT ex_lane)
+{
+    const AT ab_w = warp_sum(ab_lane), ex_w = warp_sum(ex_lane);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&sh.ledger[0], double(ab_w));
+        atomicAdd(&sh.ledger[1], double(ex_w));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (sh.ledger[0] != 0.0) atomicAdd(&a.ledger[2], sh.ledger[0]);
+        if (sh.ledger[1] != 0.0) atomicAdd(&a.ledger[3], sh.ledger[1]);
+        if (blockIdx.x == 0) {          // injected mass, once per step
+            double inj = 0.0;
+            for (int e = 0; e < a.n_src; ++e) inj += sh.src_val[e];
+            if (inj != 0.0) atomicAdd(&a.ledger[1], inj);
+        }
+    }
+}
+
+// Variant 0: matrix streamed straight into registers (D groups prefetched).
+template <class VT, class XT, class AT, int D>
+__global__ void __launch_bounds__(256) step_kernel(StepArgs a)
+{
+    __shared__ StepShared sh;
+    step_prologue(a, sh);
     const XT *__restrict__ x = static_cast<const XT *>(a.x);
-    XT *__restrict__ y = static_cast<XT *>(a.y);
     const VT *__restrict__ vals = static_cast<const VT *>(a.A.vals);
     const uint16_t *__restrict__ codes = a.A.codes;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    const int nxy = a.nx * a.ny;
     AT ab_lane = 0, ex_lane = 0;
-
     for (int64_t q = warp0; q < a.A.n_slices; q += nwarps) {
         const int64_t b = q / kDirs;
         const int m = int(q - b * kDirs);
         const int64_t v = b * kSlice + lane;
         const int len4 = a.A.slice_len4[q];
         const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
-        AT acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
-#pragma unroll 4
-        for (int g = 0; g < len4; ++g) {
-            AT w[4];
-            int c[4];
-            const int64_t idx = base + int64_t(g) * (kSlice * kGroup);
-            load4(vals + idx, w);
-            load_codes(codes + idx, c);
-            acc0 += w[0] * AT(__ldg(x + (v + s_delta[c[0]])));
-            acc1 += w[1] * AT(__ldg(x + (v + s_delta[c[1]])));
-            acc2 += w[2] * AT(__ldg(x + (v + s_delta[c[2]])));
-            acc3 += w[3] * AT(__ldg(x + (v + s_delta[c[3]])));
-        }
-        AT acc = (acc0 + acc1) + (acc2 + acc3);
-        if (a.A.row_scale) acc *= AT(a.A.row_scale[q * kSlice + lane]);
-        if (v < V) {
-            const int64_t row = int64_t(m) * V + v;
-            for (int e = 0; e < a.n_src; ++e)
-                if (s_src[e].slice == q && s_src[e].lane == lane) acc += AT(s_src_val[e]);
-            y[row] = XT(acc);
-            // column functionals of x(t): absorbed, exited, detector (Eq. 27)
-            const AT xs = AT(x[row]);
-            const int k = a.med[v];
-            ab_lane += AT(a.tab.absorb[k]) * xs;
-            const int xx = int(v % a.nx), yy = int(v / a.nx % a.ny), zz = int(v / nxy);
-            const int bx = xx == 0 ? 0 : (xx == a.nx - 1 ? 2 : 1);
-            const int by = yy == 0 ? 0 : (yy == a.ny - 1 ? 2 : 1);
-            const int bz = zz == 0 ? 0 : (zz == a.nz - 1 ? 2 : 1);
-            const int mask = bz * 9 + by * 3 + bx;
-            if (mask != 13) {
-                const int ti = (k * 27 + mask) * kDirs + m;
-                ex_lane += AT(a.tab.exit_total[ti]) * xs;
-                const double ed = a.tab.exit_det[ti];
-                if (ed > 0.0 && a.det) {
-                    // patch coordinates (u, v) = the two other axes in x, y, z order
-                    const int fa = a.det_face >> 1;
-                    const int cu = fa == 0 ? yy : xx, nu = fa == 0 ? a.ny : a.nx;
-                    const int cv = fa == 2 ? yy : zz, nv = fa == 2 ? a.ny : a.nz;
-                    const int p = int(int64_t(cv) * a.det_nv / nv) * a.det_nu +
-                                  int(int64_t(cu) * a.det_nu / nu);
-                    atomicAdd(a.det + p, ed * double(xs));
-                }
-            }
-        }
+        const AT acc = row_dot<VT, XT, AT, D>(vals, codes, base, len4, x, v, sh.delta);
+        row_epilogue<XT, AT>(a, sh, q, lane, v, m, acc, ab_lane, ex_lane);
     }
-    const AT ab_w = warp_sum(ab_lane), ex_w = warp_sum(ex_lane);
+    step_finish(a, sh, ab_lane, ex_lane);
+}
+
+// ---------------------------------------------------------------------------
+// Variant 1: the matrix stream goes through shared memory by bulk async copy
+// (cp.async.bulk, completion on an mbarrier).  Each warp owns S stages of G
+// groups; lane 0 keeps S-1 chunks of its upcoming slices in flight while the
+// warp consumes the current one, so the HBM latency is covered by copies in
+// flight rather than by registers and resident warps.
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Bounded wait for phase `parity` of bar.  Gives up after kSpinLimit polls
+// (each poll may suspend the thread for a while inside try_wait).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <class VT, int G, int S>
+struct TmaStages {
+    static constexpr uint32_t kValBytes = G * kSlice * kGroup * sizeof(VT);
+    static constexpr uint32_t kCodeBytes = G * kSlice * kGroup * sizeof(uint16_t);
+    // per-warp region rounded to 128 B so every warp's stages stay 16-byte
+    // aligned for the bulk copies
+    static constexpr uint32_t kWarpBytes = (S * (kValBytes + kCodeBytes) + S * 8 + 127) / 128 * 128;
+};
+
+template <int G>
+__device__ __forceinline__ int chunks_of(int len4) { return (len4 + G - 1) / G; }
+
+template <class VT, class XT, class AT, int G, int S>
+__global__ void __launch_bounds__(256) step_kernel_tma(StepArgs a)
+{
+    using St = TmaStages<VT, G, S>;
+    __shared__ StepShared sh;
+    extern __shared__ __align__(128) unsigned char dyn[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    unsigned char *wbase = dyn + size_t(wib) * St::kWarpBytes;
+    VT *sval = reinterpret_cast<VT *>(wbase);
+    uint16_t *scode = reinterpret_cast<uint16_t *>(wbase + S * St::kValBytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(wbase + S * (St::kValBytes + St::kCodeBytes));
+    if ((smem_u32(dyn) & 127u) != 0) {   // stage alignment the bulk copies need
+        if (threadIdx.x == 0) atomicExch(a.err, 2);
+        return;
+    }
+    if (lane == 0)
+        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+    fence_proxy_async();
+    step_prologue(a, sh);        // includes __syncthreads
+
+    const XT *__restrict__ x = static_cast<const XT *>(a.x);
+    const VT *__restrict__ vals = static_cast<const VT *>(a.A.vals);
+    const uint16_t *__restrict__ codes = a.A.codes;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int64_t nsl = a.A.n_slices;
+
+    // Issue cursor (lane 0 only): next chunk (iq, ic) to copy.  The slice
+    // table entries of the slice after iq are loaded one slice early so the
+    // copy issue never waits on a global load.
+    int64_t iq = warp0, iptr = 0, nq = warp0, nptr = 0;
+    int ic = 0, ilen4 = 0, nlen4 = 0;
+    uint32_t issued = 0, consumed = 0;
+    auto load_next = [&]() {
+        if (nq < nsl) {
+            nlen4 = a.A.slice_len4[nq];
+            nptr = a.A.slice_ptr[nq];
+        }
+    };
+    auto take_next = [&]() {     // move the cursor to slice nq
+        iq = nq;
+        ilen4 = nlen4;
+        iptr = nptr;
+        ic = 0;
+        nq += nwarps;
+        load_next();
+    };
+    auto issue = [&]() {
+        // chunk (iq, ic) into stage issued % S
+        const int g0 = ic * G;
+        const int ng = ilen4 - g0 < G ? ilen4 - g0 : G;
+        const int s = issued % S;
+        const int64_t e0 = (iptr + g0) * (kSlice * kGroup);
+        const uint32_t vb = uint32_t(ng) * kSlice * kGroup * sizeof(VT);
+        const uint32_t cb = uint32_t(ng) * kSlice * kGroup * sizeof(uint16_t);
+        // fault injection (tests): warp 0 never issues chunk number
+        // fault_skip_chunk, so its wait on that stage must run out
+        if (!(warp0 == 0 && int64_t(issued) == a.fault_skip_chunk)) {
+            mbar_arrive_expect_tx(&bar[s], vb + cb);
+            bulk_copy_g2s(sval + size_t(s) * G * kSlice * kGroup, vals + e0, vb, &bar[s]);
+            bulk_copy_g2s(scode + size_t(s) * G * kSlice * kGroup, codes + e0, cb, &bar[s]);
+        }
+        ++issued;
+        if (++ic * G >= ilen4)
+            do take_next(); while (iq < nsl && ilen4 == 0);
+    };
     if (lane == 0) {
-        atomicAdd(&s_ledger[0], double(ab_w));
-        atomicAdd(&s_ledger[1], double(ex_w));
+        load_next();
+        do take_next(); while (iq < nsl && ilen4 == 0);
+        while (issued < uint32_t(S) && iq < nsl) issue();
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_ledger[0] != 0.0) atomicAdd(&a.ledger[2], s_ledger[0]);
-        if (s_ledger[1] != 0.0) atomicAdd(&a.ledger[3], s_ledger[1]);
-        if (blockIdx.x == 0) {          // injected mass, once per step
-            double inj = 0.0;
-            for (int e = 0; e < a.n_src; ++e) inj += s_src_val[e];
-            if (inj != 0.0) atomicAdd(&a.ledger[1], inj);
+    __syncwarp();
+
+    bool ok = true;
+    AT ab_lane = 0, ex_lane = 0;
+    int len4_next = warp0 < nsl ? a.A.slice_len4[warp0] : 0;
+    for (int64_t q = warp0; q < nsl && ok; q += nwarps) {
+        const int64_t b = q / kDirs;
+        const int m = int(q - b * kDirs);
+        const int64_t v = b * kSlice + lane;
+        const int len4 = len4_next;
+        if (q + nwarps < nsl) len4_next = a.A.slice_len4[q + nwarps];
+        const int nch = chunks_of<G>(len4);
+        Acc<AT> acc;
+        for (int c = 0; c < nch; ++c) {
+            const int s = consumed % S;
+            ok = __all_sync(0xffffffffu, mbar_wait(&bar[s], (consumed / S) & 1u, a.spin_limit));
+            if (!ok) break;
+            const int ng = len4 - c * G < G ? len4 - c * G : G;
+            const VT *sv = sval + size_t(s) * G * kSlice * kGroup + lane * kGroup;
+            const uint16_t *sc = scode + size_t(s) * G * kSlice * kGroup + lane * kGroup;
+#pragma unroll 4
+            for (int g = 0; g < ng; ++g) {
+                AT w[4];
+                int cc[4];
+                load4_smem(sv + g * (kSlice * kGroup), w);
+                load_codes_smem(sc + g * (kSlice * kGroup), cc);
+                const AT p0 = w[0] * AT(__ldg(x + (v + sh.delta[cc[0]])));
+                const AT p1 = w[1] * AT(__ldg(x + (v + sh.delta[cc[1]])));
+                const AT p2 = w[2] * AT(__ldg(x + (v + sh.delta[cc[2]])));
+                const AT p3 = w[3] * AT(__ldg(x + (v + sh.delta[cc[3]])));
+                acc.add((p0 + p1) + (p2 + p3));
+            }
+            __syncwarp();
+            ++consumed;
+            if (lane == 0 && iq < nsl) {
+                fence_proxy_async();     // stage s was read by the generic proxy
+                issue();
+            }
+            __syncwarp();
+        }
+        if (!ok) break;
+        row_epilogue<XT, AT>(a, sh, q, lane, v, m, acc.value(), ab_lane, ex_lane);
+    }
+    if (!ok) {
+        if (lane == 0) atomicExch(a.err, 1);
+        // let every copy still in flight land before the block exits
+        while (consumed < issued) {
+            mbar_wait(&bar[consumed % S], (consumed / S) & 1u, a.spin_limit);
+            ++consumed;
         }
     }
+    step_finish(a, sh, ab_lane, ex_lane);
 }
 
 template <class XT>
@@ -195,28 +490,113 @@ __global__ void sum_kernel(const XT *x, int64_t n, int R, int r, double *out)
 
 }  // namespace
 
-int step_default_blocks(int precision, int R, int threads)
+namespace {
+
+// Launchable step variants: 0 = registers (LDG) path, 1/2 = bulk-copy paths
+// with (G, S) = (8, 3) and (4, 4) stage shapes.
+template <class VT, class XT, class AT, int G, int S>
+struct TmaLaunch {
+    static size_t dyn(int threads) { return size_t(TmaStages<VT, G, S>::kWarpBytes) * (threads / 32); }
+    static cudaError_t prepare(int threads)
+    {
+        return cudaFuncSetAttribute(step_kernel_tma<VT, XT, AT, G, S>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn(threads)));
+    }
+    static int per_sm(int threads)
+    {
+        int n = 0;
+        if (prepare(threads) != cudaSuccess) {
+            cudaGetLastError();       // shape too large: clear the (non-sticky) error
+            return 0;
+        }
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_tma<VT, XT, AT, G, S>, threads,
+                                                          dyn(threads)) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return n;
+    }
+    static cudaError_t launch(const StepArgs &a, int blocks, int threads, cudaStream_t s)
+    {
+        cudaError_t e = prepare(threads);
+        if (e != cudaSuccess) return e;
+        step_kernel_tma<VT, XT, AT, G, S><<<blocks, threads, dyn(threads), s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
+template <class VT, class XT, class AT, int D>
+struct RegLaunch {
+    static int per_sm(int threads)
+    {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<VT, XT, AT, D>, threads, 0);
+        return n;
+    }
+    static cudaError_t launch(const StepArgs &a, int blocks, int threads, cudaStream_t s)
+    {
+        step_kernel<VT, XT, AT, D><<<blocks, threads, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
+// Variant table: 0-2 registers path with prefetch depth 1, 2, 3;
+// 3-6 bulk-copy path with stage shapes (G groups, S stages) = (8,3), (4,3),
+// (4,4), (2,6).
+template <class VT, class XT, class AT>
+struct Variants {
+    static int per_sm(int variant, int threads)
+    {
+        switch (variant) {
+        case 0: return RegLaunch<VT, XT, AT, 1>::per_sm(threads);
+        case 1: return RegLaunch<VT, XT, AT, 2>::per_sm(threads);
+        case 2: return RegLaunch<VT, XT, AT, 3>::per_sm(threads);
+        case 3: return TmaLaunch<VT, XT, AT, 8, 3>::per_sm(threads);
+        case 4: return TmaLaunch<VT, XT, AT, 4, 3>::per_sm(threads);
+        case 5: return TmaLaunch<VT, XT, AT, 4, 4>::per_sm(threads);
+        case 6: return TmaLaunch<VT, XT, AT, 2, 6>::per_sm(threads);
+        }
+        return 0;
+    }
+    static cudaError_t launch(int variant, const StepArgs &a, int blocks, int threads, cudaStream_t s)
+    {
+        switch (variant) {
+        case 0: return RegLaunch<VT, XT, AT, 1>::launch(a, blocks, threads, s);
+        case 1: return RegLaunch<VT, XT, AT, 2>::launch(a, blocks, threads, s);
+        case 2: return RegLaunch<VT, XT, AT, 3>::launch(a, blocks, threads, s);
+        case 3: return TmaLaunch<VT, XT, AT, 8, 3>::launch(a, blocks, threads, s);
+        case 4: return TmaLaunch<VT, XT, AT, 4, 3>::launch(a, blocks, threads, s);
+        case 5: return TmaLaunch<VT, XT, AT, 4, 4>::launch(a, blocks, threads, s);
+        case 6: return TmaLaunch<VT, XT, AT, 2, 6>::launch(a, blocks, threads, s);
+        }
+        return cudaErrorInvalidValue;
+    }
+};
+
+using VarF64 = Variants<double, double, double>;
+using VarF32 = Variants<float, float, float>;
+using VarF16 = Variants<__half, float, float>;
+
+}  // namespace
+
+int step_default_blocks(int precision, int R, int threads, int variant)
 {
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (precision == DRTS_FP64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<double, double, double>, threads, 0);
-    else if (precision == DRTS_FP32)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<float, float, float>, threads, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, step_kernel<__half, float, float>, threads, 0);
     (void)R;
-    if (per_sm < 1) per_sm = 1;
-    return sms * per_sm;
+    int per_sm = precision == DRTS_FP64 ? VarF64::per_sm(variant, threads)
+               : precision == DRTS_FP32 ? VarF32::per_sm(variant, threads)
+                                        : VarF16::per_sm(variant, threads);
+    return per_sm < 1 ? 0 : sms * per_sm;
 }
 
-cudaError_t launch_step(const StepArgs &a, int blocks, int threads, cudaStream_t s)
+cudaError_t launch_step(const StepArgs &a, int variant, int blocks, int threads, cudaStream_t s)
 {
-    if (a.A.precision == DRTS_FP64) step_kernel<double, double, double><<<blocks, threads, 0, s>>>(a);
-    else if (a.A.precision == DRTS_FP32) step_kernel<float, float, float><<<blocks, threads, 0, s>>>(a);
-    else step_kernel<__half, float, float><<<blocks, threads, 0, s>>>(a);
-    return cudaGetLastError();
+    if (blocks < 1) return cudaErrorInvalidConfiguration;
+    if (a.A.precision == DRTS_FP64) return VarF64::launch(variant, a, blocks, threads, s);
+    if (a.A.precision == DRTS_FP32) return VarF32::launch(variant, a, blocks, threads, s);
+    return VarF16::launch(variant, a, blocks, threads, s);
 }
 
 cudaError_t launch_to_canonical(const void *x, int precision, int64_t V, int R, int r,

@@ -1,8 +1,10 @@
 // Host-side FP64 tables of the DRTS system matrix (Section 3 and 4.2 of
 // arXiv:1611.08536).  Everything here runs once per problem; the per-row work
 // of assembling A happens in the device assembler (drts_assemble.cu).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <numeric>
 
 #include "drts_internal.h"
 
@@ -82,6 +84,41 @@ void segment_weights(const double a[3], const double b[3], double wout[kOffs])
     for (int o = 0; o < kOffs; ++o) wout[o] /= sum;
 }
 
+// Error-diffused rounding of one medium's stencil to FP32.  Each source
+// direction n owns a column of A (its ~210 targets (o, m)); plain rounding
+// to nearest leaves every column sum off by a small amount that is the same
+// for all interior columns of that direction, so the total mass drifts by
+// about 1e-8 per step.  Rounding the entries largest first, each to the
+// neighbouring float that keeps the running sum of rounding errors nearest
+// zero, makes the FP32 column sum match the FP64 one to the last entry's
+// rounding.  Every entry is one of the two floats bracketing its FP64 value.
+void diffuse_round_fp32(const double *W, double *out)
+{
+    std::vector<int> idx;
+    for (int n = 0; n < kDirs; ++n) {
+        idx.clear();
+        for (int o = 0; o < kOffs; ++o)
+            for (int m = 0; m < kDirs; ++m)
+                if (W[(n * kOffs + o) * kDirs + m] > 0.0) idx.push_back(o * kDirs + m);
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+            return W[n * kOffs * kDirs + a] > W[n * kOffs * kDirs + b];
+        });
+        double resid = 0.0;
+        for (int e : idx) {
+            const double v = W[n * kOffs * kDirs + e];
+            // the two floats bracketing v (equal when v is a float)
+            const float f = float(v);
+            float lo = f, hi = f;
+            if (double(f) > v) lo = std::nextafter(f, 0.0f);
+            else if (double(f) < v) hi = std::nextafter(f, 2.0f);
+            const double a = double(lo), b = double(hi);
+            const double pick = std::fabs(resid + a - v) <= std::fabs(resid + b - v) ? a : b;
+            out[n * kOffs * kDirs + e] = pick;
+            resid += pick - v;
+        }
+    }
+}
+
 }  // namespace
 
 std::string build_host_tables(const drts_problem &p, HostTables &t)
@@ -136,13 +173,23 @@ std::string build_host_tables(const drts_problem &p, HostTables &t)
         }
     }
 
+    // stencil values as stored by the plain rows: FP64 as computed, FP32 with
+    // column-preserving rounding, FP16 tier from the FP64 values (the device
+    // scales and rounds them per row)
+    std::vector<double> Wstore(t.W);
+    if (p.precision == DRTS_FP32)
+        for (int k = 0; k < K; ++k) {
+            const size_t off = size_t(k) * kDirs * kOffs * kDirs;
+            diffuse_round_fp32(&t.W[off], &Wstore[off]);
+        }
+
     // plain-row templates (row direction m, column offset d = source - row)
     t.tmpl_off.assign(size_t(K) * kDirs * (kOffs + 1), 0);
     t.tmpl_n.clear();
     t.tmpl_val.clear();
     t.n_template_entries_max = 0;
     for (int k = 0; k < K; ++k) {
-        const double *Wk = &t.W[size_t(k) * kDirs * kOffs * kDirs];
+        const double *Wk = &Wstore[size_t(k) * kDirs * kOffs * kDirs];
         for (int m = 0; m < kDirs; ++m) {
             int32_t *off = &t.tmpl_off[(size_t(k) * kDirs + m) * (kOffs + 1)];
             int row_entries = 0;

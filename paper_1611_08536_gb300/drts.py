@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, EUNSUPPORTED = range(7)
 OPEN, MIRROR, FRESNEL = 0, 1, 2
 FP64, FP32, FP16_ROWSCALE = 0, 1, 2
 FACE_NONE = -1
+FAULT_NONE, FAULT_SKIP_COPY, FAULT_SPIN_LIMIT = 0, 1, 2
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE",
            6: "EUNSUPPORTED"}
 
@@ -53,6 +54,16 @@ class ProblemC(ctypes.Structure):
     ]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int32), ("threads", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("rhs_tile", ctypes.c_int32),
+                ("ms_per_step", ctypes.c_double), ("candidates", ctypes.c_int32),
+                ("from_cache", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
 class Info(ctypes.Structure):
     _fields_ = [
         ("n_states", ctypes.c_int64), ("nnz", ctypes.c_int64),
@@ -67,7 +78,7 @@ class Info(ctypes.Structure):
 SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_detectors",
            "drts_read_state", "drts_write_state", "drts_run_host", "drts_export_rows",
            "drts_column_info", "drts_get_info", "drts_set_launch", "drts_destroy",
-           "drts_last_error", "drts_state_sum_noalloc"]
+           "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_autotune"]
 
 _lib = None
 
@@ -92,8 +103,10 @@ def load(path: str = LIB_PATH):
     lib.drts_export_rows.argtypes = [vp, i64, i64, vp, vp, vp, i64]
     lib.drts_column_info.argtypes = [vp, vp, vp, vp]
     lib.drts_get_info.argtypes = [vp, ctypes.POINTER(Info)]
-    lib.drts_set_launch.argtypes = [vp, i32, i32, i32]
+    lib.drts_set_launch.argtypes = [vp, i32, i32, i32, i32]
     lib.drts_state_sum_noalloc.argtypes = [vp, i32, vp]
+    lib.drts_set_fault.argtypes = [vp, i32, i64]
+    lib.drts_autotune.argtypes = [vp, i32, ctypes.POINTER(TuneResult)]
     lib.drts_destroy.argtypes = [vp]
     lib.drts_destroy.restype = None
     lib.drts_last_error.argtypes = [vp]
@@ -223,14 +236,24 @@ class Context:
         self._check(self._lib.drts_state_sum_noalloc(self._h, int(rhs),
                                                      ctypes.c_void_p(int(out_device_ptr))))
 
+    def autotune(self, trial_steps=3):
+        """Time the launch candidates on the device and keep the fastest."""
+        r = TuneResult()
+        self._check(self._lib.drts_autotune(self._h, int(trial_steps), ctypes.byref(r)))
+        return r.as_dict()
+
+    def set_fault(self, kind, arg=0):
+        """Host-side fault injection (FAULT_NONE / FAULT_SKIP_COPY / FAULT_SPIN_LIMIT)."""
+        self._check(self._lib.drts_set_fault(self._h, int(kind), int(arg)))
+
     def info(self):
         i = Info()
         self._check(self._lib.drts_get_info(self._h, ctypes.byref(i)))
         return i
 
-    def set_launch(self, blocks_per_sm=0, threads=0, rhs_tile=0):
+    def set_launch(self, blocks_per_sm=0, threads=0, rhs_tile=0, variant=-1):
         self._check(self._lib.drts_set_launch(self._h, int(blocks_per_sm), int(threads),
-                                              int(rhs_tile)))
+                                              int(rhs_tile), int(variant)))
 
 
 def assemble(prob, max_steps=0, stream=None) -> Context:
