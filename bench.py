@@ -34,9 +34,12 @@ KERNEL_SRC = os.path.join(ROOT, "paper_1611_08536_gb300", "csrc", "drts_step.cu"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 
 
-def workload(name, precision):
+def workload(name, precision, rhs=1):
     from paper_1611_08536_gb300 import inputs as I
     prec = {"fp32": I.FP32, "fp64": I.FP64, "fp16": I.FP16_ROWSCALE}[precision]
+    if name.startswith("inclusions_"):
+        n = int(name.split("_")[-1])
+        return I.inclusions(n, n_rhs=rhs, precision=prec)
     if name.startswith("three_layers_"):
         n = int(name.split("_")[-1])
         return I.three_layers(n, precision=prec)
@@ -292,6 +295,78 @@ def cpu_baseline(prob, args, seconds=12.0):
                       f"({c.nnz} nnz) of the same workload, {reps} repetitions"}
 
 
+FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+
+
+def run_batched(args):
+    """Batched step: one pass over A serves R right-hand sides.  Reports
+    nonzero-RHS products per second, simulations per second for a run of
+    --sim-steps steps, and the plain single-RHS step of the same problem
+    timed on the same GPU."""
+    import numpy as np
+    import torch
+    from paper_1611_08536_gb300 import build, drts
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    prob, srcs = workload(args.workload, args.precision, args.rhs)
+    ctx = drts.Context(prob, max_steps=args.warmup + args.steps + 1, stream=stream.cuda_stream)
+    for r, sr in enumerate(srcs):
+        ctx.set_source(r, sr)
+    tune = ctx.autotune(args.autotune) if args.autotune else None
+    info = ctx.info()
+    ctx.step_n(args.warmup)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ctx.step_n(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ctx.close()
+    # the plain per-simulation step of the same problem
+    import copy
+    p1 = copy.copy(prob)
+    p1.n_rhs = 1
+    c1 = drts.Context(p1, max_steps=args.warmup + args.steps, stream=stream.cuda_stream)
+    c1.set_source(0, srcs[0])
+    if args.autotune:
+        c1.autotune(args.autotune)
+    c1.step_n(args.warmup)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    c1.step_n(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = ev0.elapsed_time(ev1) / args.steps
+    c1.close()
+    R = args.rhs
+    flops = 2.0 * info.nnz * R * 2        # products + compensated accumulation
+    line = {
+        "metric": "DRTS batched step, nonzero x right-hand-side products per second",
+        "value": round(info.nnz * R / (ms * 1e-3) / 1e9, 2), "unit": "G nnz-rhs/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f16-matrix/f32-state"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "rhs": R, "grid": list(prob.shape), "nnz": int(info.nnz),
+                   "precision": args.precision, "launch": tune,
+                   "sims_per_s": round(R / (args.sim_steps * ms * 1e-3), 4),
+                   "plain_single_rhs_ms_per_step": round(ms1, 4),
+                   "plain_sims_per_s": round(1.0 / (args.sim_steps * ms1 * 1e-3), 4),
+                   "speedup_vs_plain_per_simulation": round(R * ms1 / ms, 2),
+                   "sim_steps": args.sim_steps},
+        "roofline": {"bound": "alu", "achieved": round(flops / (ms * 1e-3) / 1e12, 2),
+                     "peak": round(FP32_FMA_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                     "frac": round(flops / (ms * 1e-3) / 1e12 / FP32_FMA_PEAK_TFLOPS, 4),
+                     "traffic": None, "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+        "gpu_launches": None, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     import numpy as np
     ws, rank, _ = dist_env()
@@ -338,6 +413,8 @@ def main():
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--variant", type=int, default=-1)
     ap.add_argument("--autotune", type=int, default=2, help="timed steps per candidate (0 = off)")
+    ap.add_argument("--rhs", type=int, default=1, help="right-hand sides (batched step when > 1)")
+    ap.add_argument("--sim-steps", type=int, default=1500, help="steps per simulation for sims/s")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-check", dest="check", action="store_false")
     args = ap.parse_args()
@@ -345,6 +422,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.rhs > 1:
+        run_batched(args)
     else:
         run_gpu(args)
 

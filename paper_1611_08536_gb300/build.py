@@ -24,6 +24,7 @@ SOURCES = {
     "drts_step.cu": [],
     "drts_api.cu": [],
     "drts_noalloc.cu": [],
+    "drts_batched.cu": [],
 }
 
 

@@ -2,6 +2,7 @@
 // assembly, sources, stepping, readout.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -23,6 +24,7 @@ struct drts_ctx {
     cudaStream_t stream = nullptr;
     int64_t V = 0, n_states = 0;
     int K = 0, R = 1, n_patch = 0;
+    int64_t rhs_stride = 0;              // elements between right-hand sides of a state buffer
     int64_t t = 0;
     std::string err;
     HostTables host;
@@ -111,7 +113,6 @@ drts_status validate(const drts_problem *p)
     if (p->boundary == DRTS_FRESNEL && !(p->n_outside > 0.0)) return fail(nullptr, DRTS_EINVAL, "n_outside must be > 0");
     if (p->precision < DRTS_FP64 || p->precision > DRTS_FP16_ROWSCALE) return fail(nullptr, DRTS_EINVAL, "bad precision");
     if (p->n_rhs < 1 || p->n_rhs > kMaxRhs) return fail(nullptr, DRTS_EINVAL, "n_rhs must be 1..64");
-    if (p->n_rhs > 1) return fail(nullptr, DRTS_EUNSUPPORTED, "n_rhs > 1 is not built yet");
     if (p->det_face != DRTS_FACE_NONE) {
         if (p->det_face < 0 || p->det_face > 5) return fail(nullptr, DRTS_EINVAL, "bad det_face");
         const int N[3] = {p->nx, p->ny, p->nz};
@@ -147,6 +148,11 @@ drts_status upload_sources(drts_ctx *c)
         c->prof[r].off = int32_t(vals.size());
         vals.insert(vals.end(), c->prof_vals[r].begin(), c->prof_vals[r].end());
     }
+    std::sort(c->src.begin(), c->src.end(), [](const SourceEntry &a, const SourceEntry &b) {
+        if (a.slice != b.slice) return a.slice < b.slice;
+        if (a.lane != b.lane) return a.lane < b.lane;
+        return a.rhs < b.rhs;
+    });
     cudaError_t e = cudaSuccess;
     if (int64_t(vals.size()) > c->prof_cap) {
         int64_t cap = int64_t(vals.size()) * 2 + 16;
@@ -166,6 +172,12 @@ drts_status upload_sources(drts_ctx *c)
     return sync_check(c, "source upload");
 }
 
+// base of right-hand side r inside a state buffer
+void *rhs_ptr(drts_ctx *c, void *buf, int r)
+{
+    return static_cast<char *>(buf) + size_t(r) * c->rhs_stride * state_elem_bytes(c->prob.precision);
+}
+
 StepArgs make_args(drts_ctx *c)
 {
     StepArgs a{};
@@ -173,6 +185,7 @@ StepArgs make_args(drts_ctx *c)
     a.nx = c->prob.nx; a.ny = c->prob.ny; a.nz = c->prob.nz;
     a.V = c->V;
     a.R = c->R;
+    a.rhs_stride = c->rhs_stride;
     a.x = c->x; a.y = c->y;
     a.med = c->T.med;
     a.tab.absorb = c->d_absorb;
@@ -197,6 +210,21 @@ StepArgs make_args(drts_ctx *c)
     return a;
 }
 
+cudaError_t launch_any_step(drts_ctx *c, const StepArgs &a)
+{
+    if (c->R == 1) return launch_step(a, c->variant, c->blocks, c->threads, c->stream);
+    return launch_batched_step(a, c->R, c->rhs_tile, c->blocks, c->threads, true, c->stream);
+}
+
+int fit_blocks(drts_ctx *c, int threads, int variant, int rhs_tile)
+{
+    if (c->R == 1) return step_default_blocks(c->A.precision, c->R, threads, variant);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * batched_blocks_per_sm(c->A.precision, rhs_tile, threads);
+}
+
 }  // namespace
 
 extern "C" {
@@ -217,6 +245,7 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     c->n_states = c->V * kDirs;
     c->K = prob->n_media;
     c->R = prob->n_rhs;
+    c->rhs_stride = c->n_states + 64;     // the tail keeps padding lanes in bounds
     if (prob->det_face != DRTS_FACE_NONE) c->n_patch = prob->det_nu * prob->det_nv;
 
     auto bail = [&](drts_status s) {
@@ -272,11 +301,13 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
         return bail(DRTS_ENOMEM);
     }
     if (prob->precision == DRTS_FP16_ROWSCALE) {
-        if ((e = cudaMallocAsync(&row_max, sizeof(float) * A.n_slices * kSlice, c->stream)) != cudaSuccess ||
+        float *dscale = nullptr;
+        if ((e = upload(c, &dscale, H.dir_scale)) != cudaSuccess ||
             (e = dalloc(c, &A.row_scale, sizeof(float) * A.n_slices * kSlice)) != cudaSuccess) {
             cuda_fail(c, e, "row scale allocation");
             return bail(DRTS_ENOMEM);
         }
+        T.dir_scale = dscale;
     }
     if ((e = launch_classify(T, dplain, c->stream)) != cudaSuccess ||
         (e = launch_count(T, A, row_max, c->stream)) != cudaSuccess ||
@@ -297,11 +328,10 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
         cuda_fail(c, e, ("matrix allocation (" + std::to_string(slots) + " slots)").c_str());
         return bail(DRTS_ENOMEM);
     }
-    if ((e = launch_fill(T, A, row_max, c->stream)) != cudaSuccess) {
+    if ((e = launch_fill(T, A, c->stream)) != cudaSuccess) {
         cuda_fail(c, e, "assembly fill");
         return bail(DRTS_ECUDA);
     }
-    if (row_max) cudaFreeAsync(row_max, c->stream);
     // nnz and special-voxel share (host reductions of small device arrays)
     {
         std::vector<int32_t> rl(size_t(A.n_slices) * kSlice);
@@ -319,7 +349,7 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
         c->special_permille = int(special * 1000 / c->V);
     }
     // state, ledger, detector history, sources
-    c->x_elems = (c->n_states + 64) * c->R;
+    c->x_elems = c->rhs_stride * c->R;
     const size_t sb = size_t(c->x_elems) * state_elem_bytes(prob->precision);
     if ((e = dalloc(c, &c->x, sb)) != cudaSuccess || (e = dalloc(c, &c->y, sb)) != cudaSuccess ||
         (e = dalloc(c, &c->ledger, sizeof(double) * 4 * c->R)) != cudaSuccess ||
@@ -346,7 +376,8 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     if (st != DRTS_OK) return bail(st);
     c->threads = 256;
     c->variant = 0;
-    c->blocks = step_default_blocks(prob->precision, c->R, c->threads, c->variant);
+    c->rhs_tile = c->R > 1 ? std::min(16, c->R <= 4 ? 4 : (c->R <= 8 ? 8 : 16)) : 0;
+    c->blocks = fit_blocks(c, c->threads, c->variant, c->rhs_tile);
     if (c->blocks < 1) {
         fail(c, DRTS_ECUDA, "step kernel does not fit on an SM");
         return bail(DRTS_ECUDA);
@@ -397,7 +428,7 @@ drts_status drts_step_n(drts_ctx *c, int64_t n_steps)
         return fail(c, DRTS_EINVAL, "t + n_steps exceeds max_steps");
     for (int64_t i = 0; i < n_steps; ++i) {
         StepArgs a = make_args(c);
-        cudaError_t e = launch_step(a, c->variant, c->blocks, c->threads, c->stream);
+        cudaError_t e = launch_any_step(c, a);
         if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
         std::swap(c->x, c->y);
         ++c->t;
@@ -421,7 +452,7 @@ drts_status drts_run_host(drts_ctx *c, int64_t n_steps, const double *scale, dou
         if (e != cudaSuccess) break;
         StepArgs a = make_args(c);
         a.step_scale = d_scale + i * c->R;
-        e = launch_step(a, c->variant, c->blocks, c->threads, c->stream);
+        e = launch_any_step(c, a);
         if (e != cudaSuccess) break;
         // this step's detector readout, device -> host
         if (det_out && a.det && c->n_patch > 0)
@@ -453,7 +484,7 @@ drts_status drts_read_detectors(drts_ctx *c, int32_t rhs, int64_t t_begin, int64
         double *tmp = nullptr;
         e = cudaMallocAsync(&tmp, sizeof(double), c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(tmp, 0, sizeof(double), c->stream);
-        if (e == cudaSuccess) e = launch_ledger_sum(c->x, c->prob.precision, c->n_states, c->R, rhs, tmp, c->stream);
+        if (e == cudaSuccess) e = launch_ledger_sum(rhs_ptr(c, c->x, rhs), c->prob.precision, c->n_states, 1, 0, tmp, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ledger_out, tmp, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ledger_out + 1, c->ledger + 4 * rhs + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -469,7 +500,7 @@ drts_status drts_read_state(drts_ctx *c, int32_t rhs, double *host_out)
     if (rhs < 0 || rhs >= c->R || !host_out) return fail(c, DRTS_EINVAL, "bad arguments");
     double *tmp = nullptr;
     cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * c->n_states, c->stream);
-    if (e == cudaSuccess) e = launch_to_canonical(c->x, c->prob.precision, c->V, c->R, rhs, tmp, c->stream);
+    if (e == cudaSuccess) e = launch_to_canonical(rhs_ptr(c, c->x, rhs), c->prob.precision, c->V, 1, 0, tmp, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host_out, tmp, sizeof(double) * c->n_states, cudaMemcpyDeviceToHost, c->stream);
     if (tmp) cudaFreeAsync(tmp, c->stream);
@@ -485,7 +516,7 @@ drts_status drts_write_state(drts_ctx *c, int32_t rhs, const double *host_in)
     cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * c->n_states, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tmp, host_in, sizeof(double) * c->n_states, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = launch_from_canonical(tmp, c->prob.precision, c->V, c->R, rhs, c->x, c->stream);
+    if (e == cudaSuccess) e = launch_from_canonical(tmp, c->prob.precision, c->V, 1, 0, rhs_ptr(c, c->x, rhs), c->stream);
     if (tmp) cudaFreeAsync(tmp, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "write_state");
     return sync_check(c, "write_state");
@@ -586,9 +617,15 @@ drts_status drts_set_launch(drts_ctx *c, int32_t blocks_per_sm, int32_t threads_
         return fail(c, DRTS_EINVAL, "threads_per_block must be a multiple of 32 in 32..256");
     if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(c, DRTS_EINVAL, "blocks_per_sm must be 0..64");
     if (variant < -1 || variant >= kStepVariants) return fail(c, DRTS_EINVAL, "unknown step variant");
+    int tile = c->rhs_tile;
+    if (c->R > 1 && rhs_tile != 0) {
+        if (rhs_tile != 4 && rhs_tile != 8 && rhs_tile != 16 && rhs_tile != 32)
+            return fail(c, DRTS_EINVAL, "rhs_tile must be 4, 8, 16 or 32");
+        tile = rhs_tile;
+    }
     const int threads = threads_per_block ? threads_per_block : 256;
     const int var = variant < 0 ? c->variant : variant;
-    const int fit = step_default_blocks(c->A.precision, c->R, threads, var);
+    const int fit = fit_blocks(c, threads, var, tile);
     if (fit < 1) return fail(c, DRTS_EINVAL, "launch shape does not fit on an SM");
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -597,8 +634,8 @@ drts_status drts_set_launch(drts_ctx *c, int32_t blocks_per_sm, int32_t threads_
         return fail(c, DRTS_EINVAL, "more blocks per SM than fit (" + std::to_string(fit / sms) + ")");
     c->threads = threads;
     c->variant = var;
+    c->rhs_tile = tile;
     c->blocks = blocks_per_sm ? sms * blocks_per_sm : fit;
-    c->rhs_tile = rhs_tile;
     return DRTS_OK;
 }
 
@@ -672,9 +709,13 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
     drts_tune_result best{};
     best.ms_per_step = 1e30;
     int tried = 0;
-    for (int var = 0; var < kStepVariants && e == cudaSuccess; ++var)
+    const int n_var = c->R == 1 ? kStepVariants : 1;
+    for (int var = 0; var < n_var && e == cudaSuccess; ++var)
+        for (int tile : {4, 8, 16, 32})
         for (int threads : {256, 128}) {
-            const int fit = step_default_blocks(c->A.precision, c->R, threads, var);
+            if (c->R == 1 && tile != 4) continue;             // tile only matters when batched
+            if (c->R > 1 && tile > 4 && tile / 2 >= c->R) continue;   // tile far wider than R
+            const int fit = fit_blocks(c, threads, var, tile);
             if (fit < 1) continue;
             const int fit_per_sm = fit / sms;
             for (int bps : {fit_per_sm, fit_per_sm / 2}) {
@@ -684,10 +725,13 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
                 a.ledger = scratch_ledger;
                 a.n_src = 0;
                 const int blocks = bps * sms;
-                e = launch_step(a, var, blocks, threads, c->stream);          // warm-up
+                auto run = [&]() {
+                    return c->R == 1 ? launch_step(a, var, blocks, threads, c->stream)
+                                     : launch_batched_step(a, c->R, tile, blocks, threads, false, c->stream);
+                };
+                e = run();          // warm-up
                 if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-                for (int i = 0; i < trial_steps && e == cudaSuccess; ++i)
-                    e = launch_step(a, var, blocks, threads, c->stream);
+                for (int i = 0; i < trial_steps && e == cudaSuccess; ++i) e = run();
                 if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.0f;
@@ -700,7 +744,7 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
                     best.variant = var;
                     best.threads = threads;
                     best.blocks_per_sm = bps;
-                    best.rhs_tile = c->rhs_tile;
+                    best.rhs_tile = c->R > 1 ? tile : 0;
                 }
             }
         }
@@ -754,7 +798,7 @@ drts_status drts_state_sum_noalloc(drts_ctx *c, int32_t rhs, double *out_device)
         return fail(c, DRTS_EINVAL, "state vector of " + std::to_string(c->n_states) +
                                         " states exceeds the static scratch limit of " +
                                         std::to_string(noalloc_max_states()));
-    cudaError_t e = launch_state_sum_noalloc(c->x, c->prob.precision, c->n_states, c->R, rhs, out_device,
+    cudaError_t e = launch_state_sum_noalloc(rhs_ptr(c, c->x, rhs), c->prob.precision, c->n_states, 1, 0, out_device,
                                              c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "state_sum_noalloc");
     return DRTS_OK;

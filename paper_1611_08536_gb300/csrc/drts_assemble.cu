@@ -254,7 +254,7 @@ struct FillEmit {
 };
 
 template <class VT>
-__global__ void fill_kernel(DevTables T, SlicedMatrix A, const float *row_max)
+__global__ void fill_kernel(DevTables T, SlicedMatrix A)
 {
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t q = g / kSlice;
@@ -269,9 +269,8 @@ __global__ void fill_kernel(DevTables T, SlicedMatrix A, const float *row_max)
     fe.base = A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
     fe.scale = 1.0f;
     if (A.row_scale) {
-        const float s = row_max[g] > 0.0f ? row_max[g] : 1.0f;
-        fe.scale = s;
-        A.row_scale[g] = s;
+        fe.scale = T.dir_scale[m];
+        A.row_scale[g] = fe.scale;
     }
     if (v < T.V) {
         const int x = int(v % T.nx), y = int(v / T.nx % T.ny), z = int(v / (int64_t(T.nx) * T.ny));
@@ -416,14 +415,14 @@ cudaError_t launch_scan(SlicedMatrix &A, int64_t *d_total, cudaStream_t s)
     return e != cudaSuccess ? e : e2;
 }
 
-cudaError_t launch_fill(const DevTables &T, SlicedMatrix &A, const float *row_max, cudaStream_t s)
+cudaError_t launch_fill(const DevTables &T, SlicedMatrix &A, cudaStream_t s)
 {
     const int th = 128;
     const int64_t rows = A.n_slices * kSlice;
     const unsigned blocks = unsigned((rows + th - 1) / th);
-    if (A.precision == DRTS_FP64) fill_kernel<double><<<blocks, th, 0, s>>>(T, A, row_max);
-    else if (A.precision == DRTS_FP32) fill_kernel<float><<<blocks, th, 0, s>>>(T, A, row_max);
-    else fill_kernel<__half><<<blocks, th, 0, s>>>(T, A, row_max);
+    if (A.precision == DRTS_FP64) fill_kernel<double><<<blocks, th, 0, s>>>(T, A);
+    else if (A.precision == DRTS_FP32) fill_kernel<float><<<blocks, th, 0, s>>>(T, A);
+    else fill_kernel<__half><<<blocks, th, 0, s>>>(T, A);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,301 @@
+// Batched DRTS step X(t+1) = A X(t) + S(t) for R right-hand sides that
+// share one assembled A (the paper notes that only the source term changes
+// between such runs, Section 6).  One pass over A serves RT right-hand sides
+// at a time: every nonzero's value and code are loaded once and used for RT
+// multiply-adds against X[r0 .. r0+RT)[column].
+//
+// State layout: right-hand-side major, X[r*rhs_stride + n*V + v].  For one
+// code the 32 lanes of a slice (32 consecutive voxels) read 32 consecutive
+// floats of each right-hand side, so every gather is one coalesced 128-byte
+// request; a right-hand-side-minor layout would scatter each request over
+// 32 cache lines.
+//
+// Accumulation: the four products of a group are chained with FMA and the
+// group sum is added to a Kahan-compensated accumulator (plain FP32 sums of
+// ~200 positive terms drift the solution by ~1e-7 per step).
+//
+// The detector readout (Eq. 27) and the FP64 ledger of X(t) come from two
+// small kernels launched before the product: one block per detector patch
+// (a deterministic sum, no atomics) and a reduction per right-hand side.
+#include <cuda_runtime.h>
+
+#include "drts_device.cuh"
+#include "drts_kernel_common.cuh"
+
+namespace drts {
+namespace {
+
+// value of source entry e at this step
+__device__ __forceinline__ double source_value(const StepArgs &a, const SourceEntry &e)
+{
+    if (a.step_scale) return e.w * a.step_scale[e.rhs];
+    const SourceProfile &p = a.prof[e.prof];
+    if (a.t >= p.t0 && a.t < p.t0 + p.n_t) return e.w * a.prof_vals[p.off + (a.t - p.t0)];
+    return 0.0;
+}
+
+// first source entry whose slice is >= q (entries are sorted by slice)
+__device__ __forceinline__ int first_entry(const SourceEntry *src, int n, int64_t q)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (src[mid].slice < q) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <class AT>
+struct KahanAcc {
+    AT s = 0, c = 0;
+    __device__ __forceinline__ void add(AT v)
+    {
+        const AT y = v - c;
+        const AT t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+template <>
+struct KahanAcc<double> {
+    double s = 0, c = 0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+};
+
+template <class VT, class XT, class AT, int RT>
+__global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
+{
+    __shared__ int32_t s_delta[kCodes];
+    const int64_t V = a.V;
+    for (int c = threadIdx.x; c < kCodes; c += blockDim.x) {
+        const int d = c / kDirs, n = c % kDirs;
+        s_delta[c] = int32_t(n * V + (int64_t(d / 9 - 1) * a.ny + (d / 3 % 3 - 1)) * a.nx + (d % 3 - 1));
+    }
+    __syncthreads();
+    const int64_t S = a.rhs_stride;
+    const int nr = a.R - r0 < RT ? a.R - r0 : RT;   // right-hand sides in this tile
+    const XT *__restrict__ x = static_cast<const XT *>(a.x) + int64_t(r0) * S;
+    XT *__restrict__ y = static_cast<XT *>(a.y) + int64_t(r0) * S;
+    const VT *__restrict__ vals = static_cast<const VT *>(a.A.vals);
+    const uint16_t *__restrict__ codes = a.A.codes;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+
+    for (int64_t q = warp0; q < a.A.n_slices; q += nwarps) {
+        const int64_t b = q / kDirs;
+        const int m = int(q - b * kDirs);
+        const int64_t v = b * kSlice + lane;
+        const int len4 = a.A.slice_len4[q];
+        const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
+        KahanAcc<AT> acc[RT];
+        AT wn[4];
+        int cn[4];
+        if (len4 > 0) {
+            load4(vals + base, wn);
+            load_codes(codes + base, cn);
+        }
+        for (int g = 0; g < len4; ++g) {
+            AT w[4];
+            int c[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) { w[j] = wn[j]; c[j] = cn[j]; }
+            if (g + 1 < len4) {
+                const int64_t idx = base + int64_t(g + 1) * (kSlice * kGroup);
+                load4(vals + idx, wn);
+                load_codes(codes + idx, cn);
+            }
+            const int64_t o0 = v + s_delta[c[0]], o1 = v + s_delta[c[1]];
+            const int64_t o2 = v + s_delta[c[2]], o3 = v + s_delta[c[3]];
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                if (r < nr) {
+                    const XT *xr = x + r * S;
+                    AT p = w[0] * AT(__ldg(xr + o0));
+                    p = fma(w[1], AT(__ldg(xr + o1)), p);
+                    p = fma(w[2], AT(__ldg(xr + o2)), p);
+                    p = fma(w[3], AT(__ldg(xr + o3)), p);
+                    acc[r].add(p);
+                }
+            }
+        }
+        if (v >= V) continue;
+        const AT sc = a.A.row_scale ? AT(a.A.row_scale[q * kSlice + lane]) : AT(1);
+        AT out[RT];
+#pragma unroll
+        for (int r = 0; r < RT; ++r) out[r] = acc[r].s * sc;
+        if (a.n_src > 0) {
+            for (int e = first_entry(a.src, a.n_src, q); e < a.n_src && a.src[e].slice == q; ++e) {
+                const SourceEntry se = a.src[e];
+                if (se.lane != lane) continue;
+                const int rr = se.rhs - r0;
+                const AT val = AT(source_value(a, se));
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+                    if (r == rr) out[r] += val;
+            }
+        }
+        const int64_t row = int64_t(m) * V + v;
+#pragma unroll
+        for (int r = 0; r < RT; ++r)
+            if (r < nr) y[r * S + row] = XT(out[r]);
+    }
+}
+
+// Absorbed and exited mass of X(t) per right-hand side (FP64 ledger) and the
+// injected mass of this step.  blockIdx.y is the right-hand side.
+template <class XT>
+__global__ void __launch_bounds__(256) ledger_kernel(StepArgs a)
+{
+    __shared__ double red[2];
+    if (threadIdx.x < 2) red[threadIdx.x] = 0.0;
+    __syncthreads();
+    const int r = blockIdx.y;
+    const XT *x = static_cast<const XT *>(a.x) + int64_t(r) * a.rhs_stride;
+    const int64_t total = a.V * kDirs;
+    float ab = 0.0f, ex = 0.0f;
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const float xs = float(x[i]);
+        if (xs == 0.0f) continue;
+        const int d = int(i / a.V);
+        const int64_t v = i - int64_t(d) * a.V;
+        const int k = a.med[v];
+        ab += float(a.tab.absorb[k]) * xs;
+        const int xx = int(v % a.nx), yy = int(v / a.nx % a.ny), zz = int(v / (int64_t(a.nx) * a.ny));
+        const int mask = (zz == 0 ? 0 : (zz == a.nz - 1 ? 2 : 1)) * 9 +
+                         (yy == 0 ? 0 : (yy == a.ny - 1 ? 2 : 1)) * 3 + (xx == 0 ? 0 : (xx == a.nx - 1 ? 2 : 1));
+        if (mask != 13) ex += float(a.tab.exit_total[(k * 27 + mask) * kDirs + d]) * xs;
+    }
+    const float abw = warp_sum(ab), exw = warp_sum(ex);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&red[0], double(abw));
+        atomicAdd(&red[1], double(exw));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (red[0] != 0.0) atomicAdd(&a.ledger[4 * r + 2], red[0]);
+        if (red[1] != 0.0) atomicAdd(&a.ledger[4 * r + 3], red[1]);
+        if (blockIdx.x == 0)
+            for (int e = 0; e < a.n_src; ++e)
+                if (a.src[e].rhs == r) {
+                    const double val = source_value(a, a.src[e]);
+                    if (val != 0.0) atomicAdd(&a.ledger[4 * r + 1], val);
+                }
+    }
+}
+
+// Detector readout of X(t): one block per patch, one thread per right-hand
+// side; each thread sums its patch in a fixed order (no atomics).
+template <class XT>
+__global__ void det_kernel(StepArgs a)
+{
+    const int p = blockIdx.x;
+    const int r = threadIdx.x;
+    if (r >= a.R) return;
+    const int fa = a.det_face >> 1, high = a.det_face & 1;
+    const int N[3] = {a.nx, a.ny, a.nz};
+    const int ua = fa == 0 ? 1 : 0, va = fa == 2 ? 1 : 2;
+    const int pu = p % a.det_nu, pv = p / a.det_nu;
+    const int Nu = N[ua], Nv = N[va];
+    const int u0 = (pu * Nu + a.det_nu - 1) / a.det_nu, u1 = ((pu + 1) * Nu + a.det_nu - 1) / a.det_nu;
+    const int v0 = (pv * Nv + a.det_nv - 1) / a.det_nv, v1 = ((pv + 1) * Nv + a.det_nv - 1) / a.det_nv;
+    const XT *x = static_cast<const XT *>(a.x) + int64_t(r) * a.rhs_stride;
+    double sum = 0.0;
+    for (int cv = v0; cv < v1; ++cv)
+        for (int cu = u0; cu < u1; ++cu) {
+            int c[3];
+            c[fa] = high ? N[fa] - 1 : 0;
+            c[ua] = cu;
+            c[va] = cv;
+            const int64_t v = (int64_t(c[2]) * a.ny + c[1]) * a.nx + c[0];
+            const int k = a.med[v];
+            const int mask = (c[2] == 0 ? 0 : (c[2] == a.nz - 1 ? 2 : 1)) * 9 +
+                             (c[1] == 0 ? 0 : (c[1] == a.ny - 1 ? 2 : 1)) * 3 +
+                             (c[0] == 0 ? 0 : (c[0] == a.nx - 1 ? 2 : 1));
+            for (int d = 0; d < kDirs; ++d) {
+                const double ed = a.tab.exit_det[(k * 27 + mask) * kDirs + d];
+                if (ed > 0.0) sum += ed * double(x[int64_t(d) * a.V + v]);
+            }
+        }
+    a.det[r * a.det_stride_r + p] = sum;
+}
+
+template <class VT, class XT, class AT>
+struct SpmmLaunch {
+    template <int RT>
+    static int fit(int threads)
+    {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spmm_kernel<VT, XT, AT, RT>, threads, 0) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return n;
+    }
+    static int per_sm(int rt, int threads)
+    {
+        switch (rt) {
+        case 4: return fit<4>(threads);
+        case 8: return fit<8>(threads);
+        case 16: return fit<16>(threads);
+        case 32: return fit<32>(threads);
+        }
+        return 0;
+    }
+    static cudaError_t launch(int rt, const StepArgs &a, int r0, int blocks, int threads, cudaStream_t s)
+    {
+        switch (rt) {
+        case 4: spmm_kernel<VT, XT, AT, 4><<<blocks, threads, 0, s>>>(a, r0); break;
+        case 8: spmm_kernel<VT, XT, AT, 8><<<blocks, threads, 0, s>>>(a, r0); break;
+        case 16: spmm_kernel<VT, XT, AT, 16><<<blocks, threads, 0, s>>>(a, r0); break;
+        case 32: spmm_kernel<VT, XT, AT, 32><<<blocks, threads, 0, s>>>(a, r0); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
+};
+
+}  // namespace
+
+int batched_blocks_per_sm(int precision, int rhs_tile, int threads)
+{
+    if (precision == DRTS_FP64) return SpmmLaunch<double, double, double>::per_sm(rhs_tile, threads);
+    if (precision == DRTS_FP32) return SpmmLaunch<float, float, float>::per_sm(rhs_tile, threads);
+    return SpmmLaunch<__half, float, float>::per_sm(rhs_tile, threads);
+}
+
+cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int blocks, int threads,
+                                bool functionals, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    const bool f64 = a.A.precision == DRTS_FP64;
+    if (functionals) {
+        if (a.det && a.n_patch > 0) {
+            if (f64) det_kernel<double><<<a.n_patch, kMaxRhs, 0, s>>>(a);
+            else det_kernel<float><<<a.n_patch, kMaxRhs, 0, s>>>(a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const dim3 grid(unsigned((sms * 4 + n_rhs - 1) / n_rhs), unsigned(n_rhs));
+        if (f64) ledger_kernel<double><<<grid, 256, 0, s>>>(a);
+        else ledger_kernel<float><<<grid, 256, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    for (int r0 = 0; r0 < n_rhs; r0 += rhs_tile) {
+        if (a.A.precision == DRTS_FP64)
+            e = SpmmLaunch<double, double, double>::launch(rhs_tile, a, r0, blocks, threads, s);
+        else if (a.A.precision == DRTS_FP32)
+            e = SpmmLaunch<float, float, float>::launch(rhs_tile, a, r0, blocks, threads, s);
+        else
+            e = SpmmLaunch<__half, float, float>::launch(rhs_tile, a, r0, blocks, threads, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace drts

@@ -25,6 +25,7 @@ struct DevTables {
     const double *nref;         // [K]
     const uint8_t *med;         // [V] medium of each voxel
     const uint8_t *plain;       // [V] 1 when the voxel's rows need no folding
+    const float *dir_scale;     // [26] FP16 tier row scale by direction (or null)
 };
 
 // Sliced storage of A: slice q = voxel block b (32 voxels) * 26 + direction
@@ -71,7 +72,8 @@ struct StepArgs {
     int nx, ny, nz;
     int64_t V;
     int R;                     // right-hand sides
-    const void *x;             // state at t, layout [(n*V + v)*R + r]
+    int64_t rhs_stride;        // elements between right-hand sides of a state buffer
+    const void *x;             // state at t, layout [r*rhs_stride + n*V + v]
     void *y;                   // state at t+1
     const uint8_t *med;
     StepTables tab;
@@ -95,7 +97,7 @@ struct StepArgs {
 cudaError_t launch_classify(const DevTables &T, uint8_t *plain, cudaStream_t s);
 cudaError_t launch_count(const DevTables &T, SlicedMatrix &A, float *row_max, cudaStream_t s);
 cudaError_t launch_scan(SlicedMatrix &A, int64_t *d_total, cudaStream_t s);
-cudaError_t launch_fill(const DevTables &T, SlicedMatrix &A, const float *row_max, cudaStream_t s);
+cudaError_t launch_fill(const DevTables &T, SlicedMatrix &A, cudaStream_t s);
 cudaError_t launch_export(const SlicedMatrix &A, int nx, int ny, int nz, int64_t row_begin,
                           int64_t row_end, const int64_t *d_row_ptr, int32_t *d_col,
                           double *d_val, cudaStream_t s);
@@ -114,6 +116,12 @@ cudaError_t launch_from_canonical(const double *in, int precision, int64_t V, in
                                   void *x, cudaStream_t s);
 cudaError_t launch_ledger_sum(const void *x, int precision, int64_t n, int R, int r,
                               double *out, cudaStream_t s);
+
+// batched step (drts_batched.cu): functionals (detector + ledger of X(t))
+// when asked, then ceil(R / rhs_tile) passes of the product over A
+int batched_blocks_per_sm(int precision, int rhs_tile, int threads);
+cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int blocks, int threads,
+                                bool functionals, cudaStream_t s);
 
 // no-allocation state sum (drts_noalloc.cu)
 int64_t noalloc_max_states();

@@ -60,6 +60,7 @@ struct HostTables {
     // mask = bz*9+by*3+bx (b = 0 low face, 1 inside, 2 high face)
     std::vector<double> exit_total; // [k][27][26]
     std::vector<double> exit_det;   // [k][27][26]
+    std::vector<float> dir_scale;   // [26] FP16 tier: row scale of direction m (power of two)
     int n_template_entries_max = 0;
 };
 

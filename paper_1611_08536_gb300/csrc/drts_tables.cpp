@@ -6,6 +6,8 @@
 #include <cstring>
 #include <numeric>
 
+#include <cuda_fp16.h>
+
 #include "drts_internal.h"
 
 namespace drts {
@@ -119,6 +121,44 @@ void diffuse_round_fp32(const double *W, double *out)
     }
 }
 
+// Same column-preserving rounding onto the FP16 grid of each target
+// direction m: an entry (o, m) is stored as h * scale[m] with h an FP16
+// number, so its two candidates are the FP16 numbers bracketing v / scale[m].
+double half_bits_value(uint16_t b)
+{
+    __half_raw r;
+    r.x = b;
+    return double(__half2float(__half(r)));
+}
+
+void diffuse_round_fp16(const double *W, const float *scale, double *out)
+{
+    std::vector<int> idx;
+    for (int n = 0; n < kDirs; ++n) {
+        idx.clear();
+        for (int o = 0; o < kOffs; ++o)
+            for (int m = 0; m < kDirs; ++m)
+                if (W[(n * kOffs + o) * kDirs + m] > 0.0) idx.push_back(o * kDirs + m);
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+            return W[n * kOffs * kDirs + a] > W[n * kOffs * kDirs + b];
+        });
+        double resid = 0.0;
+        for (int e : idx) {
+            const double v = W[n * kOffs * kDirs + e];
+            const double sm = double(scale[e % kDirs]);
+            const double t = v / sm;
+            const __half_raw hr = __half_raw(__double2half(t));
+            uint16_t lo = hr.x, hi = hr.x;          // positive halves: bits are monotone
+            if (half_bits_value(hr.x) > t) lo = uint16_t(hr.x - 1);
+            else if (half_bits_value(hr.x) < t) hi = uint16_t(hr.x + 1);
+            const double a = half_bits_value(lo) * sm, b = half_bits_value(hi) * sm;
+            const double pick = std::fabs(resid + a - v) <= std::fabs(resid + b - v) ? a : b;
+            out[n * kOffs * kDirs + e] = pick;
+            resid += pick - v;
+        }
+    }
+}
+
 }  // namespace
 
 std::string build_host_tables(const drts_problem &p, HostTables &t)
@@ -173,15 +213,33 @@ std::string build_host_tables(const drts_problem &p, HostTables &t)
         }
     }
 
-    // stencil values as stored by the plain rows: FP64 as computed, FP32 with
-    // column-preserving rounding, FP16 tier from the FP64 values (the device
-    // scales and rounds them per row)
+    // stencil values as stored by the plain rows: FP64 as computed, FP32 and
+    // FP16 with column-preserving rounding
     std::vector<double> Wstore(t.W);
     if (p.precision == DRTS_FP32)
         for (int k = 0; k < K; ++k) {
             const size_t off = size_t(k) * kDirs * kOffs * kDirs;
             diffuse_round_fp32(&t.W[off], &Wstore[off]);
         }
+    // FP16 tier: every row of direction m is stored as FP16 times a power of
+    // two scale[m] chosen so the largest value of any medium maps to 2^14
+    // (the FP16 normal range then covers values down to ~4e-9 of it)
+    t.dir_scale.assign(kDirs, 1.0f);
+    if (p.precision == DRTS_FP16_ROWSCALE) {
+        for (int m = 0; m < kDirs; ++m) {
+            double mx = 0.0;
+            for (int k = 0; k < K; ++k)
+                for (int n = 0; n < kDirs; ++n)
+                    for (int o = 0; o < kOffs; ++o)
+                        mx = std::fmax(mx, t.W[((size_t(k) * kDirs + n) * kOffs + o) * kDirs + m]);
+            const int e2 = mx > 0.0 ? int(std::ceil(std::log2(mx))) : 0;
+            t.dir_scale[m] = std::ldexp(1.0f, e2 - 14);
+        }
+        for (int k = 0; k < K; ++k) {
+            const size_t off = size_t(k) * kDirs * kOffs * kDirs;
+            diffuse_round_fp16(&t.W[off], t.dir_scale.data(), &Wstore[off]);
+        }
+    }
 
     // plain-row templates (row direction m, column offset d = source - row)
     t.tmpl_off.assign(size_t(K) * kDirs * (kOffs + 1), 0);

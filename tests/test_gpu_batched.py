@@ -1,0 +1,77 @@
+"""Batched step X(t+1) = A X(t) + S(t): every right-hand side must match the
+FP64 oracle run alone, and the single-RHS path of the same problem."""
+import numpy as np
+import pytest
+
+from paper_1611_08536_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1611_08536_gb300 import build, drts
+    build.build()
+    drts.load()
+    return drts
+
+
+def rel_l1(a, b):
+    return np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300)
+
+
+def run_batched(gpu, prob, srcs, steps, tile=0):
+    with gpu.Context(prob, max_steps=steps) as ctx:
+        if tile:
+            ctx.set_launch(0, 0, tile, -1)
+        for r, s in enumerate(srcs):
+            ctx.set_source(r, s)
+        ctx.step_n(steps)
+        xs, dets, leds = [], [], []
+        for r in range(len(srcs)):
+            xs.append(ctx.read_state(r))
+            d, l = ctx.read_detectors(r)
+            dets.append(d)
+            leds.append(l)
+    return xs, dets, leds
+
+
+@pytest.mark.parametrize("n_rhs,tile", [(5, 0), (5, 4), (8, 8), (13, 16), (33, 32)])
+def test_batched_fp32_matches_oracle(gpu, oracle_mod, n_rhs, tile):
+    prob, srcs = I.inclusions(12, n_rhs=n_rhs, seed=21, precision=I.FP32, n_spheres=2)
+    steps = 40
+    csr = oracle_mod.assemble(prob)
+    ci = oracle_mod.column_info(prob)
+    xs, dets, leds = run_batched(gpu, prob, srcs, steps, tile)
+    for r in range(0, n_rhs, max(1, n_rhs // 5)):
+        xo, deto, ledo = oracle_mod.run(prob, csr, steps, srcs[r].as_tuple(), colinfo=ci)
+        assert rel_l1(xs[r], xo) < 1e-5, r
+        assert rel_l1(dets[r], deto) < 1e-5, r
+        assert np.allclose(leds[r], ledo, rtol=1e-5, atol=1e-12), (r, leds[r], ledo)
+
+
+def test_batched_same_alone_and_in_mix(gpu):
+    prob, srcs = I.inclusions(14, n_rhs=6, seed=5, precision=I.FP32, n_spheres=2)
+    steps = 30
+    xs, dets, _ = run_batched(gpu, prob, srcs, steps)
+    import copy
+    for r in (0, 3, 5):
+        p1 = copy.copy(prob)
+        p1.n_rhs = 1
+        x1, d1, _ = run_batched(gpu, p1, [srcs[r]], steps)
+        assert rel_l1(xs[r], x1[0]) < 1e-6
+        assert rel_l1(dets[r], d1[0]) < 1e-6
+
+
+def test_batched_fp64_and_fp16(gpu, oracle_mod):
+    for prec, tol in ((I.FP64, 1e-12), (I.FP16_ROWSCALE, 5e-3)):
+        prob, srcs = I.inclusions(10, n_rhs=4, seed=8, precision=prec, n_spheres=1)
+        steps = 20
+        csr = oracle_mod.assemble(prob)
+        xs, _, _ = run_batched(gpu, prob, srcs, steps)
+        for r in range(4):
+            xo, _, _ = oracle_mod.run(prob, csr, steps, srcs[r].as_tuple())
+            assert rel_l1(xs[r], xo) < tol, (prec, r)

@@ -41,10 +41,11 @@ def check_rows(ctx, csr, precision):
     assert np.array_equal(rp, csr.row_ptr)
     assert np.array_equal(col, csr.col)
     if precision == I.FP16_ROWSCALE:
-        # per-row scale: error relative to the row maximum
+        # FP16 times a power-of-two row scale, column-preserving rounding:
+        # within one FP16 ulp of the value (plus the subnormal floor)
         rowmax = np.maximum.reduceat(csr.val, csr.row_ptr[:-1]) if csr.nnz else np.zeros(0)
         rm = np.repeat(rowmax, np.diff(csr.row_ptr))
-        assert np.all(np.abs(val - csr.val) <= rm * 2.0 ** -11 + 1e-30)
+        assert np.all(np.abs(val - csr.val) <= np.abs(csr.val) * 2.0 ** -10 + rm * 1e-9)
     else:
         assert np.all(np.abs(val - csr.val) <= np.abs(csr.val) * _val_tol(precision) + 1e-300)
 
@@ -137,15 +138,28 @@ def test_step_random_state(gpu, oracle_mod, name, prob):
     assert led[1] == pytest.approx(ledo[1], rel=1e-12)
 
 
-@pytest.mark.xfail(strict=False, reason="FP16 rounding of A drifts the solution; "
-                   "column-compensated rounding is not built yet")
-def test_fp16_rowscale_tier(gpu, oracle_mod):
+def _fp16_error(gpu, oracle_mod, steps):
     prob, src = I.three_layers(16, precision=I.FP16_ROWSCALE)
-    (x, det, led), (xo, deto, ledo) = _run_both(gpu, oracle_mod, prob, src, 200)
-    e = rel_l1(x, xo)
-    print(f"FP16-rowscale rel L1 after 200 steps: {e:.3e}")
+    (x, det, led), (xo, deto, ledo) = _run_both(gpu, oracle_mod, prob, src, steps)
     assert x.min() >= 0.0
+    return rel_l1(x, xo)
+
+
+@pytest.mark.xfail(strict=False, reason="16-bit values leave a systematic stencil-shape "
+                   "error of ~1e-3 per 500 steps; the 1e-4 target is not met")
+def test_fp16_rowscale_meets_1e4(gpu, oracle_mod):
+    e = _fp16_error(gpu, oracle_mod, 200)
+    print(f"FP16-rowscale rel L1 after 200 steps: {e:.3e}")
     assert e < 1e-4
+
+
+def test_fp16_rowscale_measured_bound(gpu, oracle_mod):
+    """The FP16 tier's measured error at 16^3 (37 % edge voxels): 6.5e-3 after
+    200 steps with column-preserving rounding of the plain rows (2.1e-2 with
+    rounding to nearest everywhere)."""
+    e = _fp16_error(gpu, oracle_mod, 200)
+    print(f"FP16-rowscale rel L1 after 200 steps: {e:.3e}")
+    assert e < 1e-2
 
 
 def test_empty_source_and_zero_steps(gpu):
