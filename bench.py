@@ -158,9 +158,11 @@ def run_gpu(args):
     info = ctx.info()
     ctx.set_source(0, src)
     tune = None
+    if args.step_mode == "persistent":
+        ctx.set_step_mode(drts.STEP_PERSISTENT)
     if args.blocks_per_sm or args.threads or args.variant >= 0:
         ctx.set_launch(args.blocks_per_sm, args.threads, 0, args.variant)
-    elif args.autotune:
+    elif args.autotune and args.step_mode == "launch":
         tune = ctx.autotune(args.autotune)
 
     ctx.step_n(args.warmup)
@@ -232,6 +234,7 @@ def run_gpu(args):
                    "precision": args.precision, "steps_per_s": round(1e3 / ms_step, 3),
                    "l2": "inputs larger than L2 (matrix streamed every step)",
                    "assembly_s": round(t_asm, 2), "parallelism": f"replicas x{ws}",
+                   "step_mode": args.step_mode,
                    "launch": tune},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -414,6 +417,7 @@ def main():
     ap.add_argument("--variant", type=int, default=-1)
     ap.add_argument("--autotune", type=int, default=2, help="timed steps per candidate (0 = off)")
     ap.add_argument("--rhs", type=int, default=1, help="right-hand sides (batched step when > 1)")
+    ap.add_argument("--step-mode", default="launch", choices=["launch", "persistent"])
     ap.add_argument("--sim-steps", type=int, default=1500, help="steps per simulation for sims/s")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-check", dest="check", action="store_false")

@@ -188,6 +188,19 @@ drts_status drts_set_launch(drts_ctx *ctx, int32_t blocks_per_sm,
                             int32_t threads_per_block, int32_t rhs_tile,
                             int32_t variant);
 
+/*
+ * How drts_step_n issues its steps (Fig. 3 loop):
+ *   DRTS_STEP_LAUNCH      one kernel launch per step (default);
+ *   DRTS_STEP_PERSISTENT  one cooperative launch runs all n steps, with a
+ *                         grid-wide barrier between steps whose wait is
+ *                         bounded (DRTS_ETIMEOUT instead of a hang); for
+ *                         small grids where launch gaps matter.  One
+ *                         right-hand side only.
+ */
+#define DRTS_STEP_LAUNCH 0
+#define DRTS_STEP_PERSISTENT 1
+drts_status drts_set_step_mode(drts_ctx *ctx, int32_t mode);
+
 /* Result of drts_autotune. */
 typedef struct drts_tune_result {
     int32_t variant, threads, blocks_per_sm, rhs_tile;
@@ -217,11 +230,16 @@ drts_status drts_autotune(drts_ctx *ctx, int32_t trial_steps, drts_tune_result *
  *                          runs out; the step then reports DRTS_ETIMEOUT at the
  *                          next synchronising call and the context stays usable;
  *   DRTS_FAULT_SPIN_LIMIT  polls before a device-side wait gives up (arg,
- *                          1..2^30; default 2^22).
+ *                          1..2^30; default 2^22);
+ *   DRTS_FAULT_SKIP_BARRIER in persistent mode the first block never arrives
+ *                          at the first grid barrier, so the other blocks'
+ *                          bounded waits run out (DRTS_ETIMEOUT).
  */
 #define DRTS_FAULT_NONE 0
 #define DRTS_FAULT_SKIP_COPY 1
 #define DRTS_FAULT_SPIN_LIMIT 2
+#define DRTS_FAULT_SKIP_BARRIER 3   /* persistent mode: the first block never
+                                       arrives at the first grid barrier */
 drts_status drts_set_fault(drts_ctx *ctx, int32_t kind, int64_t arg);
 
 /*

@@ -48,6 +48,10 @@ struct drts_ctx {
     int *d_err = nullptr;                // device error word of bounded waits
     uint32_t spin_limit = 1u << 22;
     int64_t fault_skip_chunk = -1;
+    int fault_skip_barrier = 0;
+    int step_mode = DRTS_STEP_LAUNCH;
+    int persist_blocks = 0;
+    unsigned *d_bar = nullptr;           // grid barrier of the persistent kernel
     int special_permille = 0;
 };
 
@@ -355,7 +359,8 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
         (e = dalloc(c, &c->ledger, sizeof(double) * 4 * c->R)) != cudaSuccess ||
         (e = dalloc(c, &c->d_src, sizeof(SourceEntry) * kMaxSrc * c->R)) != cudaSuccess ||
         (e = dalloc(c, &c->d_prof, sizeof(SourceProfile) * c->R)) != cudaSuccess ||
-        (e = dalloc(c, &c->d_err, sizeof(int))) != cudaSuccess) {
+        (e = dalloc(c, &c->d_err, sizeof(int))) != cudaSuccess ||
+        (e = dalloc(c, &c->d_bar, 2 * sizeof(unsigned))) != cudaSuccess) {
         cuda_fail(c, e, "state allocation");
         return bail(DRTS_ENOMEM);
     }
@@ -426,6 +431,15 @@ drts_status drts_step_n(drts_ctx *c, int64_t n_steps)
     if (n_steps < 0) return fail(c, DRTS_EINVAL, "n_steps < 0");
     if (c->det && c->t + n_steps > c->prob.max_steps)
         return fail(c, DRTS_EINVAL, "t + n_steps exceeds max_steps");
+    if (c->step_mode == DRTS_STEP_PERSISTENT && n_steps > 0) {
+        StepArgs a = make_args(c);
+        cudaError_t e = launch_persistent(a, c->y, n_steps, c->det, c->prob.max_steps, c->d_bar,
+                                          c->fault_skip_barrier, c->persist_blocks, c->threads, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "persistent launch");
+        if (n_steps & 1) std::swap(c->x, c->y);
+        c->t += n_steps;
+        return DRTS_OK;
+    }
     for (int64_t i = 0; i < n_steps; ++i) {
         StepArgs a = make_args(c);
         cudaError_t e = launch_any_step(c, a);
@@ -768,13 +782,36 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
     return DRTS_OK;
 }
 
+drts_status drts_set_step_mode(drts_ctx *c, int32_t mode)
+{
+    if (!c) return DRTS_EINVAL;
+    if (mode == DRTS_STEP_LAUNCH) {
+        c->step_mode = mode;
+        return DRTS_OK;
+    }
+    if (mode == DRTS_STEP_PERSISTENT) {
+        if (c->R != 1) return fail(c, DRTS_EUNSUPPORTED, "persistent mode steps one right-hand side");
+        const int blocks = persistent_blocks(c->prob.precision, c->threads);
+        if (blocks < 1) return fail(c, DRTS_EUNSUPPORTED, "cooperative launch not available");
+        c->persist_blocks = blocks;
+        c->step_mode = mode;
+        return DRTS_OK;
+    }
+    return fail(c, DRTS_EINVAL, "unknown step mode");
+}
+
 drts_status drts_set_fault(drts_ctx *c, int32_t kind, int64_t arg)
 {
     if (!c) return DRTS_EINVAL;
     switch (kind) {
     case DRTS_FAULT_NONE:
         c->fault_skip_chunk = -1;
+        c->fault_skip_barrier = 0;
         c->spin_limit = 1u << 22;
+        return DRTS_OK;
+    case DRTS_FAULT_SKIP_BARRIER:
+        if (c->step_mode != DRTS_STEP_PERSISTENT) return fail(c, DRTS_ESTATE, "no grid barrier outside persistent mode");
+        c->fault_skip_barrier = 1;
         return DRTS_OK;
     case DRTS_FAULT_SKIP_COPY:
         if (arg < 0) return fail(c, DRTS_EINVAL, "chunk index must be >= 0");

@@ -59,7 +59,17 @@ __device__ __forceinline__ void load_group(const VT *vals, const uint16_t *codes
 // Dot product of one row with x, streaming the row's groups with D groups
 // prefetched ahead so that D matrix loads per lane are in flight while the
 // current group's x gathers run.
-template <class VT, class XT, class AT, int D>
+// State loads: through the read-only cache when x is not written during the
+// kernel; coherent (L2) loads in the persistent kernel, which writes the
+// buffer it reads in the next step.
+template <bool COHERENT, class XT>
+__device__ __forceinline__ XT load_x(const XT *p)
+{
+    if constexpr (COHERENT) return __ldcg(p);
+    else return __ldg(p);
+}
+
+template <class VT, class XT, class AT, int D, bool COHERENT = false>
 __device__ __forceinline__ AT row_dot(const VT *__restrict__ vals, const uint16_t *__restrict__ codes,
                                       int64_t base, int len4, const XT *__restrict__ x, int64_t v,
                                       const int32_t *s_delta)
@@ -76,10 +86,10 @@ __device__ __forceinline__ AT row_dot(const VT *__restrict__ vals, const uint16_
             if (g < len4) {
                 const Group<AT> cur = buf[s];
                 if (g + D < len4) load_group(vals, codes, base + int64_t(g + D) * (kSlice * kGroup), buf[s]);
-                const AT p0 = cur.w[0] * AT(__ldg(x + (v + s_delta[cur.c[0]])));
-                const AT p1 = cur.w[1] * AT(__ldg(x + (v + s_delta[cur.c[1]])));
-                const AT p2 = cur.w[2] * AT(__ldg(x + (v + s_delta[cur.c[2]])));
-                const AT p3 = cur.w[3] * AT(__ldg(x + (v + s_delta[cur.c[3]])));
+                const AT p0 = cur.w[0] * AT(load_x<COHERENT>(x + (v + s_delta[cur.c[0]])));
+                const AT p1 = cur.w[1] * AT(load_x<COHERENT>(x + (v + s_delta[cur.c[1]])));
+                const AT p2 = cur.w[2] * AT(load_x<COHERENT>(x + (v + s_delta[cur.c[2]])));
+                const AT p3 = cur.w[3] * AT(load_x<COHERENT>(x + (v + s_delta[cur.c[3]])));
                 acc.add((p0 + p1) + (p2 + p3));
             }
         }
@@ -96,12 +106,17 @@ struct StepShared {
     double src_val[kMaxSrc];
 };
 
-__device__ __forceinline__ void step_prologue(const StepArgs &a, StepShared &sh)
+__device__ __forceinline__ void step_delta(const StepArgs &a, StepShared &sh)
 {
     for (int c = threadIdx.x; c < kCodes; c += blockDim.x) {
         const int d = c / kDirs, n = c % kDirs;
         sh.delta[c] = int32_t(n * a.V + (int64_t(d / 9 - 1) * a.ny + (d / 3 % 3 - 1)) * a.nx + (d % 3 - 1));
     }
+}
+
+// this step's source values and a zeroed block ledger (ends with a barrier)
+__device__ __forceinline__ void step_sources(const StepArgs &a, StepShared &sh)
+{
     if (threadIdx.x < 2) sh.ledger[threadIdx.x] = 0.0;
     for (int e = threadIdx.x; e < a.n_src; e += blockDim.x) {
         sh.src[e] = a.src[e];
@@ -114,9 +129,15 @@ __device__ __forceinline__ void step_prologue(const StepArgs &a, StepShared &sh)
     __syncthreads();
 }
 
+__device__ __forceinline__ void step_prologue(const StepArgs &a, StepShared &sh)
+{
+    step_delta(a, sh);
+    step_sources(a, sh);
+}
+
 // Finish row (voxel v, direction m) of slice q: row scale, source term, store,
 // and the column functionals of x(t) for the same state (Eq. 27, ledger).
-template <class XT, class AT>
+template <class XT, class AT, bool COHERENT = false>
 __device__ __forceinline__ void row_epilogue(const StepArgs &a, const StepShared &sh, int64_t q, int lane,
                                              int64_t v, int m, AT acc, AT &ab_lane, AT &ex_lane)
 {
@@ -128,7 +149,7 @@ __device__ __forceinline__ void row_epilogue(const StepArgs &a, const StepShared
     for (int e = 0; e < a.n_src; ++e)
         if (sh.src[e].slice == q && sh.src[e].lane == lane) acc += AT(sh.src_val[e]);
     y[row] = XT(acc);
-    const AT xs = AT(x[row]);
+    const AT xs = AT(COHERENT ? __ldcg(x + row) : x[row]);
     const int k = a.med[v];
     ab_lane += AT(a.tab.absorb[k]) * xs;
     const int nxy = a.nx * a.ny;
@@ -194,6 +215,84 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         row_epilogue<XT, AT>(a, sh, q, lane, v, m, acc, ab_lane, ex_lane);
     }
     step_finish(a, sh, ab_lane, ex_lane);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent multi-step kernel: one cooperative launch advances n_steps, with
+// a grid-wide barrier between steps.  The barrier's wait is bounded: after
+// spin_limit polls (or when another block has flagged an error) the block
+// records the failure in a.err and every block leaves the step loop, so the
+// host sees DRTS_ETIMEOUT and the context stays usable.
+
+// bar[0] = arrivals of the current round, bar[1] = round counter
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, uint32_t limit, int *err,
+                                             bool skip)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *round = bar + 1;
+        const unsigned r0 = *round;
+        __threadfence();                       // this block's writes before arriving
+        if (skip) {
+            ok = 0;                            // fault injection: never arrive
+        } else if (atomicAdd(bar, 1u) + 1u == nblocks) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(const_cast<unsigned *>(round), 1u);
+        } else {
+            for (uint32_t i = 0; *round == r0; ++i) {
+                if (i >= limit || *(volatile int *)err != 0) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (!ok && !skip) atomicExch(err, 1);
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <class VT, class XT, class AT>
+__global__ void __launch_bounds__(256) persistent_kernel(StepArgs a0, void *other, int64_t n_steps,
+                                                         double *det_base, int64_t max_steps, unsigned *bar,
+                                                         int fault_skip_barrier)
+{
+    __shared__ StepShared sh;
+    step_delta(a0, sh);
+    const VT *__restrict__ vals = static_cast<const VT *>(a0.A.vals);
+    const uint16_t *__restrict__ codes = a0.A.codes;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        StepArgs a = a0;
+        a.t = a0.t + k;
+        a.x = (k & 1) ? other : a0.x;
+        a.y = (k & 1) ? const_cast<void *>(a0.x) : other;
+        a.det = (det_base && a.t < max_steps) ? det_base + a.t * a.n_patch : nullptr;
+        step_sources(a, sh);
+        const XT *x = static_cast<const XT *>(a.x);
+        AT ab_lane = 0, ex_lane = 0;
+        for (int64_t q = warp0; q < a.A.n_slices; q += nwarps) {
+            const int64_t b = q / kDirs;
+            const int m = int(q - b * kDirs);
+            const int64_t v = b * kSlice + lane;
+            const int len4 = a.A.slice_len4[q];
+            const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
+            const AT acc = row_dot<VT, XT, AT, 1, true>(vals, codes, base, len4, x, v, sh.delta);
+            row_epilogue<XT, AT, true>(a, sh, q, lane, v, m, acc, ab_lane, ex_lane);
+        }
+        step_finish(a, sh, ab_lane, ex_lane);
+        if (k + 1 < n_steps &&
+            !grid_barrier(bar, gridDim.x, a.spin_limit, a.err, fault_skip_barrier && blockIdx.x == 0 && k == 0))
+            break;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -532,6 +631,58 @@ int step_default_blocks(int precision, int R, int threads, int variant)
                : precision == DRTS_FP32 ? VarF32::per_sm(variant, threads)
                                         : VarF16::per_sm(variant, threads);
     return per_sm < 1 ? 0 : sms * per_sm;
+}
+
+namespace {
+template <class VT, class XT, class AT>
+int persistent_fit(int threads)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, persistent_kernel<VT, XT, AT>, threads, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <class VT, class XT, class AT>
+cudaError_t persistent_launch(const StepArgs &a, void *other, int64_t n_steps, double *det_base,
+                              int64_t max_steps, unsigned *bar, int fault, int blocks, int threads,
+                              cudaStream_t s)
+{
+    StepArgs a0 = a;
+    void *args[] = {&a0, &other, &n_steps, &det_base, &max_steps, &bar, &fault};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(persistent_kernel<VT, XT, AT>), dim3(blocks),
+                                       dim3(threads), args, 0, s);
+}
+}  // namespace
+
+int persistent_blocks(int precision, int threads)
+{
+    int dev = 0, sms = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return 0;
+    const int per = precision == DRTS_FP64 ? persistent_fit<double, double, double>(threads)
+                  : precision == DRTS_FP32 ? persistent_fit<float, float, float>(threads)
+                                           : persistent_fit<__half, float, float>(threads);
+    return per * sms;
+}
+
+cudaError_t launch_persistent(const StepArgs &a, void *other, int64_t n_steps, double *det_base, int64_t max_steps,
+                              unsigned *bar, int fault_skip_barrier, int blocks, int threads, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    if (a.A.precision == DRTS_FP64)
+        return persistent_launch<double, double, double>(a, other, n_steps, det_base, max_steps, bar,
+                                                         fault_skip_barrier, blocks, threads, s);
+    if (a.A.precision == DRTS_FP32)
+        return persistent_launch<float, float, float>(a, other, n_steps, det_base, max_steps, bar,
+                                                      fault_skip_barrier, blocks, threads, s);
+    return persistent_launch<__half, float, float>(a, other, n_steps, det_base, max_steps, bar,
+                                                   fault_skip_barrier, blocks, threads, s);
 }
 
 cudaError_t launch_step(const StepArgs &a, int variant, int blocks, int threads, cudaStream_t s)

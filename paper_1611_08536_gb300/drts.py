@@ -21,7 +21,8 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, EUNSUPPORTED = range(7)
 OPEN, MIRROR, FRESNEL = 0, 1, 2
 FP64, FP32, FP16_ROWSCALE = 0, 1, 2
 FACE_NONE = -1
-FAULT_NONE, FAULT_SKIP_COPY, FAULT_SPIN_LIMIT = 0, 1, 2
+FAULT_NONE, FAULT_SKIP_COPY, FAULT_SPIN_LIMIT, FAULT_SKIP_BARRIER = 0, 1, 2, 3
+STEP_LAUNCH, STEP_PERSISTENT = 0, 1
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE",
            6: "EUNSUPPORTED"}
 
@@ -78,7 +79,8 @@ class Info(ctypes.Structure):
 SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_detectors",
            "drts_read_state", "drts_write_state", "drts_run_host", "drts_export_rows",
            "drts_column_info", "drts_get_info", "drts_set_launch", "drts_destroy",
-           "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_autotune"]
+           "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_autotune",
+           "drts_set_step_mode"]
 
 _lib = None
 
@@ -107,6 +109,7 @@ def load(path: str = LIB_PATH):
     lib.drts_state_sum_noalloc.argtypes = [vp, i32, vp]
     lib.drts_set_fault.argtypes = [vp, i32, i64]
     lib.drts_autotune.argtypes = [vp, i32, ctypes.POINTER(TuneResult)]
+    lib.drts_set_step_mode.argtypes = [vp, i32]
     lib.drts_destroy.argtypes = [vp]
     lib.drts_destroy.restype = None
     lib.drts_last_error.argtypes = [vp]
@@ -241,6 +244,11 @@ class Context:
         r = TuneResult()
         self._check(self._lib.drts_autotune(self._h, int(trial_steps), ctypes.byref(r)))
         return r.as_dict()
+
+    def set_step_mode(self, mode):
+        """STEP_LAUNCH (one launch per step) or STEP_PERSISTENT (one
+        cooperative launch for all steps of a drts_step_n call)."""
+        self._check(self._lib.drts_set_step_mode(self._h, int(mode)))
 
     def set_fault(self, kind, arg=0):
         """Host-side fault injection (FAULT_NONE / FAULT_SKIP_COPY / FAULT_SPIN_LIMIT)."""

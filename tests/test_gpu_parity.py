@@ -275,3 +275,63 @@ def test_autotune_keeps_state_and_parity(gpu, oracle_mod):
         r2 = ctx.autotune(2)                       # cached in-process
         assert r2["from_cache"] == 1 and r2["variant"] == r["variant"]
     assert rel_l1(x1, oracle_mod.spmv(csr, before)) < 1e-6
+
+
+def test_persistent_fp64_300_steps(gpu, oracle_mod):
+    """The persistent multi-step kernel on the 16^3 FP64 configuration."""
+    prob, src = I.fresnel_cube(16, precision=I.FP64)
+    csr = oracle_mod.assemble(prob)
+    xo, deto, ledo = oracle_mod.run(prob, csr, 300, src.as_tuple())
+    with gpu.Context(prob, max_steps=300) as ctx:
+        ctx.set_step_mode(gpu.STEP_PERSISTENT)
+        ctx.set_source(0, src)
+        ctx.step_n(300)
+        x = ctx.read_state()
+        det, led = ctx.read_detectors()
+    assert rel_l1(x, xo) < 1e-12
+    assert rel_l1(det, deto) < 1e-12
+    assert np.allclose(led, ledo, rtol=1e-11)
+
+
+def test_persistent_mixed_with_launches(gpu, oracle_mod):
+    prob, src = I.three_layers(16, precision=I.FP32)
+    csr = oracle_mod.assemble(prob)
+    rng = np.random.default_rng(2)
+    x0 = rng.random(prob.n_states)
+    xo, deto, _ = oracle_mod.run(prob, csr, 25, src.as_tuple(), x0=x0)
+    with gpu.Context(prob, max_steps=25) as ctx:
+        ctx.write_state(x0)
+        ctx.set_source(0, src)
+        ctx.set_step_mode(gpu.STEP_PERSISTENT)
+        ctx.step_n(9)
+        ctx.set_step_mode(gpu.STEP_LAUNCH)
+        ctx.step_n(5)
+        ctx.set_step_mode(gpu.STEP_PERSISTENT)
+        ctx.step_n(11)
+        x = ctx.read_state()
+        det, _ = ctx.read_detectors()
+    assert rel_l1(x, xo) < 1e-6
+    assert rel_l1(det, deto) < 1e-6
+
+
+def test_persistent_barrier_times_out_and_recovers(gpu, oracle_mod):
+    """A block that never arrives at the grid barrier makes the other blocks'
+    bounded waits run out: DRTS_ETIMEOUT, and the context stays usable."""
+    prob, _ = I.three_layers(12, precision=I.FP32)
+    csr = oracle_mod.assemble(prob)
+    rng = np.random.default_rng(6)
+    x0 = rng.random(prob.n_states)
+    with gpu.Context(prob, max_steps=8) as ctx:
+        ctx.set_step_mode(gpu.STEP_PERSISTENT)
+        ctx.set_fault(gpu.FAULT_SPIN_LIMIT, 5000)
+        ctx.set_fault(gpu.FAULT_SKIP_BARRIER, 0)
+        ctx.write_state(x0)
+        ctx.step_n(3)
+        with pytest.raises(gpu.DrtsError) as ei:
+            ctx.read_state()
+        assert ei.value.status == gpu.ETIMEOUT
+        ctx.set_fault(gpu.FAULT_NONE)
+        ctx.write_state(x0)
+        ctx.step_n(2)
+        x2 = ctx.read_state()
+    assert rel_l1(x2, oracle_mod.spmv(csr, oracle_mod.spmv(csr, x0))) < 1e-6
