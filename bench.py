@@ -370,6 +370,74 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Served stream: seeded Poisson arrivals submitted in real time to the
+    continuous-batching server; reports sims/s and p50/p99 latency, next to
+    the same requests run one after another through plain contexts."""
+    import numpy as np
+    import torch
+    from paper_1611_08536_gb300 import build, drts
+    from paper_1611_08536_gb300 import inputs as I
+    torch.cuda.set_device(0)
+    build.build()
+    stream = I.served_stream(args.serve_requests, args.serve_rate, seed=4)
+    for r in stream:
+        r.n_steps = max(1, int(round(r.n_steps * args.serve_step_scale)))
+    stats = None
+    lat, queue = [], []
+    with drts.Server(max_resident=args.serve_resident, steps_per_tick=args.serve_tick_steps,
+                     n_streams=args.serve_streams) as srv:
+        t0 = time.perf_counter()
+        ids, pending = [], list(stream)
+        with ClockSampler(0) as clk:
+            while pending or len(ids) == 0 or srv.stats()["completed"] + srv.stats()["failed"] < len(stream):
+                now = time.perf_counter() - t0
+                while pending and pending[0].arrival_s <= now:
+                    r = pending.pop(0)
+                    ids.append(srv.submit(r.problem, r.sources, r.n_steps))
+                st = srv.stats()
+                if st["resident"] == 0 and st["queued"] == 0 and pending:
+                    time.sleep(min(0.01, max(0.0, pending[0].arrival_s - now)))
+                    continue
+                srv.tick()
+        makespan = time.perf_counter() - t0
+        for rid in ids:
+            inf = srv.poll(rid)
+            lat.append(inf.latency_s)
+            queue.append(inf.queue_s)
+        stats = srv.stats()
+    # the same requests one after another, no batching or overlap
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for r in stream:
+        with drts.Context(r.problem, max_steps=r.n_steps) as ctx:
+            for q, sr in enumerate(r.sources):
+                ctx.inject_source(q, sr.state, sr.weight, r.sources[0].t0, r.sources[0].profile)
+            ctx.step_n(r.n_steps)
+            ctx.read_detectors(0)
+    seq = time.perf_counter() - t1
+    n = len(stream)
+    line = {
+        "metric": "DRTS served stream: simulations per second (continuous batching)",
+        "value": round(n / makespan, 4), "unit": "sims/s", "n_gpus": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "served_stream", "requests": n, "arrival_rate_per_s": args.serve_rate,
+                   "step_scale": args.serve_step_scale,
+                   "sides": list(I.SERVED_SIDES), "max_resident": args.serve_resident,
+                   "steps_per_tick": args.serve_tick_steps, "streams": args.serve_streams},
+        "latency_s": {"p50": round(float(np.percentile(lat, 50)), 3),
+                      "p99": round(float(np.percentile(lat, 99)), 3),
+                      "max": round(float(np.max(lat)), 3)},
+        "queue_s": {"p50": round(float(np.percentile(queue, 50)), 3),
+                    "p99": round(float(np.percentile(queue, 99)), 3)},
+        "makespan_s": round(makespan, 3),
+        "sequential_plain": {"sims_per_s": round(n / seq, 4), "seconds": round(seq, 3)},
+        "server_stats": stats, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     import numpy as np
     ws, rank, _ = dist_env()
@@ -418,6 +486,13 @@ def main():
     ap.add_argument("--autotune", type=int, default=2, help="timed steps per candidate (0 = off)")
     ap.add_argument("--rhs", type=int, default=1, help="right-hand sides (batched step when > 1)")
     ap.add_argument("--step-mode", default="launch", choices=["launch", "persistent"])
+    ap.add_argument("--serve", action="store_true", help="served-stream benchmark")
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-step-scale", type=float, default=0.1)
+    ap.add_argument("--serve-resident", type=int, default=16)
+    ap.add_argument("--serve-tick-steps", type=int, default=20)
+    ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--sim-steps", type=int, default=1500, help="steps per simulation for sims/s")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-check", dest="check", action="store_false")
@@ -426,6 +501,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     elif args.rhs > 1:
         run_batched(args)
     else:

@@ -265,6 +265,76 @@ drts_status drts_set_fault(drts_ctx *ctx, int32_t kind, int64_t arg);
  */
 drts_status drts_state_sum_noalloc(drts_ctx *ctx, int32_t rhs, double *out_device);
 
+/* ------------------------------------------------------------------------
+ * Serving loop: continuous batching of independent simulations.
+ *
+ * The paper's method assembles A once per medium and then only steps it
+ * (Fig. 3); a server keeps many such simulations resident at once.  Requests
+ * queue on the host.  Each drts_server_tick (1) captures the next
+ * steps_per_tick steps of every resident simulation into one CUDA graph whose
+ * branches fan out over n_streams streams (their kernels overlap on the
+ * device) and launches it, (2) while it runs, admits queued requests in
+ * arrival order as long as a resident slot and device memory (a footprint
+ * estimate against mem_budget_bytes) are free, assembling their A, and (3)
+ * retires finished simulations: detector history and ledger are copied to
+ * host and their device memory is freed.  A request submitted while others
+ * run is admitted at a later tick.  Results do not depend on what else is
+ * resident (each simulation's kernels read only its own data).
+ * ------------------------------------------------------------------------ */
+typedef struct drts_server drts_server;
+
+typedef struct drts_server_config {
+    int64_t mem_budget_bytes;        /* device bytes for resident simulations; 0 = 90% of free */
+    int32_t max_resident;            /* resident simulations at once, 1..256 */
+    int32_t steps_per_tick;          /* steps each resident simulation advances per tick */
+    int32_t n_streams;               /* streams a tick's graph fans out over, 1..32 */
+} drts_server_config;
+
+#define DRTS_REQ_QUEUED 0
+#define DRTS_REQ_RUNNING 1
+#define DRTS_REQ_DONE 2
+#define DRTS_REQ_FAILED 3
+
+typedef struct drts_request_info {
+    int32_t state;                   /* DRTS_REQ_* */
+    int32_t n_rhs, n_patch;
+    int64_t n_steps;
+    int64_t footprint_bytes;         /* device bytes reserved while resident */
+    double queue_s;                  /* submit -> admission (host clock) */
+    double latency_s;                /* submit -> completion (host clock) */
+} drts_request_info;
+
+typedef struct drts_server_stats {
+    int64_t submitted, admitted, completed, failed, ticks, graph_launches;
+    int32_t resident, queued;
+    int64_t used_bytes, budget_bytes;
+} drts_server_stats;
+
+drts_status drts_server_create(const drts_server_config *cfg, drts_server **out);
+
+/* Queue one simulation: problem (copied; max_steps is set to n_steps), its
+ * sources as n_entries (rhs, canonical state, weight) triples sharing one
+ * time profile P(t0 .. t0+n_t-1) (Eq. 26), and the number of steps.  Returns
+ * at once with the request id.  DRTS_ENOMEM if the request could never fit
+ * the budget. */
+drts_status drts_server_submit(drts_server *srv, const drts_problem *prob, int32_t n_entries,
+                               const int32_t *src_rhs, const int64_t *src_state,
+                               const double *src_weight, int64_t t0, int32_t n_t,
+                               const double *profile, int64_t n_steps, int64_t *request_id);
+
+/* One scheduling round (see above); *n_done = simulations retired. */
+drts_status drts_server_tick(drts_server *srv, int32_t *n_done);
+drts_status drts_server_poll(drts_server *srv, int64_t request_id, drts_request_info *out);
+
+/* Detector history [n_steps][n_patch] and ledger {sum x, injected, absorbed,
+ * exited} of right-hand side rhs of a finished request (either may be NULL). */
+drts_status drts_server_result(drts_server *srv, int64_t request_id, int32_t rhs,
+                               double *det_out, double *ledger_out);
+drts_status drts_server_release(drts_server *srv, int64_t request_id);
+drts_status drts_server_get_stats(const drts_server *srv, drts_server_stats *out);
+const char *drts_server_last_error(const drts_server *srv);
+void drts_server_destroy(drts_server *srv);
+
 /* Free every device and host resource of ctx (NULL is ignored). */
 void drts_destroy(drts_ctx *ctx);
 

@@ -25,6 +25,7 @@ SOURCES = {
     "drts_api.cu": [],
     "drts_noalloc.cu": [],
     "drts_batched.cu": [],
+    "drts_serve.cu": [],
 }
 
 

@@ -231,6 +231,16 @@ int fit_blocks(drts_ctx *c, int threads, int variant, int rhs_tile)
 
 }  // namespace
 
+namespace drts {
+// The serving loop borrows a context's stream while capturing its steps.
+cudaStream_t ctx_swap_stream(drts_ctx *c, cudaStream_t s)
+{
+    cudaStream_t old = c->stream;
+    c->stream = s;
+    return old;
+}
+}  // namespace drts
+
 extern "C" {
 
 drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx **out)

@@ -65,6 +65,28 @@ class TuneResult(ctypes.Structure):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_resident", ctypes.c_int32),
+                ("steps_per_tick", ctypes.c_int32), ("n_streams", ctypes.c_int32)]
+
+
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("n_rhs", ctypes.c_int32), ("n_patch", ctypes.c_int32),
+                ("n_steps", ctypes.c_int64), ("footprint_bytes", ctypes.c_int64),
+                ("queue_s", ctypes.c_double), ("latency_s", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("ticks", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
+                ("resident", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("used_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
 class Info(ctypes.Structure):
     _fields_ = [
         ("n_states", ctypes.c_int64), ("nnz", ctypes.c_int64),
@@ -80,7 +102,9 @@ SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_dete
            "drts_read_state", "drts_write_state", "drts_run_host", "drts_export_rows",
            "drts_column_info", "drts_get_info", "drts_set_launch", "drts_destroy",
            "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_autotune",
-           "drts_set_step_mode"]
+           "drts_set_step_mode", "drts_server_create", "drts_server_submit", "drts_server_tick",
+           "drts_server_poll", "drts_server_result", "drts_server_release",
+           "drts_server_get_stats", "drts_server_last_error", "drts_server_destroy"]
 
 _lib = None
 
@@ -110,6 +134,18 @@ def load(path: str = LIB_PATH):
     lib.drts_set_fault.argtypes = [vp, i32, i64]
     lib.drts_autotune.argtypes = [vp, i32, ctypes.POINTER(TuneResult)]
     lib.drts_set_step_mode.argtypes = [vp, i32]
+    lib.drts_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    lib.drts_server_submit.argtypes = [vp, ctypes.POINTER(ProblemC), i32, vp, vp, vp, i64, i32, vp,
+                                       i64, ctypes.POINTER(i64)]
+    lib.drts_server_tick.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.drts_server_poll.argtypes = [vp, i64, ctypes.POINTER(RequestInfo)]
+    lib.drts_server_result.argtypes = [vp, i64, i32, vp, vp]
+    lib.drts_server_release.argtypes = [vp, i64]
+    lib.drts_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+    lib.drts_server_last_error.argtypes = [vp]
+    lib.drts_server_last_error.restype = ctypes.c_char_p
+    lib.drts_server_destroy.argtypes = [vp]
+    lib.drts_server_destroy.restype = None
     lib.drts_destroy.argtypes = [vp]
     lib.drts_destroy.restype = None
     lib.drts_last_error.argtypes = [vp]
@@ -262,6 +298,83 @@ class Context:
     def set_launch(self, blocks_per_sm=0, threads=0, rhs_tile=0, variant=-1):
         self._check(self._lib.drts_set_launch(self._h, int(blocks_per_sm), int(threads),
                                               int(rhs_tile), int(variant)))
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
+class Server:
+    """Continuous-batching server of DRTS simulations (drts_server_*)."""
+
+    def __init__(self, mem_budget_bytes=0, max_resident=16, steps_per_tick=10, n_streams=4):
+        self._lib = load()
+        cfg = ServerConfig(int(mem_budget_bytes), int(max_resident), int(steps_per_tick),
+                           int(n_streams))
+        h = ctypes.c_void_p()
+        st = self._lib.drts_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise DrtsError(st, "drts_server_create failed")
+        self._h = h
+
+    def _check(self, st):
+        if st != OK:
+            raise DrtsError(st, self._lib.drts_server_last_error(self._h).decode())
+
+    def submit(self, prob, sources, n_steps):
+        """``sources``: list of inputs.Source, one per right-hand side (all
+        sharing the first source's time profile)."""
+        ps = problem_struct(prob, n_steps)
+        rhs = np.concatenate([np.full(s.state.size, r, np.int32) for r, s in enumerate(sources)])
+        st_ = np.concatenate([s.state for s in sources]).astype(np.int64)
+        w = np.concatenate([s.weight for s in sources]).astype(np.float64)
+        prof = np.ascontiguousarray(sources[0].profile, dtype=np.float64)
+        rid = ctypes.c_int64()
+        self._check(self._lib.drts_server_submit(self._h, ctypes.byref(ps), rhs.size, _ptr(rhs),
+                                                 _ptr(st_), _ptr(w), int(sources[0].t0), prof.size,
+                                                 _ptr(prof), int(n_steps), ctypes.byref(rid)))
+        return rid.value
+
+    def tick(self):
+        n = ctypes.c_int32()
+        self._check(self._lib.drts_server_tick(self._h, ctypes.byref(n)))
+        return n.value
+
+    def poll(self, rid):
+        info = RequestInfo()
+        self._check(self._lib.drts_server_poll(self._h, int(rid), ctypes.byref(info)))
+        return info
+
+    def result(self, rid, rhs=0):
+        info = self.poll(rid)
+        det = np.zeros((info.n_steps, max(info.n_patch, 1)), np.float64)
+        led = np.zeros(4, np.float64)
+        self._check(self._lib.drts_server_result(self._h, int(rid), int(rhs), _ptr(det), _ptr(led)))
+        return det[:, :info.n_patch], led
+
+    def release(self, rid):
+        self._check(self._lib.drts_server_release(self._h, int(rid)))
+
+    def stats(self):
+        st = ServerStats()
+        self._check(self._lib.drts_server_get_stats(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.drts_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def assemble(prob, max_steps=0, stream=None) -> Context:

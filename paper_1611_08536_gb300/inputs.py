@@ -268,7 +268,7 @@ def served_request(seed: int, index: int, sides=SERVED_SIDES,
             mov[d2 <= r * r] = 1
     n_src = int(rng.integers(1, max_sources + 1))
     prob = Problem((n, n, n), 0.1, media, mov, 1.0, FRESNEL, FP32, n_src,
-                   FACE_PZ, 16, 16, f"request_{index}_n{n}")
+                   FACE_PZ, min(16, n), min(16, n), f"request_{index}_n{n}")
     srcs = surface_sources(prob, n_src, int(rng.integers(0, 2 ** 31)))
     n_steps = int(rng.integers(steps[0], steps[1] + 1))
     return Request(0.0, prob, srcs, n_steps)

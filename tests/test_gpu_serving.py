@@ -1,0 +1,100 @@
+"""Serving loop: continuous batching of independent simulations.  Every
+result must equal the same simulation run alone, requests that arrive while
+others run must be admitted as slots and memory free up, and the memory
+budget must be respected."""
+import numpy as np
+import pytest
+
+from paper_1611_08536_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1611_08536_gb300 import build, drts
+    build.build()
+    drts.load()
+    return drts
+
+
+def rel_l1(a, b):
+    return np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300)
+
+
+def small_stream(n, seed=11):
+    return [I.served_request(seed, i, sides=(8, 12, 16), steps=(20, 60), max_sources=4)
+            for i in range(n)]
+
+
+def run_alone(gpu, req):
+    with gpu.Context(req.problem, max_steps=req.n_steps) as ctx:
+        prof = req.sources[0]
+        for r, s in enumerate(req.sources):
+            ctx.inject_source(r, s.state, s.weight, prof.t0, prof.profile)
+        ctx.step_n(req.n_steps)
+        out = [ctx.read_detectors(r) for r in range(len(req.sources))]
+    return out
+
+
+def test_server_results_equal_alone_and_admit_while_running(gpu):
+    reqs = small_stream(7)
+    with gpu.Server(max_resident=3, steps_per_tick=7, n_streams=3) as srv:
+        ids = [srv.submit(reqs[0].problem, reqs[0].sources, reqs[0].n_steps),
+               srv.submit(reqs[1].problem, reqs[1].sources, reqs[1].n_steps)]
+        srv.tick()                                  # admits the first two
+        assert srv.stats()["failed"] == 0
+        assert srv.stats()["resident"] == 2
+        for r in reqs[2:]:                          # arrive while those run
+            ids.append(srv.submit(r.problem, r.sources, r.n_steps))
+        seen_mixed = False
+        for _ in range(500):
+            srv.tick()
+            st = srv.stats()
+            states = [srv.poll(i).state for i in ids]
+            if gpu.REQ_DONE in states and gpu.REQ_RUNNING in states:
+                seen_mixed = True
+            assert st["resident"] <= 3
+            if st["completed"] + st["failed"] == len(ids):
+                break
+        st = srv.stats()
+        assert st["completed"] == len(ids) and st["failed"] == 0
+        assert seen_mixed                           # continuous batching, not one batch
+        for rid, req in zip(ids, reqs):
+            alone = run_alone(gpu, req)
+            for r in range(len(req.sources)):
+                det, led = srv.result(rid, r)
+                d0, l0 = alone[r]
+                assert rel_l1(det, d0) < 1e-6, (rid, r)
+                assert np.allclose(led, l0, rtol=1e-6, atol=1e-12), (rid, r, led, l0)
+            info = srv.poll(rid)
+            assert info.latency_s >= info.queue_s >= 0.0
+            srv.release(rid)
+
+
+def test_server_memory_budget_limits_residency(gpu):
+    reqs = small_stream(4, seed=3)
+    probe = gpu.Server(max_resident=8, steps_per_tick=5, n_streams=2)
+    rid = probe.submit(reqs[0].problem, reqs[0].sources, reqs[0].n_steps)
+    fp = max(probe.poll(rid).footprint_bytes, 1)
+    probe.close()
+    biggest = 0
+    with gpu.Server(mem_budget_bytes=int(fp * 1.5), max_resident=8, steps_per_tick=5, n_streams=2) as srv:
+        ids = []
+        for r in reqs:
+            try:
+                ids.append(srv.submit(r.problem, r.sources, r.n_steps))
+            except gpu.DrtsError as e:
+                assert e.status == gpu.ENOMEM          # larger than the whole budget
+        for _ in range(500):
+            srv.tick()
+            st = srv.stats()
+            assert st["used_bytes"] <= st["budget_bytes"]
+            biggest = max(biggest, st["resident"])
+            if st["completed"] + st["failed"] == len(ids):
+                break
+        assert srv.stats()["completed"] == len(ids)
+    assert biggest >= 1
