@@ -37,6 +37,9 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 def workload(name, precision, rhs=1):
     from paper_1611_08536_gb300 import inputs as I
     prec = {"fp32": I.FP32, "fp64": I.FP64, "fp16": I.FP16_ROWSCALE}[precision]
+    if name.startswith("ellipsoids_"):
+        n = int(name.split("_")[-1])
+        return I.ellipsoids(n, precision=prec)
     if name.startswith("inclusions_"):
         n = int(name.split("_")[-1])
         return I.inclusions(n, n_rhs=rhs, precision=prec)

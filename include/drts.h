@@ -181,7 +181,10 @@ drts_status drts_get_info(const drts_ctx *ctx, drts_info *out);
  * per pass of the batched step, and the kernel variant (-1 keeps the current
  * one; 0-2 = matrix streamed into registers with 1-3 groups prefetched, 3-6 =
  * matrix streamed into shared-memory stages by bulk async copies, stage
- * shapes (groups, stages) = (8,3), (4,3), (4,4), (2,6)).  All variants
+ * shapes (groups, stages) = (8,3), (4,3), (4,4), (2,6); 7-8 = state halo of
+ * each 32-voxel block staged in shared memory, 13 or 26 warps, grids with nx
+ * a multiple of 32 only; 9 = registers path with the matrix stream two groups
+ * ahead and the x gathers of the next group in flight).  All variants
  * compute the same step; they differ only in speed.  DRTS_EINVAL if the
  * shape does not fit on an SM. */
 drts_status drts_set_launch(drts_ctx *ctx, int32_t blocks_per_sm,

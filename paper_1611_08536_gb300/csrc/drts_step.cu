@@ -56,9 +56,60 @@ __device__ __forceinline__ void load_group(const VT *vals, const uint16_t *codes
     load_codes(codes + idx, g.c);
 }
 
-// Dot product of one row with x, streaming the row's groups with D groups
-// prefetched ahead so that D matrix loads per lane are in flight while the
-// current group's x gathers run.
+// A group as loaded: the raw 16-byte / 8-byte words, unpacked only when
+// used, so a prefetched group costs 6 registers (FP32), 4 (FP16) or 10 (FP64).
+template <class VT>
+struct RawGroup;
+template <>
+struct RawGroup<float> {
+    float4 w;
+    uint2 c;
+};
+template <>
+struct RawGroup<__half> {
+    uint2 w;
+    uint2 c;
+};
+template <>
+struct RawGroup<double> {
+    double2 w0, w1;
+    uint2 c;
+};
+
+__device__ __forceinline__ void load_raw(const float *vals, const uint16_t *codes, int64_t idx, RawGroup<float> &g)
+{
+    g.w = __ldcs(reinterpret_cast<const float4 *>(vals + idx));
+    g.c = __ldcs(reinterpret_cast<const uint2 *>(codes + idx));
+}
+__device__ __forceinline__ void load_raw(const __half *vals, const uint16_t *codes, int64_t idx,
+                                         RawGroup<__half> &g)
+{
+    g.w = __ldcs(reinterpret_cast<const uint2 *>(vals + idx));
+    g.c = __ldcs(reinterpret_cast<const uint2 *>(codes + idx));
+}
+__device__ __forceinline__ void load_raw(const double *vals, const uint16_t *codes, int64_t idx,
+                                         RawGroup<double> &g)
+{
+    g.w0 = __ldcs(reinterpret_cast<const double2 *>(vals + idx));
+    g.w1 = __ldcs(reinterpret_cast<const double2 *>(vals + idx) + 1);
+    g.c = __ldcs(reinterpret_cast<const uint2 *>(codes + idx));
+}
+
+__device__ __forceinline__ void unpack(const RawGroup<float> &g, float w[4])
+{
+    w[0] = g.w.x; w[1] = g.w.y; w[2] = g.w.z; w[3] = g.w.w;
+}
+__device__ __forceinline__ void unpack(const RawGroup<__half> &g, float w[4])
+{
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&g.w.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&g.w.y));
+    w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+}
+__device__ __forceinline__ void unpack(const RawGroup<double> &g, double w[4])
+{
+    w[0] = g.w0.x; w[1] = g.w0.y; w[2] = g.w1.x; w[3] = g.w1.y;
+}
+
 // State loads: through the read-only cache when x is not written during the
 // kernel; coherent (L2) loads in the persistent kernel, which writes the
 // buffer it reads in the next step.
@@ -69,27 +120,34 @@ __device__ __forceinline__ XT load_x(const XT *p)
     else return __ldg(p);
 }
 
+// Dot product of one row with x, streaming the row's groups with D groups
+// prefetched ahead so that D matrix loads per lane are in flight while the
+// current group's x gathers run.
 template <class VT, class XT, class AT, int D, bool COHERENT = false>
 __device__ __forceinline__ AT row_dot(const VT *__restrict__ vals, const uint16_t *__restrict__ codes,
                                       int64_t base, int len4, const XT *__restrict__ x, int64_t v,
                                       const int32_t *s_delta)
 {
-    Group<AT> buf[D];
+    RawGroup<VT> buf[D];
 #pragma unroll
     for (int s = 0; s < D; ++s)
-        if (s < len4) load_group(vals, codes, base + int64_t(s) * (kSlice * kGroup), buf[s]);
+        if (s < len4) load_raw(vals, codes, base + int64_t(s) * (kSlice * kGroup), buf[s]);
     Acc<AT> acc;
     for (int g0 = 0; g0 < len4; g0 += D) {
 #pragma unroll
         for (int s = 0; s < D; ++s) {
             const int g = g0 + s;
             if (g < len4) {
-                const Group<AT> cur = buf[s];
-                if (g + D < len4) load_group(vals, codes, base + int64_t(g + D) * (kSlice * kGroup), buf[s]);
-                const AT p0 = cur.w[0] * AT(load_x<COHERENT>(x + (v + s_delta[cur.c[0]])));
-                const AT p1 = cur.w[1] * AT(load_x<COHERENT>(x + (v + s_delta[cur.c[1]])));
-                const AT p2 = cur.w[2] * AT(load_x<COHERENT>(x + (v + s_delta[cur.c[2]])));
-                const AT p3 = cur.w[3] * AT(load_x<COHERENT>(x + (v + s_delta[cur.c[3]])));
+                const RawGroup<VT> cur = buf[s];
+                if (g + D < len4) load_raw(vals, codes, base + int64_t(g + D) * (kSlice * kGroup), buf[s]);
+                AT w[4];
+                unpack(cur, w);
+                const int c0 = int(cur.c.x & 0xffffu), c1 = int(cur.c.x >> 16);
+                const int c2 = int(cur.c.y & 0xffffu), c3 = int(cur.c.y >> 16);
+                const AT p0 = w[0] * AT(load_x<COHERENT>(x + (v + s_delta[c0])));
+                const AT p1 = w[1] * AT(load_x<COHERENT>(x + (v + s_delta[c1])));
+                const AT p2 = w[2] * AT(load_x<COHERENT>(x + (v + s_delta[c2])));
+                const AT p3 = w[3] * AT(load_x<COHERENT>(x + (v + s_delta[c3])));
                 acc.add((p0 + p1) + (p2 + p3));
             }
         }
@@ -192,6 +250,77 @@ __device__ __forceinline__ void step_finish(const StepArgs &a, StepShared &sh, A
     }
 }
 
+// Row dot product with both streams software-pipelined: the matrix group
+// two ahead is loading and the x values of the next group are being gathered
+// while the current group's products accumulate, so neither the HBM latency
+// of the matrix nor the L1/L2 latency of the gathers sits on the critical path.
+template <class VT, class XT, class AT>
+__device__ __forceinline__ AT row_dot_pipelined(const VT *__restrict__ vals, const uint16_t *__restrict__ codes,
+                                                int64_t base, int len4, const XT *__restrict__ x, int64_t v,
+                                                const int32_t *s_delta)
+{
+    constexpr int64_t kStride = kSlice * kGroup;
+    Group<AT> g1, g2;                  // matrix groups g+1 and g+2
+    AT w0[4], x0[4];                   // current group: values and gathered x
+    Acc<AT> acc;
+    if (len4 <= 0) return acc.value();
+    {
+        Group<AT> g0;
+        load_group(vals, codes, base, g0);
+        if (len4 > 1) load_group(vals, codes, base + kStride, g1);
+        if (len4 > 2) load_group(vals, codes, base + 2 * kStride, g2);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            w0[j] = g0.w[j];
+            x0[j] = AT(__ldg(x + (v + s_delta[g0.c[j]])));
+        }
+    }
+    for (int g = 0; g < len4; ++g) {
+        AT w1[4], x1[4];
+        if (g + 1 < len4) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                w1[j] = g1.w[j];
+                x1[j] = AT(__ldg(x + (v + s_delta[g1.c[j]])));
+            }
+            g1 = g2;
+            if (g + 3 < len4) load_group(vals, codes, base + int64_t(g + 3) * kStride, g2);
+        }
+        acc.add((w0[0] * x0[0] + w0[1] * x0[1]) + (w0[2] * x0[2] + w0[3] * x0[3]));
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            w0[j] = w1[j];
+            x0[j] = x1[j];
+        }
+    }
+    return acc.value();
+}
+
+// Variant 9: registers path with both streams pipelined.
+template <class VT, class XT, class AT>
+__global__ void __launch_bounds__(256) step_kernel_pipe(StepArgs a)
+{
+    __shared__ StepShared sh;
+    step_prologue(a, sh);
+    const XT *__restrict__ x = static_cast<const XT *>(a.x);
+    const VT *__restrict__ vals = static_cast<const VT *>(a.A.vals);
+    const uint16_t *__restrict__ codes = a.A.codes;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    AT ab_lane = 0, ex_lane = 0;
+    for (int64_t q = warp0; q < a.A.n_slices; q += nwarps) {
+        const int64_t b = q / kDirs;
+        const int m = int(q - b * kDirs);
+        const int64_t v = b * kSlice + lane;
+        const int len4 = a.A.slice_len4[q];
+        const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
+        const AT acc = row_dot_pipelined<VT, XT, AT>(vals, codes, base, len4, x, v, sh.delta);
+        row_epilogue<XT, AT>(a, sh, q, lane, v, m, acc, ab_lane, ex_lane);
+    }
+    step_finish(a, sh, ab_lane, ex_lane);
+}
+
 // Variant 0: matrix streamed straight into registers (D groups prefetched).
 template <class VT, class XT, class AT, int D>
 __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
@@ -213,6 +342,73 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
         const AT acc = row_dot<VT, XT, AT, D>(vals, codes, base, len4, x, v, sh.delta);
         row_epilogue<XT, AT>(a, sh, q, lane, v, m, acc, ab_lane, ex_lane);
+    }
+    step_finish(a, sh, ab_lane, ex_lane);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory halo variant (grids with nx a multiple of 32): a CTA takes a
+// whole 32-voxel block (one x-run at fixed y, z), stages the state of the
+// block's 3x3 neighbouring x-runs, widened by one voxel at each end, for all
+// 26 directions (26 x 9 x 34 values) in shared memory, and its W warps then
+// compute the block's 26 slices with every x gather served from that halo.
+
+constexpr int kHaloRow = 34;
+constexpr int kHaloElems = kDirs * 9 * kHaloRow;
+
+template <class VT, class XT, class AT, int W>
+__global__ void __launch_bounds__(W * 32) step_kernel_halo(StepArgs a)
+{
+    __shared__ StepShared sh;
+    __shared__ int32_t s_hoff[kCodes];
+    __shared__ XT s_x[kHaloElems];
+    step_prologue(a, sh);
+    for (int c = threadIdx.x; c < kCodes; c += blockDim.x) {
+        const int d = c / kDirs, n = c % kDirs;
+        s_hoff[c] = ((n * 3 + d / 9) * 3 + d / 3 % 3) * kHaloRow + d % 3;
+    }
+    const XT *__restrict__ x = static_cast<const XT *>(a.x);
+    const VT *__restrict__ vals = static_cast<const VT *>(a.A.vals);
+    const uint16_t *__restrict__ codes = a.A.codes;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int64_t n_blocks = a.A.n_slices / kDirs;
+    const int bpl = a.nx / kSlice;                 // blocks per x-line
+    AT ab_lane = 0, ex_lane = 0;
+    for (int64_t b = blockIdx.x; b < n_blocks; b += gridDim.x) {
+        const int xb = int(b % bpl) * kSlice;
+        const int64_t yz = b / bpl;
+        const int yy = int(yz % a.ny), zz = int(yz / a.ny);
+        __syncthreads();                           // previous block done with s_x
+        for (int i = threadIdx.x; i < kHaloElems; i += blockDim.x) {
+            const int row = i / kHaloRow, col = i - row * kHaloRow;
+            const int n = row / 9, dz = row / 3 % 3 - 1, dy = row % 3 - 1;
+            const int gx = xb + col - 1, gy = yy + dy, gz = zz + dz;
+            XT val = XT(0);
+            if (gx >= 0 && gx < a.nx && gy >= 0 && gy < a.ny && gz >= 0 && gz < a.nz)
+                val = x[int64_t(n) * a.V + (int64_t(gz) * a.ny + gy) * a.nx + gx];
+            s_x[i] = val;
+        }
+        __syncthreads();
+        for (int m = wib; m < kDirs; m += W) {
+            const int64_t q = b * kDirs + m;
+            const int64_t v = b * kSlice + lane;
+            const int len4 = a.A.slice_len4[q];
+            const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
+            Group<AT> nxt;
+            if (len4 > 0) load_group(vals, codes, base, nxt);
+            Acc<AT> acc;
+            for (int g = 0; g < len4; ++g) {
+                const Group<AT> cur = nxt;
+                if (g + 1 < len4) load_group(vals, codes, base + int64_t(g + 1) * (kSlice * kGroup), nxt);
+                const AT p0 = cur.w[0] * AT(s_x[s_hoff[cur.c[0]] + lane]);
+                const AT p1 = cur.w[1] * AT(s_x[s_hoff[cur.c[1]] + lane]);
+                const AT p2 = cur.w[2] * AT(s_x[s_hoff[cur.c[2]] + lane]);
+                const AT p3 = cur.w[3] * AT(s_x[s_hoff[cur.c[3]] + lane]);
+                acc.add((p0 + p1) + (p2 + p3));
+            }
+            row_epilogue<XT, AT>(a, sh, q, lane, v, m, acc.value(), ab_lane, ex_lane);
+        }
     }
     step_finish(a, sh, ab_lane, ex_lane);
 }
@@ -582,6 +778,45 @@ struct RegLaunch {
     }
 };
 
+// Halo variants run with W warps whatever thread count is asked for, and only
+// on grids whose x-lines split into whole 32-voxel blocks.
+template <class VT, class XT, class AT, int W>
+struct HaloLaunch {
+    static int per_sm(int threads)
+    {
+        (void)threads;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_halo<VT, XT, AT, W>, W * 32, 0) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return n;
+    }
+    static cudaError_t launch(const StepArgs &a, int blocks, int threads, cudaStream_t s)
+    {
+        (void)threads;
+        if (a.nx % kSlice != 0) return cudaErrorInvalidValue;
+        step_kernel_halo<VT, XT, AT, W><<<blocks, W * 32, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
+template <class VT, class XT, class AT>
+struct PipeLaunch {
+    static int per_sm(int threads)
+    {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_pipe<VT, XT, AT>, threads, 0);
+        return n;
+    }
+    static cudaError_t launch(const StepArgs &a, int blocks, int threads, cudaStream_t s)
+    {
+        step_kernel_pipe<VT, XT, AT><<<blocks, threads, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
 // Variant table: 0-2 registers path with prefetch depth 1, 2, 3;
 // 3-6 bulk-copy path with stage shapes (G groups, S stages) = (8,3), (4,3),
 // (4,4), (2,6).
@@ -597,6 +832,9 @@ struct Variants {
         case 4: return TmaLaunch<VT, XT, AT, 4, 3>::per_sm(threads);
         case 5: return TmaLaunch<VT, XT, AT, 4, 4>::per_sm(threads);
         case 6: return TmaLaunch<VT, XT, AT, 2, 6>::per_sm(threads);
+        case 7: return HaloLaunch<VT, XT, AT, 13>::per_sm(threads);
+        case 8: return HaloLaunch<VT, XT, AT, 26>::per_sm(threads);
+        case 9: return PipeLaunch<VT, XT, AT>::per_sm(threads);
         }
         return 0;
     }
@@ -610,6 +848,9 @@ struct Variants {
         case 4: return TmaLaunch<VT, XT, AT, 4, 3>::launch(a, blocks, threads, s);
         case 5: return TmaLaunch<VT, XT, AT, 4, 4>::launch(a, blocks, threads, s);
         case 6: return TmaLaunch<VT, XT, AT, 2, 6>::launch(a, blocks, threads, s);
+        case 7: return HaloLaunch<VT, XT, AT, 13>::launch(a, blocks, threads, s);
+        case 8: return HaloLaunch<VT, XT, AT, 26>::launch(a, blocks, threads, s);
+        case 9: return PipeLaunch<VT, XT, AT>::launch(a, blocks, threads, s);
         }
         return cudaErrorInvalidValue;
     }

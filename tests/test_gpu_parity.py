@@ -209,11 +209,15 @@ def test_run_host_matches_step_n(gpu):
     assert rel_l1(det[:, 0, :], da) < 1e-6
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("precision", [I.FP64, I.FP32, I.FP16_ROWSCALE])
 def test_step_variants_agree(gpu, oracle_mod, variant, precision):
-    """Every launch variant of the step computes the same step."""
+    """Every launch variant of the step computes the same step (32 x 14 x 14
+    so the halo variants, which need whole 32-voxel x-runs, apply)."""
     prob, _ = I.three_layers(14, precision=precision)
+    mov = np.repeat(np.asarray(prob.medium_of_voxel)[:, :, :1], 32, axis=2)
+    prob = I.Problem((32, 14, 14), prob.voxel_mm, prob.media, mov, prob.n_outside,
+                     prob.boundary, precision, 1, prob.det_face, 14, 14, "layers_32x14x14")
     rng = np.random.default_rng(9)
     x0 = rng.random(prob.n_states)
     src = I.Source(np.array([prob.state(7, 7, 0, 21)], np.int64), np.ones(1), 0, np.ones(4))
