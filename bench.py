@@ -140,6 +140,23 @@ def algorithmic_bytes(info, precision):
     return b
 
 
+def max_over_ranks(value, device="cuda"):
+    """Max of a per-rank float over all ranks (the timing rule: the slowest
+    rank's time); the value itself on a single rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gnnz(nnz, steps, ms, world_size):
+    """Whole-job throughput: every rank streams its own replica's nnz per step."""
+    return nnz * steps / (ms * 1e-3) / 1e9 * world_size
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -181,14 +198,11 @@ def run_gpu(args):
         ctx.step_n(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
     if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     ms_step = ms / args.steps
-    gnnz = info.nnz * args.steps / (ms * 1e-3) / 1e9 * ws
+    gnnz = whole_job_gnnz(info.nnz, args.steps, ms, ws)
 
     # end to end: per step, source factors host->device and the detector
     # readout device->host, from pinned host buffers, through the C ABI
@@ -205,11 +219,7 @@ def run_gpu(args):
         t0 = time.perf_counter()
         ctx.run_host(sc, det.numpy())
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = max_over_ranks(time.perf_counter() - t0)
         e2e = {"value": round(info.nnz * n / dt / 1e9 * ws, 3), "unit": UNIT,
                "h2d_bytes_per_step": 8, "d2h_bytes_per_step": 8 * info.n_patch,
                "steps": n, "ms_per_step": round(dt * 1e3 / n, 4)}

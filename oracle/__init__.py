@@ -39,21 +39,26 @@ OPEN, MIRROR, FRESNEL = 0, 1, 2
 NDIR = 26
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP when available)."""
+def build(force: bool = False, plant: str | None = None) -> str:
+    """Compile the oracle with gcc (OpenMP when available).  ``plant`` names a
+    planted mistake (PLANT_* in drts_oracle.c) for the pin self-test; it is
+    built into a separate library and never used otherwise."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
+    lib = _LIB if plant is None else os.path.join(_BUILD, f"liboracle_{plant}.so")
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= os.path.getmtime(_SRC)):
+        return lib
     base = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11",
-            _SRC, "-o", _LIB + ".tmp", "-lm"]
+            _SRC, "-o", lib + ".tmp", "-lm"]
+    if plant is not None:
+        base.insert(1, f"-D{plant}")
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        capture_output=True)
     except subprocess.CalledProcessError:
         subprocess.run(base, check=True, capture_output=True)
-    os.replace(_LIB + ".tmp", _LIB)
-    return _LIB
+    os.replace(lib + ".tmp", lib)
+    return lib
 
 
 class _Problem(ctypes.Structure):
@@ -71,29 +76,52 @@ class _Problem(ctypes.Structure):
     ]
 
 
+def _bind(path):
+    lib = ctypes.CDLL(path)
+    P = ctypes.POINTER(_Problem)
+    vp = ctypes.c_void_p
+    lib.orc_assemble.restype = vp
+    lib.orc_assemble.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.orc_csr_info.argtypes = [vp, vp, vp, vp]
+    lib.orc_csr_copy.argtypes = [vp, vp, vp, vp]
+    lib.orc_csr_free.argtypes = [vp]
+    lib.orc_column_info.argtypes = [P, vp, vp, vp, vp]
+    lib.orc_spmv.argtypes = [vp, vp, vp, ctypes.c_int]
+    lib.orc_run.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int64,
+                            ctypes.c_int32, vp, vp, ctypes.c_int64,
+                            ctypes.c_int32, vp, vp, vp, vp, vp,
+                            ctypes.c_int32, vp, vp, ctypes.c_int]
+    lib.orc_raw_stencil.argtypes = [P, ctypes.c_int, vp]
+    lib.orc_fresnel.restype = ctypes.c_double
+    lib.orc_fresnel.argtypes = [ctypes.c_double] * 3
+    lib.orc_direction.argtypes = [ctypes.c_int, vp]
+    return lib
+
+
+class planted:
+    """Context manager: route the module's functions to an oracle built with
+    one planted mistake (pin self-test only)."""
+
+    def __init__(self, name):
+        self.name = name
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self.saved = _lib
+        _lib = _bind(build(plant=self.name))
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.saved
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.POINTER(_Problem)
-            vp = ctypes.c_void_p
-            lib.orc_assemble.restype = vp
-            lib.orc_assemble.argtypes = [P, ctypes.c_int, ctypes.c_int]
-            lib.orc_csr_info.argtypes = [vp, vp, vp, vp]
-            lib.orc_csr_copy.argtypes = [vp, vp, vp, vp]
-            lib.orc_csr_free.argtypes = [vp]
-            lib.orc_column_info.argtypes = [P, vp, vp, vp, vp]
-            lib.orc_spmv.argtypes = [vp, vp, vp, ctypes.c_int]
-            lib.orc_run.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int64,
-                                    ctypes.c_int32, vp, vp, ctypes.c_int64,
-                                    ctypes.c_int32, vp, vp, vp, vp, vp,
-                                    ctypes.c_int32, vp, vp, ctypes.c_int]
-            lib.orc_raw_stencil.argtypes = [P, ctypes.c_int, vp]
-            lib.orc_fresnel.restype = ctypes.c_double
-            lib.orc_fresnel.argtypes = [ctypes.c_double] * 3
-            lib.orc_direction.argtypes = [ctypes.c_int, vp]
-            _lib = lib
+            _lib = _bind(build())
     return _lib
 
 

@@ -38,6 +38,8 @@
 #endif
 
 #define NDIR 26
+/* Planted mistakes (test builds only, -DPLANT_...): the pin tests compile
+ * the oracle with one of these and must fail.  None is set in normal builds. */
 /* A lattice point is a nearest neighbour when its (squared, in units of h)
  * distance is below 1 by this margin: points exactly 2dr away are excluded
  * whatever the rounding of the evaluation (strict inequality of Eq. 18/19). */
@@ -130,6 +132,9 @@ static double hg(double g, double mu)
 double orc_fresnel(double cos_i, double n1, double n2)
 {
     if (n1 == n2) return 0.0;
+#ifdef PLANT_FRESNEL_SWAP
+    { double tmp = n1; n1 = n2; n2 = tmp; }
+#endif
     double sin_i = sqrt(1.0 - cos_i * cos_i);
     double sin_t = n1 / n2 * sin_i;
     if (sin_t >= 1.0) return 1.0;
@@ -150,7 +155,11 @@ static void hg_table(double g, double G[NDIR][NDIR])
             G[n][m] = hg(g, mu);
             sum += G[n][m];
         }
+#ifndef PLANT_HG_UNNORMALISED
         for (int m = 0; m < NDIR; ++m) G[n][m] /= sum;
+#else
+        (void)sum;
+#endif
     }
 }
 
@@ -180,6 +189,9 @@ static int build_stencil(const orc_problem *P, int k, orc_stencil *S)
     double surv_a = exp(-P->mu_a[k] * L);         /* Eq. 8 */
     double surv_s = exp(-P->mu_s[k] * L);         /* Eq. 3 */
     double f0 = surv_s * surv_a;                  /* Eq. 9 */
+#ifdef PLANT_ABSORB_ONCE
+    f0 = surv_s;                                  /* absorption dropped from N0 */
+#endif
     double f1 = (1.0 - surv_s) * surv_a;          /* Eq. 10 */
     double G[NDIR][NDIR];
     hg_table(P->g[k], G);
@@ -191,6 +203,9 @@ static int build_stencil(const orc_problem *P, int k, orc_stencil *S)
         double B[3] = {lam * DIRS[n][0], lam * DIRS[n][1], lam * DIRS[n][2]};
 
         /* Eq. 18: unscattered population to the neighbours of B */
+#ifdef PLANT_DROP_UNSCATTERED
+        f0 = 0.0;
+#endif
         if (f0 > 0.0) {
             double wsum = 0.0, wr[125]; int oo[125][3], cnt = 0;
             for (int z = -2; z <= 2; ++z) for (int y = -2; y <= 2; ++y) for (int x = -2; x <= 2; ++x) {
@@ -209,7 +224,11 @@ static int build_stencil(const orc_problem *P, int k, orc_stencil *S)
         /* Eq. 19: scattered population S_n -> S_m around the segment AB */
         if (f1 > 0.0) {
             for (int m = 0; m < NDIR; ++m) {
+#ifdef PLANT_SEGMENT_SIGN
+                double A[3] = {-lam * DIRS[m][0], -lam * DIRS[m][1], -lam * DIRS[m][2]};
+#else
                 double A[3] = {lam * DIRS[m][0], lam * DIRS[m][1], lam * DIRS[m][2]};
+#endif
                 double wsum = 0.0, wr[125]; int oo[125][3], cnt = 0;
                 for (int z = -2; z <= 2; ++z) for (int y = -2; y <= 2; ++y) for (int x = -2; x <= 2; ++x) {
                     double p[3] = {x, y, z};
@@ -300,7 +319,11 @@ static int orc_fold(const orc_problem *P, const int i[3], int k, const orc_entry
         int face = 2 * a + (t[a] >= N[a] ? 1 : 0);
         exit[face] += w * (1.0 - R);
         w *= R;
+#ifdef PLANT_MIRROR_INDEX
+        t[a] = t[a] < 0 ? 1 : N[a] - 2;
+#else
         t[a] = t[a] < 0 ? 0 : N[a] - 1;
+#endif
         dv[a] = -dv[a];
     }
     if (w == 0.0) return 0;
@@ -413,6 +436,10 @@ orc_csr *orc_assemble(const orc_problem *P, int z0, int z1)
                             }
                             T[nt].row = (int32_t)(((int64_t)out[u].t[1] * P->nx + out[u].t[0]) * NDIR + out[u].m);
                             T[nt].col = col;
+#ifdef PLANT_WRONG_DIRECTION_INDEX
+                            T[nt].row = (int32_t)(((int64_t)out[u].t[1] * P->nx + out[u].t[0]) * NDIR
+                                                  + (NDIR - 1 - out[u].m));
+#endif
                             T[nt].val = out[u].w;
                             ++nt;
                         }

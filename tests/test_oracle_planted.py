@@ -1,0 +1,46 @@
+"""The pins catch plausible mistakes: the oracle is rebuilt with one planted
+mistake at a time (on the CPU) and at least one pin must fail.  Each check
+below is one of the pins of test_oracle_pins.py, run against the mutant."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1611_08536_gb300 import inputs as I
+from tests import test_oracle_pins as pins
+
+PLANTS = ["PLANT_DROP_UNSCATTERED", "PLANT_ABSORB_ONCE", "PLANT_SEGMENT_SIGN",
+          "PLANT_HG_UNNORMALISED", "PLANT_MIRROR_INDEX", "PLANT_FRESNEL_SWAP",
+          "PLANT_WRONG_DIRECTION_INDEX"]
+
+CHECKS = [
+    pins.test_axis_direction_single_target,
+    pins.test_edge_direction_closed_form,
+    pins.test_unscattered_survival_factor,
+    pins.test_perpendicular_scatter_four_points,
+    pins.test_isotropic_kernel_uniform,
+    lambda o: pins.test_interior_column_sums_equal_absorption_survival(o, 10.0, 0.01, 0.9),
+    pins.test_mirror_columns_sum_to_survival_everywhere,
+    pins.test_energy_conservation_mirror_with_interface,
+    pins.test_ballistic_axis_translation_exact,
+    pins.test_fresnel_normal_incidence_at_edge,
+    pins.test_total_internal_reflection_corner_direction,
+    pins.test_interface_transmission_normal_incidence,
+]
+
+
+@pytest.mark.parametrize("plant", PLANTS)
+def test_planted_mistake_is_caught(oracle_mod, plant):
+    failed = []
+    with oracle_mod.planted(plant):
+        for chk in CHECKS:
+            try:
+                chk(oracle_mod)
+            except (AssertionError, ValueError, RuntimeError):
+                failed.append(getattr(chk, "__name__", "lambda"))
+    assert failed, f"no pin caught {plant}"
+
+
+def test_unplanted_oracle_passes_the_same_checks(oracle_mod):
+    for chk in CHECKS:
+        chk(oracle_mod)
