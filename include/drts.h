@@ -204,6 +204,20 @@ drts_status drts_set_launch(drts_ctx *ctx, int32_t blocks_per_sm,
 #define DRTS_STEP_PERSISTENT 1
 drts_status drts_set_step_mode(drts_ctx *ctx, int32_t mode);
 
+/*
+ * Checkpoint / resume.  A checkpoint holds t, the state of every right-hand
+ * side (canonical order, FP64), the ledger and the detector history up to t;
+ * A itself is not stored (it is rebuilt by drts_assemble from the same
+ * problem, deterministically).  drts_checkpoint_size gives the bytes needed,
+ * drts_checkpoint_save writes them into a caller-owned host buffer, and
+ * drts_checkpoint_load restores them into a context assembled from the same
+ * problem (DRTS_EINVAL otherwise).  Stepping on from a restored context
+ * gives the same states as the uninterrupted run.  Synchronous.
+ */
+drts_status drts_checkpoint_size(drts_ctx *ctx, int64_t *bytes);
+drts_status drts_checkpoint_save(drts_ctx *ctx, void *host_buf, int64_t cap);
+drts_status drts_checkpoint_load(drts_ctx *ctx, const void *host_buf, int64_t size);
+
 /* Result of drts_autotune. */
 typedef struct drts_tune_result {
     int32_t variant, threads, blocks_per_sm, rhs_tile;

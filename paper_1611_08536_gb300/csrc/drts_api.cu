@@ -793,6 +793,86 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
     return DRTS_OK;
 }
 
+namespace {
+struct CheckpointHeader {
+    uint64_t magic;                      // "DRTSCKP1"
+    int32_t nx, ny, nz, precision, n_rhs, n_patch;
+    int64_t nnz, t, max_steps;
+};
+constexpr uint64_t kCkpMagic = 0x31504b4353545244ull;
+
+int64_t checkpoint_bytes(const drts_ctx *c)
+{
+    return int64_t(sizeof(CheckpointHeader)) + int64_t(c->R) * (c->n_states * 8 + 4 * 8) +
+           (c->det ? int64_t(c->R) * c->t * c->n_patch * 8 : 0);
+}
+}  // namespace
+
+drts_status drts_checkpoint_size(drts_ctx *c, int64_t *bytes)
+{
+    if (!c || !bytes) return DRTS_EINVAL;
+    *bytes = checkpoint_bytes(c);
+    return DRTS_OK;
+}
+
+drts_status drts_checkpoint_save(drts_ctx *c, void *host_buf, int64_t cap)
+{
+    if (!c || !host_buf) return DRTS_EINVAL;
+    const int64_t need = checkpoint_bytes(c);
+    if (cap < need) return fail(c, DRTS_EINVAL, "checkpoint buffer too small (" + std::to_string(need) + " bytes)");
+    CheckpointHeader h{kCkpMagic, c->prob.nx, c->prob.ny, c->prob.nz, c->prob.precision, c->R, c->n_patch,
+                       c->A.nnz, c->t, c->prob.max_steps};
+    char *p = static_cast<char *>(host_buf);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    for (int r = 0; r < c->R; ++r) {
+        drts_status st = drts_read_state(c, r, reinterpret_cast<double *>(p));
+        if (st != DRTS_OK) return st;
+        p += c->n_states * 8;
+    }
+    cudaError_t e = cudaMemcpy(p, c->ledger, sizeof(double) * 4 * c->R, cudaMemcpyDeviceToHost);
+    p += 4 * 8 * c->R;
+    for (int r = 0; r < c->R && e == cudaSuccess && c->det && c->t > 0; ++r) {
+        e = cudaMemcpy(p, c->det + size_t(r) * c->prob.max_steps * c->n_patch, sizeof(double) * c->t * c->n_patch,
+                       cudaMemcpyDeviceToHost);
+        p += c->t * c->n_patch * 8;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint_save");
+    return DRTS_OK;
+}
+
+drts_status drts_checkpoint_load(drts_ctx *c, const void *host_buf, int64_t size)
+{
+    if (!c || !host_buf || size < int64_t(sizeof(CheckpointHeader))) return DRTS_EINVAL;
+    CheckpointHeader h;
+    std::memcpy(&h, host_buf, sizeof(h));
+    if (h.magic != kCkpMagic) return fail(c, DRTS_EINVAL, "not a DRTS checkpoint");
+    if (h.nx != c->prob.nx || h.ny != c->prob.ny || h.nz != c->prob.nz || h.precision != c->prob.precision ||
+        h.n_rhs != c->R || h.n_patch != c->n_patch || h.nnz != c->A.nnz)
+        return fail(c, DRTS_EINVAL, "checkpoint is of another problem");
+    if (c->det && h.t > c->prob.max_steps) return fail(c, DRTS_EINVAL, "checkpoint time beyond max_steps");
+    const int64_t det_steps = (c->det && h.max_steps > 0) ? h.t : 0;
+    const int64_t need = int64_t(sizeof(h)) + int64_t(c->R) * (c->n_states * 8 + 32) + int64_t(c->R) * det_steps * c->n_patch * 8;
+    if (size < need) return fail(c, DRTS_EINVAL, "checkpoint truncated");
+    c->t = h.t;
+    if (c->t & 1) std::swap(c->x, c->y);      // keep the state buffer parity of an uninterrupted run
+    const char *p = static_cast<const char *>(host_buf) + sizeof(h);
+    for (int r = 0; r < c->R; ++r) {
+        drts_status st = drts_write_state(c, r, reinterpret_cast<const double *>(p));
+        if (st != DRTS_OK) return st;
+        p += c->n_states * 8;
+    }
+    cudaError_t e = cudaMemcpy(c->ledger, p, sizeof(double) * 4 * c->R, cudaMemcpyHostToDevice);
+    p += 32 * c->R;
+    for (int r = 0; r < c->R && e == cudaSuccess && det_steps > 0; ++r) {
+        e = cudaMemcpy(c->det + size_t(r) * c->prob.max_steps * c->n_patch, p, sizeof(double) * det_steps * c->n_patch,
+                       cudaMemcpyHostToDevice);
+        p += det_steps * c->n_patch * 8;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint_load");
+    return DRTS_OK;
+}
+
 drts_status drts_set_step_mode(drts_ctx *c, int32_t mode)
 {
     if (!c) return DRTS_EINVAL;

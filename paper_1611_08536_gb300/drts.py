@@ -104,7 +104,8 @@ SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_dete
            "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_autotune",
            "drts_set_step_mode", "drts_server_create", "drts_server_submit", "drts_server_tick",
            "drts_server_poll", "drts_server_result", "drts_server_release",
-           "drts_server_get_stats", "drts_server_last_error", "drts_server_destroy"]
+           "drts_server_get_stats", "drts_server_last_error", "drts_server_destroy",
+           "drts_checkpoint_size", "drts_checkpoint_save", "drts_checkpoint_load"]
 
 _lib = None
 
@@ -134,6 +135,9 @@ def load(path: str = LIB_PATH):
     lib.drts_set_fault.argtypes = [vp, i32, i64]
     lib.drts_autotune.argtypes = [vp, i32, ctypes.POINTER(TuneResult)]
     lib.drts_set_step_mode.argtypes = [vp, i32]
+    lib.drts_checkpoint_size.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.drts_checkpoint_save.argtypes = [vp, vp, i64]
+    lib.drts_checkpoint_load.argtypes = [vp, vp, i64]
     lib.drts_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     lib.drts_server_submit.argtypes = [vp, ctypes.POINTER(ProblemC), i32, vp, vp, vp, i64, i32, vp,
                                        i64, ctypes.POINTER(i64)]
@@ -280,6 +284,18 @@ class Context:
         r = TuneResult()
         self._check(self._lib.drts_autotune(self._h, int(trial_steps), ctypes.byref(r)))
         return r.as_dict()
+
+    def checkpoint(self) -> bytes:
+        """t, states, ledger and detector history as bytes (A is not stored)."""
+        n = ctypes.c_int64()
+        self._check(self._lib.drts_checkpoint_size(self._h, ctypes.byref(n)))
+        buf = np.empty(n.value, np.uint8)
+        self._check(self._lib.drts_checkpoint_save(self._h, _ptr(buf), n.value))
+        return buf.tobytes()
+
+    def restore(self, data: bytes):
+        buf = np.frombuffer(data, np.uint8).copy()
+        self._check(self._lib.drts_checkpoint_load(self._h, _ptr(buf), buf.size))
 
     def set_step_mode(self, mode):
         """STEP_LAUNCH (one launch per step) or STEP_PERSISTENT (one

@@ -339,3 +339,31 @@ def test_persistent_barrier_times_out_and_recovers(gpu, oracle_mod):
         ctx.step_n(2)
         x2 = ctx.read_state()
     assert rel_l1(x2, oracle_mod.spmv(csr, oracle_mod.spmv(csr, x0))) < 1e-6
+
+
+@pytest.mark.parametrize("precision", [I.FP32, I.FP64])
+def test_checkpoint_resume_equals_uninterrupted(gpu, precision):
+    prob, src = I.three_layers(16, precision=precision)
+    with gpu.Context(prob, max_steps=40) as a:
+        a.set_source(0, src)
+        a.step_n(40)
+        xa = a.read_state()
+        da, la = a.read_detectors()
+    with gpu.Context(prob, max_steps=40) as b:
+        b.set_source(0, src)
+        b.step_n(17)
+        data = b.checkpoint()
+    with gpu.Context(prob, max_steps=40) as c:
+        c.set_source(0, src)
+        c.restore(data)
+        assert c.info().t == 17
+        c.step_n(23)
+        xc = c.read_state()
+        dc, lc = c.read_detectors()
+    assert np.array_equal(xa, xc)                 # the state is deterministic
+    assert rel_l1(dc, da) < 1e-12
+    assert np.allclose(lc, la, rtol=1e-12)
+    other, _ = I.three_layers(12, precision=precision)
+    with gpu.Context(other, max_steps=40) as d:
+        with pytest.raises(gpu.DrtsError):
+            d.restore(data)
