@@ -85,7 +85,16 @@ typedef struct drts_problem {
     int32_t det_face;                /* detector face or DRTS_FACE_NONE */
     int32_t det_nu, det_nv;          /* detector patch grid on that face */
     int64_t max_steps;               /* detector history capacity in steps */
+    int32_t batched_kernel;          /* n_rhs > 1: DRTS_BATCHED_CUDA_CORES or DRTS_BATCHED_TENSOR */
 } drts_problem;
+
+/* Batched step (n_rhs > 1) implementations:
+ *   DRTS_BATCHED_CUDA_CORES  sliced sparse A, one pass per tile of 4..32 rhs;
+ *   DRTS_BATCHED_TENSOR      A as 27 dense 32x32 blocks per voxel (bf16 high and
+ *                            low parts) on the tensor cores, all rhs in one pass
+ *                            (DRTS_FP32 precision, n_rhs <= 64). */
+#define DRTS_BATCHED_CUDA_CORES 0
+#define DRTS_BATCHED_TENSOR 1
 
 typedef struct drts_ctx drts_ctx;
 

@@ -26,6 +26,7 @@ SOURCES = {
     "drts_noalloc.cu": [],
     "drts_batched.cu": [],
     "drts_serve.cu": [],
+    "drts_tensor.cu": [],
 }
 
 

@@ -25,6 +25,10 @@ struct drts_ctx {
     int64_t V = 0, n_states = 0;
     int K = 0, R = 1, n_patch = 0;
     int64_t rhs_stride = 0;              // elements between right-hand sides of a state buffer
+    bool tc = false;                     // tensor-core batched step, state X[v][r][32]
+    int tc_rp = 0;                       // its right-hand-side stride (multiple of 8)
+    void *tc_blocks = nullptr;
+    uint8_t *d_src_voxel = nullptr;      // [V] voxels that receive a source term
     int64_t t = 0;
     std::string err;
     HostTables host;
@@ -125,6 +129,10 @@ drts_status validate(const drts_problem *p)
             return fail(nullptr, DRTS_EINVAL, "detector patch grid must be 1..side");
     }
     if (p->max_steps < 0) return fail(nullptr, DRTS_EINVAL, "max_steps < 0");
+    if (p->batched_kernel != DRTS_BATCHED_CUDA_CORES && p->batched_kernel != DRTS_BATCHED_TENSOR)
+        return fail(nullptr, DRTS_EINVAL, "bad batched_kernel");
+    if (p->batched_kernel == DRTS_BATCHED_TENSOR && p->n_rhs > 1 && p->precision != DRTS_FP32)
+        return fail(nullptr, DRTS_EUNSUPPORTED, "the tensor-core batched step runs FP32 problems");
     return DRTS_OK;
 }
 
@@ -170,6 +178,15 @@ drts_status upload_sources(drts_ctx *c)
         e = cudaMemcpyAsync(c->d_prof_vals, vals.data(), vals.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && !c->src.empty())
         e = cudaMemcpyAsync(c->d_src, c->src.data(), c->src.size() * sizeof(SourceEntry), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && c->d_src_voxel) {
+        e = cudaMemsetAsync(c->d_src_voxel, 0, size_t(c->V), c->stream);
+        std::vector<int64_t> vox;
+        for (const SourceEntry &se : c->src) vox.push_back((int64_t(se.slice) / kDirs) * kSlice + se.lane);
+        std::sort(vox.begin(), vox.end());
+        vox.erase(std::unique(vox.begin(), vox.end()), vox.end());
+        for (size_t q = 0; q < vox.size() && e == cudaSuccess; ++q)
+            e = cudaMemsetAsync(c->d_src_voxel + vox[q], 1, 1, c->stream);
+    }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_prof, c->prof.data(), c->prof.size() * sizeof(SourceProfile), cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "source upload");
@@ -190,6 +207,8 @@ StepArgs make_args(drts_ctx *c)
     a.V = c->V;
     a.R = c->R;
     a.rhs_stride = c->rhs_stride;
+    a.tc_blocks = static_cast<const uint4 *>(c->tc_blocks);
+    a.src_voxel = c->d_src_voxel;
     a.x = c->x; a.y = c->y;
     a.med = c->T.med;
     a.tab.absorb = c->d_absorb;
@@ -217,6 +236,7 @@ StepArgs make_args(drts_ctx *c)
 cudaError_t launch_any_step(drts_ctx *c, const StepArgs &a)
 {
     if (c->R == 1) return launch_step(a, c->variant, c->blocks, c->threads, c->stream);
+    if (c->tc) return launch_tc_step(a, c->tc_rp, c->rhs_tile, c->blocks, c->threads, true, c->stream);
     return launch_batched_step(a, c->R, c->rhs_tile, c->blocks, c->threads, true, c->stream);
 }
 
@@ -225,6 +245,11 @@ int fit_blocks(drts_ctx *c, int threads, int variant, int rhs_tile)
     if (c->R == 1 && variant >= 7 && c->prob.nx % kSlice != 0) return 0;   // halo variants: whole blocks
     if (c->R == 1) return step_default_blocks(c->A.precision, c->R, threads, variant);
     int dev = 0, sms = 0;
+    if (c->tc) {
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        return sms * tc_blocks_per_sm(c->tc_rp, threads, rhs_tile);
+    }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms * batched_blocks_per_sm(c->A.precision, rhs_tile, threads);
@@ -261,6 +286,8 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     c->K = prob->n_media;
     c->R = prob->n_rhs;
     c->rhs_stride = c->n_states + 64;     // the tail keeps padding lanes in bounds
+    c->tc = prob->n_rhs > 1 && prob->batched_kernel == DRTS_BATCHED_TENSOR;
+    c->tc_rp = c->tc ? tc_rhs_stride(c->R) : 0;
     if (prob->det_face != DRTS_FACE_NONE) c->n_patch = prob->det_nu * prob->det_nv;
 
     auto bail = [&](drts_status s) {
@@ -364,14 +391,27 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
         c->special_permille = int(special * 1000 / c->V);
     }
     // state, ledger, detector history, sources
-    c->x_elems = c->rhs_stride * c->R;
+    c->x_elems = c->tc ? c->V * c->tc_rp * 32 + 64 : c->rhs_stride * c->R;
+    if (c->tc) {
+        const size_t bb = size_t(c->V) * 27 * 6144;
+        if ((e = dalloc(c, &c->tc_blocks, bb)) != cudaSuccess) {
+            cuda_fail(c, e, "tensor-core block allocation");
+            return bail(DRTS_ENOMEM);
+        }
+        if ((e = cudaMemsetAsync(c->tc_blocks, 0, bb, c->stream)) != cudaSuccess ||
+            (e = launch_block_fill(T, c->tc_blocks, c->stream)) != cudaSuccess) {
+            cuda_fail(c, e, "tensor-core block fill");
+            return bail(DRTS_ECUDA);
+        }
+    }
     const size_t sb = size_t(c->x_elems) * state_elem_bytes(prob->precision);
     if ((e = dalloc(c, &c->x, sb)) != cudaSuccess || (e = dalloc(c, &c->y, sb)) != cudaSuccess ||
         (e = dalloc(c, &c->ledger, sizeof(double) * 4 * c->R)) != cudaSuccess ||
         (e = dalloc(c, &c->d_src, sizeof(SourceEntry) * kMaxSrc * c->R)) != cudaSuccess ||
         (e = dalloc(c, &c->d_prof, sizeof(SourceProfile) * c->R)) != cudaSuccess ||
         (e = dalloc(c, &c->d_err, sizeof(int))) != cudaSuccess ||
-        (e = dalloc(c, &c->d_bar, 2 * sizeof(unsigned))) != cudaSuccess) {
+        (e = dalloc(c, &c->d_bar, 2 * sizeof(unsigned))) != cudaSuccess ||
+        (e = dalloc(c, &c->d_src_voxel, size_t(c->V))) != cudaSuccess) {
         cuda_fail(c, e, "state allocation");
         return bail(DRTS_ENOMEM);
     }
@@ -386,6 +426,7 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     cudaMemsetAsync(c->y, 0, sb, c->stream);
     cudaMemsetAsync(c->ledger, 0, sizeof(double) * 4 * c->R, c->stream);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    cudaMemsetAsync(c->d_src_voxel, 0, size_t(c->V), c->stream);
     c->prof.assign(c->R, SourceProfile{0, 0, 0, 0, 0});
     c->prof_vals.assign(c->R, std::vector<double>());
     st = upload_sources(c);
@@ -393,6 +434,7 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     c->threads = 256;
     c->variant = 0;
     c->rhs_tile = c->R > 1 ? std::min(16, c->R <= 4 ? 4 : (c->R <= 8 ? 8 : 16)) : 0;
+    if (c->tc) c->rhs_tile = std::min(32, c->tc_rp);
     c->blocks = fit_blocks(c, c->threads, c->variant, c->rhs_tile);
     if (c->blocks < 1) {
         fail(c, DRTS_ECUDA, "step kernel does not fit on an SM");
@@ -509,7 +551,8 @@ drts_status drts_read_detectors(drts_ctx *c, int32_t rhs, int64_t t_begin, int64
         double *tmp = nullptr;
         e = cudaMallocAsync(&tmp, sizeof(double), c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(tmp, 0, sizeof(double), c->stream);
-        if (e == cudaSuccess) e = launch_ledger_sum(rhs_ptr(c, c->x, rhs), c->prob.precision, c->n_states, 1, 0, tmp, c->stream);
+        if (e == cudaSuccess) e = (c->tc ? launch_tc_sum(c->x, c->V, c->tc_rp, rhs, tmp, c->stream)
+                                      : launch_ledger_sum(rhs_ptr(c, c->x, rhs), c->prob.precision, c->n_states, 1, 0, tmp, c->stream));
         if (e == cudaSuccess) e = cudaMemcpyAsync(ledger_out, tmp, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ledger_out + 1, c->ledger + 4 * rhs + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -525,7 +568,9 @@ drts_status drts_read_state(drts_ctx *c, int32_t rhs, double *host_out)
     if (rhs < 0 || rhs >= c->R || !host_out) return fail(c, DRTS_EINVAL, "bad arguments");
     double *tmp = nullptr;
     cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * c->n_states, c->stream);
-    if (e == cudaSuccess) e = launch_to_canonical(rhs_ptr(c, c->x, rhs), c->prob.precision, c->V, 1, 0, tmp, c->stream);
+    if (e == cudaSuccess)
+        e = c->tc ? launch_tc_to_canonical(c->x, c->V, c->tc_rp, rhs, tmp, c->stream)
+                  : launch_to_canonical(rhs_ptr(c, c->x, rhs), c->prob.precision, c->V, 1, 0, tmp, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host_out, tmp, sizeof(double) * c->n_states, cudaMemcpyDeviceToHost, c->stream);
     if (tmp) cudaFreeAsync(tmp, c->stream);
@@ -541,7 +586,9 @@ drts_status drts_write_state(drts_ctx *c, int32_t rhs, const double *host_in)
     cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * c->n_states, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tmp, host_in, sizeof(double) * c->n_states, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = launch_from_canonical(tmp, c->prob.precision, c->V, 1, 0, rhs_ptr(c, c->x, rhs), c->stream);
+    if (e == cudaSuccess)
+        e = c->tc ? launch_tc_from_canonical(tmp, c->V, c->tc_rp, rhs, c->x, c->stream)
+                  : launch_from_canonical(tmp, c->prob.precision, c->V, 1, 0, rhs_ptr(c, c->x, rhs), c->stream);
     if (tmp) cudaFreeAsync(tmp, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "write_state");
     return sync_check(c, "write_state");
@@ -646,6 +693,8 @@ drts_status drts_set_launch(drts_ctx *c, int32_t blocks_per_sm, int32_t threads_
     if (c->R > 1 && rhs_tile != 0) {
         if (rhs_tile != 4 && rhs_tile != 8 && rhs_tile != 16 && rhs_tile != 32)
             return fail(c, DRTS_EINVAL, "rhs_tile must be 4, 8, 16 or 32");
+        if (c->tc && (rhs_tile < 8 || rhs_tile > c->tc_rp))
+            return fail(c, DRTS_EINVAL, "tensor-core rhs_tile must be 8..stride");
         tile = rhs_tile;
     }
     const int threads = threads_per_block ? threads_per_block : 256;
@@ -739,6 +788,7 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
         for (int tile : {4, 8, 16, 32})
         for (int threads : {256, 128}) {
             if (c->R == 1 && tile != 4) continue;             // tile only matters when batched
+            if (c->tc && (tile < 8 || tile > c->tc_rp)) continue;
             if (c->R > 1 && tile > 4 && tile / 2 >= c->R) continue;   // tile far wider than R
             const int fit = fit_blocks(c, threads, var, tile);
             if (fit < 1) continue;
@@ -751,8 +801,9 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
                 a.n_src = 0;
                 const int blocks = bps * sms;
                 auto run = [&]() {
-                    return c->R == 1 ? launch_step(a, var, blocks, threads, c->stream)
-                                     : launch_batched_step(a, c->R, tile, blocks, threads, false, c->stream);
+                    if (c->R == 1) return launch_step(a, var, blocks, threads, c->stream);
+                    if (c->tc) return launch_tc_step(a, c->tc_rp, tile, blocks, threads, false, c->stream);
+                    return launch_batched_step(a, c->R, tile, blocks, threads, false, c->stream);
                 };
                 e = run();          // warm-up
                 if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
@@ -922,6 +973,7 @@ drts_status drts_state_sum_noalloc(drts_ctx *c, int32_t rhs, double *out_device)
 {
     if (!c) return DRTS_EINVAL;
     if (rhs < 0 || rhs >= c->R || !out_device) return fail(c, DRTS_EINVAL, "bad arguments");
+    if (c->tc) return fail(c, DRTS_EUNSUPPORTED, "not available for the tensor-core state layout");
     if (c->n_states > noalloc_max_states())
         return fail(c, DRTS_EINVAL, "state vector of " + std::to_string(c->n_states) +
                                         " states exceeds the static scratch limit of " +

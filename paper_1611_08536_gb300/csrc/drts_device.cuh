@@ -89,6 +89,8 @@ struct StepArgs {
     const double *step_scale;  // [R] host-supplied source factors of this step, or null
     int rhs_tile;
     int *err;                  // set to 1 when a bounded device wait gives up
+    const uint4 *tc_blocks;    // tensor-core batched step: fragment blocks of A
+    const uint8_t *src_voxel;  // [V] 1 where some source entry targets the voxel
     uint32_t spin_limit;       // polls before a device wait gives up
     int64_t fault_skip_chunk;  // tests only: chunk warp 0 never copies (-1 none)
 };
@@ -128,6 +130,16 @@ cudaError_t launch_ledger_sum(const void *x, int precision, int64_t n, int R, in
 int batched_blocks_per_sm(int precision, int rhs_tile, int threads);
 cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int blocks, int threads,
                                 bool functionals, cudaStream_t s);
+
+// tensor-core batched step (drts_tensor.cu); state layout X[v][r][32]
+int tc_rhs_stride(int n_rhs);
+int tc_blocks_per_sm(int Rp, int threads, int tile);
+cudaError_t launch_tc_step(const StepArgs &a, int Rp, int tile, int blocks, int threads, bool functionals,
+                           cudaStream_t s);
+cudaError_t launch_tc_to_canonical(const void *x, int64_t V, int Rp, int r, double *out, cudaStream_t s);
+cudaError_t launch_tc_from_canonical(const double *in, int64_t V, int Rp, int r, void *x, cudaStream_t s);
+cudaError_t launch_tc_sum(const void *x, int64_t V, int Rp, int r, double *out, cudaStream_t s);
+cudaError_t launch_block_fill(const DevTables &T, void *blocks, cudaStream_t s);
 
 // no-allocation state sum (drts_noalloc.cu)
 int64_t noalloc_max_states();

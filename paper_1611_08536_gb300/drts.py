@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, ESTATE, EUNSUPPORTED = range(7)
 OPEN, MIRROR, FRESNEL = 0, 1, 2
 FP64, FP32, FP16_ROWSCALE = 0, 1, 2
 FACE_NONE = -1
+BATCHED_CUDA_CORES, BATCHED_TENSOR = 0, 1
 FAULT_NONE, FAULT_SKIP_COPY, FAULT_SPIN_LIMIT, FAULT_SKIP_BARRIER = 0, 1, 2, 3
 STEP_LAUNCH, STEP_PERSISTENT = 0, 1
 _STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE",
@@ -52,6 +53,7 @@ class ProblemC(ctypes.Structure):
         ("det_face", ctypes.c_int32),
         ("det_nu", ctypes.c_int32), ("det_nv", ctypes.c_int32),
         ("max_steps", ctypes.c_int64),
+        ("batched_kernel", ctypes.c_int32),
     ]
 
 
@@ -172,7 +174,7 @@ def problem_struct(prob, max_steps=0):
     s = ProblemC(nx, ny, nz, float(prob.voxel_mm), len(prob.media), media, _ptr(mov),
                  float(prob.n_outside), int(prob.boundary), int(prob.precision),
                  int(prob.n_rhs), int(prob.det_face), int(prob.det_nu),
-                 int(prob.det_nv), int(max_steps))
+                 int(prob.det_nv), int(max_steps), int(getattr(prob, "batched_kernel", 0)))
     s._keep = (media, mov)
     return s
 

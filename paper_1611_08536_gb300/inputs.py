@@ -61,6 +61,7 @@ class Problem:
     det_nu: int = 16
     det_nv: int = 16
     name: str = ""
+    batched_kernel: int = 0        # 0 CUDA cores, 1 tensor cores (n_rhs > 1)
 
     @property
     def n_voxels(self) -> int:
