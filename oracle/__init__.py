@@ -15,7 +15,14 @@ Parity status of each function (pins are in ``tests/test_oracle_pins.py``):
                       irreducibility.
   * ``column_info``   pinned: Fresnel normal incidence, total internal
                       reflection, ledger closure.
-  * ``run``           pinned: conservation, pure decay, dense matrix powers.
+  * ``run``           pinned: conservation, pure decay, dense matrix powers;
+                      sparse detector rows against the face detector, the
+                      state itself and the ledger.
+  * ``sensor_response`` pinned: delta response, box window vs a library
+                      convolution, linearity.
+  * ``source_column`` pinned: closed-form axis-direction split (1 - f, f),
+                      column sums exp(-mu_a f L), f -> 0 Dirac, f = 1 equals
+                      A's column, mirror conservation.
   * interface / edge folding geometry (Section 4.2 readings): parity
     unpinned beyond the invariants above; the paper prints no numbers for it.
 """
@@ -90,7 +97,14 @@ def _bind(path):
     lib.orc_run.argtypes = [vp, vp, ctypes.c_int64, ctypes.c_int64,
                             ctypes.c_int32, vp, vp, ctypes.c_int64,
                             ctypes.c_int32, vp, vp, vp, vp, vp,
-                            ctypes.c_int32, vp, vp, ctypes.c_int]
+                            ctypes.c_int32, vp, vp,
+                            ctypes.c_int64, vp, vp, vp, ctypes.c_int32, vp,
+                            ctypes.c_int]
+    lib.orc_sensor_response.argtypes = [vp, ctypes.c_int64, ctypes.c_int32,
+                                        ctypes.c_int32, vp, vp]
+    lib.orc_source_column.restype = ctypes.c_int
+    lib.orc_source_column.argtypes = [P, ctypes.c_int64, ctypes.c_double,
+                                      ctypes.c_int32, vp, vp, vp]
     lib.orc_raw_stencil.argtypes = [P, ctypes.c_int, vp]
     lib.orc_fresnel.restype = ctypes.c_double
     lib.orc_fresnel.argtypes = [ctypes.c_double] * 3
@@ -219,12 +233,14 @@ def spmv(csr: CSR, x: np.ndarray, n_threads: int = 0) -> np.ndarray:
 
 
 def run(prob, csr: CSR, n_steps: int, sources, x0=None, t_begin: int = 0,
-        colinfo=None, n_threads: int = 0):
+        colinfo=None, n_threads: int = 0, point=None):
     """Run Eq. 26 for ``n_steps`` from ``x0`` (zeros by default).
 
     ``sources`` = (state_idx int64[], weight float64[], t0, profile float64[]).
     Returns (x, det[n_steps][n_patch], ledger[4] = {sum x, injected,
-    absorbed, exited}).
+    absorbed, exited}).  With ``point`` = (n_det, det int32[], state int64[],
+    weight float64[]) (sparse detector rows F of Eq. 27) a fourth item,
+    pdet[n_steps][n_det], is returned.
     """
     lib = _load()
     P = prob if isinstance(prob, Problem) else Problem(prob)
@@ -240,13 +256,53 @@ def run(prob, csr: CSR, n_steps: int, sources, x0=None, t_begin: int = 0,
     n_patch = max(int(patch.max()) + 1, 1)
     det = np.zeros((n_steps, n_patch), np.float64)
     ledger = np.zeros(4, np.float64)
+    if point is not None:
+        n_fdet = int(point[0])
+        fd = np.ascontiguousarray(point[1], dtype=np.int32)
+        fs = np.ascontiguousarray(point[2], dtype=np.int64)
+        fw = np.ascontiguousarray(point[3], dtype=np.float64)
+        pdet = np.zeros((n_steps, max(n_fdet, 1)), np.float64)
+        fargs = (fd.size, _ptr(fd), _ptr(fs), _ptr(fw), n_fdet, _ptr(pdet))
+    else:
+        fargs = (0, None, None, None, 0, None)
     rc = lib.orc_run(csr._h, _ptr(x), int(t_begin), int(n_steps), st.size,
                      _ptr(st), _ptr(w), int(t0), prof.size, _ptr(prof),
                      _ptr(ab), _ptr(ex), _ptr(ed), _ptr(patch), n_patch,
-                     _ptr(det), _ptr(ledger), int(n_threads))
+                     _ptr(det), _ptr(ledger), *fargs, int(n_threads))
     if rc:
         raise RuntimeError(f"oracle run failed ({rc})")
+    if point is not None:
+        return x, det, ledger, pdet[:, :n_fdet]
     return x, det, ledger
+
+
+def sensor_response(D, w: int, h):
+    """Eq. 27 sensor output M[t][d] = sum_{|t-k| <= w} h[t-k+w] D[k][d]."""
+    lib = _load()
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    if D.ndim != 2 or h.size != 2 * w + 1:
+        raise ValueError("D must be [T][n_det] and h must have 2w+1 taps")
+    M = np.empty_like(D)
+    lib.orc_sensor_response(_ptr(D), D.shape[0], D.shape[1], int(w), _ptr(h), _ptr(M))
+    return M
+
+
+def source_column(prob, state: int, frac: float, cap: int = 4096):
+    """States and values reached at the end of a step by a unit population
+    emitted from ``state`` after the fraction 1 - ``frac`` of the step
+    (Section 4.1 / Eq. 26 source partition).  Returns (states, values,
+    exit_mass)."""
+    lib = _load()
+    P = prob if isinstance(prob, Problem) else Problem(prob)
+    out_s = np.empty(cap, np.int64)
+    out_w = np.empty(cap, np.float64)
+    ex = np.zeros(1, np.float64)
+    cnt = lib.orc_source_column(ctypes.byref(P.s), int(state), float(frac), int(cap),
+                                _ptr(out_s), _ptr(out_w), _ptr(ex))
+    if cnt < 0:
+        raise ValueError(f"oracle: source_column failed ({cnt})")
+    return out_s[:cnt].copy(), out_w[:cnt].copy(), float(ex[0])
 
 
 def raw_stencil(prob, k: int) -> np.ndarray:

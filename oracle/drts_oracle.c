@@ -181,10 +181,10 @@ static void add_entry(orc_stencil *S, int n, int cap, const int o[3], int m, dou
  * Eq. 18 (unscattered, target direction n) and Eq. 19 (scattered into every m),
  * combined by Eq. 21.  Offsets are searched over {-2..2}^3; a target outside
  * {-1,0,1}^3 cannot occur when L <= h and aborts (self-check). */
-static int build_stencil(const orc_problem *P, int k, orc_stencil *S)
+static int build_stencil_frac(const orc_problem *P, int k, double frac, orc_stencil *S)
 {
     const int cap = 27 * NDIR;
-    double lam = min_index(P) / P->n[k];          /* L_k / h */
+    double lam = frac * min_index(P) / P->n[k];   /* path length / h */
     double L = lam * P->h;
     double surv_a = exp(-P->mu_a[k] * L);         /* Eq. 8 */
     double surv_s = exp(-P->mu_s[k] * L);         /* Eq. 3 */
@@ -246,6 +246,12 @@ static int build_stencil(const orc_problem *P, int k, orc_stencil *S)
         }
     }
     return 0;
+}
+
+/* the stencil of a whole step: path L_k = c_k dt */
+static int build_stencil(const orc_problem *P, int k, orc_stencil *S)
+{
+    return build_stencil_frac(P, k, 1.0, S);
 }
 
 static void free_stencil(orc_stencil *S)
@@ -577,21 +583,39 @@ int orc_max_threads(void)
  *     x_{t+1} = A x_t + s(t),  s(t) = sum_e w_e P(t) e_{state_e}
  * P(t) = profile[t - t0] for t0 <= t < t0 + n_t, else 0.
  * ledger[4] = {sum x at the end, injected, absorbed, exited} (accumulated).
+ * Optional sparse detector rows (Eq. 27 with a general F: point detectors,
+ * chosen (voxel, direction) states): fdet[t - t_begin][d] = sum over entries
+ * e with fe_det[e] = d of fe_w[e] x_t[fe_state[e]], in entry order.
  */
 int orc_run(const orc_csr *C, double *x, int64_t t_begin, int64_t n_steps,
             int32_t n_src, const int64_t *src_state, const double *src_w,
             int64_t t0, int32_t n_t, const double *profile,
             const double *absorb, const double *exit_total, const double *exit_det,
             const int32_t *det_patch, int32_t n_patch, double *det, double *ledger,
-            int n_threads)
+            int64_t n_fe, const int32_t *fe_det, const int64_t *fe_state, const double *fe_w,
+            int32_t n_fdet, double *fdet, int n_threads)
 {
     if (C->row0 != 0) return -1;
     int64_t n = C->n_rows;
+    for (int64_t e = 0; e < n_fe; ++e)
+        if (fe_det[e] < 0 || fe_det[e] >= n_fdet || fe_state[e] < 0 || fe_state[e] >= n) return -3;
     double *y = (double *)malloc(sizeof(double) * n);
     if (!y) return -2;
     for (int64_t t = t_begin; t < t_begin + n_steps; ++t) {
         double *dt = det ? det + (t - t_begin) * n_patch : NULL;
         if (dt) for (int p = 0; p < n_patch; ++p) dt[p] = 0.0;
+        /* sparse detector rows F of Eq. 27: one weighted sum of x_t per detector */
+        if (fdet) {
+            double *ft = fdet + (t - t_begin) * n_fdet;
+            for (int32_t d = 0; d < n_fdet; ++d) ft[d] = 0.0;
+            for (int64_t e = 0; e < n_fe; ++e) {
+#ifdef PLANT_POINT_OFF_BY_ONE
+                ft[fe_det[e]] += fe_w[e] * x[fe_state[e] > 0 ? fe_state[e] - 1 : 0];
+#else
+                ft[fe_det[e]] += fe_w[e] * x[fe_state[e]];
+#endif
+            }
+        }
         double ab = 0.0, ex = 0.0;
         for (int64_t s = 0; s < n; ++s) {
             ab += absorb[s] * x[s];
@@ -634,4 +658,92 @@ int orc_raw_stencil(const orc_problem *P, int k, double *W)
         }
     free_stencil(&S);
     return 0;
+}
+
+/*
+ * Sensor response of Eq. 27: a sensor integrates the photons reaching it with
+ * an impulse response h over a window of +-w steps around t,
+ *   M[t][d] = sum over k in [t - w, t + w], 0 <= k < T, of h[t - k + w] D[k][d],
+ * where D[k][d] is the detector readout of step k (the F-weighted photon count
+ * of x_k) and h[j + w] the response at lag j (in steps).
+ */
+void orc_sensor_response(const double *D, int64_t T, int32_t n_det, int32_t w, const double *h,
+                         double *M)
+{
+    for (int64_t t = 0; t < T; ++t)
+        for (int32_t d = 0; d < n_det; ++d) {
+            double acc = 0.0;
+            for (int64_t k = t - w; k <= t + w; ++k) {
+                if (k < 0 || k >= T) continue;
+#ifdef PLANT_SENSOR_LAG_SIGN
+                acc += h[k - t + w] * D[k * n_det + d];
+#else
+                acc += h[t - k + w] * D[k * n_det + d];
+#endif
+            }
+            M[t * n_det + d] = acc;
+        }
+}
+
+/*
+ * Column of the source matrix B of Eq. 26 for photons emitted during a step
+ * (Section 4.1: the source function is partitioned in time within the step).
+ * A unit population leaves the centre of voxel i in direction n and travels
+ * the fraction frac of the step's path L_k before the step ends: the same
+ * absorption / scattering split and lattice weights as the system matrix
+ * (Eq. 18, 19, 21) with the path frac * L_k, folded at the domain edge and at
+ * interfaces the same way.  frac = 1 gives column (i, n) of A; frac -> 0
+ * leaves the unit population in state (i, n).
+ * Writes the distinct target states in ascending order with their values;
+ * returns their count (or -1 on bad input, -2 if cap is too small) and the
+ * mass that leaves the grid in exit_mass.
+ */
+int orc_source_column(const orc_problem *P, int64_t state, double frac, int32_t cap,
+                      int64_t *out_state, double *out_w, double *exit_mass)
+{
+    init_dirs();
+    if (check_problem(P) || frac <= 0.0 || frac > 1.0) return -1;
+    int64_t V = (int64_t)P->nx * P->ny * P->nz;
+    if (state < 0 || state >= V * NDIR) return -1;
+    int64_t v = state / NDIR;
+    int n = (int)(state % NDIR);
+    int i[3] = {(int)(v % P->nx), (int)(v / P->nx % P->ny), (int)(v / ((int64_t)P->nx * P->ny))};
+    int k = P->medium[v];
+    orc_stencil S;
+#ifdef PLANT_SOURCE_FULL_PATH
+    frac = 1.0;
+#endif
+    if (build_stencil_frac(P, k, frac, &S)) return -1;
+    int64_t tcap = 2 * (int64_t)S.count[n] + 1;
+    int64_t *ts = (int64_t *)malloc(sizeof(int64_t) * tcap);
+    double *tw = (double *)malloc(sizeof(double) * tcap);
+    int64_t nt = 0;
+    double ex[6] = {0, 0, 0, 0, 0, 0};
+    for (int q = 0; q < S.count[n]; ++q) {
+        orc_out out[2];
+        int no = orc_fold(P, i, k, &S.e[n][q], out, ex);
+        for (int u = 0; u < no; ++u) {
+            ts[nt] = vox(P, out[u].t[0], out[u].t[1], out[u].t[2]) * NDIR + out[u].m;
+            tw[nt] = out[u].w;
+            ++nt;
+        }
+    }
+    /* insertion sort by target state (stable), then merge equal targets */
+    for (int64_t a = 1; a < nt; ++a) {
+        int64_t sk = ts[a]; double wk = tw[a]; int64_t b = a - 1;
+        while (b >= 0 && ts[b] > sk) { ts[b + 1] = ts[b]; tw[b + 1] = tw[b]; --b; }
+        ts[b + 1] = sk; tw[b + 1] = wk;
+    }
+    int64_t cnt = 0;
+    for (int64_t a = 0; a < nt; ++a) {
+        if (cnt > 0 && ts[a] == out_state[cnt - 1]) { out_w[cnt - 1] += tw[a]; continue; }
+        if (cnt >= cap) { cnt = -2; break; }
+        out_state[cnt] = ts[a];
+        out_w[cnt] = tw[a];
+        ++cnt;
+    }
+    if (exit_mass) *exit_mass = ex[0] + ex[1] + ex[2] + ex[3] + ex[4] + ex[5];
+    free(ts); free(tw);
+    free_stencil(&S);
+    return (int)cnt;
 }

@@ -1,17 +1,20 @@
 """The pins catch plausible mistakes: the oracle is rebuilt with one planted
 mistake at a time (on the CPU) and at least one pin must fail.  Each check
-below is one of the pins of test_oracle_pins.py, run against the mutant."""
+below is one of the pins of test_oracle_pins.py or test_oracle_extensions.py,
+run against the mutant."""
 import math
 
 import numpy as np
 import pytest
 
 from paper_1611_08536_gb300 import inputs as I
+from tests import test_oracle_extensions as ext
 from tests import test_oracle_pins as pins
 
 PLANTS = ["PLANT_DROP_UNSCATTERED", "PLANT_ABSORB_ONCE", "PLANT_SEGMENT_SIGN",
           "PLANT_HG_UNNORMALISED", "PLANT_MIRROR_INDEX", "PLANT_FRESNEL_SWAP",
-          "PLANT_WRONG_DIRECTION_INDEX"]
+          "PLANT_WRONG_DIRECTION_INDEX", "PLANT_POINT_OFF_BY_ONE", "PLANT_SENSOR_LAG_SIGN",
+          "PLANT_SOURCE_FULL_PATH"]
 
 CHECKS = [
     pins.test_axis_direction_single_target,
@@ -26,6 +29,9 @@ CHECKS = [
     pins.test_fresnel_normal_incidence_at_edge,
     pins.test_total_internal_reflection_corner_direction,
     pins.test_interface_transmission_normal_incidence,
+    ext.test_point_row_reads_the_state,
+    ext.test_sensor_delayed_impulse_shifts,
+    lambda o: ext.test_source_column_axis_closed_form(o, 0.25),
 ]
 
 
