@@ -150,6 +150,86 @@ drts_status drts_step_n(drts_ctx *ctx, int64_t n_steps);
 drts_status drts_read_detectors(drts_ctx *ctx, int32_t rhs, int64_t t_begin,
                                 int64_t t_end, double *host_out, double *ledger_out);
 
+/*
+ * Point detectors: Eq. 27 with a general sparse F (Section 4.2 places a
+ * sensor anywhere in the volume; a point detector reads chosen
+ * (voxel, direction) states).  Detector d of rhs r reads, at every step t,
+ *   pdet[r][t][d] = sum over entries e with det[e] = d of weight[e] * x_t[state_idx[e]]
+ * from x(t), the state the step starts from (the face detector's timing).
+ * n_entries (state, detector, weight) triples, host arrays, copied; entries of
+ * one detector are summed in their given order with a fixed reduction (the
+ * readout is deterministic).  0 <= n_det <= 65535; n_det = 0 removes them.
+ * The history holds max_steps steps (DRTS_ESTATE when max_steps is 0) and
+ * is cleared by this call; steps before it read 0.  While point detectors
+ * are set, t + n_steps may not exceed max_steps.  Works in every step mode
+ * and for every right-hand side.  Synchronises.
+ */
+drts_status drts_set_point_detectors(drts_ctx *ctx, int32_t n_det, int64_t n_entries,
+                                     const int32_t *det, const int64_t *state_idx,
+                                     const double *weight);
+
+/* Copy the point-detector history of rhs for steps [t_begin, t_end) to
+ * host_out ([t][n_det] FP64, caller-owned).  Synchronises.  DRTS_ESTATE if
+ * no point detectors are set. */
+drts_status drts_read_point_detectors(drts_ctx *ctx, int32_t rhs, int64_t t_begin,
+                                      int64_t t_end, double *host_out);
+
+/*
+ * Sensor response of Eq. 27: a sensor integrates the photons it receives
+ * with an impulse response h over a window of +-w steps,
+ *   M[t][d] = sum over k in [t - w, t + w], 0 <= k < t_rec, of h[t - k + w] D[k][d],
+ * where D is the recorded readout of rhs (which = DRTS_SENSOR_FACE: the face
+ * patches, DRTS_SENSOR_POINT: the point detectors), h[j + w] the response at
+ * lag j steps (2w+1 host FP64 taps, 0 <= w <= 2^20) and t_rec = min(t,
+ * max_steps) the steps recorded so far.  Writes M for t in [t_begin, t_end)
+ * (t_end <= t_rec) to host_out ([t][d] FP64).  Products and sums are rounded
+ * separately in k order.  Synchronises.
+ */
+#define DRTS_SENSOR_FACE 0
+#define DRTS_SENSOR_POINT 1
+drts_status drts_sensor_response(drts_ctx *ctx, int32_t rhs, int32_t which, int64_t t_begin,
+                                 int64_t t_end, int32_t w, const double *h, double *host_out);
+
+/*
+ * Source partition within a step (Section 4.1: for accuracy the source
+ * function is sampled in time intervals of dr/c, shorter than the step).
+ *
+ * drts_source_column: where a unit population is at the end of a step when
+ * it leaves the centre of voxel i in direction n (state_idx = i*26 + n) and
+ * travels only the fraction frac (0 < frac <= 1) of the step's path L_k:
+ * Eq. 18/19/21 evaluated for the path frac * L_k, folded at the domain edge
+ * and at interfaces as the system matrix is.  frac = 1 is column state_idx
+ * of A; as frac -> 0 the population stays in state_idx.  Writes the target
+ * states (ascending) and values to host arrays of capacity cap; *count
+ * receives the number of targets (DRTS_EINVAL, with *count set, if it
+ * exceeds cap) and, if exit_mass is not NULL, *exit_mass the mass that
+ * leaves the grid.  FP64.  Synchronises.
+ *
+ * drts_inject_source_substeps: sub-step source of right-hand side rhs.
+ * Entry e (state_idx[e], weight[e]) emits weight[e] * profile[(t - t0) *
+ * n_sub + j] in sub-interval j of step t (0 <= j < n_sub, t0 <= t < t0 +
+ * n_t).  Sub-interval j is taken at its midpoint, so its population travels
+ * frac_j = 1 - (j + 1/2) / n_sub of the step and lands in x(t+1) as
+ * drts_source_column(state_idx[e], frac_j).  1 <= n_sub <= 64; the
+ * paper's dr/c partition is drts_substep_count's n_sub.  0 <= n_entries <=
+ * 64; n_entries = 0 removes rhs's sub-step source.
+ * Replaces any earlier sub-step source of rhs and adds to the plain source
+ * of drts_inject_source.  The ledger's injected mass counts what lands in
+ * the state.  Not available in the persistent step mode nor with
+ * drts_run_host (DRTS_EUNSUPPORTED).  Synchronises.
+ */
+/* drts_substep_count: the number of sub-intervals of length dr/c in one step
+ * of the medium of state_idx's voxel: its path L_k in half voxels (2 dr =
+ * h), rounded up (2 when L_k = h). */
+drts_status drts_substep_count(drts_ctx *ctx, int64_t state_idx, int32_t *n_sub);
+drts_status drts_source_column(drts_ctx *ctx, int64_t state_idx, double frac, int32_t cap,
+                               int64_t *out_state, double *out_value, int32_t *count,
+                               double *exit_mass);
+drts_status drts_inject_source_substeps(drts_ctx *ctx, int32_t rhs, int32_t n_entries,
+                                        const int64_t *state_idx, const double *weight,
+                                        int32_t n_sub, int64_t t0, int32_t n_t,
+                                        const double *profile);
+
 /* Copy x(t) of rhs to host_out (canonical order, n_states FP64). Synchronises. */
 drts_status drts_read_state(drts_ctx *ctx, int32_t rhs, double *host_out);
 
@@ -193,9 +273,12 @@ drts_status drts_get_info(const drts_ctx *ctx, drts_info *out);
  * shapes (groups, stages) = (8,3), (4,3), (4,4), (2,6); 7-8 = state halo of
  * each 32-voxel block staged in shared memory, 13 or 26 warps, grids with nx
  * a multiple of 32 only; 9 = registers path with the matrix stream two groups
- * ahead and the x gathers of the next group in flight).  All variants
- * compute the same step; they differ only in speed.  DRTS_EINVAL if the
- * shape does not fit on an SM. */
+ * ahead and the x gathers of the next group in flight).  For a batched
+ * context on the CUDA cores the variant is the slice order: 0 = warps
+ * stride over all slices, 1 = block-major (one CTA works through all 26
+ * direction slices of a voxel block); the tensor-core form has variant 0
+ * only.  All variants compute the same step; they differ only in speed.
+ * DRTS_EINVAL if the shape does not fit on an SM or the variant is unknown. */
 drts_status drts_set_launch(drts_ctx *ctx, int32_t blocks_per_sm,
                             int32_t threads_per_block, int32_t rhs_tile,
                             int32_t variant);
@@ -215,13 +298,15 @@ drts_status drts_set_step_mode(drts_ctx *ctx, int32_t mode);
 
 /*
  * Checkpoint / resume.  A checkpoint holds t, the state of every right-hand
- * side (canonical order, FP64), the ledger and the detector history up to t;
- * A itself is not stored (it is rebuilt by drts_assemble from the same
- * problem, deterministically).  drts_checkpoint_size gives the bytes needed,
- * drts_checkpoint_save writes them into a caller-owned host buffer, and
- * drts_checkpoint_load restores them into a context assembled from the same
- * problem (DRTS_EINVAL otherwise).  Stepping on from a restored context
- * gives the same states as the uninterrupted run.  Synchronous.
+ * side (canonical order, FP64), the ledger and the face- and point-detector
+ * histories up to t; A itself is not stored (it is rebuilt by drts_assemble
+ * from the same problem, deterministically) and neither are the sources and
+ * point-detector definitions (set them again before loading).
+ * drts_checkpoint_size gives the bytes needed, drts_checkpoint_save writes
+ * them into a caller-owned host buffer, and drts_checkpoint_load restores
+ * them into a context assembled from the same problem with the same number
+ * of point detectors (DRTS_EINVAL otherwise).  Stepping on from a restored
+ * context gives the same states as the uninterrupted run.  Synchronous.
  */
 drts_status drts_checkpoint_size(drts_ctx *ctx, int64_t *bytes);
 drts_status drts_checkpoint_save(drts_ctx *ctx, void *host_buf, int64_t cap);

@@ -27,6 +27,7 @@ SOURCES = {
     "drts_batched.cu": [],
     "drts_serve.cu": [],
     "drts_tensor.cu": [],
+    "drts_functionals.cu": [],
 }
 
 

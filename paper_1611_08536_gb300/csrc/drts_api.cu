@@ -57,6 +57,30 @@ struct drts_ctx {
     int persist_blocks = 0;
     unsigned *d_bar = nullptr;           // grid barrier of the persistent kernel
     int special_permille = 0;
+    std::vector<drts_medium> media;      // the problem's media (partial-path tables)
+    uint8_t *d_med = nullptr;            // [V] medium of each voxel (device)
+    std::vector<uint8_t> med_host;       // [V] medium of each voxel (host copy)
+    // point detectors (sparse detector rows F of Eq. 27)
+    int n_pdet = 0;
+    int64_t *d_pdet_off = nullptr, *d_pdet_state = nullptr;
+    double *d_pdet_w = nullptr, *d_pdet_hist = nullptr;
+    // sub-step sources, per rhs: entries (state, weight), n_sub, t0, n_t, profile [n_t][n_sub]
+    struct SubstepSource {
+        std::vector<int64_t> state;
+        std::vector<double> weight;
+        int n_sub = 0;
+        int64_t t0 = 0;
+        int32_t n_t = 0;
+        std::vector<double> profile;
+        std::vector<std::vector<std::pair<int64_t, double>>> columns;   // [entry * n_sub + j]
+    };
+    std::vector<SubstepSource> substep;  // [R]
+    int n_bulk_groups = 0;
+    BulkGroup *d_bulk_groups = nullptr;
+    int32_t *d_bulk_rhs_off = nullptr;
+    BulkEntry *d_bulk_entries = nullptr;
+    SourceProfile *d_bulk_prof = nullptr;
+    double *d_bulk_prof_vals = nullptr;
 };
 
 namespace {
@@ -230,14 +254,33 @@ StepArgs make_args(drts_ctx *c)
     a.err = c->d_err;
     a.spin_limit = c->spin_limit;
     a.fault_skip_chunk = c->fault_skip_chunk;
+    a.tc_rp = c->tc ? c->tc_rp : 0;
+    a.pd.n_det = c->n_pdet;
+    a.pd.off = c->d_pdet_off;
+    a.pd.state = c->d_pdet_state;
+    a.pd.w = c->d_pdet_w;
+    a.pd.hist = (c->n_pdet > 0 && c->t < c->prob.max_steps) ? c->d_pdet_hist : nullptr;
+    a.pd.stride_r = c->prob.max_steps * c->n_pdet;
+    a.bulk.n_groups = c->n_bulk_groups;
+    a.bulk.groups = c->d_bulk_groups;
+    a.bulk.rhs_off = c->d_bulk_rhs_off;
+    a.bulk.entries = c->d_bulk_entries;
+    a.bulk.prof = c->d_bulk_prof;
+    a.bulk.prof_vals = c->d_bulk_prof_vals;
     return a;
 }
 
+// One step from x(t): point detectors of x(t), the product with the fused
+// source / face-detector / ledger terms, then the sub-step sources.
 cudaError_t launch_any_step(drts_ctx *c, const StepArgs &a)
 {
-    if (c->R == 1) return launch_step(a, c->variant, c->blocks, c->threads, c->stream);
-    if (c->tc) return launch_tc_step(a, c->tc_rp, c->rhs_tile, c->blocks, c->threads, true, c->stream);
-    return launch_batched_step(a, c->R, c->rhs_tile, c->blocks, c->threads, true, c->stream);
+    cudaError_t e = launch_point_detectors(a, c->stream);
+    if (e != cudaSuccess) return e;
+    if (c->R == 1) e = launch_step(a, c->variant, c->blocks, c->threads, c->stream);
+    else if (c->tc) e = launch_tc_step(a, c->tc_rp, c->rhs_tile, c->blocks, c->threads, true, c->stream);
+    else e = launch_batched_step(a, c->R, c->rhs_tile, c->variant, c->blocks, c->threads, true, c->stream);
+    if (e != cudaSuccess) return e;
+    return launch_bulk_sources(a, c->stream);
 }
 
 int fit_blocks(drts_ctx *c, int threads, int variant, int rhs_tile)
@@ -252,7 +295,7 @@ int fit_blocks(drts_ctx *c, int threads, int variant, int rhs_tile)
     }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms * batched_blocks_per_sm(c->A.precision, rhs_tile, threads);
+    return sms * batched_blocks_per_sm(c->A.precision, rhs_tile, threads, variant);
 }
 
 }  // namespace
@@ -280,6 +323,8 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     c->prob = *prob;
     c->prob.media = nullptr;
     c->prob.medium_of_voxel = nullptr;
+    c->media.assign(prob->media, prob->media + prob->n_media);
+    c->substep.assign(size_t(prob->n_rhs), drts_ctx::SubstepSource());
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->V = int64_t(prob->nx) * prob->ny * prob->nz;
     c->n_states = c->V * kDirs;
@@ -328,6 +373,8 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     T.V = c->V; T.K = c->K;
     T.W = dW; T.tmpl_off = dto; T.tmpl_n = dtn; T.tmpl_val = dtv;
     T.r_edge = dre; T.r_int = dri; T.nref = dnr; T.med = dmed; T.plain = dplain;
+    c->d_med = dmed;
+    c->med_host = med;
 
     // slices and counts
     SlicedMatrix &A = c->A;
@@ -433,7 +480,24 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     if (st != DRTS_OK) return bail(st);
     c->threads = 256;
     c->variant = 0;
-    c->rhs_tile = c->R > 1 ? std::min(16, c->R <= 4 ? 4 : (c->R <= 8 ? 8 : 16)) : 0;
+    c->rhs_tile = 0;
+    if (c->R > 1 && !c->tc) {
+        // measured defaults of the CUDA-core batched step (GB300, FP32): 8
+        // right-hand sides per pass while an x-y plane is small; above that
+        // wider tiles lose their x lines from L1 and 4 per pass wins, with
+        // 128-thread blocks up to ~88^2 per plane and block-major slice
+        // order beyond (the autotuner refines this per problem)
+        const int64_t plane = int64_t(prob->nx) * prob->ny;
+        if (plane <= 64 * 64) {
+            c->rhs_tile = c->R <= 4 ? 4 : 8;
+        } else if (plane <= 88 * 88) {
+            c->rhs_tile = 4;
+            c->threads = 128;
+        } else {
+            c->rhs_tile = 4;
+            c->variant = 1;
+        }
+    }
     if (c->tc) c->rhs_tile = std::min(32, c->tc_rp);
     c->blocks = fit_blocks(c, c->threads, c->variant, c->rhs_tile);
     if (c->blocks < 1) {
@@ -482,9 +546,11 @@ drts_status drts_step_n(drts_ctx *c, int64_t n_steps)
 {
     if (!c) return DRTS_EINVAL;
     if (n_steps < 0) return fail(c, DRTS_EINVAL, "n_steps < 0");
-    if (c->det && c->t + n_steps > c->prob.max_steps)
+    if ((c->det || c->n_pdet > 0) && c->t + n_steps > c->prob.max_steps)
         return fail(c, DRTS_EINVAL, "t + n_steps exceeds max_steps");
     if (c->step_mode == DRTS_STEP_PERSISTENT && n_steps > 0) {
+        if (c->n_bulk_groups > 0)
+            return fail(c, DRTS_EUNSUPPORTED, "sub-step sources need the launch step mode");
         StepArgs a = make_args(c);
         cudaError_t e = launch_persistent(a, c->y, n_steps, c->det, c->prob.max_steps, c->d_bar,
                                           c->fault_skip_barrier, c->persist_blocks, c->threads, c->stream);
@@ -507,7 +573,9 @@ drts_status drts_run_host(drts_ctx *c, int64_t n_steps, const double *scale, dou
 {
     if (!c) return DRTS_EINVAL;
     if (n_steps < 0 || !scale) return fail(c, DRTS_EINVAL, "bad arguments");
-    if (c->det && c->t + n_steps > c->prob.max_steps)
+    if (c->n_bulk_groups > 0)
+        return fail(c, DRTS_EUNSUPPORTED, "run_host scales the plain sources; sub-step sources are set");
+    if ((c->det || c->n_pdet > 0) && c->t + n_steps > c->prob.max_steps)
         return fail(c, DRTS_EINVAL, "t + n_steps exceeds max_steps");
     if (n_steps == 0) return DRTS_OK;
     double *d_scale = nullptr;
@@ -688,7 +756,8 @@ drts_status drts_set_launch(drts_ctx *c, int32_t blocks_per_sm, int32_t threads_
     if (threads_per_block != 0 && (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32))
         return fail(c, DRTS_EINVAL, "threads_per_block must be a multiple of 32 in 32..256");
     if (blocks_per_sm < 0 || blocks_per_sm > 64) return fail(c, DRTS_EINVAL, "blocks_per_sm must be 0..64");
-    if (variant < -1 || variant >= kStepVariants) return fail(c, DRTS_EINVAL, "unknown step variant");
+    const int n_variants = c->R == 1 ? kStepVariants : (c->tc ? 1 : kBatchedOrders);
+    if (variant < -1 || variant >= n_variants) return fail(c, DRTS_EINVAL, "unknown step variant");
     int tile = c->rhs_tile;
     if (c->R > 1 && rhs_tile != 0) {
         if (rhs_tile != 4 && rhs_tile != 8 && rhs_tile != 16 && rhs_tile != 32)
@@ -783,7 +852,7 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
     drts_tune_result best{};
     best.ms_per_step = 1e30;
     int tried = 0;
-    const int n_var = c->R == 1 ? kStepVariants : 1;
+    const int n_var = c->R == 1 ? kStepVariants : (c->tc ? 1 : kBatchedOrders);
     for (int var = 0; var < n_var && e == cudaSuccess; ++var)
         for (int tile : {4, 8, 16, 32})
         for (int threads : {256, 128}) {
@@ -803,7 +872,7 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
                 auto run = [&]() {
                     if (c->R == 1) return launch_step(a, var, blocks, threads, c->stream);
                     if (c->tc) return launch_tc_step(a, c->tc_rp, tile, blocks, threads, false, c->stream);
-                    return launch_batched_step(a, c->R, tile, blocks, threads, false, c->stream);
+                    return launch_batched_step(a, c->R, tile, var, blocks, threads, false, c->stream);
                 };
                 e = run();          // warm-up
                 if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
@@ -846,16 +915,18 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
 
 namespace {
 struct CheckpointHeader {
-    uint64_t magic;                      // "DRTSCKP1"
+    uint64_t magic;                      // "DRTSCKP2"
     int32_t nx, ny, nz, precision, n_rhs, n_patch;
     int64_t nnz, t, max_steps;
+    int32_t n_pdet, pad;
 };
-constexpr uint64_t kCkpMagic = 0x31504b4353545244ull;
+constexpr uint64_t kCkpMagic = 0x32504b4353545244ull;
 
 int64_t checkpoint_bytes(const drts_ctx *c)
 {
     return int64_t(sizeof(CheckpointHeader)) + int64_t(c->R) * (c->n_states * 8 + 4 * 8) +
-           (c->det ? int64_t(c->R) * c->t * c->n_patch * 8 : 0);
+           (c->det ? int64_t(c->R) * c->t * c->n_patch * 8 : 0) +
+           (c->n_pdet > 0 ? int64_t(c->R) * c->t * c->n_pdet * 8 : 0);
 }
 }  // namespace
 
@@ -872,7 +943,7 @@ drts_status drts_checkpoint_save(drts_ctx *c, void *host_buf, int64_t cap)
     const int64_t need = checkpoint_bytes(c);
     if (cap < need) return fail(c, DRTS_EINVAL, "checkpoint buffer too small (" + std::to_string(need) + " bytes)");
     CheckpointHeader h{kCkpMagic, c->prob.nx, c->prob.ny, c->prob.nz, c->prob.precision, c->R, c->n_patch,
-                       c->A.nnz, c->t, c->prob.max_steps};
+                       c->A.nnz, c->t, c->prob.max_steps, c->n_pdet, 0};
     char *p = static_cast<char *>(host_buf);
     std::memcpy(p, &h, sizeof(h));
     p += sizeof(h);
@@ -888,6 +959,11 @@ drts_status drts_checkpoint_save(drts_ctx *c, void *host_buf, int64_t cap)
                        cudaMemcpyDeviceToHost);
         p += c->t * c->n_patch * 8;
     }
+    for (int r = 0; r < c->R && e == cudaSuccess && c->n_pdet > 0 && c->t > 0; ++r) {
+        e = cudaMemcpy(p, c->d_pdet_hist + size_t(r) * c->prob.max_steps * c->n_pdet,
+                       sizeof(double) * c->t * c->n_pdet, cudaMemcpyDeviceToHost);
+        p += c->t * c->n_pdet * 8;
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint_save");
     return DRTS_OK;
 }
@@ -901,9 +977,14 @@ drts_status drts_checkpoint_load(drts_ctx *c, const void *host_buf, int64_t size
     if (h.nx != c->prob.nx || h.ny != c->prob.ny || h.nz != c->prob.nz || h.precision != c->prob.precision ||
         h.n_rhs != c->R || h.n_patch != c->n_patch || h.nnz != c->A.nnz)
         return fail(c, DRTS_EINVAL, "checkpoint is of another problem");
-    if (c->det && h.t > c->prob.max_steps) return fail(c, DRTS_EINVAL, "checkpoint time beyond max_steps");
+    if (h.n_pdet != c->n_pdet)
+        return fail(c, DRTS_EINVAL, "checkpoint has another set of point detectors (set them before loading)");
+    if ((c->det || c->n_pdet > 0) && h.t > c->prob.max_steps)
+        return fail(c, DRTS_EINVAL, "checkpoint time beyond max_steps");
     const int64_t det_steps = (c->det && h.max_steps > 0) ? h.t : 0;
-    const int64_t need = int64_t(sizeof(h)) + int64_t(c->R) * (c->n_states * 8 + 32) + int64_t(c->R) * det_steps * c->n_patch * 8;
+    const int64_t pdet_steps = c->n_pdet > 0 ? h.t : 0;
+    const int64_t need = int64_t(sizeof(h)) + int64_t(c->R) * (c->n_states * 8 + 32) +
+                         int64_t(c->R) * det_steps * c->n_patch * 8 + int64_t(c->R) * pdet_steps * c->n_pdet * 8;
     if (size < need) return fail(c, DRTS_EINVAL, "checkpoint truncated");
     c->t = h.t;
     if (c->t & 1) std::swap(c->x, c->y);      // keep the state buffer parity of an uninterrupted run
@@ -920,6 +1001,11 @@ drts_status drts_checkpoint_load(drts_ctx *c, const void *host_buf, int64_t size
                        cudaMemcpyHostToDevice);
         p += det_steps * c->n_patch * 8;
     }
+    for (int r = 0; r < c->R && e == cudaSuccess && pdet_steps > 0; ++r) {
+        e = cudaMemcpy(c->d_pdet_hist + size_t(r) * c->prob.max_steps * c->n_pdet, p,
+                       sizeof(double) * pdet_steps * c->n_pdet, cudaMemcpyHostToDevice);
+        p += pdet_steps * c->n_pdet * 8;
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint_load");
     return DRTS_OK;
 }
@@ -933,6 +1019,7 @@ drts_status drts_set_step_mode(drts_ctx *c, int32_t mode)
     }
     if (mode == DRTS_STEP_PERSISTENT) {
         if (c->R != 1) return fail(c, DRTS_EUNSUPPORTED, "persistent mode steps one right-hand side");
+        if (c->n_bulk_groups > 0) return fail(c, DRTS_EUNSUPPORTED, "sub-step sources need the launch step mode");
         const int blocks = persistent_blocks(c->prob.precision, c->threads);
         if (blocks < 1) return fail(c, DRTS_EUNSUPPORTED, "cooperative launch not available");
         c->persist_blocks = blocks;
@@ -982,6 +1069,269 @@ drts_status drts_state_sum_noalloc(drts_ctx *c, int32_t rhs, double *out_device)
                                              c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "state_sum_noalloc");
     return DRTS_OK;
+}
+
+namespace {
+
+// Column `state` of the matrix built for the path fraction frac (Eq. 18/19/21
+// with the path frac * L_k, folded like the system matrix), as (target
+// state, value) pairs in ascending state order, and the mass that leaves the
+// grid.  Synchronous.
+drts_status source_column_host(drts_ctx *c, int64_t state, double frac,
+                               std::vector<std::pair<int64_t, double>> &col, double *exit_mass)
+{
+    HostTables tf;
+    drts_problem p = c->prob;
+    p.media = c->media.data();
+    const std::string terr = build_host_tables(p, tf, frac);
+    if (!terr.empty()) return fail(c, DRTS_EINVAL, terr);
+    double *dW = nullptr, *dout = nullptr;
+    std::vector<double> out(size_t(kOffs) * kDirs, 0.0);
+    cudaError_t e = cudaMalloc(&dW, tf.W.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dout, out.size() * sizeof(double));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dW, tf.W.data(), tf.W.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    DevTables Tf = c->T;
+    Tf.W = dW;
+    if (e == cudaSuccess) e = launch_source_column(Tf, state, dout, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out.data(), dout, out.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (dW) cudaFree(dW);
+    if (dout) cudaFree(dout);
+    if (e != cudaSuccess) return cuda_fail(c, e, "source column");
+    const int nx = c->prob.nx, ny = c->prob.ny, nz = c->prob.nz;
+    const int64_t v = state / kDirs;
+    const int n = int(state % kDirs);
+    const int x = int(v % nx), y = int(v / nx % ny), z = int(v / (int64_t(nx) * ny));
+    col.clear();
+    for (int g = 0; g < kOffs * kDirs; ++g) {
+        if (!(out[g] > 0.0)) continue;
+        const int d = g / kDirs, m = g % kDirs;
+        const int64_t vj = (int64_t(z + d / 9 - 1) * ny + (y + d / 3 % 3 - 1)) * nx + (x + d % 3 - 1);
+        col.emplace_back(vj * kDirs + m, out[g]);
+    }
+    if (exit_mass) {
+        const int bx = x == 0 ? 0 : (x == nx - 1 ? 2 : 1);
+        const int by = y == 0 ? 0 : (y == ny - 1 ? 2 : 1);
+        const int bz = z == 0 ? 0 : (z == nz - 1 ? 2 : 1);
+        const int k = c->med_host[size_t(v)];
+        *exit_mass = tf.exit_total[(size_t(k) * 27 + bz * 9 + by * 3 + bx) * kDirs + n];
+    }
+    return DRTS_OK;
+}
+
+// Flatten every rhs's sub-step source into (state, rhs) groups and upload.
+drts_status upload_bulk(drts_ctx *c)
+{
+    std::vector<BulkGroup> groups;
+    std::vector<int32_t> rhs_off(size_t(c->R) + 1, 0);
+    std::vector<BulkEntry> entries;
+    std::vector<SourceProfile> prof;
+    std::vector<double> vals;
+    struct Trip { int64_t state; double w; int32_t prof; };
+    for (int r = 0; r < c->R; ++r) {
+        rhs_off[r] = int32_t(groups.size());
+        const drts_ctx::SubstepSource &ss = c->substep[r];
+        if (ss.state.empty() || ss.n_t == 0) continue;
+        const int32_t prof0 = int32_t(prof.size());
+        for (int j = 0; j < ss.n_sub; ++j) {
+            prof.push_back(SourceProfile{ss.t0, ss.n_t, int32_t(vals.size()), 0, 0});
+            for (int32_t t = 0; t < ss.n_t; ++t) vals.push_back(ss.profile[size_t(t) * ss.n_sub + j]);
+        }
+        std::vector<Trip> tr;
+        for (size_t i = 0; i < ss.state.size(); ++i)
+            for (int j = 0; j < ss.n_sub; ++j)
+                for (const auto &pv : ss.columns[i * ss.n_sub + j])
+                    tr.push_back(Trip{pv.first, ss.weight[i] * pv.second, prof0 + j});
+        std::stable_sort(tr.begin(), tr.end(), [](const Trip &a, const Trip &b) { return a.state < b.state; });
+        for (size_t q = 0; q < tr.size();) {
+            BulkGroup g{tr[q].state, r, int32_t(entries.size()), 0, 0};
+            for (; q < tr.size() && tr[q].state == g.state; ++q) {
+                entries.push_back(BulkEntry{tr[q].w, tr[q].prof, 0});
+                ++g.count;
+            }
+            groups.push_back(g);
+        }
+    }
+    rhs_off[c->R] = int32_t(groups.size());
+    if (entries.size() > size_t(1) << 30) return fail(c, DRTS_EINVAL, "too many sub-step source entries");
+    cudaError_t e = cudaSuccess;
+    if (!groups.empty()) {
+        if ((e = upload(c, &c->d_bulk_groups, groups)) != cudaSuccess ||
+            (e = upload(c, &c->d_bulk_rhs_off, rhs_off)) != cudaSuccess ||
+            (e = upload(c, &c->d_bulk_entries, entries)) != cudaSuccess ||
+            (e = upload(c, &c->d_bulk_prof, prof)) != cudaSuccess ||
+            (e = upload(c, &c->d_bulk_prof_vals, vals)) != cudaSuccess)
+            return cuda_fail(c, e, "sub-step source upload");
+    }
+    c->n_bulk_groups = int(groups.size());
+    return sync_check(c, "sub-step source upload");
+}
+
+}  // namespace
+
+drts_status drts_source_column(drts_ctx *c, int64_t state_idx, double frac, int32_t cap, int64_t *out_state,
+                               double *out_value, int32_t *count, double *exit_mass)
+{
+    if (!c) return DRTS_EINVAL;
+    if (state_idx < 0 || state_idx >= c->n_states) return fail(c, DRTS_EINVAL, "state out of range");
+    if (!(frac > 0.0 && frac <= 1.0)) return fail(c, DRTS_EINVAL, "frac must be in (0, 1]");
+    if (!count || cap < 0 || (cap > 0 && (!out_state || !out_value)))
+        return fail(c, DRTS_EINVAL, "bad output arrays");
+    std::vector<std::pair<int64_t, double>> col;
+    drts_status st = source_column_host(c, state_idx, frac, col, exit_mass);
+    if (st != DRTS_OK) return st;
+    *count = int32_t(col.size());
+    if (int64_t(col.size()) > cap)
+        return fail(c, DRTS_EINVAL, "cap too small (" + std::to_string(col.size()) + " entries)");
+    for (size_t i = 0; i < col.size(); ++i) {
+        out_state[i] = col[i].first;
+        out_value[i] = col[i].second;
+    }
+    return DRTS_OK;
+}
+
+drts_status drts_inject_source_substeps(drts_ctx *c, int32_t rhs, int32_t n_entries, const int64_t *state_idx,
+                                        const double *weight, int32_t n_sub, int64_t t0, int32_t n_t,
+                                        const double *profile)
+{
+    if (!c) return DRTS_EINVAL;
+    if (rhs < 0 || rhs >= c->R) return fail(c, DRTS_EINVAL, "rhs out of range");
+    if (n_entries < 0 || n_entries > kMaxSrc) return fail(c, DRTS_EINVAL, "n_entries must be 0..64");
+    if (n_sub < 1 || n_sub > 64) return fail(c, DRTS_EINVAL, "n_sub must be 1..64");
+    if (n_t < 0 || (n_t > 0 && n_entries > 0 && !profile)) return fail(c, DRTS_EINVAL, "bad profile");
+    if (n_entries > 0 && (!state_idx || !weight)) return fail(c, DRTS_EINVAL, "NULL source arrays");
+    drts_ctx::SubstepSource ss;
+    const int ns = n_sub;
+    for (int i = 0; i < n_entries; ++i) {
+        if (state_idx[i] < 0 || state_idx[i] >= c->n_states) return fail(c, DRTS_EINVAL, "source state out of range");
+        if (!std::isfinite(weight[i])) return fail(c, DRTS_EINVAL, "source weight not finite");
+    }
+    if (n_entries > 0 && n_t > 0) {
+        for (int64_t q = 0; q < int64_t(n_t) * ns; ++q)
+            if (!std::isfinite(profile[q])) return fail(c, DRTS_EINVAL, "profile value not finite");
+        ss.state.assign(state_idx, state_idx + n_entries);
+        ss.weight.assign(weight, weight + n_entries);
+        ss.n_sub = ns;
+        ss.t0 = t0;
+        ss.n_t = n_t;
+        ss.profile.assign(profile, profile + int64_t(n_t) * ns);
+        for (int i = 0; i < n_entries; ++i)
+            for (int j = 0; j < ns; ++j) {
+                // sub-interval j, taken at its midpoint: the rest of the step is frac of the path
+                const double frac = 1.0 - (j + 0.5) / ns;
+                std::vector<std::pair<int64_t, double>> col;
+                drts_status st = source_column_host(c, state_idx[i], frac, col, nullptr);
+                if (st != DRTS_OK) return st;
+                ss.columns.push_back(std::move(col));
+            }
+    }
+    c->substep[rhs] = std::move(ss);
+    return upload_bulk(c);
+}
+
+drts_status drts_substep_count(drts_ctx *c, int64_t state_idx, int32_t *n_sub)
+{
+    if (!c || !n_sub) return DRTS_EINVAL;
+    if (state_idx < 0 || state_idx >= c->n_states) return fail(c, DRTS_EINVAL, "state out of range");
+    // sub-intervals of dr / c: the path L_k in half voxels (2 dr = h), rounded up
+    const int k = c->med_host[size_t(state_idx / kDirs)];
+    *n_sub = std::max(1, int(std::ceil(2.0 * c->host.lam[k] - 1e-9)));
+    return DRTS_OK;
+}
+
+drts_status drts_set_point_detectors(drts_ctx *c, int32_t n_det, int64_t n_entries, const int32_t *det,
+                                     const int64_t *state_idx, const double *weight)
+{
+    if (!c) return DRTS_EINVAL;
+    if (n_det < 0 || n_det > 65535) return fail(c, DRTS_EINVAL, "n_det must be 0..65535");
+    if (n_entries < 0 || (n_entries > 0 && (!det || !state_idx || !weight)))
+        return fail(c, DRTS_EINVAL, "bad entry arrays");
+    if (n_det == 0) {
+        c->n_pdet = 0;
+        return DRTS_OK;
+    }
+    if (c->prob.max_steps <= 0)
+        return fail(c, DRTS_ESTATE, "point detectors keep a history: max_steps must be > 0");
+    if (c->t > c->prob.max_steps) return fail(c, DRTS_ESTATE, "t is beyond max_steps");
+    std::vector<int64_t> off(size_t(n_det) + 1, 0);
+    for (int64_t e = 0; e < n_entries; ++e) {
+        if (det[e] < 0 || det[e] >= n_det) return fail(c, DRTS_EINVAL, "detector index out of range");
+        if (state_idx[e] < 0 || state_idx[e] >= c->n_states) return fail(c, DRTS_EINVAL, "state out of range");
+        if (!std::isfinite(weight[e])) return fail(c, DRTS_EINVAL, "weight not finite");
+        ++off[size_t(det[e]) + 1];
+    }
+    for (int d = 0; d < n_det; ++d) off[d + 1] += off[d];
+    std::vector<int64_t> st(static_cast<size_t>(n_entries));
+    std::vector<double> w(static_cast<size_t>(n_entries));
+    std::vector<int64_t> pos(off.begin(), off.end() - 1);
+    for (int64_t e = 0; e < n_entries; ++e) {      // grouped by detector, entry order kept
+        const int64_t q = pos[det[e]]++;
+        st[q] = state_idx[e];
+        w[q] = weight[e];
+    }
+    cudaError_t e = cudaSuccess;
+    if ((e = upload(c, &c->d_pdet_off, off)) != cudaSuccess || (e = upload(c, &c->d_pdet_state, st)) != cudaSuccess ||
+        (e = upload(c, &c->d_pdet_w, w)) != cudaSuccess ||
+        (e = dalloc(c, &c->d_pdet_hist, sizeof(double) * size_t(c->R) * c->prob.max_steps * n_det)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c->d_pdet_hist, 0, sizeof(double) * size_t(c->R) * c->prob.max_steps * n_det,
+                             c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "point detector upload");
+    c->n_pdet = n_det;
+    return sync_check(c, "point detector upload");
+}
+
+drts_status drts_read_point_detectors(drts_ctx *c, int32_t rhs, int64_t t_begin, int64_t t_end, double *host_out)
+{
+    if (!c) return DRTS_EINVAL;
+    if (rhs < 0 || rhs >= c->R) return fail(c, DRTS_EINVAL, "rhs out of range");
+    if (c->n_pdet <= 0) return fail(c, DRTS_ESTATE, "no point detectors set");
+    if (t_begin < 0 || t_end < t_begin || t_end > std::min(c->t, c->prob.max_steps))
+        return fail(c, DRTS_EINVAL, "bad step range");
+    if (t_end == t_begin) return DRTS_OK;
+    if (!host_out) return fail(c, DRTS_EINVAL, "host_out is NULL");
+    cudaError_t e = cudaMemcpyAsync(host_out, c->d_pdet_hist + (size_t(rhs) * c->prob.max_steps + t_begin) * c->n_pdet,
+                                    sizeof(double) * (t_end - t_begin) * c->n_pdet, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "read_point_detectors");
+    return sync_check(c, "read_point_detectors");
+}
+
+drts_status drts_sensor_response(drts_ctx *c, int32_t rhs, int32_t which, int64_t t_begin, int64_t t_end, int32_t w,
+                                 const double *h, double *host_out)
+{
+    if (!c) return DRTS_EINVAL;
+    if (rhs < 0 || rhs >= c->R) return fail(c, DRTS_EINVAL, "rhs out of range");
+    if (w < 0 || w > (1 << 20) || !h) return fail(c, DRTS_EINVAL, "w must be 0..2^20 and h non-NULL");
+    const double *D = nullptr;
+    int n_det = 0;
+    if (which == DRTS_SENSOR_FACE) {
+        if (!c->det || c->n_patch <= 0) return fail(c, DRTS_ESTATE, "no face detector history");
+        D = c->det + size_t(rhs) * c->prob.max_steps * c->n_patch;
+        n_det = c->n_patch;
+    } else if (which == DRTS_SENSOR_POINT) {
+        if (c->n_pdet <= 0) return fail(c, DRTS_ESTATE, "no point detectors set");
+        D = c->d_pdet_hist + size_t(rhs) * c->prob.max_steps * c->n_pdet;
+        n_det = c->n_pdet;
+    } else {
+        return fail(c, DRTS_EINVAL, "which must be DRTS_SENSOR_FACE or DRTS_SENSOR_POINT");
+    }
+    const int64_t t_rec = std::min(c->t, c->prob.max_steps);
+    if (t_begin < 0 || t_end < t_begin || t_end > t_rec) return fail(c, DRTS_EINVAL, "bad step range");
+    if (t_end == t_begin) return DRTS_OK;
+    if (!host_out) return fail(c, DRTS_EINVAL, "host_out is NULL");
+    double *dh = nullptr, *dm = nullptr;
+    const size_t nm = size_t(t_end - t_begin) * n_det;
+    cudaError_t e = cudaMallocAsync(&dh, sizeof(double) * (2 * size_t(w) + 1), c->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync(&dm, sizeof(double) * nm, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dh, h, sizeof(double) * (2 * size_t(w) + 1), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_sensor_response(D, t_rec, n_det, t_begin, t_end, w, dh, dm, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, dm, sizeof(double) * nm, cudaMemcpyDeviceToHost, c->stream);
+    if (dh) cudaFreeAsync(dh, c->stream);
+    if (dm) cudaFreeAsync(dm, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sensor_response");
+    return sync_check(c, "sensor_response");
 }
 
 void drts_destroy(drts_ctx *c)

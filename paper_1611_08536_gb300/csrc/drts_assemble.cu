@@ -324,6 +324,28 @@ __global__ void block_fill_kernel(DevTables T, uint16_t *blocks)
     enumerate_row(T, x, y, z, m, be);
 }
 
+// Column `state` = (voxel i, direction n) of the matrix built from Tf: thread
+// g = d*26 + m evaluates the mass that (i, n) sends to (i + d, m), with the
+// same folding as the rows (plain rows need none: there folded_contribution
+// reduces to the stencil value).
+__global__ void source_column_kernel(DevTables T, int64_t state, double *out)
+{
+    const int g = int(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= kOffs * kDirs) return;
+    const int d = g / kDirs, m = g % kDirs;
+    const int64_t v = state / kDirs;
+    const int n = int(state % kDirs);
+    const int i[3] = {int(v % T.nx), int(v / T.nx % T.ny), int(v / (int64_t(T.nx) * T.ny))};
+    const int j[3] = {i[0] + d % 3 - 1, i[1] + d / 3 % 3 - 1, i[2] + d / 9 - 1};
+    if (j[0] < 0 || j[1] < 0 || j[2] < 0 || j[0] >= T.nx || j[1] >= T.ny || j[2] >= T.nz) {
+        out[g] = 0.0;
+        return;
+    }
+    const int k = T.med[v];
+    const int kj = T.med[vox_of(T, j[0], j[1], j[2])];
+    out[g] = folded_contribution(T, i, k, __ldg(&T.nref[k]), n, j, kj, __ldg(&T.nref[kj]), m);
+}
+
 // exclusive scan of slice_len4 into slice_ptr (three passes, 1024 per block)
 constexpr int kScanBlock = 1024;
 
@@ -463,6 +485,14 @@ cudaError_t launch_fill(const DevTables &T, SlicedMatrix &A, cudaStream_t s)
     if (A.precision == DRTS_FP64) fill_kernel<double><<<blocks, th, 0, s>>>(T, A);
     else if (A.precision == DRTS_FP32) fill_kernel<float><<<blocks, th, 0, s>>>(T, A);
     else fill_kernel<__half><<<blocks, th, 0, s>>>(T, A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_source_column(const DevTables &Tf, int64_t state, double *out, cudaStream_t s)
+{
+    cudaError_t e = upload_dirs();
+    if (e != cudaSuccess) return e;
+    source_column_kernel<<<(kOffs * kDirs + 127) / 128, 128, 0, s>>>(Tf, state, out);
     return cudaGetLastError();
 }
 

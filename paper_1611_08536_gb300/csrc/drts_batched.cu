@@ -63,7 +63,13 @@ struct KahanAcc<double> {
     __device__ __forceinline__ void add(double v) { s += v; }
 };
 
-template <class VT, class XT, class AT, int RT>
+// ORDER 0: warps stride over slices (consecutive warps take consecutive
+// slices of the whole matrix).  ORDER 1: block-major - the CTA owns voxel
+// blocks b = blockIdx.x + k * gridDim.x and its warps share out the 26 slices
+// (directions m) of those blocks in turn, so the x neighbourhood of one voxel
+// block (read by all 26 of its slices) is gathered by warps of the same SM
+// while it is still in L1.
+template <class VT, class XT, class AT, int RT, int ORDER>
 __global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
 {
     __shared__ int32_t s_delta[kCodes];
@@ -80,10 +86,28 @@ __global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
     const VT *__restrict__ vals = static_cast<const VT *>(a.A.vals);
     const uint16_t *__restrict__ codes = a.A.codes;
     const int lane = threadIdx.x & 31;
-    const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    int64_t first, count, stride;
+    if (ORDER == 0) {
+        first = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+        stride = (int64_t(gridDim.x) * blockDim.x) >> 5;
+        count = a.A.n_slices;
+    } else {
+        // items i = (k, m) of this CTA's blocks, k-major; warp w takes w, w + nw, ...
+        const int64_t nb = a.A.n_slices / kDirs;
+        const int64_t mine = blockIdx.x < nb ? (nb - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+        first = threadIdx.x >> 5;
+        stride = blockDim.x >> 5;
+        count = mine * kDirs;
+    }
 
-    for (int64_t q = warp0; q < a.A.n_slices; q += nwarps) {
+    for (int64_t it = first; it < count; it += stride) {
+        int64_t q;
+        if (ORDER == 0) {
+            q = it;
+        } else {
+            const int64_t k = it / kDirs;
+            q = (int64_t(blockIdx.x) + k * gridDim.x) * kDirs + (it - k * kDirs);
+        }
         const int64_t b = q / kDirs;
         const int m = int(q - b * kDirs);
         const int64_t v = b * kSlice + lane;
@@ -224,50 +248,62 @@ __global__ void det_kernel(StepArgs a)
 
 template <class VT, class XT, class AT>
 struct SpmmLaunch {
-    template <int RT>
+    template <int RT, int ORDER>
     static int fit(int threads)
     {
         int n = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spmm_kernel<VT, XT, AT, RT>, threads, 0) !=
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spmm_kernel<VT, XT, AT, RT, ORDER>, threads, 0) !=
             cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
         return n;
     }
-    static int per_sm(int rt, int threads)
+    template <int ORDER>
+    static int per_sm_order(int rt, int threads)
     {
         switch (rt) {
-        case 4: return fit<4>(threads);
-        case 8: return fit<8>(threads);
-        case 16: return fit<16>(threads);
-        case 32: return fit<32>(threads);
+        case 4: return fit<4, ORDER>(threads);
+        case 8: return fit<8, ORDER>(threads);
+        case 16: return fit<16, ORDER>(threads);
+        case 32: return fit<32, ORDER>(threads);
         }
         return 0;
     }
-    static cudaError_t launch(int rt, const StepArgs &a, int r0, int blocks, int threads, cudaStream_t s)
+    static int per_sm(int rt, int threads, int order)
+    {
+        return order == 0 ? per_sm_order<0>(rt, threads) : per_sm_order<1>(rt, threads);
+    }
+    template <int ORDER>
+    static cudaError_t launch_order(int rt, const StepArgs &a, int r0, int blocks, int threads, cudaStream_t s)
     {
         switch (rt) {
-        case 4: spmm_kernel<VT, XT, AT, 4><<<blocks, threads, 0, s>>>(a, r0); break;
-        case 8: spmm_kernel<VT, XT, AT, 8><<<blocks, threads, 0, s>>>(a, r0); break;
-        case 16: spmm_kernel<VT, XT, AT, 16><<<blocks, threads, 0, s>>>(a, r0); break;
-        case 32: spmm_kernel<VT, XT, AT, 32><<<blocks, threads, 0, s>>>(a, r0); break;
+        case 4: spmm_kernel<VT, XT, AT, 4, ORDER><<<blocks, threads, 0, s>>>(a, r0); break;
+        case 8: spmm_kernel<VT, XT, AT, 8, ORDER><<<blocks, threads, 0, s>>>(a, r0); break;
+        case 16: spmm_kernel<VT, XT, AT, 16, ORDER><<<blocks, threads, 0, s>>>(a, r0); break;
+        case 32: spmm_kernel<VT, XT, AT, 32, ORDER><<<blocks, threads, 0, s>>>(a, r0); break;
         default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
+    }
+    static cudaError_t launch(int rt, int order, const StepArgs &a, int r0, int blocks, int threads,
+                              cudaStream_t s)
+    {
+        return order == 0 ? launch_order<0>(rt, a, r0, blocks, threads, s)
+                          : launch_order<1>(rt, a, r0, blocks, threads, s);
     }
 };
 
 }  // namespace
 
-int batched_blocks_per_sm(int precision, int rhs_tile, int threads)
+int batched_blocks_per_sm(int precision, int rhs_tile, int threads, int order)
 {
-    if (precision == DRTS_FP64) return SpmmLaunch<double, double, double>::per_sm(rhs_tile, threads);
-    if (precision == DRTS_FP32) return SpmmLaunch<float, float, float>::per_sm(rhs_tile, threads);
-    return SpmmLaunch<__half, float, float>::per_sm(rhs_tile, threads);
+    if (precision == DRTS_FP64) return SpmmLaunch<double, double, double>::per_sm(rhs_tile, threads, order);
+    if (precision == DRTS_FP32) return SpmmLaunch<float, float, float>::per_sm(rhs_tile, threads, order);
+    return SpmmLaunch<__half, float, float>::per_sm(rhs_tile, threads, order);
 }
 
-cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int blocks, int threads,
+cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int order, int blocks, int threads,
                                 bool functionals, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
@@ -288,11 +324,11 @@ cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int 
     }
     for (int r0 = 0; r0 < n_rhs; r0 += rhs_tile) {
         if (a.A.precision == DRTS_FP64)
-            e = SpmmLaunch<double, double, double>::launch(rhs_tile, a, r0, blocks, threads, s);
+            e = SpmmLaunch<double, double, double>::launch(rhs_tile, order, a, r0, blocks, threads, s);
         else if (a.A.precision == DRTS_FP32)
-            e = SpmmLaunch<float, float, float>::launch(rhs_tile, a, r0, blocks, threads, s);
+            e = SpmmLaunch<float, float, float>::launch(rhs_tile, order, a, r0, blocks, threads, s);
         else
-            e = SpmmLaunch<__half, float, float>::launch(rhs_tile, a, r0, blocks, threads, s);
+            e = SpmmLaunch<__half, float, float>::launch(rhs_tile, order, a, r0, blocks, threads, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

@@ -67,6 +67,41 @@ struct StepTables {
     const double *exit_det;    // [K][27][26]
 };
 
+// Sparse detector rows F of Eq. 27 (point detectors): the entries of
+// detector d are off[d] .. off[d+1], each a canonical state and a weight.
+struct PointDetectors {
+    int n_det;
+    const int64_t *off;        // [n_det + 1]
+    const int64_t *state;      // canonical state of each entry
+    const double *w;
+    double *hist;              // [r][max_steps][n_det] readout history, or null
+    int64_t stride_r;          // max_steps * n_det
+};
+
+// Sub-step sources (Section 4.1 time partition of the source term): groups of
+// entries that land on one (state, rhs); group g adds
+// sum_e w_e P_{prof_e}(t) to y[state] after the product.
+struct BulkGroup {
+    int64_t state;
+    int32_t rhs;
+    int32_t first;             // entries first .. first + count - 1
+    int32_t count;
+    int32_t pad;
+};
+struct BulkEntry {
+    double w;
+    int32_t prof;              // index into the sub-step profiles
+    int32_t pad;
+};
+struct BulkSources {
+    int n_groups;
+    const BulkGroup *groups;   // sorted by (rhs, state)
+    const int32_t *rhs_off;    // [R + 1] group range of each rhs
+    const BulkEntry *entries;
+    const SourceProfile *prof;
+    const double *prof_vals;
+};
+
 struct StepArgs {
     SlicedMatrix A;
     int nx, ny, nz;
@@ -93,6 +128,9 @@ struct StepArgs {
     const uint8_t *src_voxel;  // [V] 1 where some source entry targets the voxel
     uint32_t spin_limit;       // polls before a device wait gives up
     int64_t fault_skip_chunk;  // tests only: chunk warp 0 never copies (-1 none)
+    int tc_rp;                 // > 0: tensor-core state layout X[(v*tc_rp + r)*32 + d]
+    PointDetectors pd;         // point detectors read from x (n_det = 0: none)
+    BulkSources bulk;          // sub-step sources added to y (n_groups = 0: none)
 };
 
 // assembler (drts_assemble.cu)
@@ -126,9 +164,11 @@ cudaError_t launch_ledger_sum(const void *x, int precision, int64_t n, int R, in
                               double *out, cudaStream_t s);
 
 // batched step (drts_batched.cu): functionals (detector + ledger of X(t))
-// when asked, then ceil(R / rhs_tile) passes of the product over A
-int batched_blocks_per_sm(int precision, int rhs_tile, int threads);
-cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int blocks, int threads,
+// when asked, then ceil(R / rhs_tile) passes of the product over A; order 0
+// strides warps over slices, order 1 is block-major (kBatchedOrders orders)
+constexpr int kBatchedOrders = 2;
+int batched_blocks_per_sm(int precision, int rhs_tile, int threads, int order);
+cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int order, int blocks, int threads,
                                 bool functionals, cudaStream_t s);
 
 // tensor-core batched step (drts_tensor.cu); state layout X[v][r][32]
@@ -140,6 +180,17 @@ cudaError_t launch_tc_to_canonical(const void *x, int64_t V, int Rp, int r, doub
 cudaError_t launch_tc_from_canonical(const double *in, int64_t V, int Rp, int r, void *x, cudaStream_t s);
 cudaError_t launch_tc_sum(const void *x, int64_t V, int Rp, int r, double *out, cudaStream_t s);
 cudaError_t launch_block_fill(const DevTables &T, void *blocks, cudaStream_t s);
+
+// Eq. 26/27 extensions (drts_functionals.cu): point detectors of x(t) (one
+// CTA per detector and rhs), sub-step sources added to y(t+1), and the
+// sensor response of a detector history
+cudaError_t launch_point_detectors(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_bulk_sources(const StepArgs &a, cudaStream_t s);
+cudaError_t launch_sensor_response(const double *D, int64_t t_rec, int n_det, int64_t t_begin, int64_t t_end,
+                                   int w, const double *h, double *M, cudaStream_t s);
+// column (state) of the system matrix built with a partial path (tables Tf):
+// out[d*26 + m] = mass reaching (voxel + offset d, direction m), 0 off the grid
+cudaError_t launch_source_column(const DevTables &Tf, int64_t state, double *out, cudaStream_t s);
 
 // no-allocation state sum (drts_noalloc.cu)
 int64_t noalloc_max_states();

@@ -64,6 +64,8 @@ struct HostTables {
     int n_template_entries_max = 0;
 };
 
-std::string build_host_tables(const drts_problem &p, HostTables &t);
+// path_frac scales every medium's path L_k (1 for the system matrix; a
+// fraction of the step for sources emitted within it, Section 4.1)
+std::string build_host_tables(const drts_problem &p, HostTables &t, double path_frac = 1.0);
 
 }  // namespace drts

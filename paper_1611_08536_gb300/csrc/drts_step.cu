@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "drts_device.cuh"
+#include "drts_functionals.cuh"
 #include "drts_kernel_common.cuh"
 
 namespace drts {
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(256) persistent_kernel(StepArgs a0, void *othe
                                                          int fault_skip_barrier)
 {
     __shared__ StepShared sh;
+    __shared__ double pd_red[32];
     step_delta(a0, sh);
     const VT *__restrict__ vals = static_cast<const VT *>(a0.A.vals);
     const uint16_t *__restrict__ codes = a0.A.codes;
@@ -474,6 +476,10 @@ __global__ void __launch_bounds__(256) persistent_kernel(StepArgs a0, void *othe
         a.det = (det_base && a.t < max_steps) ? det_base + a.t * a.n_patch : nullptr;
         step_sources(a, sh);
         const XT *x = static_cast<const XT *>(a.x);
+        // point detectors of x(t): CTA b reads detectors b, b + grid, ...
+        if (a.pd.n_det > 0 && a.pd.hist && a.t < max_steps)
+            for (int d = blockIdx.x; d < a.pd.n_det; d += gridDim.x)
+                point_detector_block<XT, true>(a, x, 0, d, pd_red);
         AT ab_lane = 0, ex_lane = 0;
         for (int64_t q = warp0; q < a.A.n_slices; q += nwarps) {
             const int64_t b = q / kDirs;

@@ -161,7 +161,7 @@ void diffuse_round_fp16(const double *W, const float *scale, double *out)
 
 }  // namespace
 
-std::string build_host_tables(const drts_problem &p, HostTables &t)
+std::string build_host_tables(const drts_problem &p, HostTables &t, double path_frac)
 {
     const Directions &D = dirs();
     const int K = p.n_media;
@@ -175,7 +175,7 @@ std::string build_host_tables(const drts_problem &p, HostTables &t)
     t.W.assign(size_t(K) * kDirs * kOffs * kDirs, 0.0);
     for (int k = 0; k < K; ++k) {
         const drts_medium &md = p.media[k];
-        const double lam = nmin / md.n;             // L_k / h  (dt = h / c_max)
+        const double lam = path_frac * nmin / md.n;   // path / h  (L_k = h n_min / n_k)
         const double L = lam * p.voxel_mm;
         const double keep_a = std::exp(-md.mu_a * L);      // Eq. 8
         const double keep_s = std::exp(-md.mu_s * L);      // Eq. 3 / 6

@@ -107,7 +107,9 @@ SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_dete
            "drts_set_step_mode", "drts_server_create", "drts_server_submit", "drts_server_tick",
            "drts_server_poll", "drts_server_result", "drts_server_release",
            "drts_server_get_stats", "drts_server_last_error", "drts_server_destroy",
-           "drts_checkpoint_size", "drts_checkpoint_save", "drts_checkpoint_load"]
+           "drts_checkpoint_size", "drts_checkpoint_save", "drts_checkpoint_load",
+           "drts_set_point_detectors", "drts_read_point_detectors", "drts_sensor_response",
+           "drts_source_column", "drts_inject_source_substeps", "drts_substep_count"]
 
 _lib = None
 
@@ -140,6 +142,13 @@ def load(path: str = LIB_PATH):
     lib.drts_checkpoint_size.argtypes = [vp, ctypes.POINTER(i64)]
     lib.drts_checkpoint_save.argtypes = [vp, vp, i64]
     lib.drts_checkpoint_load.argtypes = [vp, vp, i64]
+    lib.drts_set_point_detectors.argtypes = [vp, i32, i64, vp, vp, vp]
+    lib.drts_read_point_detectors.argtypes = [vp, i32, i64, i64, vp]
+    lib.drts_sensor_response.argtypes = [vp, i32, i32, i64, i64, i32, vp, vp]
+    lib.drts_source_column.argtypes = [vp, i64, ctypes.c_double, i32, vp, vp,
+                                       ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_double)]
+    lib.drts_inject_source_substeps.argtypes = [vp, i32, i32, vp, vp, i32, i64, i32, vp]
+    lib.drts_substep_count.argtypes = [vp, i64, ctypes.POINTER(i32)]
     lib.drts_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
     lib.drts_server_submit.argtypes = [vp, ctypes.POINTER(ProblemC), i32, vp, vp, vp, i64, i32, vp,
                                        i64, ctypes.POINTER(i64)]
@@ -295,6 +304,70 @@ class Context:
         self._check(self._lib.drts_checkpoint_save(self._h, _ptr(buf), n.value))
         return buf.tobytes()
 
+    def set_point_detectors(self, n_det, det, state_idx, weight):
+        """Sparse detector rows F of Eq. 27: detector det[e] reads
+        weight[e] * x_t[state_idx[e]], summed per detector every step."""
+        d = np.ascontiguousarray(det, dtype=np.int32)
+        st = np.ascontiguousarray(state_idx, dtype=np.int64)
+        w = np.ascontiguousarray(weight, dtype=np.float64)
+        if not (d.size == st.size == w.size):
+            raise ValueError("det, state_idx and weight differ in length")
+        self._check(self._lib.drts_set_point_detectors(self._h, int(n_det), d.size, _ptr(d),
+                                                       _ptr(st), _ptr(w)))
+        self._n_pdet = int(n_det)
+
+    def read_point_detectors(self, rhs=0, t_begin=0, t_end=None):
+        if t_end is None:
+            t_end = self.info().t
+        out = np.zeros((max(t_end - t_begin, 0), max(getattr(self, "_n_pdet", 0), 1)), np.float64)
+        self._check(self._lib.drts_read_point_detectors(self._h, int(rhs), int(t_begin), int(t_end),
+                                                        _ptr(out)))
+        return out[:, :getattr(self, "_n_pdet", 0)]
+
+    def sensor_response(self, w, h, rhs=0, which=0, t_begin=0, t_end=None, n_det=None):
+        """Eq. 27 sensor output M[t][d] = sum_{|t-k| <= w} h[t-k+w] D[k][d] of the
+        face (which=SENSOR_FACE) or point (SENSOR_POINT) detector history."""
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        if h.size != 2 * w + 1:
+            raise ValueError("h must have 2w+1 taps")
+        if t_end is None:
+            t_end = self.info().t
+        if n_det is None:
+            n_det = self.info().n_patch if which == SENSOR_FACE else getattr(self, "_n_pdet", 0)
+        out = np.zeros((max(t_end - t_begin, 0), max(n_det, 1)), np.float64)
+        self._check(self._lib.drts_sensor_response(self._h, int(rhs), int(which), int(t_begin),
+                                                   int(t_end), int(w), _ptr(h), _ptr(out)))
+        return out[:, :n_det]
+
+    def source_column(self, state_idx, frac, cap=4096):
+        """(states, values, exit_mass) of a unit population emitted from
+        state_idx that travels the fraction frac of a step (Section 4.1)."""
+        st = np.empty(cap, np.int64)
+        val = np.empty(cap, np.float64)
+        cnt = ctypes.c_int32()
+        ex = ctypes.c_double()
+        self._check(self._lib.drts_source_column(self._h, int(state_idx), float(frac), int(cap),
+                                                 _ptr(st), _ptr(val), ctypes.byref(cnt),
+                                                 ctypes.byref(ex)))
+        return st[:cnt.value].copy(), val[:cnt.value].copy(), ex.value
+
+    def substep_count(self, state_idx):
+        """Sub-intervals of length dr/c in one step of state_idx's medium."""
+        n = ctypes.c_int32()
+        self._check(self._lib.drts_substep_count(self._h, int(state_idx), ctypes.byref(n)))
+        return n.value
+
+    def inject_source_substeps(self, rhs, state_idx, weight, t0, profile):
+        """Sub-step source of rhs: profile[t - t0][j] is emitted in sub-interval
+        j of step t; n_sub is the profile's second extent."""
+        s = np.ascontiguousarray(state_idx, dtype=np.int64)
+        w = np.ascontiguousarray(weight, dtype=np.float64)
+        p = np.ascontiguousarray(profile, dtype=np.float64)
+        if p.ndim != 2:
+            raise ValueError("profile must be [n_t][n_sub]")
+        self._check(self._lib.drts_inject_source_substeps(self._h, int(rhs), s.size, _ptr(s), _ptr(w),
+                                                          p.shape[1], int(t0), p.shape[0], _ptr(p)))
+
     def restore(self, data: bytes):
         buf = np.frombuffer(data, np.uint8).copy()
         self._check(self._lib.drts_checkpoint_load(self._h, _ptr(buf), buf.size))
@@ -319,6 +392,7 @@ class Context:
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+SENSOR_FACE, SENSOR_POINT = 0, 1
 
 
 class Server:

@@ -23,10 +23,10 @@ def rel_l1(a, b):
     return np.abs(a - b).sum() / max(np.abs(b).sum(), 1e-300)
 
 
-def run_batched(gpu, prob, srcs, steps, tile=0):
+def run_batched(gpu, prob, srcs, steps, tile=0, order=-1):
     with gpu.Context(prob, max_steps=steps) as ctx:
-        if tile:
-            ctx.set_launch(0, 0, tile, -1)
+        if tile or order >= 0:
+            ctx.set_launch(0, 0, tile, order)
         for r, s in enumerate(srcs):
             ctx.set_source(r, s)
         ctx.step_n(steps)
@@ -39,13 +39,17 @@ def run_batched(gpu, prob, srcs, steps, tile=0):
     return xs, dets, leds
 
 
-@pytest.mark.parametrize("n_rhs,tile", [(5, 0), (5, 4), (8, 8), (13, 16), (33, 32)])
-def test_batched_fp32_matches_oracle(gpu, oracle_mod, n_rhs, tile):
+@pytest.mark.parametrize("n_rhs,tile,order", [(5, 0, -1), (5, 4, 0), (8, 8, 0), (13, 16, 0), (33, 32, 0),
+                                              (5, 4, 1), (8, 8, 1), (13, 16, 1), (33, 32, 1)])
+def test_batched_fp32_matches_oracle(gpu, oracle_mod, n_rhs, tile, order):
+    """Both slice orders (warps striding over slices; block-major) and every
+    right-hand-side tile, on a 12^3 grid whose 54 voxel blocks of 32 wrap
+    across x rows (ragged block boundaries)."""
     prob, srcs = I.inclusions(12, n_rhs=n_rhs, seed=21, precision=I.FP32, n_spheres=2)
     steps = 40
     csr = oracle_mod.assemble(prob)
     ci = oracle_mod.column_info(prob)
-    xs, dets, leds = run_batched(gpu, prob, srcs, steps, tile)
+    xs, dets, leds = run_batched(gpu, prob, srcs, steps, tile, order)
     for r in range(0, n_rhs, max(1, n_rhs // 5)):
         xo, deto, ledo = oracle_mod.run(prob, csr, steps, srcs[r].as_tuple(), colinfo=ci)
         assert rel_l1(xs[r], xo) < 1e-5, r
@@ -66,12 +70,13 @@ def test_batched_same_alone_and_in_mix(gpu):
         assert rel_l1(dets[r], d1[0]) < 1e-6
 
 
-def test_batched_fp64_and_fp16(gpu, oracle_mod):
+@pytest.mark.parametrize("order", [0, 1])
+def test_batched_fp64_and_fp16(gpu, oracle_mod, order):
     for prec, tol in ((I.FP64, 1e-12), (I.FP16_ROWSCALE, 5e-3)):
         prob, srcs = I.inclusions(10, n_rhs=4, seed=8, precision=prec, n_spheres=1)
         steps = 20
         csr = oracle_mod.assemble(prob)
-        xs, _, _ = run_batched(gpu, prob, srcs, steps)
+        xs, _, _ = run_batched(gpu, prob, srcs, steps, 4, order)
         for r in range(4):
             xo, _, _ = oracle_mod.run(prob, csr, steps, srcs[r].as_tuple())
             assert rel_l1(xs[r], xo) < tol, (prec, r)
