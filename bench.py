@@ -522,6 +522,72 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_functionals(args):
+    """Cost of the Eq. 26/27 extensions on the headline workload: the plain
+    step, then with --point-detectors sparse detector rows (16 states each),
+    then also with a sub-step source (the Gaussian pulse split over the dr/c
+    sub-intervals of each step)."""
+    import numpy as np
+    import torch
+    from paper_1611_08536_gb300 import build, drts
+    from paper_1611_08536_gb300 import inputs as I
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build.build()
+    stream = torch.cuda.current_stream()
+    prob, src = workload(args.workload, args.precision)
+    total = 3 * (args.warmup + args.steps) + 1
+    ctx = drts.Context(prob, max_steps=total, stream=stream.cuda_stream)
+    ctx.set_source(0, src)
+    tune = ctx.autotune(args.autotune) if args.autotune else None
+    info = ctx.info()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed():
+        ctx.step_n(args.warmup)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ctx.step_n(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / args.steps
+
+    with ClockSampler(local) as clk:
+        ms_plain = timed()
+        # point detectors: 4x4 blocks of +z states on the middle plane
+        nx, ny, nz = prob.shape
+        n_det = args.point_detectors
+        det, st = [], []
+        dz = I.direction_index(0, 0, 1)
+        for d in range(n_det):
+            bx, by = (d * 4) % (nx - 4), ((d * 4) // (nx - 4) * 4) % (ny - 4)
+            for q in range(16):
+                det.append(d)
+                st.append(prob.state(bx + q % 4, by + q // 4, nz // 2, dz))
+        ctx.set_point_detectors(n_det, det, st, np.ones(len(st)))
+        ms_point = timed()
+        n_sub = ctx.substep_count(int(src.state[0]))
+        prof = np.repeat(src.profile[:, None] / n_sub, n_sub, 1)
+        ctx.inject_source_substeps(0, src.state, src.weight, src.t0, prof)
+        ms_both = timed()
+    ctx.close()
+    line = {
+        "metric": "DRTS step with point detectors and sub-step sources (overhead vs plain step)",
+        "value": round(100.0 * (ms_both / ms_plain - 1.0), 2), "unit": "% of the plain step",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_both, 4),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f16-matrix/f32-state"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, "nnz": int(info.nnz), "launch": tune,
+                   "point_detectors": n_det, "point_entries": len(st), "substeps": int(n_sub),
+                   "ms_plain": round(ms_plain, 4), "ms_point_detectors": round(ms_point, 4),
+                   "ms_point_and_substep": round(ms_both, 4),
+                   "gnnz_per_s_plain": round(info.nnz / (ms_plain * 1e-3) / 1e9, 1)},
+        "gpu_launches": None, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -546,6 +612,9 @@ def main():
     ap.add_argument("--serve-streams", type=int, default=4)
     ap.add_argument("--sim-steps", type=int, default=1500, help="steps per simulation for sims/s")
     ap.add_argument("--batched-kernel", default="cuda", choices=["cuda", "tensor"])
+    ap.add_argument("--functionals", action="store_true",
+                    help="cost of point detectors and sub-step sources on the workload")
+    ap.add_argument("--point-detectors", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-check", dest="check", action="store_false")
     args = ap.parse_args()
@@ -555,6 +624,8 @@ def main():
         run_reference(args)
     elif args.serve:
         run_serve(args)
+    elif args.functionals:
+        run_functionals(args)
     elif args.rhs > 1:
         run_batched(args)
     else:

@@ -121,44 +121,6 @@ void diffuse_round_fp32(const double *W, double *out)
     }
 }
 
-// Same column-preserving rounding onto the FP16 grid of each target
-// direction m: an entry (o, m) is stored as h * scale[m] with h an FP16
-// number, so its two candidates are the FP16 numbers bracketing v / scale[m].
-double half_bits_value(uint16_t b)
-{
-    __half_raw r;
-    r.x = b;
-    return double(__half2float(__half(r)));
-}
-
-void diffuse_round_fp16(const double *W, const float *scale, double *out)
-{
-    std::vector<int> idx;
-    for (int n = 0; n < kDirs; ++n) {
-        idx.clear();
-        for (int o = 0; o < kOffs; ++o)
-            for (int m = 0; m < kDirs; ++m)
-                if (W[(n * kOffs + o) * kDirs + m] > 0.0) idx.push_back(o * kDirs + m);
-        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
-            return W[n * kOffs * kDirs + a] > W[n * kOffs * kDirs + b];
-        });
-        double resid = 0.0;
-        for (int e : idx) {
-            const double v = W[n * kOffs * kDirs + e];
-            const double sm = double(scale[e % kDirs]);
-            const double t = v / sm;
-            const __half_raw hr = __half_raw(__double2half(t));
-            uint16_t lo = hr.x, hi = hr.x;          // positive halves: bits are monotone
-            if (half_bits_value(hr.x) > t) lo = uint16_t(hr.x - 1);
-            else if (half_bits_value(hr.x) < t) hi = uint16_t(hr.x + 1);
-            const double a = half_bits_value(lo) * sm, b = half_bits_value(hi) * sm;
-            const double pick = std::fabs(resid + a - v) <= std::fabs(resid + b - v) ? a : b;
-            out[n * kOffs * kDirs + e] = pick;
-            resid += pick - v;
-        }
-    }
-}
-
 }  // namespace
 
 std::string build_host_tables(const drts_problem &p, HostTables &t, double path_frac)
@@ -213,8 +175,8 @@ std::string build_host_tables(const drts_problem &p, HostTables &t, double path_
         }
     }
 
-    // stencil values as stored by the plain rows: FP64 as computed, FP32 and
-    // FP16 with column-preserving rounding
+    // stencil values as stored by the plain rows: FP64 as computed, FP32 with
+    // column-preserving rounding, FP16 as computed (rounded at fill time)
     std::vector<double> Wstore(t.W);
     if (p.precision == DRTS_FP32)
         for (int k = 0; k < K; ++k) {
@@ -235,10 +197,8 @@ std::string build_host_tables(const drts_problem &p, HostTables &t, double path_
             const int e2 = mx > 0.0 ? int(std::ceil(std::log2(mx))) : 0;
             t.dir_scale[m] = std::ldexp(1.0f, e2 - 14);
         }
-        for (int k = 0; k < K; ++k) {
-            const size_t off = size_t(k) * kDirs * kOffs * kDirs;
-            diffuse_round_fp16(&t.W[off], t.dir_scale.data(), &Wstore[off]);
-        }
+        // the FP16 values are rounded per entry in the fill kernel (spatially
+        // dithered), so the templates keep the FP64 values
     }
 
     // plain-row templates (row direction m, column offset d = source - row)

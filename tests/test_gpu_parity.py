@@ -145,8 +145,8 @@ def _fp16_error(gpu, oracle_mod, steps):
     return rel_l1(x, xo)
 
 
-@pytest.mark.xfail(strict=False, reason="16-bit values leave a systematic stencil-shape "
-                   "error of ~1e-3 per 500 steps; the 1e-4 target is not met")
+@pytest.mark.xfail(strict=False, reason="11-bit values: unbiased dithered rounding leaves "
+                   "~2e-4 after 200 steps at 16^3; the 1e-4 target is not met")
 def test_fp16_rowscale_meets_1e4(gpu, oracle_mod):
     e = _fp16_error(gpu, oracle_mod, 200)
     print(f"FP16-rowscale rel L1 after 200 steps: {e:.3e}")
@@ -154,12 +154,25 @@ def test_fp16_rowscale_meets_1e4(gpu, oracle_mod):
 
 
 def test_fp16_rowscale_measured_bound(gpu, oracle_mod):
-    """The FP16 tier's measured error at 16^3 (37 % edge voxels): 6.5e-3 after
-    200 steps with column-preserving rounding of the plain rows (2.1e-2 with
-    rounding to nearest everywhere)."""
+    """The FP16 tier's error at 16^3 three layers (37 % edge voxels) after 200
+    steps.  A CPU emulation of the stored values on the oracle's matrix gives
+    1.9e-4 for the spatially dithered rounding the fill kernel uses; the
+    earlier rounding (shared column-preserving rounding of the interior
+    stencil, nearest elsewhere) measured 6.5e-3, nearest everywhere 3.0e-2."""
     e = _fp16_error(gpu, oracle_mod, 200)
     print(f"FP16-rowscale rel L1 after 200 steps: {e:.3e}")
-    assert e < 1e-2
+    assert e < 5e-4
+
+
+def test_fp16_rowscale_inclusions_500_steps(gpu, oracle_mod):
+    """FP16 tier on a 24^3 cube with absorbing inclusions, 500 steps (emulated
+    1.4e-4; the shared-stencil rounding gave 1.1e-2)."""
+    prob, srcs = I.inclusions(24, n_rhs=1, seed=3, precision=I.FP16_ROWSCALE)
+    (x, det, led), (xo, deto, ledo) = _run_both(gpu, oracle_mod, prob, srcs[0], 500)
+    e = rel_l1(x, xo)
+    print(f"FP16-rowscale inclusions 24^3 rel L1 after 500 steps: {e:.3e}")
+    assert e < 4e-4
+    assert rel_l1(det, deto) < 4e-4
 
 
 def test_empty_source_and_zero_steps(gpu):
