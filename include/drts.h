@@ -276,8 +276,10 @@ drts_status drts_get_info(const drts_ctx *ctx, drts_info *out);
  * ahead and the x gathers of the next group in flight).  For a batched
  * context on the CUDA cores the variant is the slice order: 0 = warps
  * stride over all slices, 1 = block-major (one CTA works through all 26
- * direction slices of a voxel block); the tensor-core form has variant 0
- * only.  All variants compute the same step; they differ only in speed.
+ * direction slices of a voxel block), 2 = block-major with the block's x
+ * halo staged in shared memory (fixed shape: 26 warps, one CTA per SM, 4
+ * FP32 / 2 FP64 right-hand sides per pass; rhs_tile, threads and blocks are
+ * ignored); the tensor-core form has variant 0 only.  All variants compute the same step; they differ only in speed.
  * DRTS_EINVAL if the shape does not fit on an SM or the variant is unknown. */
 drts_status drts_set_launch(drts_ctx *ctx, int32_t blocks_per_sm,
                             int32_t threads_per_block, int32_t rhs_tile,

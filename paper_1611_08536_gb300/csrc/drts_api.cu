@@ -859,6 +859,7 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
             if (c->R == 1 && tile != 4) continue;             // tile only matters when batched
             if (c->tc && (tile < 8 || tile > c->tc_rp)) continue;
             if (c->R > 1 && tile > 4 && tile / 2 >= c->R) continue;   // tile far wider than R
+            if (c->R > 1 && !c->tc && var == 2 && (tile != 4 || threads != 256)) continue;   // fixed shape
             const int fit = fit_blocks(c, threads, var, tile);
             if (fit < 1) continue;
             const int fit_per_sm = fit / sms;

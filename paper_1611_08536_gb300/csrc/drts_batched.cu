@@ -167,6 +167,172 @@ __global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
     }
 }
 
+// ORDER 2: the x halo of one voxel block in shared memory.  A CTA of 26
+// warps owns voxel blocks b = blockIdx.x + k * gridDim.x; for each tile of RT
+// right-hand sides it first stages every x value the block's 26 x 32 rows
+// can read - nine row ranges (dy, dz) of 34 voxels (the 32 of the block and
+// one on each side), 26 directions, RT right-hand sides, stored
+// [range][n][voxel][r] - then warp m computes slice (b, m) from shared
+// memory: one 16-byte load gives the RT values of a code.  Every x value is
+// then read from L2 once per block instead of once per row, and the gathers
+// no longer miss.  RT = 16 bytes / sizeof(XT): 4 FP32 or 2 FP64 values
+// (127,296 bytes of halo).
+constexpr int kHaloRanges = 9, kHaloVox = kSlice + 2;
+constexpr int kHaloThreads = kDirs * 32;
+
+template <class XT>
+struct HaloRT {
+    static constexpr int value = 16 / int(sizeof(XT));
+};
+
+__device__ __forceinline__ void load_rt(const float *p, float o[4])
+{
+    const float4 t = *reinterpret_cast<const float4 *>(p);
+    o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+}
+__device__ __forceinline__ void load_rt(const double *p, double o[2])
+{
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    o[0] = t.x; o[1] = t.y;
+}
+
+template <class XT>
+constexpr size_t halo_smem_bytes()
+{
+    return size_t(kHaloRanges) * kDirs * kHaloVox * HaloRT<XT>::value * sizeof(XT) + kCodes * sizeof(int32_t);
+}
+
+template <class VT, class XT, class AT>
+__global__ void __launch_bounds__(kHaloThreads, 1) spmm_halo_kernel(StepArgs a)
+{
+    constexpr int RT = HaloRT<XT>::value;
+    extern __shared__ __align__(16) unsigned char halo_raw[];
+    XT *xs = reinterpret_cast<XT *>(halo_raw);
+    int32_t *s_off = reinterpret_cast<int32_t *>(xs + kHaloRanges * kDirs * kHaloVox * RT);
+    for (int c = threadIdx.x; c < kCodes; c += blockDim.x) {
+        const int d = c / kDirs, n = c % kDirs;
+        const int rr = (d / 9) * 3 + (d / 3 % 3);            // (dz + 1) * 3 + (dy + 1)
+        s_off[c] = ((rr * kDirs + n) * kHaloVox + d % 3) * RT;  // voxel slot lane + dx + 1
+    }
+    const int64_t V = a.V;
+    const int64_t S = a.rhs_stride;
+    const XT *__restrict__ x = static_cast<const XT *>(a.x);
+    XT *__restrict__ y = static_cast<XT *>(a.y);
+    const VT *__restrict__ vals = static_cast<const VT *>(a.A.vals);
+    const uint16_t *__restrict__ codes = a.A.codes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    const int64_t n_vb = a.A.n_slices / kDirs;
+    constexpr int kHaloElems = kHaloRanges * kDirs * kHaloVox;
+    for (int64_t b = blockIdx.x; b < n_vb; b += gridDim.x) {
+        const int64_t v0 = b * kSlice;
+        for (int r0 = 0; r0 < a.R; r0 += RT) {
+            const int nr = a.R - r0 < RT ? a.R - r0 : RT;
+            __syncthreads();                 // the previous tile's readers are done
+            for (int i = threadIdx.x; i < kHaloElems * RT; i += blockDim.x) {
+                const int p = i % kHaloVox;
+                int rest = i / kHaloVox;
+                const int n = rest % kDirs;
+                rest /= kDirs;
+                const int rr = rest % kHaloRanges;
+                const int r = rest / kHaloRanges;
+                const int64_t g = v0 + (int64_t(rr / 3 - 1) * a.ny + (rr % 3 - 1)) * a.nx - 1 + p;
+                XT val = XT(0);
+                if (r < nr && g >= 0 && g < V) val = x[int64_t(r0 + r) * S + int64_t(n) * V + g];
+                xs[((rr * kDirs + n) * kHaloVox + p) * RT + r] = val;
+            }
+            __syncthreads();
+            for (int m = warp; m < kDirs; m += nwarps) {
+                const int64_t q = b * kDirs + m;
+                const int64_t v = v0 + lane;
+                const int len4 = a.A.slice_len4[q];
+                const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
+                KahanAcc<AT> acc[RT];
+                AT wn[4];
+                int cn[4];
+                if (len4 > 0) {
+                    load4(vals + base, wn);
+                    load_codes(codes + base, cn);
+                }
+                for (int g = 0; g < len4; ++g) {
+                    AT w[4];
+                    int c[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) { w[j] = wn[j]; c[j] = cn[j]; }
+                    if (g + 1 < len4) {
+                        const int64_t idx = base + int64_t(g + 1) * (kSlice * kGroup);
+                        load4(vals + idx, wn);
+                        load_codes(codes + idx, cn);
+                    }
+                    XT xv[4][RT];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) load_rt(xs + s_off[c[j]] + lane * RT, xv[j]);
+#pragma unroll
+                    for (int r = 0; r < RT; ++r) {
+                        AT p = w[0] * AT(xv[0][r]);
+                        p = fma(w[1], AT(xv[1][r]), p);
+                        p = fma(w[2], AT(xv[2][r]), p);
+                        p = fma(w[3], AT(xv[3][r]), p);
+                        acc[r].add(p);
+                    }
+                }
+                if (v >= V) continue;
+                const AT sc = a.A.row_scale ? AT(a.A.row_scale[q * kSlice + lane]) : AT(1);
+                AT out[RT];
+#pragma unroll
+                for (int r = 0; r < RT; ++r) out[r] = acc[r].s * sc;
+                if (a.n_src > 0) {
+                    for (int e = first_entry(a.src, a.n_src, q); e < a.n_src && a.src[e].slice == q; ++e) {
+                        const SourceEntry se = a.src[e];
+                        if (se.lane != lane) continue;
+                        const int rr = se.rhs - r0;
+                        const AT val = AT(source_value(a, se));
+#pragma unroll
+                        for (int r = 0; r < RT; ++r)
+                            if (r == rr) out[r] += val;
+                    }
+                }
+                const int64_t row = int64_t(m) * V + v;
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+                    if (r < nr) y[int64_t(r0 + r) * S + row] = XT(out[r]);
+            }
+        }
+    }
+}
+
+template <class VT, class XT, class AT>
+int halo_blocks_per_sm()
+{
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(spmm_halo_kernel<VT, XT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(halo_smem_bytes<XT>())) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        attr = true;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spmm_halo_kernel<VT, XT, AT>, kHaloThreads,
+                                                      halo_smem_bytes<XT>()) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <class VT, class XT, class AT>
+cudaError_t launch_halo(const StepArgs &a, cudaStream_t s)
+{
+    const int per = halo_blocks_per_sm<VT, XT, AT>();
+    if (per < 1) return cudaErrorInvalidConfiguration;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    spmm_halo_kernel<VT, XT, AT><<<sms * per, kHaloThreads, halo_smem_bytes<XT>(), s>>>(a);
+    return cudaGetLastError();
+}
+
 // Absorbed and exited mass of X(t) per right-hand side (FP64 ledger) and the
 // injected mass of this step.  blockIdx.y is the right-hand side.
 template <class XT>
@@ -272,6 +438,7 @@ struct SpmmLaunch {
     }
     static int per_sm(int rt, int threads, int order)
     {
+        if (order == 2) return halo_blocks_per_sm<VT, XT, AT>();
         return order == 0 ? per_sm_order<0>(rt, threads) : per_sm_order<1>(rt, threads);
     }
     template <int ORDER>
@@ -321,6 +488,11 @@ cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int 
         if (f64) ledger_kernel<double><<<grid, 256, 0, s>>>(a);
         else ledger_kernel<float><<<grid, 256, 0, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (order == 2) {           // one launch: the kernel loops over the right-hand-side tiles
+        if (a.A.precision == DRTS_FP64) return launch_halo<double, double, double>(a, s);
+        if (a.A.precision == DRTS_FP32) return launch_halo<float, float, float>(a, s);
+        return launch_halo<__half, float, float>(a, s);
     }
     for (int r0 = 0; r0 < n_rhs; r0 += rhs_tile) {
         if (a.A.precision == DRTS_FP64)

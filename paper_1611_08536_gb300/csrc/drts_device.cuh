@@ -165,8 +165,10 @@ cudaError_t launch_ledger_sum(const void *x, int precision, int64_t n, int R, in
 
 // batched step (drts_batched.cu): functionals (detector + ledger of X(t))
 // when asked, then ceil(R / rhs_tile) passes of the product over A; order 0
-// strides warps over slices, order 1 is block-major (kBatchedOrders orders)
-constexpr int kBatchedOrders = 2;
+// strides warps over slices, order 1 is block-major, order 2 stages each
+// voxel block's x halo in shared memory (one launch, fixed tile and block
+// shape: 26 warps, 4 FP32 / 2 FP64 right-hand sides per pass)
+constexpr int kBatchedOrders = 3;
 int batched_blocks_per_sm(int precision, int rhs_tile, int threads, int order);
 cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int order, int blocks, int threads,
                                 bool functionals, cudaStream_t s);

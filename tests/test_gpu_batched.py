@@ -40,11 +40,13 @@ def run_batched(gpu, prob, srcs, steps, tile=0, order=-1):
 
 
 @pytest.mark.parametrize("n_rhs,tile,order", [(5, 0, -1), (5, 4, 0), (8, 8, 0), (13, 16, 0), (33, 32, 0),
-                                              (5, 4, 1), (8, 8, 1), (13, 16, 1), (33, 32, 1)])
+                                              (5, 4, 1), (8, 8, 1), (13, 16, 1), (33, 32, 1),
+                                              (2, 4, 2), (5, 4, 2), (13, 4, 2), (33, 4, 2)])
 def test_batched_fp32_matches_oracle(gpu, oracle_mod, n_rhs, tile, order):
-    """Both slice orders (warps striding over slices; block-major) and every
-    right-hand-side tile, on a 12^3 grid whose 54 voxel blocks of 32 wrap
-    across x rows (ragged block boundaries)."""
+    """All slice orders (warps striding over slices; block-major; block-major
+    with the x halo in shared memory) and every right-hand-side tile, on a
+    12^3 grid whose 54 voxel blocks of 32 wrap across x rows (ragged block
+    boundaries, halo ranges reaching past both ends of the state)."""
     prob, srcs = I.inclusions(12, n_rhs=n_rhs, seed=21, precision=I.FP32, n_spheres=2)
     steps = 40
     csr = oracle_mod.assemble(prob)
@@ -70,7 +72,7 @@ def test_batched_same_alone_and_in_mix(gpu):
         assert rel_l1(dets[r], d1[0]) < 1e-6
 
 
-@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("order", [0, 1, 2])
 def test_batched_fp64_and_fp16(gpu, oracle_mod, order):
     for prec, tol in ((I.FP64, 1e-12), (I.FP16_ROWSCALE, 5e-3)):
         prob, srcs = I.inclusions(10, n_rhs=4, seed=8, precision=prec, n_spheres=1)
