@@ -328,6 +328,21 @@ def batched_roofline(args, flops, ms):
             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
 
+def batched_launches(args, tune, info, R):
+    """Kernels launched in the timed region of the batched run: per step the
+    detector readout (when there are patches), the ledger reduction and the
+    product (one launch per tile of right-hand sides, one for the
+    shared-memory-halo order and the tensor-core form)."""
+    if tune is None:
+        return None
+    per = (1 if info.n_patch > 0 else 0) + 1
+    if args.batched_kernel == "tensor" or tune["variant"] == 2:
+        per += 1
+    else:
+        per += -(-R // tune["rhs_tile"])
+    return per * args.steps
+
+
 def run_batched(args):
     """Batched step: one pass over A serves R right-hand sides.  Reports
     nonzero-RHS products per second, simulations per second for a run of
@@ -345,6 +360,8 @@ def run_batched(args):
     ctx = drts.Context(prob, max_steps=args.warmup + args.steps + 1, stream=stream.cuda_stream)
     for r, sr in enumerate(srcs):
         ctx.set_source(r, sr)
+    if args.variant >= 0 or args.threads or args.blocks_per_sm or args.rhs_tile:
+        ctx.set_launch(args.blocks_per_sm, args.threads, args.rhs_tile, args.variant)
     tune = ctx.autotune(args.autotune) if args.autotune else None
     info = ctx.info()
     ctx.step_n(args.warmup)
@@ -397,7 +414,7 @@ def run_batched(args):
                    "speedup_vs_plain_per_simulation": round(R * ms1 / ms, 2),
                    "sim_steps": args.sim_steps},
         "roofline": batched_roofline(args, flops, ms),
-        "gpu_launches": None, "clocks": clk.summary(),
+        "gpu_launches": batched_launches(args, tune, info, R), "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -583,7 +600,8 @@ def run_functionals(args):
                    "ms_plain": round(ms_plain, 4), "ms_point_detectors": round(ms_point, 4),
                    "ms_point_and_substep": round(ms_both, 4),
                    "gnnz_per_s_plain": round(info.nnz / (ms_plain * 1e-3) / 1e9, 1)},
-        "gpu_launches": None, "clocks": clk.summary(),
+        # per step: point detectors, product, sub-step sources
+        "gpu_launches": 3 * args.steps, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
 
@@ -602,6 +620,7 @@ def main():
     ap.add_argument("--variant", type=int, default=-1)
     ap.add_argument("--autotune", type=int, default=2, help="timed steps per candidate (0 = off)")
     ap.add_argument("--rhs", type=int, default=1, help="right-hand sides (batched step when > 1)")
+    ap.add_argument("--rhs-tile", type=int, default=0, help="batched: right-hand sides per pass (0 = default)")
     ap.add_argument("--step-mode", default="launch", choices=["launch", "persistent"])
     ap.add_argument("--serve", action="store_true", help="served-stream benchmark")
     ap.add_argument("--serve-requests", type=int, default=24)
