@@ -273,7 +273,9 @@ drts_status drts_get_info(const drts_ctx *ctx, drts_info *out);
  * shapes (groups, stages) = (8,3), (4,3), (4,4), (2,6); 7-8 = state halo of
  * each 32-voxel block staged in shared memory, 13 or 26 warps, grids with nx
  * a multiple of 32 only; 9 = registers path with the matrix stream two groups
- * ahead and the x gathers of the next group in flight).  For a batched
+ * ahead and the x gathers of the next group in flight; 10-11 = two or four
+ * warps per slice, each summing a contiguous part of the rows, for grids too
+ * small to give every warp slot a slice).  For a batched
  * context on the CUDA cores the variant is the slice order: 0 = warps
  * stride over all slices, 1 = block-major (one CTA works through all 26
  * direction slices of a voxel block), 2 = block-major with the block's x

@@ -285,7 +285,7 @@ cudaError_t launch_any_step(drts_ctx *c, const StepArgs &a)
 
 int fit_blocks(drts_ctx *c, int threads, int variant, int rhs_tile)
 {
-    if (c->R == 1 && variant >= 7 && c->prob.nx % kSlice != 0) return 0;   // halo variants: whole blocks
+    if (c->R == 1 && (variant == 7 || variant == 8) && c->prob.nx % kSlice != 0) return 0;   // halo: whole blocks
     if (c->R == 1) return step_default_blocks(c->A.precision, c->R, threads, variant);
     int dev = 0, sms = 0;
     if (c->tc) {

@@ -148,10 +148,11 @@ cudaError_t launch_count_export(const SlicedMatrix &A, int64_t V, int64_t row_be
 // variant: 0-2 registers path (prefetch depth 1-3), 3-6 bulk-copy paths
 // (shared-memory stages of (G, S) = (8,3), (4,3), (4,4), (2,6)), 7-8
 // shared-memory x-halo paths with 13 or 26 warps (nx a multiple of 32), 9
-// registers path with matrix and gather streams both pipelined
+// registers path with matrix and gather streams both pipelined, 10-11 two
+// or four warps per slice (small grids)
 cudaError_t launch_step(const StepArgs &a, int variant, int blocks, int threads, cudaStream_t s);
 int step_default_blocks(int precision, int R, int threads, int variant);
-constexpr int kStepVariants = 10;
+constexpr int kStepVariants = 12;
 // persistent multi-step kernel (cooperative launch, bounded grid barrier)
 int persistent_blocks(int precision, int threads);
 cudaError_t launch_persistent(const StepArgs &a, void *other, int64_t n_steps, double *det_base, int64_t max_steps,

@@ -113,7 +113,9 @@ __device__ __forceinline__ void unpack(const RawGroup<double> &g, double w[4])
 
 // State loads: through the read-only cache when x is not written during the
 // kernel; coherent (L2) loads in the persistent kernel, which writes the
-// buffer it reads in the next step.
+// buffer it reads in the next step.  (Ordinary L1-cached loads after the
+// grid barrier measured slower there: 118 vs 97 us per step at 16^3 FP64,
+// 61.5 vs 44.7 ms at 192^3 FP16.)
 template <bool COHERENT, class XT>
 __device__ __forceinline__ XT load_x(const XT *p)
 {
@@ -343,6 +345,56 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
         const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
         const AT acc = row_dot<VT, XT, AT, D>(vals, codes, base, len4, x, v, sh.delta);
         row_epilogue<XT, AT>(a, sh, q, lane, v, m, acc, ab_lane, ex_lane);
+    }
+    step_finish(a, sh, ab_lane, ex_lane);
+}
+
+// Variants 10-11: K warps per slice (K = 2, 4).  On small grids a slice
+// per warp leaves most warp slots empty and each warp walks ~50 groups of
+// its row one after another; splitting every slice's groups into K
+// contiguous parts run by K warps of the CTA multiplies the matrix loads in
+// flight by K.  The parts' sums meet in shared memory and warp part 0 adds
+// them in part order (deterministic) and finishes the rows.
+template <class VT, class XT, class AT, int K>
+__global__ void __launch_bounds__(256) step_kernel_split(StepArgs a)
+{
+    __shared__ StepShared sh;
+    __shared__ AT part[8][kSlice];
+    step_prologue(a, sh);
+    const XT *__restrict__ x = static_cast<const XT *>(a.x);
+    const VT *__restrict__ vals = static_cast<const VT *>(a.A.vals);
+    const uint16_t *__restrict__ codes = a.A.codes;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per_cta = (blockDim.x >> 5) / K;                 // slices per CTA round
+    const int k = warp % K, slot = warp / K;
+    const int64_t rounds = (a.A.n_slices + int64_t(gridDim.x) * per_cta - 1) / (int64_t(gridDim.x) * per_cta);
+    AT ab_lane = 0, ex_lane = 0;
+    for (int64_t rd = 0; rd < rounds; ++rd) {
+        const int64_t q = (rd * gridDim.x + blockIdx.x) * per_cta + slot;
+        const bool live = slot < per_cta && q < a.A.n_slices;
+        AT acc = 0;
+        int64_t b = 0, v = 0;
+        int m = 0;
+        if (live) {
+            b = q / kDirs;
+            m = int(q - b * kDirs);
+            v = b * kSlice + lane;
+            const int len4 = a.A.slice_len4[q];
+            const int chunk = (len4 + K - 1) / K;
+            const int g0 = k * chunk < len4 ? k * chunk : len4;
+            const int g1 = g0 + chunk < len4 ? g0 + chunk : len4;
+            const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup + int64_t(g0) * (kSlice * kGroup);
+            acc = row_dot<VT, XT, AT, 2>(vals, codes, base, g1 - g0, x, v, sh.delta);
+        }
+        part[warp][lane] = acc;
+        __syncthreads();
+        if (live && k == 0) {
+            AT sum = part[warp][lane];
+#pragma unroll
+            for (int j = 1; j < K; ++j) sum += part[warp + j][lane];
+            row_epilogue<XT, AT>(a, sh, q, lane, v, m, sum, ab_lane, ex_lane);
+        }
+        __syncthreads();
     }
     step_finish(a, sh, ab_lane, ex_lane);
 }
@@ -786,6 +838,26 @@ struct RegLaunch {
 
 // Halo variants run with W warps whatever thread count is asked for, and only
 // on grids whose x-lines split into whole 32-voxel blocks.
+template <class VT, class XT, class AT, int K>
+struct SplitLaunch {
+    static int per_sm(int threads)
+    {
+        if (threads < 32 * K) return 0;
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_split<VT, XT, AT, K>, threads, 0) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return n;
+    }
+    static cudaError_t launch(const StepArgs &a, int blocks, int threads, cudaStream_t s)
+    {
+        step_kernel_split<VT, XT, AT, K><<<blocks, threads, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
 template <class VT, class XT, class AT, int W>
 struct HaloLaunch {
     static int per_sm(int threads)
@@ -841,6 +913,8 @@ struct Variants {
         case 7: return HaloLaunch<VT, XT, AT, 13>::per_sm(threads);
         case 8: return HaloLaunch<VT, XT, AT, 26>::per_sm(threads);
         case 9: return PipeLaunch<VT, XT, AT>::per_sm(threads);
+        case 10: return SplitLaunch<VT, XT, AT, 2>::per_sm(threads);
+        case 11: return SplitLaunch<VT, XT, AT, 4>::per_sm(threads);
         }
         return 0;
     }
@@ -857,6 +931,8 @@ struct Variants {
         case 7: return HaloLaunch<VT, XT, AT, 13>::launch(a, blocks, threads, s);
         case 8: return HaloLaunch<VT, XT, AT, 26>::launch(a, blocks, threads, s);
         case 9: return PipeLaunch<VT, XT, AT>::launch(a, blocks, threads, s);
+        case 10: return SplitLaunch<VT, XT, AT, 2>::launch(a, blocks, threads, s);
+        case 11: return SplitLaunch<VT, XT, AT, 4>::launch(a, blocks, threads, s);
         }
         return cudaErrorInvalidValue;
     }

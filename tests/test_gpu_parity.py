@@ -222,7 +222,7 @@ def test_run_host_matches_step_n(gpu):
     assert rel_l1(det[:, 0, :], da) < 1e-6
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("variant", list(range(12)))
 @pytest.mark.parametrize("precision", [I.FP64, I.FP32, I.FP16_ROWSCALE])
 def test_step_variants_agree(gpu, oracle_mod, variant, precision):
     """Every launch variant of the step computes the same step (32 x 14 x 14
@@ -249,6 +249,33 @@ def test_step_variants_agree(gpu, oracle_mod, variant, precision):
         x = ctx.read_state()
     tol = {I.FP64: 1e-12, I.FP32: 1e-6, I.FP16_ROWSCALE: 2e-3}[precision]
     assert rel_l1(x, xo) < tol
+
+
+@pytest.mark.parametrize("variant,threads", [(9, 256), (10, 256), (10, 96), (11, 256), (11, 128)])
+def test_step_variants_ragged_grid(gpu, oracle_mod, variant, threads):
+    """The register variants that take any grid (pipelined, two and four
+    warps per slice) on a 13 x 11 x 9 FP64 grid whose 32-voxel blocks wrap
+    across x rows, with detector and ledger, including block shapes whose
+    warp count is not a multiple of the warps per slice."""
+    prob, _ = I.three_layers(9, precision=I.FP64)
+    mov = np.repeat(np.repeat(np.asarray(prob.medium_of_voxel)[:, :1, :1], 11, axis=1), 13, axis=2)
+    prob = I.Problem((13, 11, 9), prob.voxel_mm, prob.media, mov, prob.n_outside,
+                     prob.boundary, I.FP64, 1, prob.det_face, 4, 3, "layers_13x11x9")
+    rng = np.random.default_rng(21)
+    x0 = rng.random(prob.n_states)
+    src = I.Source(np.array([prob.state(6, 5, 0, 21)], np.int64), np.ones(1), 0, np.ones(3))
+    csr = oracle_mod.assemble(prob)
+    xo, deto, ledo = oracle_mod.run(prob, csr, 8, src.as_tuple(), x0=x0)
+    with gpu.Context(prob, max_steps=8) as ctx:
+        ctx.set_launch(0, threads, 0, variant)
+        ctx.write_state(x0)
+        ctx.set_source(0, src)
+        ctx.step_n(8)
+        x = ctx.read_state()
+        det, led = ctx.read_detectors()
+    assert rel_l1(x, xo) < 1e-12
+    assert rel_l1(det, deto) < 1e-12
+    assert np.allclose(led[1:], ledo[1:], rtol=1e-11)
 
 
 def test_bounded_wait_times_out_and_recovers(gpu, oracle_mod):
@@ -283,7 +310,9 @@ def test_autotune_keeps_state_and_parity(gpu, oracle_mod):
         ctx.write_state(x0)
         before = ctx.read_state()
         r = ctx.autotune(2)
-        assert 0 <= r["variant"] < 7 and r["candidates"] > 0 and r["ms_per_step"] > 0
+        # 16^3: the halo variants (7, 8: whole 32-voxel x-runs only) do not apply
+        assert 0 <= r["variant"] < 12 and r["variant"] not in (7, 8)
+        assert r["candidates"] > 0 and r["ms_per_step"] > 0
         assert np.array_equal(ctx.read_state(), before)
         det, led = ctx.read_detectors()
         assert np.all(led[1:] == 0.0)              # trial steps leave the ledger alone
