@@ -458,7 +458,7 @@ def run_serve(args):
     # the same requests one after another, no batching or overlap
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    for r in stream:
+    for r in (stream if args.serve_baselines else []):
         with drts.Context(r.problem, max_steps=r.n_steps) as ctx:
             for q, sr in enumerate(r.sources):
                 ctx.inject_source(q, sr.state, sr.weight, r.sources[0].t0, r.sources[0].profile)
@@ -469,7 +469,7 @@ def run_serve(args):
     import copy
     t2 = time.perf_counter()
     n_single = 0
-    for r in stream:
+    for r in (stream if args.serve_baselines else []):
         p1 = copy.copy(r.problem)
         p1.n_rhs = 1
         for sr in r.sources:
@@ -496,11 +496,13 @@ def run_serve(args):
                     "p99": round(float(np.percentile(queue, 99)), 3)},
         "makespan_s": round(makespan, 3),
         "sequential_requests": {"requests_per_s": round(n / seq, 4), "seconds": round(seq, 3),
-                                "note": "each request alone, its sources batched"},
+                                "note": "each request alone, its sources batched"}
+        if args.serve_baselines else None,
         "plain_per_simulation": {"simulations": n_single, "seconds": round(plain, 3),
                                  "requests_per_s": round(n / plain, 4),
-                                 "note": "every source a separate single-rhs run, one after another"},
-        "speedup_vs_plain_per_simulation": round(plain / makespan, 3),
+                                 "note": "every source a separate single-rhs run, one after another"}
+        if args.serve_baselines else None,
+        "speedup_vs_plain_per_simulation": round(plain / makespan, 3) if args.serve_baselines else None,
         "server_stats": stats, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
@@ -629,6 +631,8 @@ def main():
     ap.add_argument("--serve-resident", type=int, default=16)
     ap.add_argument("--serve-tick-steps", type=int, default=20)
     ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--no-serve-baselines", dest="serve_baselines", action="store_false",
+                    help="skip the one-after-another and per-simulation baseline runs")
     ap.add_argument("--sim-steps", type=int, default=1500, help="steps per simulation for sims/s")
     ap.add_argument("--batched-kernel", default="cuda", choices=["cuda", "tensor"])
     ap.add_argument("--functionals", action="store_true",
