@@ -419,6 +419,8 @@ typedef struct drts_request_info {
     double latency_s;                /* submit -> completion (host clock) */
 } drts_request_info;
 
+/* Counters since creation; resident, queued and used_bytes are the counts at
+ * the time of the call. */
 typedef struct drts_server_stats {
     int64_t submitted, admitted, completed, failed, ticks, graph_launches;
     int32_t resident, queued;

@@ -303,14 +303,21 @@ __global__ void __launch_bounds__(kHaloThreads, 1) spmm_halo_kernel(StepArgs a)
 template <class VT, class XT, class AT>
 int halo_blocks_per_sm()
 {
-    static bool attr = false;
-    if (!attr) {
+    // the shared-memory opt-in is a per-device function attribute: set it
+    // once on every device the kernel is used on
+    static bool attr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (!attr[dev]) {
         if (cudaFuncSetAttribute(spmm_halo_kernel<VT, XT, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(halo_smem_bytes<XT>())) != cudaSuccess) {
             cudaGetLastError();
             return 0;
         }
-        attr = true;
+        attr[dev] = true;
     }
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, spmm_halo_kernel<VT, XT, AT>, kHaloThreads,

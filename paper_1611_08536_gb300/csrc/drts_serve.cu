@@ -346,6 +346,9 @@ drts_status drts_server_get_stats(const drts_server *s, drts_server_stats *out)
 {
     if (!s || !out) return DRTS_EINVAL;
     *out = s->stats;
+    out->resident = int32_t(s->resident.size());     // live counts, not the last tick's
+    out->queued = int32_t(s->queue.size());
+    out->used_bytes = s->used;
     out->budget_bytes = s->budget;
     return DRTS_OK;
 }
