@@ -41,7 +41,7 @@ def check_rows(ctx, csr, precision):
     assert np.array_equal(rp, csr.row_ptr)
     assert np.array_equal(col, csr.col)
     if precision == I.FP16_ROWSCALE:
-        # FP16 times a power-of-two row scale, column-preserving rounding:
+        # FP16 times a power-of-two row scale, dithered rounding to a neighbour:
         # within one FP16 ulp of the value (plus the subnormal floor)
         rowmax = np.maximum.reduceat(csr.val, csr.row_ptr[:-1]) if csr.nnz else np.zeros(0)
         rm = np.repeat(rowmax, np.diff(csr.row_ptr))

@@ -98,3 +98,23 @@ def test_server_memory_budget_limits_residency(gpu):
                 break
         assert srv.stats()["completed"] == len(ids)
     assert biggest >= 1
+
+
+def test_server_stats_count_submissions_before_a_tick(gpu):
+    """A request is counted as queued as soon as it is submitted (a serving
+    loop that waits for queued work must see it before the next tick)."""
+    reqs = small_stream(2, seed=5)
+    with gpu.Server(max_resident=1, steps_per_tick=10, n_streams=2) as srv:
+        assert srv.stats()["queued"] == 0
+        ids = [srv.submit(r.problem, r.sources, r.n_steps) for r in reqs]
+        st = srv.stats()
+        assert st["queued"] == 2 and st["resident"] == 0 and st["submitted"] == 2
+        srv.tick()                                     # admits one (one slot)
+        st = srv.stats()
+        assert st["resident"] == 1 and st["queued"] == 1 and st["used_bytes"] > 0
+        while srv.stats()["completed"] < 2:
+            srv.tick()
+        st = srv.stats()
+        assert st["resident"] == 0 and st["queued"] == 0 and st["used_bytes"] == 0
+        for i in ids:
+            assert srv.poll(i).state == gpu.REQ_DONE
