@@ -112,6 +112,21 @@ cudaError_t dalloc(drts_ctx *c, T **p, size_t bytes)
     return e;
 }
 
+// Free a buffer from dalloc and forget it (the context stream is drained
+// first: kernels already queued may still read it).  No-op on NULL.
+template <class T>
+void drelease(drts_ctx *c, T *&p)
+{
+    if (!p) return;
+    cudaStreamSynchronize(c->stream);
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), static_cast<void *>(p));
+    if (it != c->allocs.end()) {
+        c->allocs.erase(it);
+        cudaFree(p);
+    }
+    p = nullptr;
+}
+
 template <class T>
 cudaError_t upload(drts_ctx *c, T **p, const std::vector<T> &v)
 {
@@ -1158,6 +1173,12 @@ drts_status upload_bulk(drts_ctx *c)
     rhs_off[c->R] = int32_t(groups.size());
     if (entries.size() > size_t(1) << 30) return fail(c, DRTS_EINVAL, "too many sub-step source entries");
     cudaError_t e = cudaSuccess;
+    drelease(c, c->d_bulk_groups);          // the previous set (if any)
+    drelease(c, c->d_bulk_rhs_off);
+    drelease(c, c->d_bulk_entries);
+    drelease(c, c->d_bulk_prof);
+    drelease(c, c->d_bulk_prof_vals);
+    c->n_bulk_groups = 0;
     if (!groups.empty()) {
         if ((e = upload(c, &c->d_bulk_groups, groups)) != cudaSuccess ||
             (e = upload(c, &c->d_bulk_rhs_off, rhs_off)) != cudaSuccess ||
@@ -1249,8 +1270,15 @@ drts_status drts_set_point_detectors(drts_ctx *c, int32_t n_det, int64_t n_entri
     if (n_det < 0 || n_det > 65535) return fail(c, DRTS_EINVAL, "n_det must be 0..65535");
     if (n_entries < 0 || (n_entries > 0 && (!det || !state_idx || !weight)))
         return fail(c, DRTS_EINVAL, "bad entry arrays");
-    if (n_det == 0) {
+    auto drop_old = [&]() {                 // the previous set (if any) goes
         c->n_pdet = 0;
+        drelease(c, c->d_pdet_off);
+        drelease(c, c->d_pdet_state);
+        drelease(c, c->d_pdet_w);
+        drelease(c, c->d_pdet_hist);
+    };
+    if (n_det == 0) {
+        drop_old();
         return DRTS_OK;
     }
     if (c->prob.max_steps <= 0)
@@ -1272,6 +1300,7 @@ drts_status drts_set_point_detectors(drts_ctx *c, int32_t n_det, int64_t n_entri
         st[q] = state_idx[e];
         w[q] = weight[e];
     }
+    drop_old();
     cudaError_t e = cudaSuccess;
     if ((e = upload(c, &c->d_pdet_off, off)) != cudaSuccess || (e = upload(c, &c->d_pdet_state, st)) != cudaSuccess ||
         (e = upload(c, &c->d_pdet_w, w)) != cudaSuccess ||

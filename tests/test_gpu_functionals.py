@@ -296,3 +296,42 @@ def test_substep_source_mode_limits(gpu):
         ctx.inject_source_substeps(0, [], [], 0, np.ones((1, 2)))      # removes it
         ctx.set_step_mode(gpu.STEP_PERSISTENT)
         ctx.step_n(2)
+
+
+def test_point_detectors_replaced_and_kept_on_error(gpu, oracle_mod):
+    """Setting detectors again replaces the set and clears its history (steps
+    before the call read 0); a rejected call leaves the current set alone."""
+    prob = _layered(8, I.FP64)
+    src = I.Source(np.array([prob.state(4, 4, 0, I.direction_index(0, 0, 1))], np.int64),
+                   np.ones(1), 0, np.ones(1))
+    first, second = _point_rows(prob, seed=1, n_det=3), _point_rows(prob, seed=2, n_det=5)
+    csr = oracle_mod.assemble(prob)
+    _, _, _, pdo = _oracle_point(oracle_mod, prob, csr, 12, src, second)
+    with gpu.Context(prob, max_steps=12) as ctx:
+        ctx.set_source(0, src)
+        ctx.set_point_detectors(*first)
+        ctx.step_n(5)
+        ctx.set_point_detectors(*second)
+        with pytest.raises(gpu.DrtsError):
+            ctx.set_point_detectors(2, [5], [0], [1.0])        # detector index out of range
+        ctx.step_n(7)
+        pd = ctx.read_point_detectors()
+    assert pd.shape == (12, 5)
+    assert not pd[:5].any()
+    np.testing.assert_allclose(pd[5:], pdo[5:], rtol=1e-12, atol=1e-300)
+
+
+def test_substep_source_replaced(gpu, oracle_mod):
+    """A second sub-step source for the same rhs replaces the first."""
+    prob = _layered(8, I.FP64)
+    s1 = prob.state(4, 4, 0, I.direction_index(0, 0, 1))
+    s2 = prob.state(3, 5, 0, I.direction_index(1, 0, 1))
+    prof = np.array([[0.3, 0.7]])
+    csr = oracle_mod.assemble(prob)
+    xo, _, _ = _substep_oracle(oracle_mod, prob, csr, 10, s2, 2.0, 0, prof)
+    with gpu.Context(prob, max_steps=10) as ctx:
+        ctx.inject_source_substeps(0, [s1], [1.0], 0, prof)
+        ctx.inject_source_substeps(0, [s2], [2.0], 0, prof)
+        ctx.step_n(10)
+        x = ctx.read_state()
+    assert rel_l1(x, xo) < 1e-12
