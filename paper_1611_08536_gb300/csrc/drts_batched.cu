@@ -19,6 +19,8 @@
 // (a deterministic sum, no atomics) and a reduction per right-hand side.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "drts_device.cuh"
 #include "drts_kernel_common.cuh"
 
@@ -120,28 +122,48 @@ __global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
             load4(vals + base, wn);
             load_codes(codes + base, cn);
         }
-        for (int g = 0; g < len4; ++g) {
-            AT w[4];
-            int c[4];
+        // state indices fit 32 bits (fewer than 2^31 states); 32-bit offsets
+        // save address arithmetic for narrow tiles, wide tiles keep 64-bit
+        // ones (fewer registers there)
+        using OT = typename std::conditional<(RT <= 4), int32_t, int64_t>::type;
+        const OT v32 = OT(v);
+        // products of H groups per compensated addition: two while the tile
+        // is narrow (fewer additions), one for wide tiles (registers)
+        constexpr int H = RT <= 4 ? 2 : 1;
+        for (int g0 = 0; g0 < len4; g0 += H) {
+            AT p[RT];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) { w[j] = wn[j]; c[j] = cn[j]; }
-            if (g + 1 < len4) {
-                const int64_t idx = base + int64_t(g + 1) * (kSlice * kGroup);
-                load4(vals + idx, wn);
-                load_codes(codes + idx, cn);
-            }
-            const int64_t o0 = v + s_delta[c[0]], o1 = v + s_delta[c[1]];
-            const int64_t o2 = v + s_delta[c[2]], o3 = v + s_delta[c[3]];
+            for (int h = 0; h < H; ++h) {
+                const int g = g0 + h;
+                if (g >= len4) break;
+                AT w[4];
+                int c[4];
 #pragma unroll
-            for (int r = 0; r < RT; ++r) {
-                if (r < nr) {
-                    const XT *xr = x + r * S;
-                    AT p = w[0] * AT(__ldg(xr + o0));
-                    p = fma(w[1], AT(__ldg(xr + o1)), p);
-                    p = fma(w[2], AT(__ldg(xr + o2)), p);
-                    p = fma(w[3], AT(__ldg(xr + o3)), p);
-                    acc[r].add(p);
+                for (int j = 0; j < 4; ++j) { w[j] = wn[j]; c[j] = cn[j]; }
+                if (g + 1 < len4) {
+                    const int64_t idx = base + int64_t(g + 1) * (kSlice * kGroup);
+                    load4(vals + idx, wn);
+                    load_codes(codes + idx, cn);
                 }
+                const OT o0 = v32 + s_delta[c[0]], o1 = v32 + s_delta[c[1]];
+                const OT o2 = v32 + s_delta[c[2]], o3 = v32 + s_delta[c[3]];
+#pragma unroll
+                for (int r = 0; r < RT; ++r) {
+                    if (r < nr) {
+                        const XT *xr = x + r * S;
+                        AT q = h ? fma(w[0], AT(__ldg(xr + o0)), p[r]) : w[0] * AT(__ldg(xr + o0));
+                        q = fma(w[1], AT(__ldg(xr + o1)), q);
+                        q = fma(w[2], AT(__ldg(xr + o2)), q);
+                        q = fma(w[3], AT(__ldg(xr + o3)), q);
+                        if constexpr (H == 1) acc[r].add(q);
+                        else p[r] = q;
+                    }
+                }
+            }
+            if constexpr (H > 1) {
+#pragma unroll
+                for (int r = 0; r < RT; ++r)
+                    if (r < nr) acc[r].add(p[r]);
             }
         }
         if (v >= V) continue;
