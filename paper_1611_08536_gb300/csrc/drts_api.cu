@@ -497,21 +497,10 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     c->variant = 0;
     c->rhs_tile = 0;
     if (c->R > 1 && !c->tc) {
-        // measured defaults of the CUDA-core batched step (GB300, FP32): 8
-        // right-hand sides per pass while an x-y plane is small; above that
-        // wider tiles lose their x lines from L1 and 4 per pass wins, with
-        // 128-thread blocks up to ~88^2 per plane and block-major slice
-        // order beyond (the autotuner refines this per problem)
-        const int64_t plane = int64_t(prob->nx) * prob->ny;
-        if (plane <= 64 * 64) {
-            c->rhs_tile = c->R <= 4 ? 4 : 8;
-        } else if (plane <= 88 * 88) {
-            c->rhs_tile = 4;
-            c->threads = 128;
-        } else {
-            c->rhs_tile = 4;
-            c->variant = 1;
-        }
+        // measured default of the CUDA-core batched step (GB300, FP32, grids
+        // 48^3 - 96^3): 4 right-hand sides per pass, warps striding over the
+        // slices (the autotuner refines this per problem)
+        c->rhs_tile = 4;
     }
     if (c->tc) c->rhs_tile = std::min(32, c->tc_rp);
     c->blocks = fit_blocks(c, c->threads, c->variant, c->rhs_tile);

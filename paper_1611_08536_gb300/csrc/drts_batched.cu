@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
         const OT v32 = OT(v);
         // products of H groups per compensated addition: two while the tile
         // is narrow (fewer additions), one for wide tiles (registers)
-        constexpr int H = RT <= 4 ? 2 : 1;
+        constexpr int H = RT <= 4 ? 4 : 1;
         for (int g0 = 0; g0 < len4; g0 += H) {
             AT p[RT];
 #pragma unroll
