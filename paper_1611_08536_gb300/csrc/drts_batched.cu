@@ -10,9 +10,11 @@
 // request; a right-hand-side-minor layout would scatter each request over
 // 32 cache lines.
 //
-// Accumulation: the four products of a group are chained with FMA and the
-// group sum is added to a Kahan-compensated accumulator (plain FP32 sums of
-// ~200 positive terms drift the solution by ~1e-7 per step).
+// Accumulation: products are chained with FMA and the chain is added to a
+// Kahan-compensated accumulator (plain FP32 sums of ~200 positive terms
+// drift the solution by ~1e-7 per step).  With 4 right-hand sides per pass
+// a chain covers four groups (16 products), which saves instructions - the
+// resource this kernel runs out of first; wider tiles add every group.
 //
 // The detector readout (Eq. 27) and the FP64 ledger of X(t) come from two
 // small kernels launched before the product: one block per detector patch
