@@ -232,10 +232,18 @@ drts_status upload_sources(drts_ctx *c)
     return sync_check(c, "source upload");
 }
 
-// base of right-hand side r inside a state buffer
-void *rhs_ptr(drts_ctx *c, void *buf, int r)
+// Right-hand side r inside a state buffer: first element and the distance
+// between consecutive states (1 for one right-hand side; 4 for the batched
+// layout, which keeps groups of four right-hand sides side by side).
+struct RhsView {
+    void *base;
+    int stride;
+};
+RhsView rhs_view(drts_ctx *c, void *buf, int r)
 {
-    return static_cast<char *>(buf) + size_t(r) * c->rhs_stride * state_elem_bytes(c->prob.precision);
+    if (c->R == 1) return RhsView{buf, 1};
+    const size_t elems = (size_t(r >> 2) * c->rhs_stride) * 4 + size_t(r & 3);
+    return RhsView{static_cast<char *>(buf) + elems * state_elem_bytes(c->prob.precision), 4};
 }
 
 StepArgs make_args(drts_ctx *c)
@@ -453,7 +461,8 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
         c->special_permille = int(special * 1000 / c->V);
     }
     // state, ledger, detector history, sources
-    c->x_elems = c->tc ? c->V * c->tc_rp * 32 + 64 : c->rhs_stride * c->R;
+    c->x_elems = c->tc ? c->V * c->tc_rp * 32 + 64
+                       : (c->R == 1 ? c->rhs_stride : c->rhs_stride * ((c->R + 3) / 4) * 4);
     if (c->tc) {
         const size_t bb = size_t(c->V) * 27 * 6144;
         if ((e = dalloc(c, &c->tc_blocks, bb)) != cudaSuccess) {
@@ -498,9 +507,11 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     c->rhs_tile = 0;
     if (c->R > 1 && !c->tc) {
         // measured default of the CUDA-core batched step (GB300, FP32, grids
-        // 48^3 - 96^3): 4 right-hand sides per pass, warps striding over the
-        // slices (the autotuner refines this per problem)
-        c->rhs_tile = 4;
+        // 48^3 - 96^3): 8 right-hand sides per pass (two 16-byte gathers per
+        // nonzero), warps striding over the slices, block-major above ~88^2
+        // voxels per x-y plane (the autotuner refines this per problem)
+        c->rhs_tile = c->R <= 4 ? 4 : 8;
+        if (int64_t(prob->nx) * prob->ny > 88 * 88) c->variant = 1;
     }
     if (c->tc) c->rhs_tile = std::min(32, c->tc_rp);
     c->blocks = fit_blocks(c, c->threads, c->variant, c->rhs_tile);
@@ -624,7 +635,8 @@ drts_status drts_read_detectors(drts_ctx *c, int32_t rhs, int64_t t_begin, int64
         e = cudaMallocAsync(&tmp, sizeof(double), c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(tmp, 0, sizeof(double), c->stream);
         if (e == cudaSuccess) e = (c->tc ? launch_tc_sum(c->x, c->V, c->tc_rp, rhs, tmp, c->stream)
-                                      : launch_ledger_sum(rhs_ptr(c, c->x, rhs), c->prob.precision, c->n_states, 1, 0, tmp, c->stream));
+                                      : launch_ledger_sum(rhs_view(c, c->x, rhs).base, c->prob.precision, c->n_states,
+                                                          rhs_view(c, c->x, rhs).stride, 0, tmp, c->stream));
         if (e == cudaSuccess) e = cudaMemcpyAsync(ledger_out, tmp, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ledger_out + 1, c->ledger + 4 * rhs + 1, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -642,7 +654,8 @@ drts_status drts_read_state(drts_ctx *c, int32_t rhs, double *host_out)
     cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * c->n_states, c->stream);
     if (e == cudaSuccess)
         e = c->tc ? launch_tc_to_canonical(c->x, c->V, c->tc_rp, rhs, tmp, c->stream)
-                  : launch_to_canonical(rhs_ptr(c, c->x, rhs), c->prob.precision, c->V, 1, 0, tmp, c->stream);
+                  : launch_to_canonical(rhs_view(c, c->x, rhs).base, c->prob.precision, c->V,
+                                        rhs_view(c, c->x, rhs).stride, 0, tmp, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host_out, tmp, sizeof(double) * c->n_states, cudaMemcpyDeviceToHost, c->stream);
     if (tmp) cudaFreeAsync(tmp, c->stream);
@@ -660,7 +673,8 @@ drts_status drts_write_state(drts_ctx *c, int32_t rhs, const double *host_in)
         e = cudaMemcpyAsync(tmp, host_in, sizeof(double) * c->n_states, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = c->tc ? launch_tc_from_canonical(tmp, c->V, c->tc_rp, rhs, c->x, c->stream)
-                  : launch_from_canonical(tmp, c->prob.precision, c->V, 1, 0, rhs_ptr(c, c->x, rhs), c->stream);
+                  : launch_from_canonical(tmp, c->prob.precision, c->V, rhs_view(c, c->x, rhs).stride, 0,
+                                          rhs_view(c, c->x, rhs).base, c->stream);
     if (tmp) cudaFreeAsync(tmp, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "write_state");
     return sync_check(c, "write_state");
@@ -1070,7 +1084,8 @@ drts_status drts_state_sum_noalloc(drts_ctx *c, int32_t rhs, double *out_device)
         return fail(c, DRTS_EINVAL, "state vector of " + std::to_string(c->n_states) +
                                         " states exceeds the static scratch limit of " +
                                         std::to_string(noalloc_max_states()));
-    cudaError_t e = launch_state_sum_noalloc(rhs_ptr(c, c->x, rhs), c->prob.precision, c->n_states, 1, 0, out_device,
+    cudaError_t e = launch_state_sum_noalloc(rhs_view(c, c->x, rhs).base, c->prob.precision, c->n_states,
+                                             rhs_view(c, c->x, rhs).stride, 0, out_device,
                                              c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "state_sum_noalloc");
     return DRTS_OK;

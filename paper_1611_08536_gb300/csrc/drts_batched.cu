@@ -4,17 +4,18 @@
 // at a time: every nonzero's value and code are loaded once and used for RT
 // multiply-adds against X[r0 .. r0+RT)[column].
 //
-// State layout: right-hand-side major, X[r*rhs_stride + n*V + v].  For one
-// code the 32 lanes of a slice (32 consecutive voxels) read 32 consecutive
-// floats of each right-hand side, so every gather is one coalesced 128-byte
-// request; a right-hand-side-minor layout would scatter each request over
-// 32 cache lines.
+// State layout: right-hand sides in groups of four, each group state-major
+// with the group's four values of a state side by side:
+//   X[((r/4) * rhs_stride + n*V + v) * 4 + r%4].
+// For one code the 32 lanes of a slice (32 consecutive voxels) read 32
+// consecutive 16-byte vectors, i.e. one coalesced 512-byte request serves
+// four right-hand sides with a single load instruction per lane.
 //
 // Accumulation: products are chained with FMA and the chain is added to a
 // Kahan-compensated accumulator (plain FP32 sums of ~200 positive terms
 // drift the solution by ~1e-7 per step).  With 4 right-hand sides per pass
-// a chain covers four groups (16 products), which saves instructions - the
-// resource this kernel runs out of first; wider tiles add every group.
+// a chain covers four groups (16 products), which saves instructions;
+// wider tiles add every group.
 //
 // The detector readout (Eq. 27) and the FP64 ledger of X(t) come from two
 // small kernels launched before the product: one block per detector patch
@@ -67,6 +68,33 @@ struct KahanAcc<double> {
     __device__ __forceinline__ void add(double v) { s += v; }
 };
 
+// the four values of state o in a group of right-hand sides
+__device__ __forceinline__ void load_rhs4(const float *g, int32_t o, float out[4])
+{
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(g) + o);
+    out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
+}
+__device__ __forceinline__ void load_rhs4(const float *g, int64_t o, float out[4])
+{
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(g) + o);
+    out[0] = t.x; out[1] = t.y; out[2] = t.z; out[3] = t.w;
+}
+__device__ __forceinline__ void load_rhs4(const double *g, int64_t o, double out[4])
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(g) + 2 * o);
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(g) + 2 * o + 1);
+    out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+}
+__device__ __forceinline__ void store_rhs4(float *g, int64_t o, const float v[4])
+{
+    reinterpret_cast<float4 *>(g)[o] = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store_rhs4(double *g, int64_t o, const double v[4])
+{
+    reinterpret_cast<double2 *>(g)[2 * o] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2 *>(g)[2 * o + 1] = make_double2(v[2], v[3]);
+}
+
 // ORDER 0: warps stride over slices (consecutive warps take consecutive
 // slices of the whole matrix).  ORDER 1: block-major - the CTA owns voxel
 // blocks b = blockIdx.x + k * gridDim.x and its warps share out the 26 slices
@@ -85,8 +113,10 @@ __global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
     __syncthreads();
     const int64_t S = a.rhs_stride;
     const int nr = a.R - r0 < RT ? a.R - r0 : RT;   // right-hand sides in this tile
-    const XT *__restrict__ x = static_cast<const XT *>(a.x) + int64_t(r0) * S;
-    XT *__restrict__ y = static_cast<XT *>(a.y) + int64_t(r0) * S;
+    constexpr int NG = RT / 4;                       // groups of four per tile
+    const int ngr = (nr + 3) >> 2;                   // groups holding live right-hand sides
+    const XT *__restrict__ x = static_cast<const XT *>(a.x) + int64_t(r0 >> 2) * 4 * S;
+    XT *__restrict__ y = static_cast<XT *>(a.y) + int64_t(r0 >> 2) * 4 * S;
     const VT *__restrict__ vals = static_cast<const VT *>(a.A.vals);
     const uint16_t *__restrict__ codes = a.A.codes;
     const int lane = threadIdx.x & 31;
@@ -125,12 +155,14 @@ __global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
             load_codes(codes + base, cn);
         }
         // state indices fit 32 bits (fewer than 2^31 states); 32-bit offsets
-        // save address arithmetic for narrow tiles, wide tiles keep 64-bit
-        // ones (fewer registers there)
-        using OT = typename std::conditional<(RT <= 4), int32_t, int64_t>::type;
+        // save address arithmetic for narrow FP32 tiles, the others keep
+        // 64-bit ones (fewer registers for wide tiles; FP64 vectors index
+        // twice the offset)
+        using OT = typename std::conditional<(RT <= 4 && sizeof(XT) == 4), int32_t, int64_t>::type;
         const OT v32 = OT(v);
-        // products of H groups per compensated addition: two while the tile
-        // is narrow (fewer additions), one for wide tiles (registers)
+        // products of H groups per compensated addition: four while the tile
+        // is narrow (fewer additions); one for wider tiles, where longer
+        // chains measured slower (RT 8: 2.5x against 3.1x per simulation)
         constexpr int H = RT <= 4 ? 4 : 1;
         for (int g0 = 0; g0 < len4; g0 += H) {
             AT p[RT];
@@ -150,22 +182,31 @@ __global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
                 const OT o0 = v32 + s_delta[c[0]], o1 = v32 + s_delta[c[1]];
                 const OT o2 = v32 + s_delta[c[2]], o3 = v32 + s_delta[c[3]];
 #pragma unroll
-                for (int r = 0; r < RT; ++r) {
-                    if (r < nr) {
-                        const XT *xr = x + r * S;
-                        AT q = h ? fma(w[0], AT(__ldg(xr + o0)), p[r]) : w[0] * AT(__ldg(xr + o0));
-                        q = fma(w[1], AT(__ldg(xr + o1)), q);
-                        q = fma(w[2], AT(__ldg(xr + o2)), q);
-                        q = fma(w[3], AT(__ldg(xr + o3)), q);
-                        if constexpr (H == 1) acc[r].add(q);
-                        else p[r] = q;
+                for (int gi = 0; gi < NG; ++gi) {
+                    if (gi < ngr) {
+                        const XT *xg = x + int64_t(gi) * 4 * S;
+                        XT x0[4], x1[4], x2[4], x3[4];
+                        load_rhs4(xg, o0, x0);
+                        load_rhs4(xg, o1, x1);
+                        load_rhs4(xg, o2, x2);
+                        load_rhs4(xg, o3, x3);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int r = gi * 4 + k;
+                            AT q = h ? fma(w[0], AT(x0[k]), p[r]) : w[0] * AT(x0[k]);
+                            q = fma(w[1], AT(x1[k]), q);
+                            q = fma(w[2], AT(x2[k]), q);
+                            q = fma(w[3], AT(x3[k]), q);
+                            if constexpr (H == 1) acc[r].add(q);
+                            else p[r] = q;
+                        }
                     }
                 }
             }
             if constexpr (H > 1) {
 #pragma unroll
                 for (int r = 0; r < RT; ++r)
-                    if (r < nr) acc[r].add(p[r]);
+                    if ((r >> 2) < ngr) acc[r].add(p[r]);
             }
         }
         if (v >= V) continue;
@@ -186,8 +227,13 @@ __global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
         }
         const int64_t row = int64_t(m) * V + v;
 #pragma unroll
-        for (int r = 0; r < RT; ++r)
-            if (r < nr) y[r * S + row] = XT(out[r]);
+        for (int gi = 0; gi < NG; ++gi)
+            if (gi < ngr) {
+                XT o4[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) o4[k] = XT(out[gi * 4 + k]);
+                store_rhs4(y + int64_t(gi) * 4 * S, row, o4);
+            }
     }
 }
 
@@ -261,7 +307,8 @@ __global__ void __launch_bounds__(kHaloThreads, 1) spmm_halo_kernel(StepArgs a)
                 const int r = rest / kHaloRanges;
                 const int64_t g = v0 + (int64_t(rr / 3 - 1) * a.ny + (rr % 3 - 1)) * a.nx - 1 + p;
                 XT val = XT(0);
-                if (r < nr && g >= 0 && g < V) val = x[int64_t(r0 + r) * S + int64_t(n) * V + g];
+                const int ra = r0 + r;
+                if (r < nr && g >= 0 && g < V) val = x[(int64_t(ra >> 2) * S + int64_t(n) * V + g) * 4 + (ra & 3)];
                 xs[((rr * kDirs + n) * kHaloVox + p) * RT + r] = val;
             }
             __syncthreads();
@@ -318,7 +365,10 @@ __global__ void __launch_bounds__(kHaloThreads, 1) spmm_halo_kernel(StepArgs a)
                 const int64_t row = int64_t(m) * V + v;
 #pragma unroll
                 for (int r = 0; r < RT; ++r)
-                    if (r < nr) y[int64_t(r0 + r) * S + row] = XT(out[r]);
+                    if (r < nr) {
+                        const int ra = r0 + r;
+                        y[(int64_t(ra >> 2) * S + row) * 4 + (ra & 3)] = XT(out[r]);
+                    }
             }
         }
     }
@@ -373,12 +423,12 @@ __global__ void __launch_bounds__(256) ledger_kernel(StepArgs a)
     if (threadIdx.x < 2) red[threadIdx.x] = 0.0;
     __syncthreads();
     const int r = blockIdx.y;
-    const XT *x = static_cast<const XT *>(a.x) + int64_t(r) * a.rhs_stride;
+    const XT *x = static_cast<const XT *>(a.x) + int64_t(r >> 2) * 4 * a.rhs_stride + (r & 3);
     const int64_t total = a.V * kDirs;
     float ab = 0.0f, ex = 0.0f;
     for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
          i += int64_t(gridDim.x) * blockDim.x) {
-        const float xs = float(x[i]);
+        const float xs = float(x[i * 4]);
         if (xs == 0.0f) continue;
         const int d = int(i / a.V);
         const int64_t v = i - int64_t(d) * a.V;
@@ -422,7 +472,7 @@ __global__ void det_kernel(StepArgs a)
     const int Nu = N[ua], Nv = N[va];
     const int u0 = (pu * Nu + a.det_nu - 1) / a.det_nu, u1 = ((pu + 1) * Nu + a.det_nu - 1) / a.det_nu;
     const int v0 = (pv * Nv + a.det_nv - 1) / a.det_nv, v1 = ((pv + 1) * Nv + a.det_nv - 1) / a.det_nv;
-    const XT *x = static_cast<const XT *>(a.x) + int64_t(r) * a.rhs_stride;
+    const XT *x = static_cast<const XT *>(a.x) + int64_t(r >> 2) * 4 * a.rhs_stride + (r & 3);
     double sum = 0.0;
     for (int cv = v0; cv < v1; ++cv)
         for (int cu = u0; cu < u1; ++cu) {
@@ -437,7 +487,7 @@ __global__ void det_kernel(StepArgs a)
                              (c[0] == 0 ? 0 : (c[0] == a.nx - 1 ? 2 : 1));
             for (int d = 0; d < kDirs; ++d) {
                 const double ed = a.tab.exit_det[(k * 27 + mask) * kDirs + d];
-                if (ed > 0.0) sum += ed * double(x[int64_t(d) * a.V + v]);
+                if (ed > 0.0) sum += ed * double(x[(int64_t(d) * a.V + v) * 4]);
             }
         }
     a.det[r * a.det_stride_r + p] = sum;

@@ -13,7 +13,9 @@ __device__ __forceinline__ int64_t state_offset(const StepArgs &a, int64_t s, in
     const int64_t v = s / kDirs;
     const int d = int(s - v * kDirs);
     if (a.tc_rp > 0) return (v * a.tc_rp + r) * 32 + d;
-    return int64_t(r) * a.rhs_stride + int64_t(d) * a.V + v;
+    if (a.R == 1) return int64_t(d) * a.V + v;
+    // batched: groups of four right-hand sides, the four values side by side
+    return (int64_t(r >> 2) * a.rhs_stride + int64_t(d) * a.V + v) * 4 + (r & 3);
 }
 
 // Point detector d of right-hand side r on x(t) (Eq. 27 with a sparse F):

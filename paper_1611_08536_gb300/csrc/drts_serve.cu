@@ -89,7 +89,8 @@ int64_t footprint_estimate(const drts_problem &p)
     const int64_t sb = p.precision == DRTS_FP64 ? 8 : 4;
     const int64_t n_patch = p.det_face >= 0 ? int64_t(p.det_nu) * p.det_nv : 0;
     int64_t b = states * 220 * (vb + 2);                      // values + codes
-    b += 2 * (states + 64) * sb * p.n_rhs;                    // state ping-pong
+    const int64_t rhs_alloc = p.n_rhs == 1 ? 1 : (int64_t(p.n_rhs) + 3) / 4 * 4;   // groups of four
+    b += 2 * (states + 64) * sb * rhs_alloc;                  // state ping-pong
     b += n_patch * p.max_steps * 8 * p.n_rhs;                 // detector history
     b += V * 2 + states * 4 + (states / 32) * 12 + (64 << 20);   // maps, row lengths, slice table, tables
     return b;
