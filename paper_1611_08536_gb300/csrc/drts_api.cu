@@ -508,10 +508,9 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     if (c->R > 1 && !c->tc) {
         // measured default of the CUDA-core batched step (GB300, FP32, grids
         // 48^3 - 96^3): 8 right-hand sides per pass (two 16-byte gathers per
-        // nonzero), warps striding over the slices, block-major above ~88^2
-        // voxels per x-y plane (the autotuner refines this per problem)
+        // nonzero), warps striding over the slices (the autotuner refines
+        // this per problem)
         c->rhs_tile = c->R <= 4 ? 4 : 8;
-        if (int64_t(prob->nx) * prob->ny > 88 * 88) c->variant = 1;
     }
     if (c->tc) c->rhs_tile = std::min(32, c->tc_rp);
     c->blocks = fit_blocks(c, c->threads, c->variant, c->rhs_tile);

@@ -101,8 +101,11 @@ __device__ __forceinline__ void store_rhs4(double *g, int64_t o, const double v[
 // (directions m) of those blocks in turn, so the x neighbourhood of one voxel
 // block (read by all 26 of its slices) is gathered by warps of the same SM
 // while it is still in L1.
+// The FP32 8-per-pass instance is held to 64 registers so that four
+// 256-thread CTAs fit an SM (32 warps to hide the gathers' L2 latency; at
+// 66 registers only three fit, and the step ran ~13 % slower).
 template <class VT, class XT, class AT, int RT, int ORDER>
-__global__ void __launch_bounds__(256) spmm_kernel(StepArgs a, int r0)
+__global__ void __launch_bounds__(256, (RT == 8 && sizeof(XT) == 4) ? 4 : 1) spmm_kernel(StepArgs a, int r0)
 {
     __shared__ int32_t s_delta[kCodes];
     const int64_t V = a.V;
