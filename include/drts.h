@@ -89,10 +89,14 @@ typedef struct drts_problem {
 } drts_problem;
 
 /* Batched step (n_rhs > 1) implementations:
- *   DRTS_BATCHED_CUDA_CORES  sliced sparse A, one pass per tile of 4..32 rhs;
- *   DRTS_BATCHED_TENSOR      A as 27 dense 32x32 blocks per voxel (bf16 high and
- *                            low parts) on the tensor cores, all rhs in one pass
- *                            (DRTS_FP32 precision, n_rhs <= 64). */
+ *   DRTS_BATCHED_CUDA_CORES  sliced sparse A, one pass per tile of 4..32 rhs,
+ *                            compensated FP32 sums (the accurate default);
+ *                            state kept in groups of four right-hand sides;
+ *   DRTS_BATCHED_TENSOR      A as 27 dense 32x32 blocks per voxel, each value
+ *                            split exactly into three bf16 parts, on the tensor
+ *                            cores, all rhs in one pass (DRTS_FP32 precision,
+ *                            n_rhs <= 64; the tensor cores' FP32 accumulation
+ *                            leaves ~1e-7 relative per step). */
 #define DRTS_BATCHED_CUDA_CORES 0
 #define DRTS_BATCHED_TENSOR 1
 
@@ -158,7 +162,8 @@ drts_status drts_read_detectors(drts_ctx *ctx, int32_t rhs, int64_t t_begin,
  * from x(t), the state the step starts from (the face detector's timing).
  * n_entries (state, detector, weight) triples, host arrays, copied; entries of
  * one detector are summed in their given order with a fixed reduction (the
- * readout is deterministic).  0 <= n_det <= 65535; n_det = 0 removes them.
+ * readout is deterministic).  0 <= n_det <= 65535; n_det = 0 removes them;
+ * a new set replaces (and frees) the previous one, a rejected call keeps it.
  * The history holds max_steps steps (DRTS_ESTATE when max_steps is 0) and
  * is cleared by this call; steps before it read 0.  While point detectors
  * are set, t + n_steps may not exceed max_steps.  Works in every step mode
