@@ -305,10 +305,21 @@ def cpu_baseline(prob, args, seconds=12.0):
         dt = time.perf_counter() - t0
         if dt > seconds:
             break
-    return {"value": round(c.nnz * reps / dt / 1e9, 4), "unit": UNIT, "cores": threads,
-            "kind": "oracle",
-            "sample": f"FP64 CSR SpMV over the {c.n_rows} rows of z-plane {z} "
-                      f"({c.nnz} nnz) of the same workload, {reps} repetitions"}
+    out = {"value": round(c.nnz * reps / dt / 1e9, 4), "unit": UNIT, "cores": threads,
+           "kind": "oracle",
+           "sample": f"FP64 CSR SpMV over the {c.n_rows} rows of z-plane {z} "
+                     f"({c.nnz} nnz) of the same workload, {reps} repetitions"}
+    # the same oracle on one core (a few seconds)
+    reps1, t1 = 0, time.perf_counter()
+    while True:
+        oracle.spmv(c, x, 1)
+        reps1 += 1
+        dt1 = time.perf_counter() - t1
+        if dt1 > seconds / 4:
+            break
+    out["single_core"] = {"value": round(c.nnz * reps1 / dt1 / 1e9, 4), "unit": UNIT, "cores": 1,
+                          "repetitions": reps1}
+    return out
 
 
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
