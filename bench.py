@@ -445,8 +445,9 @@ def run_serve(args):
         r.n_steps = max(1, int(round(r.n_steps * args.serve_step_scale)))
     stats = None
     lat, queue = [], []
+    policy = drts.SERVE_SHORTEST_FIRST if args.serve_policy == "shortest" else drts.SERVE_FIFO
     with drts.Server(max_resident=args.serve_resident, steps_per_tick=args.serve_tick_steps,
-                     n_streams=args.serve_streams) as srv:
+                     n_streams=args.serve_streams, policy=policy) as srv:
         t0 = time.perf_counter()
         ids, pending = [], list(stream)
         with ClockSampler(0) as clk:
@@ -499,7 +500,8 @@ def run_serve(args):
         "config": {"workload": "served_stream", "requests": n, "arrival_rate_per_s": args.serve_rate,
                    "step_scale": args.serve_step_scale,
                    "sides": list(I.SERVED_SIDES), "max_resident": args.serve_resident,
-                   "steps_per_tick": args.serve_tick_steps, "streams": args.serve_streams},
+                   "steps_per_tick": args.serve_tick_steps, "streams": args.serve_streams,
+                   "policy": args.serve_policy},
         "latency_s": {"p50": round(float(np.percentile(lat, 50)), 3),
                       "p99": round(float(np.percentile(lat, 99)), 3),
                       "max": round(float(np.max(lat)), 3)},
@@ -642,6 +644,8 @@ def main():
     ap.add_argument("--serve-resident", type=int, default=16)
     ap.add_argument("--serve-tick-steps", type=int, default=20)
     ap.add_argument("--serve-streams", type=int, default=4)
+    ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "shortest"],
+                    help="admission order of queued requests")
     ap.add_argument("--no-serve-baselines", dest="serve_baselines", action="store_false",
                     help="skip the one-after-another and per-simulation baseline runs")
     ap.add_argument("--sim-steps", type=int, default=1500, help="steps per simulation for sims/s")

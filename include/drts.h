@@ -403,11 +403,20 @@ drts_status drts_state_sum_noalloc(drts_ctx *ctx, int32_t rhs, double *out_devic
  * ------------------------------------------------------------------------ */
 typedef struct drts_server drts_server;
 
+/* Admission order of queued requests: DRTS_SERVE_FIFO admits in arrival
+ * order; DRTS_SERVE_SHORTEST_FIRST admits the queued request with the least
+ * estimated work (voxels x 26 x passes over A per step x steps) first, which
+ * lowers the median latency of a burst; under sustained overload it can keep
+ * postponing large requests (there is no ageing). */
+#define DRTS_SERVE_FIFO 0
+#define DRTS_SERVE_SHORTEST_FIRST 1
+
 typedef struct drts_server_config {
     int64_t mem_budget_bytes;        /* device bytes for resident simulations; 0 = 90% of free */
     int32_t max_resident;            /* resident simulations at once, 1..256 */
     int32_t steps_per_tick;          /* steps each resident simulation advances per tick */
     int32_t n_streams;               /* streams a tick's graph fans out over, 1..32 */
+    int32_t policy;                  /* DRTS_SERVE_FIFO or DRTS_SERVE_SHORTEST_FIRST */
 } drts_server_config;
 
 #define DRTS_REQ_QUEUED 0

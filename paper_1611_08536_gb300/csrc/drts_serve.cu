@@ -46,6 +46,7 @@ struct Request {
     int32_t state = DRTS_REQ_QUEUED;
     drts_ctx *ctx = nullptr;
     int64_t footprint = 0;
+    double work = 0.0;            // admission priority: voxels x 26 x passes per step x steps
     int32_t n_patch = 0;
     std::vector<double> det;      // [rhs][n_steps][n_patch]
     std::vector<double> ledger;   // [rhs][4]
@@ -133,7 +134,8 @@ drts_status drts_server_create(const drts_server_config *cfg, drts_server **out)
     if (!cfg || !out) return DRTS_EINVAL;
     *out = nullptr;
     if (cfg->max_resident < 1 || cfg->max_resident > 256 || cfg->steps_per_tick < 1 || cfg->n_streams < 1 ||
-        cfg->n_streams > 32 || cfg->mem_budget_bytes < 0)
+        cfg->n_streams > 32 || cfg->mem_budget_bytes < 0 ||
+        (cfg->policy != DRTS_SERVE_FIFO && cfg->policy != DRTS_SERVE_SHORTEST_FIRST))
         return DRTS_EINVAL;
     std::unique_ptr<drts_server> s(new drts_server);
     s->cfg = *cfg;
@@ -183,6 +185,8 @@ drts_status drts_server_submit(drts_server *s, const drts_problem *prob, int32_t
     r->profile.assign(profile, profile + n_t);
     r->n_steps = n_steps;
     r->footprint = footprint_estimate(r->prob);
+    // one pass over A per 8 right-hand sides (the batched step's default tile)
+    r->work = double(V) * 26.0 * double((prob->n_rhs + 7) / 8) * double(n_steps);
     if (r->footprint > s->budget) return sfail(s, DRTS_ENOMEM, "request larger than the memory budget");
     r->t_submit = Clock::now();
     *request_id = r->id;
@@ -237,7 +241,11 @@ drts_status drts_server_tick(drts_server *s, int32_t *n_done)
     }
     // 2. admissions overlap the tick on the admission stream
     while (!s->queue.empty() && int(s->resident.size()) < s->cfg.max_resident) {
-        Request &r = *s->reqs[s->queue.front()];
+        auto pick = s->queue.begin();
+        if (s->cfg.policy == DRTS_SERVE_SHORTEST_FIRST)
+            for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+                if (s->reqs[*it]->work < s->reqs[*pick]->work) pick = it;
+        Request &r = *s->reqs[*pick];
         if (s->used + r.footprint > s->budget) break;
         drts_ctx *ctx = nullptr;
         drts_status st = drts_assemble(&r.prob, s->admit, &ctx);
@@ -254,7 +262,7 @@ drts_status drts_server_tick(drts_server *s, int32_t *n_done)
                                         int32_t(r.profile.size()), r.profile.data());
             }
         }
-        s->queue.pop_front();
+        s->queue.erase(pick);
         if (st != DRTS_OK) {
             r.error = ctx ? drts_last_error(ctx) : drts_last_error(nullptr);
             if (ctx) drts_destroy(ctx);

@@ -69,7 +69,8 @@ class TuneResult(ctypes.Structure):
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_resident", ctypes.c_int32),
-                ("steps_per_tick", ctypes.c_int32), ("n_streams", ctypes.c_int32)]
+                ("steps_per_tick", ctypes.c_int32), ("n_streams", ctypes.c_int32),
+                ("policy", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -393,15 +394,18 @@ class Context:
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 SENSOR_FACE, SENSOR_POINT = 0, 1
+SERVE_FIFO, SERVE_SHORTEST_FIRST = 0, 1
 
 
 class Server:
     """Continuous-batching server of DRTS simulations (drts_server_*)."""
 
-    def __init__(self, mem_budget_bytes=0, max_resident=16, steps_per_tick=10, n_streams=4):
+    def __init__(self, mem_budget_bytes=0, max_resident=16, steps_per_tick=10, n_streams=4,
+                 policy=0):
+        """policy: SERVE_FIFO (arrival order) or SERVE_SHORTEST_FIRST."""
         self._lib = load()
         cfg = ServerConfig(int(mem_budget_bytes), int(max_resident), int(steps_per_tick),
-                           int(n_streams))
+                           int(n_streams), int(policy))
         h = ctypes.c_void_p()
         st = self._lib.drts_server_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != OK:

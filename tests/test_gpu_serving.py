@@ -118,3 +118,29 @@ def test_server_stats_count_submissions_before_a_tick(gpu):
         assert st["resident"] == 0 and st["queued"] == 0 and st["used_bytes"] == 0
         for i in ids:
             assert srv.poll(i).state == gpu.REQ_DONE
+
+
+@pytest.mark.parametrize("policy,order", [(0, [0, 1, 2]), (1, [1, 2, 0])])
+def test_server_admission_policy(gpu, policy, order):
+    """One slot, three requests queued together (steps 60, 20, 40): arrival
+    order is kept by DRTS_SERVE_FIFO; DRTS_SERVE_SHORTEST_FIRST runs the least
+    work first.  Results are the same either way."""
+    base = small_stream(1, seed=3)[0]
+    steps = [60, 20, 40]
+    with gpu.Server(max_resident=1, steps_per_tick=10, n_streams=1, policy=policy) as srv:
+        ids = [srv.submit(base.problem, base.sources, n) for n in steps]
+        done = []
+        while len(done) < 3:
+            srv.tick()
+            for k, i in enumerate(ids):
+                if k not in done and srv.poll(i).state == gpu.REQ_DONE:
+                    done.append(k)
+        assert done == order
+        det = srv.result(ids[1])[0]
+    alone = run_alone(gpu, type(base)(base.arrival_s, base.problem, base.sources, 20))
+    assert rel_l1(det, alone[0][0]) < 1e-6
+
+
+def test_server_rejects_unknown_policy(gpu):
+    with pytest.raises(gpu.DrtsError):
+        gpu.Server(policy=7)
