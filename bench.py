@@ -134,7 +134,8 @@ def traffic_per_launch(workload_name, precision, nnz):
 def algorithmic_bytes(info, precision):
     vb = {"fp32": 4, "fp64": 8, "fp16": 2}[precision]
     sb = 8 if precision == "fp64" else 4
-    b = info.nnz * (vb + 2) + 2 * info.n_states * sb
+    # stored entries: FP16 keeps a few large values per row as two terms
+    b = info.nnz_stored * (vb + 2) + 2 * info.n_states * sb
     if precision == "fp16":
         b += info.n_states * 4
     return b
@@ -242,6 +243,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": args.workload, "grid": list(prob.shape), "directions": 26,
                    "states": int(info.n_states), "nnz": int(info.nnz),
+                   "nnz_stored": int(info.nnz_stored),
                    "nnz_padded": int(info.nnz_padded), "matrix_GB": round(info.matrix_bytes / 1e9, 3),
                    "format": "SELL-32 (slice = 32 voxels x 1 direction), 16-bit stencil codes",
                    "precision": args.precision, "steps_per_s": round(1e3 / ms_step, 3),

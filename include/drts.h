@@ -53,7 +53,9 @@ typedef int32_t drts_status;
 /* storage / arithmetic precision of the time step */
 #define DRTS_FP64 0          /* A, state and accumulation in FP64 */
 #define DRTS_FP32 1          /* A and state in FP32, FP32 accumulation */
-#define DRTS_FP16_ROWSCALE 2 /* A in FP16 with a per-row FP32 scale, FP32 state */
+#define DRTS_FP16_ROWSCALE 2 /* A in FP16 with a per-row FP32 scale, FP32 state; a value
+                                 of 512 or more times its row scale is kept as two FP16
+                                 terms (hi + lo, 21 significant bits) */
 
 /* detector faces: 2*axis + (1 for the high side) */
 #define DRTS_FACE_MX 0
@@ -113,6 +115,9 @@ typedef struct drts_info {
     int64_t t;                       /* steps taken so far */
     int32_t precision, n_rhs, n_patch;
     int32_t special_voxels_permille; /* voxels that needed edge/interface folding */
+    int64_t nnz_stored;              /* entries the step streams (no padding): nnz, plus
+                                        for DRTS_FP16_ROWSCALE the second FP16 term of
+                                        each large value stored as two (hi + lo) */
 } drts_info;
 
 /*

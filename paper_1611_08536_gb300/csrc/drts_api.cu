@@ -403,12 +403,14 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     SlicedMatrix &A = c->A;
     A.precision = prob->precision;
     A.n_slices = ((c->V + kSlice - 1) / kSlice) * kDirs;
-    float *row_max = nullptr;
     int64_t *d_total = nullptr;
+    unsigned long long *d_split = nullptr;
     if ((e = dalloc(c, &A.slice_ptr, sizeof(int64_t) * A.n_slices)) != cudaSuccess ||
         (e = dalloc(c, &A.slice_len4, sizeof(int32_t) * A.n_slices)) != cudaSuccess ||
         (e = dalloc(c, &A.row_len, sizeof(int32_t) * A.n_slices * kSlice)) != cudaSuccess ||
-        (e = dalloc(c, &d_total, sizeof(int64_t))) != cudaSuccess) {
+        (e = dalloc(c, &d_total, sizeof(int64_t))) != cudaSuccess ||
+        (e = dalloc(c, &d_split, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_split, 0, sizeof(unsigned long long), c->stream)) != cudaSuccess) {
         cuda_fail(c, e, "slice table allocation");
         return bail(DRTS_ENOMEM);
     }
@@ -422,13 +424,15 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
         T.dir_scale = dscale;
     }
     if ((e = launch_classify(T, dplain, c->stream)) != cudaSuccess ||
-        (e = launch_count(T, A, row_max, c->stream)) != cudaSuccess ||
+        (e = launch_count(T, A, d_split, c->stream)) != cudaSuccess ||
         (e = launch_scan(A, d_total, c->stream)) != cudaSuccess) {
         cuda_fail(c, e, "assembly count");
         return bail(DRTS_ECUDA);
     }
     int64_t groups = 0;
+    unsigned long long n_split = 0;
     if ((e = cudaMemcpyAsync(&groups, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&n_split, d_split, sizeof(n_split), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) {
         cuda_fail(c, e, "assembly count");
         return bail(DRTS_ECUDA);
@@ -458,6 +462,7 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
         for (int32_t x : rl) nnz += x;
         for (uint8_t x : pl) special += x == 0;
         A.nnz = nnz;
+        A.nnz_stored = nnz + int64_t(n_split);
         c->special_permille = int(special * 1000 / c->V);
     }
     // state, ledger, detector history, sources
@@ -752,6 +757,7 @@ drts_status drts_get_info(const drts_ctx *c, drts_info *out)
     std::memset(out, 0, sizeof(*out));
     out->n_states = c->n_states;
     out->nnz = c->A.nnz;
+    out->nnz_stored = c->A.nnz_stored;
     out->nnz_padded = c->A.n_groups * kSlice * kGroup;
     out->n_slices = c->A.n_slices;
     out->matrix_bytes = out->nnz_padded * int64_t(value_bytes(c->A.precision) + sizeof(uint16_t)) +
@@ -809,7 +815,7 @@ std::string tune_key(const drts_ctx *c, int sms)
 {
     std::ostringstream k;
     k << c->prob.nx << 'x' << c->prob.ny << 'x' << c->prob.nz << ":p" << c->prob.precision << ":r" << c->R
-      << ":sm" << sms << ":nnz" << c->A.nnz;
+      << ":sm" << sms << ":nnz" << c->A.nnz_stored;
     return k.str();
 }
 

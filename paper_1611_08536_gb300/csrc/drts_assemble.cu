@@ -196,19 +196,28 @@ __global__ void classify_kernel(DevTables T, uint8_t *plain)
     plain[v] = ok;
 }
 
+// FP16 tier: a value whose scaled size v / scale reaches kHalfSplitAt (the
+// scale puts each direction's largest stencil value in (2^13, 2^14], so these
+// are the few largest entries of a row, mostly the unscattered streaming ones)
+// is stored as two FP16 terms with the same code, hi = RN(v/scale) and lo =
+// RN(v/scale - hi): 21 significant bits instead of 11.  The step sums the two
+// like any other entries; the export adds them back into one.
+constexpr double kHalfSplitAt = 512.0;
+
 struct CountEmit {
+    double split_scale = 0.0;   // FP16: the row's scale; 0 = no split entries
     int count = 0;
-    double vmax = 0.0;
+    int split = 0;
     __device__ void operator()(int, double v)
     {
         ++count;
-        vmax = v > vmax ? v : vmax;
+        if (split_scale > 0.0 && v / split_scale >= kHalfSplitAt) ++split;
     }
 };
 
 // one thread per row; a warp is exactly one slice
 __global__ void count_kernel(DevTables T, int64_t n_slices, int32_t *row_len,
-                             int32_t *slice_len4, float *row_max)
+                             int32_t *slice_len4, unsigned long long *n_split)
 {
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t q = g / kSlice;
@@ -218,14 +227,17 @@ __global__ void count_kernel(DevTables T, int64_t n_slices, int32_t *row_len,
     const int m = int(q % kDirs);
     const int64_t v = b * kSlice + lane;
     CountEmit ce;
+    if (T.dir_scale) ce.split_scale = double(T.dir_scale[m]);
     if (v < T.V) {
         const int x = int(v % T.nx), y = int(v / T.nx % T.ny), z = int(v / (int64_t(T.nx) * T.ny));
         enumerate_row(T, x, y, z, m, ce);
     }
     row_len[g] = ce.count;
-    if (row_max) row_max[g] = float(ce.vmax);
-    int mx = __reduce_max_sync(0xffffffffu, unsigned(ce.count));
+    const int stored = ce.count + ce.split;
+    int mx = __reduce_max_sync(0xffffffffu, unsigned(stored));
     if (lane == 0) slice_len4[q] = (mx + kGroup - 1) / kGroup;
+    const unsigned ns = __reduce_add_sync(0xffffffffu, unsigned(ce.split));
+    if (lane == 0 && ns) atomicAdd(n_split, (unsigned long long)ns);
 }
 
 template <class VT>
@@ -280,11 +292,25 @@ struct FillEmit {
     int64_t base;      // element index of group 0 of this lane
     float scale;
     int x, y, z, m;    // the row's voxel and direction
+    int cap;           // entries the slice holds per row (count_kernel's maximum)
     int e = 0;
     __device__ void operator()(int code, double v)
     {
+        if (e >= cap) return;   // count and fill enumerate the same entries; never write past the slice
         const int64_t idx = base + int64_t(e / kGroup) * (kSlice * kGroup) + (e % kGroup);
         if constexpr (std::is_same<VT, __half>::value) {
+            const double t = v / double(scale);
+            if (t >= kHalfSplitAt && e + 1 < cap) {
+                const __half hi = __double2half(t);
+                vals[idx] = hi;
+                codes[idx] = uint16_t(code);
+                ++e;
+                const int64_t i2 = base + int64_t(e / kGroup) * (kSlice * kGroup) + (e % kGroup);
+                vals[i2] = __double2half(t - double(__half2float(hi)));
+                codes[i2] = uint16_t(code);
+                ++e;
+                return;
+            }
             const int d = code / kDirs;             // source voxel = row voxel + offset d
             vals[idx] = round_dithered(v, scale, x + d % 3 - 1, y + d / 3 % 3 - 1, z + d / 9 - 1, code, m);
         } else {
@@ -309,6 +335,7 @@ __global__ void fill_kernel(DevTables T, SlicedMatrix A)
     fe.vals = static_cast<VT *>(A.vals);
     fe.codes = A.codes;
     fe.base = A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
+    fe.cap = A.slice_len4[q] * kGroup;
     fe.scale = 1.0f;
     if (A.row_scale) {
         fe.scale = T.dir_scale[m];
@@ -470,17 +497,28 @@ __global__ void export_kernel(SlicedMatrix A, int nx, int ny, int nz, int64_t ro
     const int64_t base = A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
     const VT *vals = static_cast<const VT *>(A.vals);
     const float scale = A.row_scale ? A.row_scale[g] : 1.0f;
-    int64_t out = row_ptr[r - row_begin];
-    for (int e = 0; e < len; ++e) {
+    const int64_t out0 = row_ptr[r - row_begin];
+    int64_t out = out0;
+    // FP16 split values are two consecutive entries with one code (the codes
+    // of a row are otherwise distinct): add the second into the first
+    const int stored = A.slice_len4[q] * kGroup;
+    int prev = -1;
+    for (int e = 0; e < stored; ++e) {
         const int64_t idx = base + int64_t(e / kGroup) * (kSlice * kGroup) + (e % kGroup);
         const int code = A.codes[idx];
-        const int d = code / kDirs, n = code % kDirs;
-        const int64_t off = int64_t(d / 9 - 1) * nx * ny + int64_t(d / 3 % 3 - 1) * nx + (d % 3 - 1);
-        col[out] = int32_t((v + off) * kDirs + n);
         double x;
         if constexpr (sizeof(VT) == 2) x = double(__half2float(vals[idx])) * double(scale);
         else x = double(vals[idx]);
+        if (sizeof(VT) == 2 && code == prev && out > out0) {
+            val[out - 1] += x;                      // exact: two FP16 terms times a power of two
+            continue;
+        }
+        if (out - out0 == len) break;               // padding
+        const int d = code / kDirs, n = code % kDirs;
+        const int64_t off = int64_t(d / 9 - 1) * nx * ny + int64_t(d / 3 % 3 - 1) * nx + (d % 3 - 1);
+        col[out] = int32_t((v + off) * kDirs + n);
         val[out] = x;
+        prev = code;
         ++out;
     }
 }
@@ -496,14 +534,14 @@ cudaError_t launch_classify(const DevTables &T, uint8_t *plain, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_count(const DevTables &T, SlicedMatrix &A, float *row_max, cudaStream_t s)
+cudaError_t launch_count(const DevTables &T, SlicedMatrix &A, unsigned long long *n_split, cudaStream_t s)
 {
     cudaError_t e = upload_dirs();
     if (e != cudaSuccess) return e;
     const int th = 128;
     const int64_t rows = A.n_slices * kSlice;
     count_kernel<<<unsigned((rows + th - 1) / th), th, 0, s>>>(T, A.n_slices, A.row_len,
-                                                                 A.slice_len4, row_max);
+                                                                 A.slice_len4, n_split);
     return cudaGetLastError();
 }
 

@@ -37,6 +37,7 @@ struct SlicedMatrix {
     int64_t n_slices = 0;
     int64_t n_groups = 0;       // sum of slice_len4 (units of 32 lanes x 4)
     int64_t nnz = 0;
+    int64_t nnz_stored = 0;     // nnz + second FP16 terms of split values
     void *vals = nullptr;       // double / float / __half [n_groups*128]
     uint16_t *codes = nullptr;  // [n_groups*128] offset_index*26 + n
     float *row_scale = nullptr; // FP16 tier: [n_slices*32]
@@ -135,7 +136,7 @@ struct StepArgs {
 
 // assembler (drts_assemble.cu)
 cudaError_t launch_classify(const DevTables &T, uint8_t *plain, cudaStream_t s);
-cudaError_t launch_count(const DevTables &T, SlicedMatrix &A, float *row_max, cudaStream_t s);
+cudaError_t launch_count(const DevTables &T, SlicedMatrix &A, unsigned long long *n_split, cudaStream_t s);
 cudaError_t launch_scan(SlicedMatrix &A, int64_t *d_total, cudaStream_t s);
 cudaError_t launch_fill(const DevTables &T, SlicedMatrix &A, cudaStream_t s);
 cudaError_t launch_export(const SlicedMatrix &A, int nx, int ny, int nz, int64_t row_begin,

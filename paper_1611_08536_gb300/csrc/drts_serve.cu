@@ -89,7 +89,8 @@ int64_t footprint_estimate(const drts_problem &p)
     const int64_t vb = p.precision == DRTS_FP64 ? 8 : (p.precision == DRTS_FP32 ? 4 : 2);
     const int64_t sb = p.precision == DRTS_FP64 ? 8 : 4;
     const int64_t n_patch = p.det_face >= 0 ? int64_t(p.det_nu) * p.det_nv : 0;
-    int64_t b = states * 220 * (vb + 2);                      // values + codes
+    // values + codes (FP16: a few large values per row stored as two terms)
+    int64_t b = states * (p.precision == DRTS_FP16_ROWSCALE ? 225 : 220) * (vb + 2);
     const int64_t rhs_alloc = p.n_rhs == 1 ? 1 : (int64_t(p.n_rhs) + 3) / 4 * 4;   // groups of four
     b += 2 * (states + 64) * sb * rhs_alloc;                  // state ping-pong
     b += n_patch * p.max_steps * 8 * p.n_rhs;                 // detector history

@@ -98,6 +98,7 @@ class Info(ctypes.Structure):
         ("t", ctypes.c_int64),
         ("precision", ctypes.c_int32), ("n_rhs", ctypes.c_int32),
         ("n_patch", ctypes.c_int32), ("special_voxels_permille", ctypes.c_int32),
+        ("nnz_stored", ctypes.c_int64),
     ]
 
 

@@ -7,8 +7,9 @@ import types
 import bench
 
 
-def _info(nnz, n_states, n_patch=256):
-    return types.SimpleNamespace(nnz=nnz, n_states=n_states, n_patch=n_patch)
+def _info(nnz, n_states, n_patch=256, nnz_stored=None):
+    return types.SimpleNamespace(nnz=nnz, n_states=n_states, n_patch=n_patch,
+                                 nnz_stored=nnz if nnz_stored is None else nnz_stored)
 
 
 def test_algorithmic_bytes_per_precision():
@@ -16,8 +17,10 @@ def test_algorithmic_bytes_per_precision():
     # values + 16-bit codes per nonzero, x read and y written once per state
     assert bench.algorithmic_bytes(info, "fp32") == 1000 * 6 + 2 * 100 * 4
     assert bench.algorithmic_bytes(info, "fp64") == 1000 * 10 + 2 * 100 * 8
-    # FP16 values, FP32 state, plus a 4-byte row scale per row
-    assert bench.algorithmic_bytes(info, "fp16") == 1000 * 4 + 2 * 100 * 4 + 100 * 4
+    # FP16 values, FP32 state, plus a 4-byte row scale per row; the stored
+    # entries include the second terms of split values
+    info16 = _info(1000, 100, nnz_stored=1020)
+    assert bench.algorithmic_bytes(info16, "fp16") == 1020 * 4 + 2 * 100 * 4 + 100 * 4
 
 
 def test_traffic_follows_kernel_source():
