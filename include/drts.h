@@ -16,7 +16,9 @@
  *
  * Conventions shared by every call:
  *   - Every call returns a drts_status; nothing aborts or traps.  After an
- *     error, drts_last_error(ctx) describes it.
+ *     error, drts_last_error(ctx) describes it.  No C++ exception leaves the
+ *     library: a host allocation that fails inside a call is DRTS_ENOMEM
+ *     (the call's partial work on a new context is freed).
  *   - Caller-owned host inputs are copied during the call; the context owns
  *     all device memory it allocates and frees it in drts_destroy.
  *   - Work is queued on the CUDA stream given to drts_assemble (NULL = the

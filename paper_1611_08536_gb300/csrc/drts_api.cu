@@ -9,6 +9,7 @@
 #include <cstring>
 #include <fstream>
 #include <map>
+#include <exception>
 #include <mutex>
 #include <new>
 #include <sstream>
@@ -92,6 +93,30 @@ drts_status fail(drts_ctx *c, drts_status s, const std::string &msg)
     if (c) c->err = msg;
     else g_assemble_error = msg;
     return s;
+}
+
+// No C++ exception may cross the C ABI: each entry point's handler turns the
+// one in flight into a status (a failed host allocation is DRTS_ENOMEM,
+// anything else DRTS_EINVAL) and records the message.  Call only from a catch
+// handler.
+drts_status caught(drts_ctx *c, const char *where) noexcept
+{
+    drts_status st = DRTS_EINVAL;
+    const char *what = "unknown exception";
+    try {
+        throw;
+    } catch (const std::bad_alloc &) {
+        st = DRTS_ENOMEM;
+        what = "host allocation failed";
+    } catch (const std::exception &ex) {
+        what = ex.what();
+    } catch (...) {
+    }
+    try {
+        fail(c, st, std::string(where) + ": " + what);
+    } catch (...) {
+    }
+    return st;
 }
 
 drts_status cuda_fail(drts_ctx *c, cudaError_t e, const char *where)
@@ -336,7 +361,7 @@ cudaStream_t ctx_swap_stream(drts_ctx *c, cudaStream_t s)
 extern "C" {
 
 drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx **out)
-{
+try {
     if (!out) return fail(nullptr, DRTS_EINVAL, "out is NULL");
     *out = nullptr;
     drts_status st = validate(prob);
@@ -358,8 +383,14 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     c->tc_rp = c->tc ? tc_rhs_stride(c->R) : 0;
     if (prob->det_face != DRTS_FACE_NONE) c->n_patch = prob->det_nu * prob->det_nv;
 
+    // a host allocation that throws below must not leak the partial context
+    struct Unwind {
+        drts_ctx *c;
+        ~Unwind() { if (c) drts_destroy(c); }
+    } unwind{c};
     auto bail = [&](drts_status s) {
         g_assemble_error = c->err;
+        unwind.c = nullptr;
         drts_destroy(c);
         return s;
     };
@@ -525,13 +556,16 @@ drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx 
     }
     st = sync_check(c, "assembly");
     if (st != DRTS_OK) return bail(st);
+    unwind.c = nullptr;
     *out = c;
     return DRTS_OK;
+} catch (...) {
+    return caught(nullptr, "drts_assemble");
 }
 
 drts_status drts_inject_source(drts_ctx *c, int32_t rhs, int32_t n_entries, const int64_t *state_idx,
                                const double *weight, int64_t t0, int32_t n_t, const double *profile)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (rhs < 0 || rhs >= c->R) return fail(c, DRTS_EINVAL, "rhs out of range");
     if (n_entries < 0 || n_entries > kMaxSrc) return fail(c, DRTS_EINVAL, "n_entries must be 0..64");
@@ -559,10 +593,12 @@ drts_status drts_inject_source(drts_ctx *c, int32_t rhs, int32_t n_entries, cons
     c->prof[rhs] = SourceProfile{t0, n_t, 0, 0, 0};
     c->prof_vals[rhs].assign(profile, profile + n_t);
     return upload_sources(c);
+} catch (...) {
+    return caught(c, "drts_inject_source");
 }
 
 drts_status drts_step_n(drts_ctx *c, int64_t n_steps)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (n_steps < 0) return fail(c, DRTS_EINVAL, "n_steps < 0");
     if ((c->det || c->n_pdet > 0) && c->t + n_steps > c->prob.max_steps)
@@ -586,10 +622,12 @@ drts_status drts_step_n(drts_ctx *c, int64_t n_steps)
         ++c->t;
     }
     return DRTS_OK;
+} catch (...) {
+    return caught(c, "drts_step_n");
 }
 
 drts_status drts_run_host(drts_ctx *c, int64_t n_steps, const double *scale, double *det_out)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (n_steps < 0 || !scale) return fail(c, DRTS_EINVAL, "bad arguments");
     if (c->n_bulk_groups > 0)
@@ -619,11 +657,13 @@ drts_status drts_run_host(drts_ctx *c, int64_t n_steps, const double *scale, dou
     if (d_scale) cudaFreeAsync(d_scale, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "run_host");
     return sync_check(c, "run_host");
+} catch (...) {
+    return caught(c, "drts_run_host");
 }
 
 drts_status drts_read_detectors(drts_ctx *c, int32_t rhs, int64_t t_begin, int64_t t_end, double *host_out,
                                 double *ledger_out)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (rhs < 0 || rhs >= c->R) return fail(c, DRTS_EINVAL, "rhs out of range");
     if (t_begin < 0 || t_end < t_begin || t_end > c->t) return fail(c, DRTS_EINVAL, "bad step range");
@@ -648,10 +688,12 @@ drts_status drts_read_detectors(drts_ctx *c, int32_t rhs, int64_t t_begin, int64
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "read_detectors");
     return sync_check(c, "read_detectors");
+} catch (...) {
+    return caught(c, "drts_read_detectors");
 }
 
 drts_status drts_read_state(drts_ctx *c, int32_t rhs, double *host_out)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (rhs < 0 || rhs >= c->R || !host_out) return fail(c, DRTS_EINVAL, "bad arguments");
     double *tmp = nullptr;
@@ -665,10 +707,12 @@ drts_status drts_read_state(drts_ctx *c, int32_t rhs, double *host_out)
     if (tmp) cudaFreeAsync(tmp, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "read_state");
     return sync_check(c, "read_state");
+} catch (...) {
+    return caught(c, "drts_read_state");
 }
 
 drts_status drts_write_state(drts_ctx *c, int32_t rhs, const double *host_in)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (rhs < 0 || rhs >= c->R || !host_in) return fail(c, DRTS_EINVAL, "bad arguments");
     double *tmp = nullptr;
@@ -682,11 +726,13 @@ drts_status drts_write_state(drts_ctx *c, int32_t rhs, const double *host_in)
     if (tmp) cudaFreeAsync(tmp, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "write_state");
     return sync_check(c, "write_state");
+} catch (...) {
+    return caught(c, "drts_write_state");
 }
 
 drts_status drts_export_rows(drts_ctx *c, int64_t row_begin, int64_t row_end, int64_t *row_ptr, int32_t *col,
                              double *val, int64_t cap)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (row_begin < 0 || row_end < row_begin || row_end > c->n_states || !row_ptr)
         return fail(c, DRTS_EINVAL, "bad row range");
@@ -723,10 +769,12 @@ drts_status drts_export_rows(drts_ctx *c, int64_t row_begin, int64_t row_end, in
     cudaFreeAsync(dcount, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "export_rows");
     return sync_check(c, "export_rows");
+} catch (...) {
+    return caught(c, "drts_export_rows");
 }
 
 drts_status drts_column_info(drts_ctx *c, double *absorb, double *exit_total, double *exit_det)
-{
+try {
     if (!c) return DRTS_EINVAL;
     // host evaluation of the per-(medium, face mask, direction) tables over
     // the medium map (a one-off readout, not part of the step)
@@ -749,6 +797,8 @@ drts_status drts_column_info(drts_ctx *c, double *absorb, double *exit_total, do
         }
     }
     return DRTS_OK;
+} catch (...) {
+    return caught(c, "drts_column_info");
 }
 
 drts_status drts_get_info(const drts_ctx *c, drts_info *out)
@@ -774,7 +824,7 @@ drts_status drts_get_info(const drts_ctx *c, drts_info *out)
 
 drts_status drts_set_launch(drts_ctx *c, int32_t blocks_per_sm, int32_t threads_per_block, int32_t rhs_tile,
                             int32_t variant)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (threads_per_block != 0 && (threads_per_block < 32 || threads_per_block > 256 || threads_per_block % 32))
         return fail(c, DRTS_EINVAL, "threads_per_block must be a multiple of 32 in 32..256");
@@ -803,6 +853,8 @@ drts_status drts_set_launch(drts_ctx *c, int32_t blocks_per_sm, int32_t threads_
     c->rhs_tile = tile;
     c->blocks = blocks_per_sm ? sms * blocks_per_sm : fit;
     return DRTS_OK;
+} catch (...) {
+    return caught(c, "drts_set_launch");
 }
 
 namespace {
@@ -841,7 +893,7 @@ void tune_file_store(const char *path, const std::string &key, const drts_tune_r
 }  // namespace
 
 drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *out)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (trial_steps < 1 || trial_steps > 1000) return fail(c, DRTS_EINVAL, "trial_steps must be 1..1000");
     int dev = 0, sms = 0;
@@ -935,6 +987,8 @@ drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *ou
     }
     if (out) *out = best;
     return DRTS_OK;
+} catch (...) {
+    return caught(c, "drts_autotune");
 }
 
 namespace {
@@ -955,14 +1009,16 @@ int64_t checkpoint_bytes(const drts_ctx *c)
 }  // namespace
 
 drts_status drts_checkpoint_size(drts_ctx *c, int64_t *bytes)
-{
+try {
     if (!c || !bytes) return DRTS_EINVAL;
     *bytes = checkpoint_bytes(c);
     return DRTS_OK;
+} catch (...) {
+    return caught(c, "drts_checkpoint_size");
 }
 
 drts_status drts_checkpoint_save(drts_ctx *c, void *host_buf, int64_t cap)
-{
+try {
     if (!c || !host_buf) return DRTS_EINVAL;
     const int64_t need = checkpoint_bytes(c);
     if (cap < need) return fail(c, DRTS_EINVAL, "checkpoint buffer too small (" + std::to_string(need) + " bytes)");
@@ -990,10 +1046,12 @@ drts_status drts_checkpoint_save(drts_ctx *c, void *host_buf, int64_t cap)
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint_save");
     return DRTS_OK;
+} catch (...) {
+    return caught(c, "drts_checkpoint_save");
 }
 
 drts_status drts_checkpoint_load(drts_ctx *c, const void *host_buf, int64_t size)
-{
+try {
     if (!c || !host_buf || size < int64_t(sizeof(CheckpointHeader))) return DRTS_EINVAL;
     CheckpointHeader h;
     std::memcpy(&h, host_buf, sizeof(h));
@@ -1032,10 +1090,12 @@ drts_status drts_checkpoint_load(drts_ctx *c, const void *host_buf, int64_t size
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint_load");
     return DRTS_OK;
+} catch (...) {
+    return caught(c, "drts_checkpoint_load");
 }
 
 drts_status drts_set_step_mode(drts_ctx *c, int32_t mode)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (mode == DRTS_STEP_LAUNCH) {
         c->step_mode = mode;
@@ -1051,10 +1111,12 @@ drts_status drts_set_step_mode(drts_ctx *c, int32_t mode)
         return DRTS_OK;
     }
     return fail(c, DRTS_EINVAL, "unknown step mode");
+} catch (...) {
+    return caught(c, "drts_set_step_mode");
 }
 
 drts_status drts_set_fault(drts_ctx *c, int32_t kind, int64_t arg)
-{
+try {
     if (!c) return DRTS_EINVAL;
     switch (kind) {
     case DRTS_FAULT_NONE:
@@ -1078,6 +1140,8 @@ drts_status drts_set_fault(drts_ctx *c, int32_t kind, int64_t arg)
     default:
         return fail(c, DRTS_EINVAL, "unknown fault kind");
     }
+} catch (...) {
+    return caught(c, "drts_set_fault");
 }
 
 drts_status drts_state_sum_noalloc(drts_ctx *c, int32_t rhs, double *out_device)
@@ -1204,7 +1268,7 @@ drts_status upload_bulk(drts_ctx *c)
 
 drts_status drts_source_column(drts_ctx *c, int64_t state_idx, double frac, int32_t cap, int64_t *out_state,
                                double *out_value, int32_t *count, double *exit_mass)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (state_idx < 0 || state_idx >= c->n_states) return fail(c, DRTS_EINVAL, "state out of range");
     if (!(frac > 0.0 && frac <= 1.0)) return fail(c, DRTS_EINVAL, "frac must be in (0, 1]");
@@ -1221,12 +1285,14 @@ drts_status drts_source_column(drts_ctx *c, int64_t state_idx, double frac, int3
         out_value[i] = col[i].second;
     }
     return DRTS_OK;
+} catch (...) {
+    return caught(c, "drts_source_column");
 }
 
 drts_status drts_inject_source_substeps(drts_ctx *c, int32_t rhs, int32_t n_entries, const int64_t *state_idx,
                                         const double *weight, int32_t n_sub, int64_t t0, int32_t n_t,
                                         const double *profile)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (rhs < 0 || rhs >= c->R) return fail(c, DRTS_EINVAL, "rhs out of range");
     if (n_entries < 0 || n_entries > kMaxSrc) return fail(c, DRTS_EINVAL, "n_entries must be 0..64");
@@ -1260,21 +1326,25 @@ drts_status drts_inject_source_substeps(drts_ctx *c, int32_t rhs, int32_t n_entr
     }
     c->substep[rhs] = std::move(ss);
     return upload_bulk(c);
+} catch (...) {
+    return caught(c, "drts_inject_source_substeps");
 }
 
 drts_status drts_substep_count(drts_ctx *c, int64_t state_idx, int32_t *n_sub)
-{
+try {
     if (!c || !n_sub) return DRTS_EINVAL;
     if (state_idx < 0 || state_idx >= c->n_states) return fail(c, DRTS_EINVAL, "state out of range");
     // sub-intervals of dr / c: the path L_k in half voxels (2 dr = h), rounded up
     const int k = c->med_host[size_t(state_idx / kDirs)];
     *n_sub = std::max(1, int(std::ceil(2.0 * c->host.lam[k] - 1e-9)));
     return DRTS_OK;
+} catch (...) {
+    return caught(c, "drts_substep_count");
 }
 
 drts_status drts_set_point_detectors(drts_ctx *c, int32_t n_det, int64_t n_entries, const int32_t *det,
                                      const int64_t *state_idx, const double *weight)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (n_det < 0 || n_det > 65535) return fail(c, DRTS_EINVAL, "n_det must be 0..65535");
     if (n_entries < 0 || (n_entries > 0 && (!det || !state_idx || !weight)))
@@ -1319,10 +1389,12 @@ drts_status drts_set_point_detectors(drts_ctx *c, int32_t n_det, int64_t n_entri
         return cuda_fail(c, e, "point detector upload");
     c->n_pdet = n_det;
     return sync_check(c, "point detector upload");
+} catch (...) {
+    return caught(c, "drts_set_point_detectors");
 }
 
 drts_status drts_read_point_detectors(drts_ctx *c, int32_t rhs, int64_t t_begin, int64_t t_end, double *host_out)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (rhs < 0 || rhs >= c->R) return fail(c, DRTS_EINVAL, "rhs out of range");
     if (c->n_pdet <= 0) return fail(c, DRTS_ESTATE, "no point detectors set");
@@ -1334,11 +1406,13 @@ drts_status drts_read_point_detectors(drts_ctx *c, int32_t rhs, int64_t t_begin,
                                     sizeof(double) * (t_end - t_begin) * c->n_pdet, cudaMemcpyDeviceToHost, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "read_point_detectors");
     return sync_check(c, "read_point_detectors");
+} catch (...) {
+    return caught(c, "drts_read_point_detectors");
 }
 
 drts_status drts_sensor_response(drts_ctx *c, int32_t rhs, int32_t which, int64_t t_begin, int64_t t_end, int32_t w,
                                  const double *h, double *host_out)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (rhs < 0 || rhs >= c->R) return fail(c, DRTS_EINVAL, "rhs out of range");
     if (w < 0 || w > (1 << 20) || !h) return fail(c, DRTS_EINVAL, "w must be 0..2^20 and h non-NULL");
@@ -1371,6 +1445,8 @@ drts_status drts_sensor_response(drts_ctx *c, int32_t rhs, int32_t which, int64_
     if (dm) cudaFreeAsync(dm, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "sensor_response");
     return sync_check(c, "sensor_response");
+} catch (...) {
+    return caught(c, "drts_sensor_response");
 }
 
 void drts_destroy(drts_ctx *c)

@@ -16,8 +16,10 @@
 #include <chrono>
 #include <cstring>
 #include <deque>
+#include <exception>
 #include <map>
 #include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -79,6 +81,29 @@ drts_status sfail(drts_server *s, drts_status st, const std::string &m)
     return st;
 }
 
+// The exception in flight at an entry point as a status (no C++ exception
+// crosses the C ABI): DRTS_ENOMEM for a failed host allocation, else
+// DRTS_EINVAL.  Call only from a catch handler.
+drts_status scaught(drts_server *s, const char *where) noexcept
+{
+    drts_status st = DRTS_EINVAL;
+    const char *what = "unknown exception";
+    try {
+        throw;
+    } catch (const std::bad_alloc &) {
+        st = DRTS_ENOMEM;
+        what = "host allocation failed";
+    } catch (const std::exception &ex) {
+        what = ex.what();
+    } catch (...) {
+    }
+    try {
+        sfail(s, st, std::string(where) + ": " + what);
+    } catch (...) {
+    }
+    return st;
+}
+
 // Device bytes a request will hold: the sliced matrix (about 220 stored
 // slots per state with padding), two state buffers per right-hand side, the
 // detector history and the per-voxel tables.
@@ -131,7 +156,7 @@ drts_status retire(drts_server *s, Request &r)
 extern "C" {
 
 drts_status drts_server_create(const drts_server_config *cfg, drts_server **out)
-{
+try {
     if (!cfg || !out) return DRTS_EINVAL;
     *out = nullptr;
     if (cfg->max_resident < 1 || cfg->max_resident > 256 || cfg->steps_per_tick < 1 || cfg->n_streams < 1 ||
@@ -155,12 +180,14 @@ drts_status drts_server_create(const drts_server_config *cfg, drts_server **out)
             return DRTS_ECUDA;
     *out = s.release();
     return DRTS_OK;
+} catch (...) {
+    return scaught(nullptr, "drts_server_create");
 }
 
 drts_status drts_server_submit(drts_server *s, const drts_problem *prob, int32_t n_entries, const int32_t *src_rhs,
                                const int64_t *src_state, const double *src_weight, int64_t t0, int32_t n_t,
                                const double *profile, int64_t n_steps, int64_t *request_id)
-{
+try {
     if (!s || !prob || !request_id) return DRTS_EINVAL;
     if (n_steps < 1) return sfail(s, DRTS_EINVAL, "n_steps must be >= 1");
     if (!prob->media || !prob->medium_of_voxel || prob->n_media < 1 || prob->nx < 2 || prob->ny < 2 || prob->nz < 2)
@@ -195,10 +222,12 @@ drts_status drts_server_submit(drts_server *s, const drts_problem *prob, int32_t
     s->reqs[r->id] = std::move(r);
     s->stats.submitted++;
     return DRTS_OK;
+} catch (...) {
+    return scaught(s, "drts_server_submit");
 }
 
 drts_status drts_server_tick(drts_server *s, int32_t *n_done)
-{
+try {
     if (!s) return DRTS_EINVAL;
     int32_t done = 0;
     // 1. the steps of every resident simulation, captured in one graph
@@ -304,10 +333,12 @@ drts_status drts_server_tick(drts_server *s, int32_t *n_done)
     s->stats.used_bytes = s->used;
     if (n_done) *n_done = done;
     return DRTS_OK;
+} catch (...) {
+    return scaught(s, "drts_server_tick");
 }
 
 drts_status drts_server_poll(drts_server *s, int64_t id, drts_request_info *out)
-{
+try {
     if (!s || !out) return DRTS_EINVAL;
     auto it = s->reqs.find(id);
     if (it == s->reqs.end()) return sfail(s, DRTS_EINVAL, "unknown request");
@@ -324,10 +355,12 @@ drts_status drts_server_poll(drts_server *s, int64_t id, drts_request_info *out)
     if (r.state == DRTS_REQ_RUNNING || r.state == DRTS_REQ_DONE) out->queue_s = secs(r.t_submit, r.t_admit);
     if (r.state == DRTS_REQ_DONE || r.state == DRTS_REQ_FAILED) out->latency_s = secs(r.t_submit, r.t_done);
     return DRTS_OK;
+} catch (...) {
+    return scaught(s, "drts_server_poll");
 }
 
 drts_status drts_server_result(drts_server *s, int64_t id, int32_t rhs, double *det_out, double *ledger_out)
-{
+try {
     if (!s) return DRTS_EINVAL;
     auto it = s->reqs.find(id);
     if (it == s->reqs.end()) return sfail(s, DRTS_EINVAL, "unknown request");
@@ -339,10 +372,12 @@ drts_status drts_server_result(drts_server *s, int64_t id, int32_t rhs, double *
                     sizeof(double) * r.n_steps * r.n_patch);
     if (ledger_out) std::memcpy(ledger_out, r.ledger.data() + 4 * rhs, 4 * sizeof(double));
     return DRTS_OK;
+} catch (...) {
+    return scaught(s, "drts_server_result");
 }
 
 drts_status drts_server_release(drts_server *s, int64_t id)
-{
+try {
     if (!s) return DRTS_EINVAL;
     auto it = s->reqs.find(id);
     if (it == s->reqs.end()) return sfail(s, DRTS_EINVAL, "unknown request");
@@ -350,6 +385,8 @@ drts_status drts_server_release(drts_server *s, int64_t id)
         return sfail(s, DRTS_ESTATE, "request still queued or running");
     s->reqs.erase(it);
     return DRTS_OK;
+} catch (...) {
+    return scaught(s, "drts_server_release");
 }
 
 drts_status drts_server_get_stats(const drts_server *s, drts_server_stats *out)

@@ -49,3 +49,31 @@ def test_assemble_rejects_null_without_gpu(lib):
     out = ctypes.c_void_p()
     assert lib.drts_assemble(None, None, ctypes.byref(out)) == 1      # DRTS_EINVAL
     assert b"NULL" in lib.drts_last_error(None)
+
+
+def test_host_allocation_failure_returns_status():
+    """No C++ exception crosses the C ABI: drts_assemble with its address
+    space capped below the host copy of the medium map (a 400^3 grid, 64 MB)
+    returns DRTS_ENOMEM with a message instead of terminating the process.
+    The copy is taken before any CUDA call, so this runs without a GPU."""
+    import subprocess
+    import sys
+    code = r"""
+import ctypes, resource
+from paper_1611_08536_gb300 import drts, inputs as I
+lib = drts.load()
+prob = I.homogeneous(400, 0.1, (10.0, 0.01, 0.9, 1.4))
+ps = drts.problem_struct(prob, 0)
+h = ctypes.c_void_p()
+vm = int(open("/proc/self/statm").read().split()[0]) * resource.getpagesize()
+soft, hard = resource.getrlimit(resource.RLIMIT_AS)
+resource.setrlimit(resource.RLIMIT_AS, (vm + (16 << 20), hard))
+st = lib.drts_assemble(ctypes.byref(ps), None, ctypes.byref(h))
+resource.setrlimit(resource.RLIMIT_AS, (soft, hard))
+print(st, h.value is None, lib.drts_last_error(None).decode())
+"""
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    st, null, msg = r.stdout.strip().split(" ", 2)
+    assert int(st) == 2 and null == "True", r.stdout
+    assert "drts_assemble" in msg and "host allocation failed" in msg, msg
