@@ -476,8 +476,9 @@ void drts_server_destroy(drts_server *srv);
 /* Free every device and host resource of ctx (NULL is ignored). */
 void drts_destroy(drts_ctx *ctx);
 
-/* Text of the last error on ctx (or of the last failed drts_assemble when
- * ctx is NULL).  Valid until the next call on ctx. */
+/* Text of the last error on ctx (or, when ctx is NULL, of the last failed
+ * drts_assemble on the calling thread).  Valid until the next call on ctx
+ * (or the thread's next drts_assemble). */
 const char *drts_last_error(const drts_ctx *ctx);
 
 #ifdef __cplusplus

@@ -86,7 +86,8 @@ struct drts_ctx {
 
 namespace {
 
-std::string g_assemble_error;
+// message of the last failed drts_assemble on this thread
+thread_local std::string g_assemble_error;
 
 drts_status fail(drts_ctx *c, drts_status s, const std::string &msg)
 {

@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <type_traits>
 
 #include "drts_device.cuh"
@@ -29,8 +30,15 @@ __constant__ int8_t c_dir_index[27];
 
 cudaError_t upload_dirs()
 {
-    static bool done = false;
-    if (done) return cudaSuccess;
+    // __constant__ memory is per device: upload once on every device used
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done[dev]) return cudaSuccess;
     const Directions &D = dirs();
     int8_t v[kDirs][3], nz[kDirs], idx[27];
     for (int d = 0; d < kDirs; ++d) {
@@ -38,10 +46,10 @@ cudaError_t upload_dirs()
         nz[d] = int8_t(D.nnzc[d]);
     }
     for (int i = 0; i < 27; ++i) idx[i] = int8_t(D.index_of[i]);
-    cudaError_t e = cudaMemcpyToSymbol(c_dir, v, sizeof(v));
+    e = cudaMemcpyToSymbol(c_dir, v, sizeof(v));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_nnzc, nz, sizeof(nz));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_dir_index, idx, sizeof(idx));
-    if (e == cudaSuccess) done = true;
+    if (e == cudaSuccess) done[dev] = true;
     return e;
 }
 
