@@ -1062,6 +1062,7 @@ try {
         return fail(c, DRTS_EINVAL, "checkpoint is of another problem");
     if (h.n_pdet != c->n_pdet)
         return fail(c, DRTS_EINVAL, "checkpoint has another set of point detectors (set them before loading)");
+    if (h.t < 0) return fail(c, DRTS_EINVAL, "checkpoint time < 0");
     if ((c->det || c->n_pdet > 0) && h.t > c->prob.max_steps)
         return fail(c, DRTS_EINVAL, "checkpoint time beyond max_steps");
     const int64_t det_steps = (c->det && h.max_steps > 0) ? h.t : 0;
@@ -1069,8 +1070,8 @@ try {
     const int64_t need = int64_t(sizeof(h)) + int64_t(c->R) * (c->n_states * 8 + 32) +
                          int64_t(c->R) * det_steps * c->n_patch * 8 + int64_t(c->R) * pdet_steps * c->n_pdet * 8;
     if (size < need) return fail(c, DRTS_EINVAL, "checkpoint truncated");
+    if ((c->t ^ h.t) & 1) std::swap(c->x, c->y);   // keep the state buffer parity of an uninterrupted run
     c->t = h.t;
-    if (c->t & 1) std::swap(c->x, c->y);      // keep the state buffer parity of an uninterrupted run
     const char *p = static_cast<const char *>(host_buf) + sizeof(h);
     for (int r = 0; r < c->R; ++r) {
         drts_status st = drts_write_state(c, r, reinterpret_cast<const double *>(p));

@@ -410,6 +410,13 @@ def test_checkpoint_resume_equals_uninterrupted(gpu, precision):
     assert np.array_equal(xa, xc)                 # the state is deterministic
     assert rel_l1(dc, da) < 1e-12
     assert np.allclose(lc, la, rtol=1e-12)
+    with gpu.Context(prob, max_steps=40) as e:    # restore into a context that has stepped
+        e.set_source(0, src)
+        e.step_n(3)
+        e.restore(data)
+        assert e.info().t == 17
+        e.step_n(23)
+        assert np.array_equal(xa, e.read_state())
     other, _ = I.three_layers(12, precision=precision)
     with gpu.Context(other, max_steps=40) as d:
         with pytest.raises(gpu.DrtsError):
