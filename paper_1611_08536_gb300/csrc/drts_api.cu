@@ -738,9 +738,9 @@ try {
     if (row_begin < 0 || row_end < row_begin || row_end > c->n_states || !row_ptr)
         return fail(c, DRTS_EINVAL, "bad row range");
     const int64_t n = row_end - row_begin;
+    std::vector<int64_t> cnt(size_t(n) + 1, 0);     // before the device buffer: a throw here leaks nothing
     int64_t *dcount = nullptr;
     cudaError_t e = cudaMallocAsync(&dcount, sizeof(int64_t) * (n + 1), c->stream);
-    std::vector<int64_t> cnt(size_t(n) + 1, 0);
     if (e == cudaSuccess) e = launch_count_export(c->A, c->V, row_begin, row_end, dcount, c->stream);
     if (e == cudaSuccess && n > 0)
         e = cudaMemcpyAsync(cnt.data(), dcount, sizeof(int64_t) * n, cudaMemcpyDeviceToHost, c->stream);
