@@ -25,6 +25,9 @@ Parity status of each function (pins are in ``tests/test_oracle_pins.py``):
                       A's column, mirror conservation.
   * interface / edge folding geometry (Section 4.2 readings): parity
     unpinned beyond the invariants above; the paper prints no numbers for it.
+
+``oracle.fcc`` (numpy) is the same step on the close-packed sphere partition
+of Section 3; its pins are in ``tests/test_oracle_fcc.py``.
 """
 from __future__ import annotations
 
