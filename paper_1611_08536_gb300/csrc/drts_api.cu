@@ -363,6 +363,7 @@ extern "C" {
 
 drts_status drts_assemble(const drts_problem *prob, void *cuda_stream, drts_ctx **out)
 try {
+    NvtxRange nvtx("drts_assemble");
     if (!out) return fail(nullptr, DRTS_EINVAL, "out is NULL");
     *out = nullptr;
     drts_status st = validate(prob);
@@ -600,6 +601,7 @@ try {
 
 drts_status drts_step_n(drts_ctx *c, int64_t n_steps)
 try {
+    NvtxRange nvtx("drts_step_n");
     if (!c) return DRTS_EINVAL;
     if (n_steps < 0) return fail(c, DRTS_EINVAL, "n_steps < 0");
     if ((c->det || c->n_pdet > 0) && c->t + n_steps > c->prob.max_steps)
@@ -629,6 +631,7 @@ try {
 
 drts_status drts_run_host(drts_ctx *c, int64_t n_steps, const double *scale, double *det_out)
 try {
+    NvtxRange nvtx("drts_run_host");
     if (!c) return DRTS_EINVAL;
     if (n_steps < 0 || !scale) return fail(c, DRTS_EINVAL, "bad arguments");
     if (c->n_bulk_groups > 0)
@@ -895,6 +898,7 @@ void tune_file_store(const char *path, const std::string &key, const drts_tune_r
 
 drts_status drts_autotune(drts_ctx *c, int32_t trial_steps, drts_tune_result *out)
 try {
+    NvtxRange nvtx("drts_autotune");
     if (!c) return DRTS_EINVAL;
     if (trial_steps < 1 || trial_steps > 1000) return fail(c, DRTS_EINVAL, "trial_steps must be 1..1000");
     int dev = 0, sms = 0;
@@ -1020,6 +1024,7 @@ try {
 
 drts_status drts_checkpoint_save(drts_ctx *c, void *host_buf, int64_t cap)
 try {
+    NvtxRange nvtx("drts_checkpoint_save");
     if (!c || !host_buf) return DRTS_EINVAL;
     const int64_t need = checkpoint_bytes(c);
     if (cap < need) return fail(c, DRTS_EINVAL, "checkpoint buffer too small (" + std::to_string(need) + " bytes)");
@@ -1053,6 +1058,7 @@ try {
 
 drts_status drts_checkpoint_load(drts_ctx *c, const void *host_buf, int64_t size)
 try {
+    NvtxRange nvtx("drts_checkpoint_load");
     if (!c || !host_buf || size < int64_t(sizeof(CheckpointHeader))) return DRTS_EINVAL;
     CheckpointHeader h;
     std::memcpy(&h, host_buf, sizeof(h));

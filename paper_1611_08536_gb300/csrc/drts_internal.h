@@ -5,9 +5,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "drts.h"
 
 namespace drts {
+
+// Named NVTX range over a scope: assembly, steps, autotuning, checkpoints and
+// serving ticks appear by name in profiler timelines and can select ncu
+// captures (nothing is recorded unless a tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kDirs = 26;         // lattice directions
 constexpr int kOffs = 27;         // neighbour offsets {-1,0,1}^3

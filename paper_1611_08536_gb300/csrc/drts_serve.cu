@@ -228,6 +228,7 @@ try {
 
 drts_status drts_server_tick(drts_server *s, int32_t *n_done)
 try {
+    drts::NvtxRange nvtx("drts_server_tick");
     if (!s) return DRTS_EINVAL;
     int32_t done = 0;
     // 1. the steps of every resident simulation, captured in one graph
