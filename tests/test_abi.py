@@ -77,3 +77,44 @@ print(st, h.value is None, lib.drts_last_error(None).decode())
     st, null, msg = r.stdout.strip().split(" ", 2)
     assert int(st) == 2 and null == "True", r.stdout
     assert "drts_assemble" in msg and "host allocation failed" in msg, msg
+
+
+STRUCTS = [("Medium", "drts_medium"), ("ProblemC", "drts_problem"), ("Info", "drts_info"),
+           ("TuneResult", "drts_tune_result"), ("ServerConfig", "drts_server_config"),
+           ("RequestInfo", "drts_request_info"), ("ServerStats", "drts_server_stats")]
+
+
+def test_binding_structs_match_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the C header's layout: the
+    same field names at the same offsets with the same sizes, and the same
+    total size (a C program compiled against include/drts.h prints them)."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    from paper_1611_08536_gb300 import drts
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "drts.h"', "int main(void) {"]
+    for py, c in STRUCTS:
+        lines.append(f'printf("{py} sizeof %zu\\n", sizeof({c}));')
+        for name, _ in getattr(drts, py)._fields_:
+            lines.append(f'printf("{py} {name} %zu %zu\\n", offsetof({c}, {name}), sizeof((({c} *)0)->{name}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    seen = 0
+    for ln in filter(None, out):
+        parts = ln.split()
+        cls = getattr(drts, parts[0])
+        if parts[1] == "sizeof":
+            assert C.sizeof(cls) == int(parts[2]), parts
+        else:
+            f = getattr(cls, parts[1])
+            assert (f.offset, f.size) == (int(parts[2]), int(parts[3])), parts
+        seen += 1
+    assert seen == sum(1 + len(getattr(drts, py)._fields_) for py, _ in STRUCTS)
