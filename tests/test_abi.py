@@ -118,3 +118,40 @@ def test_binding_structs_match_header_layout(tmp_path):
             assert (f.offset, f.size) == (int(parts[2]), int(parts[3])), parts
         seen += 1
     assert seen == sum(1 + len(getattr(drts, py)._fields_) for py, _ in STRUCTS)
+
+
+def _prototypes():
+    """(return type, name, [parameter declarations]) of every function the
+    header declares."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "drts.h")).read(), flags=re.S)
+    out = []
+    for m in re.finditer(r"^([A-Za-z_][\w \*]*?)\b(drts_\w+)\s*\(([^)]*)\)\s*;", text, flags=re.M):
+        params = [p.strip() for p in m.group(3).split(",") if p.strip() and p.strip() != "void"]
+        out.append((m.group(1).strip(), m.group(2), params))
+    return out
+
+
+def test_binding_signatures_match_header():
+    """The binding's argtypes follow each prototype: same number of
+    parameters, the same scalar types, pointers where the header has them;
+    char-pointer and void returns declared as such."""
+    import ctypes as C
+    from paper_1611_08536_gb300 import drts
+    lib = drts.load()
+    scalar = {"int32_t": C.c_int32, "int64_t": C.c_int64, "double": C.c_double}
+    protos = _prototypes()
+    assert len(protos) >= 30
+    for ret, name, params in protos:
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == len(params), name
+        for decl, t in zip(params, fn.argtypes):
+            if "*" in decl:
+                assert t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer), (name, decl, t)
+            else:
+                base = decl.split()[-2] if len(decl.split()) > 1 else decl
+                assert t is scalar[base], (name, decl, t)
+        if ret.replace(" ", "") == "constchar*":
+            assert fn.restype is C.c_char_p, name
+        elif ret == "void":
+            assert fn.restype is None, name
