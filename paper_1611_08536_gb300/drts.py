@@ -259,7 +259,8 @@ class Context:
 
     def write_state(self, x, rhs=0):
         x = np.ascontiguousarray(x, dtype=np.float64)
-        assert x.size == self.n_states
+        if x.size != self.n_states:
+            raise ValueError(f"state has {x.size} values, the problem {self.n_states}")
         self._check(self._lib.drts_write_state(self._h, int(rhs), _ptr(x)))
 
     def run_host(self, scale, det_out=None):
