@@ -277,6 +277,28 @@ drts_status drts_column_info(drts_ctx *ctx, double *absorb, double *exit_total,
 
 drts_status drts_get_info(const drts_ctx *ctx, drts_info *out);
 
+/*
+ * Host-built tables of one medium of a problem, computed without a device
+ * (a diagnostic of the inputs the device assembler reads; the step does not
+ * need it).  Outputs are caller-owned FP64/FP32 arrays, any may be NULL:
+ *   stencil_out    [26][27][26]: W_k[n][o][m], the mass a state of direction
+ *                  n in a voxel of medium k sends in one step to the voxel at
+ *                  offset o (index (oz+1)*9 + (oy+1)*3 + (ox+1)) in direction
+ *                  m (Eq. 18, 19, 21), before edge or interface folding;
+ *   exit_total_out [27][26]: fraction of a state of medium k, direction n,
+ *                  that leaves the grid in one step, by the voxel's face mask
+ *                  bz*9 + by*3 + bx (b = 0 at the low face, 1 inside, 2 at
+ *                  the high face of that axis; Section 4.2 with R4);
+ *   exit_det_out   [27][26]: the part of it that leaves through the detector
+ *                  face (Eq. 27);
+ *   dir_scale_out  [26]: the FP16 tier's power-of-two row scale per direction
+ *                  (1 for the other precisions).
+ * DRTS_EINVAL for a problem drts_assemble would reject or a medium outside
+ * 0..n_media-1 (message in drts_last_error(NULL)).
+ */
+drts_status drts_host_tables(const drts_problem *prob, int32_t medium, double *stencil_out,
+                             double *exit_total_out, double *exit_det_out, float *dir_scale_out);
+
 /* Set the launch shape of the step kernel (0 = library default): blocks per
  * SM (must fit), threads per block (multiple of 32, <= 256), right-hand sides
  * per pass of the batched step, and the kernel variant (-1 keeps the current

@@ -777,6 +777,25 @@ try {
     return caught(c, "drts_export_rows");
 }
 
+drts_status drts_host_tables(const drts_problem *prob, int32_t medium, double *stencil_out,
+                             double *exit_total_out, double *exit_det_out, float *dir_scale_out)
+try {
+    drts_status st = validate(prob);
+    if (st != DRTS_OK) return st;
+    if (medium < 0 || medium >= prob->n_media) return fail(nullptr, DRTS_EINVAL, "medium out of range");
+    HostTables H;
+    const std::string err = build_host_tables(*prob, H);
+    if (!err.empty()) return fail(nullptr, DRTS_EINVAL, err);
+    const size_t nw = size_t(kDirs) * kOffs * kDirs, ne = size_t(27) * kDirs;
+    if (stencil_out) std::memcpy(stencil_out, H.W.data() + size_t(medium) * nw, nw * sizeof(double));
+    if (exit_total_out) std::memcpy(exit_total_out, H.exit_total.data() + size_t(medium) * ne, ne * sizeof(double));
+    if (exit_det_out) std::memcpy(exit_det_out, H.exit_det.data() + size_t(medium) * ne, ne * sizeof(double));
+    if (dir_scale_out) std::memcpy(dir_scale_out, H.dir_scale.data(), kDirs * sizeof(float));
+    return DRTS_OK;
+} catch (...) {
+    return caught(nullptr, "drts_host_tables");
+}
+
 drts_status drts_column_info(drts_ctx *c, double *absorb, double *exit_total, double *exit_det)
 try {
     if (!c) return DRTS_EINVAL;

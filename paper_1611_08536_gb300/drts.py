@@ -104,7 +104,7 @@ class Info(ctypes.Structure):
 
 SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_detectors",
            "drts_read_state", "drts_write_state", "drts_run_host", "drts_export_rows",
-           "drts_column_info", "drts_get_info", "drts_set_launch", "drts_destroy",
+           "drts_column_info", "drts_get_info", "drts_host_tables", "drts_set_launch", "drts_destroy",
            "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_autotune",
            "drts_set_step_mode", "drts_server_create", "drts_server_submit", "drts_server_tick",
            "drts_server_poll", "drts_server_result", "drts_server_release",
@@ -136,6 +136,7 @@ def load(path: str = LIB_PATH):
     lib.drts_export_rows.argtypes = [vp, i64, i64, vp, vp, vp, i64]
     lib.drts_column_info.argtypes = [vp, vp, vp, vp]
     lib.drts_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    lib.drts_host_tables.argtypes = [ctypes.POINTER(ProblemC), i32, vp, vp, vp, vp]
     lib.drts_set_launch.argtypes = [vp, i32, i32, i32, i32]
     lib.drts_state_sum_noalloc.argtypes = [vp, i32, vp]
     lib.drts_set_fault.argtypes = [vp, i32, i64]
@@ -175,6 +176,23 @@ def load(path: str = LIB_PATH):
 
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def host_tables(prob, medium):
+    """Host-built tables of one medium, computed without a device: the
+    stencil W[n][o][m] (Eq. 18-21, before folding), the exit fractions
+    exit_total[mask][n] and exit_det[mask][n] by face mask, and the FP16
+    row scale per direction (drts_host_tables)."""
+    lib = load()
+    ps = problem_struct(prob, 0)
+    W = np.empty((26, 27, 26), np.float64)
+    ex = np.empty((27, 26), np.float64)
+    ed = np.empty((27, 26), np.float64)
+    sc = np.empty(26, np.float32)
+    st = lib.drts_host_tables(ctypes.byref(ps), int(medium), _ptr(W), _ptr(ex), _ptr(ed), _ptr(sc))
+    if st != OK:
+        raise DrtsError(st, lib.drts_last_error(None).decode())
+    return W, ex, ed, sc
 
 
 def problem_struct(prob, max_steps=0):
