@@ -503,6 +503,38 @@ void drts_destroy(drts_ctx *ctx);
  * (or the thread's next drts_assemble). */
 const char *drts_last_error(const drts_ctx *ctx);
 
+/* ---- Close-packed sphere partition (Section 3) ------------------------
+ *
+ * The paper partitions the medium into touching spheres of radius dr in
+ * close packing (face-centred cubic).  Sites: integer triples (i, j, k) with
+ * i + j + k even, 0 <= i < nx (nx even), 0 <= j < ny, 0 <= k < nz, centred
+ * at (i, j, k) * 2dr / sqrt(2); site index ((k*ny + j)*nx + i) / 2.
+ * Directions: the 12 unit vectors towards the nearest neighbours,
+ * (dx, dy, dz) / sqrt(2) with two nonzero components, dz slowest and dx
+ * fastest; state index site*12 + d.  One step moves light 2dr (all media
+ * share one refractive index: there is no interface folding), and the edges
+ * are open: mass whose target site lies outside the box leaves.  The matrix
+ * follows Eq. 18-21 and 23 as on the voxel grid.  Only the host assembly
+ * exists so far; the device step for this partition is not built.
+ */
+typedef struct drts_fcc_problem {
+    int32_t nx, ny, nz;              /* integer box; nx even, ny, nz >= 1 */
+    double spacing_mm;               /* 2dr, the distance of touching sphere centres */
+    int32_t n_media;                 /* 1..255, one refractive index */
+    const drts_medium *media;        /* [n_media], host, read during the call */
+    const uint8_t *medium_of_site;   /* [nx*ny*nz/2] in site order, host */
+} drts_fcc_problem;
+
+/*
+ * Rows [row_begin, row_end) of the close-packed partition's matrix A,
+ * assembled on the host in FP64: row_ptr [row_end - row_begin + 1] relative
+ * to row_begin, col / val [cap] with ascending columns per row (caller-owned).
+ * DRTS_EINVAL for a bad problem, row range or a cap below the entry count
+ * (row_ptr is filled either way); messages in drts_last_error(NULL).
+ */
+drts_status drts_fcc_host_rows(const drts_fcc_problem *prob, int64_t row_begin, int64_t row_end,
+                               int64_t *row_ptr, int32_t *col, double *val, int64_t cap);
+
 #ifdef __cplusplus
 }
 #endif

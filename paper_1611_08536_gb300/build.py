@@ -28,6 +28,7 @@ SOURCES = {
     "drts_serve.cu": [],
     "drts_tensor.cu": [],
     "drts_functionals.cu": [],
+    "drts_fcc.cpp": [],
 }
 
 

@@ -86,7 +86,8 @@ struct drts_ctx {
 
 namespace {
 
-// message of the last failed drts_assemble on this thread
+// message of the last failed context-free call (drts_assemble and the
+// diagnostics) on this thread
 thread_local std::string g_assemble_error;
 
 drts_status fail(drts_ctx *c, drts_status s, const std::string &msg)
@@ -358,6 +359,11 @@ cudaStream_t ctx_swap_stream(drts_ctx *c, cudaStream_t s)
     return old;
 }
 }  // namespace drts
+
+void drts::set_global_error(const std::string &msg)
+{
+    g_assemble_error = msg;
+}
 
 extern "C" {
 

@@ -80,4 +80,8 @@ struct HostTables {
 // fraction of the step for sources emitted within it, Section 4.1)
 std::string build_host_tables(const drts_problem &p, HostTables &t, double path_frac = 1.0);
 
+// Record the message drts_last_error(NULL) returns on this thread (calls
+// that have no context).
+void set_global_error(const std::string &msg);
+
 }  // namespace drts

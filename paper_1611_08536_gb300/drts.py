@@ -57,6 +57,12 @@ class ProblemC(ctypes.Structure):
     ]
 
 
+class FccProblemC(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("spacing_mm", ctypes.c_double), ("n_media", ctypes.c_int32),
+                ("media", ctypes.POINTER(Medium)), ("medium_of_site", ctypes.c_void_p)]
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("variant", ctypes.c_int32), ("threads", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("rhs_tile", ctypes.c_int32),
@@ -111,7 +117,8 @@ SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_dete
            "drts_server_get_stats", "drts_server_last_error", "drts_server_destroy",
            "drts_checkpoint_size", "drts_checkpoint_save", "drts_checkpoint_load",
            "drts_set_point_detectors", "drts_read_point_detectors", "drts_sensor_response",
-           "drts_source_column", "drts_inject_source_substeps", "drts_substep_count"]
+           "drts_source_column", "drts_inject_source_substeps", "drts_substep_count",
+           "drts_fcc_host_rows"]
 
 _lib = None
 
@@ -137,6 +144,7 @@ def load(path: str = LIB_PATH):
     lib.drts_column_info.argtypes = [vp, vp, vp, vp]
     lib.drts_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.drts_host_tables.argtypes = [ctypes.POINTER(ProblemC), i32, vp, vp, vp, vp]
+    lib.drts_fcc_host_rows.argtypes = [ctypes.POINTER(FccProblemC), i64, i64, vp, vp, vp, i64]
     lib.drts_set_launch.argtypes = [vp, i32, i32, i32, i32]
     lib.drts_state_sum_noalloc.argtypes = [vp, i32, vp]
     lib.drts_set_fault.argtypes = [vp, i32, i64]
@@ -193,6 +201,31 @@ def host_tables(prob, medium):
     if st != OK:
         raise DrtsError(st, lib.drts_last_error(None).decode())
     return W, ex, ed, sc
+
+
+def fcc_host_rows(shape, spacing_mm, media, medium_of_site, row_begin=0, row_end=None, cap=None):
+    """Rows of the close-packed partition's matrix A assembled on the host
+    (drts_fcc_host_rows): (row_ptr, col, val) in CSR form."""
+    lib = load()
+    nx, ny, nz = shape
+    n_states = nx * ny * nz // 2 * 12
+    if row_end is None:
+        row_end = n_states
+    med = (Medium * len(media))(*[Medium(*m) for m in media])
+    mos = np.ascontiguousarray(medium_of_site, dtype=np.uint8).ravel()
+    p = FccProblemC(nx, ny, nz, float(spacing_mm), len(media), med, _ptr(mos))
+    n = row_end - row_begin
+    rp = np.zeros(max(n, 0) + 1, np.int64)
+    if cap is None:
+        cap = 700 * max(n, 0) + 16
+    col = np.empty(cap, np.int32)
+    val = np.empty(cap, np.float64)
+    st = lib.drts_fcc_host_rows(ctypes.byref(p), int(row_begin), int(row_end), _ptr(rp), _ptr(col),
+                                _ptr(val), int(cap))
+    if st != OK:
+        raise DrtsError(st, lib.drts_last_error(None).decode())
+    nnz = int(rp[-1])
+    return rp, col[:nnz].copy(), val[:nnz].copy()
 
 
 def problem_struct(prob, max_steps=0):
