@@ -18,6 +18,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
