@@ -12,7 +12,8 @@ Parity status of each function (pins are in ``tests/test_oracle_pins.py``):
                       column sums.
   * ``assemble``      pinned: column sums, mirror conservation, dense brute
                       force on 4^3, ballistic translation, single-scatter line,
-                      irreducibility.
+                      irreducibility, invariance under the cube's symmetries
+                      (tests/test_oracle_symmetry.py).
   * ``column_info``   pinned: Fresnel normal incidence, total internal
                       reflection, ledger closure.
   * ``run``           pinned: conservation, pure decay, dense matrix powers;

@@ -330,7 +330,11 @@ static int orc_fold(const orc_problem *P, const int i[3], int k, const orc_entry
 #else
         t[a] = t[a] < 0 ? 0 : N[a] - 1;
 #endif
+#ifdef PLANT_HIGH_FACE_NO_FLIP
+        if (t[a] == 0) dv[a] = -dv[a];
+#else
         dv[a] = -dv[a];
+#endif
     }
     if (w == 0.0) return 0;
 

@@ -10,11 +10,12 @@ import pytest
 from paper_1611_08536_gb300 import inputs as I
 from tests import test_oracle_extensions as ext
 from tests import test_oracle_pins as pins
+from tests import test_oracle_symmetry as sym
 
 PLANTS = ["PLANT_DROP_UNSCATTERED", "PLANT_ABSORB_ONCE", "PLANT_SEGMENT_SIGN",
           "PLANT_HG_UNNORMALISED", "PLANT_MIRROR_INDEX", "PLANT_FRESNEL_SWAP",
           "PLANT_WRONG_DIRECTION_INDEX", "PLANT_POINT_OFF_BY_ONE", "PLANT_SENSOR_LAG_SIGN",
-          "PLANT_SOURCE_FULL_PATH"]
+          "PLANT_SOURCE_FULL_PATH", "PLANT_HIGH_FACE_NO_FLIP"]
 
 CHECKS = [
     pins.test_axis_direction_single_target,
@@ -32,6 +33,7 @@ CHECKS = [
     ext.test_point_row_reads_the_state,
     ext.test_sensor_delayed_impulse_shifts,
     lambda o: ext.test_source_column_axis_closed_form(o, 0.25),
+    lambda o: sym.test_homogeneous_cube_has_the_48_symmetries(o, I.MIRROR),
 ]
 
 
