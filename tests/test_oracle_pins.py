@@ -324,6 +324,47 @@ def test_interface_transmission_normal_incidence(oracle_mod):
     assert x1.sum() == pytest.approx(1.0, abs=1e-15)
 
 
+def _fresnel_unpolarised(cos_i, n1, n2):
+    # textbook Fresnel power reflectance, mean of s and p (reading R5)
+    sin_t = n1 / n2 * math.sqrt(1.0 - cos_i * cos_i)
+    if sin_t >= 1.0:
+        return 1.0
+    cos_t = math.sqrt(1.0 - sin_t * sin_t)
+    rs = ((n1 * cos_i - n2 * cos_t) / (n1 * cos_i + n2 * cos_t)) ** 2
+    rp = ((n1 * cos_t - n2 * cos_i) / (n1 * cos_t + n2 * cos_i)) ** 2
+    return 0.5 * (rs + rp)
+
+
+def test_interface_split_oblique_edge_direction(oracle_mod):
+    """Section 4.2 with readings R5/R6: an unscattered edge-direction photon
+    (0, 1, 1) leaving the last voxel of medium 1 (n = 1.37) towards medium 2
+    (n = 1.45) across a z interface.  Eq. 18 spreads it over (0,1,1), (0,1,0)
+    and (0,0,1); the two targets across the interface split with the Fresnel
+    reflectance at 45 degrees: 1 - R stays in direction (0, 1, 1) beyond the
+    interface, R comes back mirrored in z with direction (0, 1, -1); the
+    target in medium 1 takes its weight unsplit."""
+    prob = _prob((4, 4, 6), [(0.0, 0.0, 0.9, 1.37), (0.0, 0.0, 0.9, 1.45)],
+                 boundary=I.MIRROR,
+                 mov=np.repeat(np.array([0, 0, 0, 1, 1, 1], np.uint8), 16).reshape(6, 4, 4))
+    c = oracle_mod.assemble(prob)
+    x0 = np.zeros(prob.n_states)
+    x0[prob.state(1, 1, 2, D(0, 1, 1))] = 1.0
+    x1 = oracle_mod.spmv(c, x0)
+    R = _fresnel_unpolarised(1 / math.sqrt(2), 1.37, 1.45)
+    assert 0.0 < R < GOLD["fresnel_normal_1p45_to_1p37"] * 2      # a small oblique reflectance
+    wa, wb = GOLD["edge_unscattered_diag"], GOLD["edge_unscattered_axis"]
+    want = {prob.state(1, 2, 3, D(0, 1, 1)): (1 - R) * wa,
+            prob.state(1, 2, 2, D(0, 1, -1)): R * wa,
+            prob.state(1, 1, 3, D(0, 1, 1)): (1 - R) * wb,
+            prob.state(1, 1, 2, D(0, 1, -1)): R * wb,
+            prob.state(1, 2, 2, D(0, 1, 1)): wb}
+    got = {int(s): float(x1[s]) for s in np.flatnonzero(x1)}
+    assert set(got) == set(want)
+    for st, v in want.items():
+        assert got[st] == pytest.approx(v, rel=1e-12)
+    assert x1.sum() == pytest.approx(1.0, abs=1e-15)
+
+
 def test_ledger_closure_fresnel(oracle_mod):
     prob, src = I.fresnel_cube(8)
     c = oracle_mod.assemble(prob)

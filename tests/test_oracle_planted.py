@@ -30,6 +30,7 @@ CHECKS = [
     pins.test_fresnel_normal_incidence_at_edge,
     pins.test_total_internal_reflection_corner_direction,
     pins.test_interface_transmission_normal_incidence,
+    pins.test_interface_split_oblique_edge_direction,
     ext.test_point_row_reads_the_state,
     ext.test_sensor_delayed_impulse_shifts,
     lambda o: ext.test_source_column_axis_closed_form(o, 0.25),
