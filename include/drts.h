@@ -157,6 +157,8 @@ drts_status drts_step_n(drts_ctx *ctx, int64_t n_steps);
  * ([t][patch], FP64, caller-owned, (t_end-t_begin)*n_patch values) and, if
  * ledger_out is not NULL, the ledger {sum of x(t), injected, absorbed,
  * exited} (4 FP64, cumulative since t = 0).  Synchronises the stream.
+ * DRTS_EINVAL for a bad rhs or a range outside [0, t]; DRTS_ESTATE for a
+ * non-empty range without a detector history (det_face none or max_steps 0).
  */
 drts_status drts_read_detectors(drts_ctx *ctx, int32_t rhs, int64_t t_begin,
                                 int64_t t_end, double *host_out, double *ledger_out);
@@ -242,11 +244,13 @@ drts_status drts_inject_source_substeps(drts_ctx *ctx, int32_t rhs, int32_t n_en
                                         int32_t n_sub, int64_t t0, int32_t n_t,
                                         const double *profile);
 
-/* Copy x(t) of rhs to host_out (canonical order, n_states FP64). Synchronises. */
+/* Copy x(t) of rhs to host_out (canonical order, n_states FP64, caller-owned).
+ * Synchronises.  DRTS_EINVAL for a bad rhs or a NULL buffer. */
 drts_status drts_read_state(drts_ctx *ctx, int32_t rhs, double *host_out);
 
 /* Overwrite x(t) of rhs from host_in (canonical order, n_states FP64,
- * rounded to the state precision).  t is unchanged.  Synchronises. */
+ * caller-owned, read during the call, rounded to the state precision).  t is
+ * unchanged.  Synchronises.  DRTS_EINVAL for a bad rhs or a NULL buffer. */
 drts_status drts_write_state(drts_ctx *ctx, int32_t rhs, const double *host_in);
 
 /*
@@ -254,7 +258,10 @@ drts_status drts_write_state(drts_ctx *ctx, int32_t rhs, const double *host_in);
  * step's source scale factors host->device (scale[i*n_rhs + r] multiplies the
  * injected weights of rhs r at step t+i, replacing P(t)), advance one step,
  * and copy that step's detector readout device->host into
- * det_out[i][r][patch].  host buffers should be pinned for overlap.
+ * det_out[i][r][patch] (NULL: no readout).  Both buffers are caller-owned;
+ * pinned host memory lets the copies overlap.  Synchronises at the end.
+ * DRTS_EINVAL for a NULL scale or as drts_step_n; DRTS_EUNSUPPORTED while
+ * sub-step sources are set.
  */
 drts_status drts_run_host(drts_ctx *ctx, int64_t n_steps, const double *scale,
                           double *det_out);
@@ -264,7 +271,9 @@ drts_status drts_run_host(drts_ctx *ctx, int64_t n_steps, const double *scale,
  * (rows in canonical state order, columns ascending): row_ptr has
  * row_end-row_begin+1 entries starting at 0, col and val have room for cap
  * entries (DRTS_EINVAL if too small; row_ptr is still filled).  Values are
- * the stored ones (FP64, FP32, or FP16 times the row scale) widened to FP64.
+ * the stored ones (FP64, FP32, or FP16 times the row scale) widened to FP64;
+ * a value kept as two FP16 terms is exported as their sum, so the structure
+ * is the matrix's in every precision.  Synchronises.
  */
 drts_status drts_export_rows(drts_ctx *ctx, int64_t row_begin, int64_t row_end,
                              int64_t *row_ptr, int32_t *col, double *val, int64_t cap);
@@ -275,6 +284,8 @@ drts_status drts_export_rows(drts_ctx *ctx, int64_t row_begin, int64_t row_end,
 drts_status drts_column_info(drts_ctx *ctx, double *absorb, double *exit_total,
                              double *exit_det);
 
+/* Sizes and step count of ctx (drts_info above) into *out.  Does not
+ * synchronise.  DRTS_EINVAL for a NULL argument. */
 drts_status drts_get_info(const drts_ctx *ctx, drts_info *out);
 
 /*
