@@ -340,6 +340,9 @@ drts_status drts_set_launch(drts_ctx *ctx, int32_t blocks_per_sm,
  *                         bounded (DRTS_ETIMEOUT instead of a hang); for
  *                         small grids where launch gaps matter.  One
  *                         right-hand side only.
+ * DRTS_EINVAL for an unknown mode; DRTS_EUNSUPPORTED for the persistent mode
+ * with several right-hand sides, with sub-step sources set, or where the
+ * device offers no cooperative launch.  Takes effect at the next step.
  */
 #define DRTS_STEP_LAUNCH 0
 #define DRTS_STEP_PERSISTENT 1
@@ -375,7 +378,7 @@ typedef struct drts_tune_result {
  * launches each, CUDA events on the context stream) and apply it.  The state,
  * t, detectors and ledger are left unchanged (the trial steps write the spare
  * state buffer and a scratch ledger).  Results are cached per (grid,
- * precision, rhs, SM count, nnz) in the process and, when the environment
+ * precision, rhs, SM count, stored entries) in the process and, when the environment
  * variable DRTS_TUNE_CACHE names a file, appended to it and read back by later
  * processes.  Synchronises.  out may be NULL.
  */
