@@ -437,7 +437,7 @@ drts_status drts_state_sum_noalloc(drts_ctx *ctx, int32_t rhs, double *out_devic
  * steps_per_tick steps of every resident simulation into one CUDA graph whose
  * branches fan out over n_streams streams (their kernels overlap on the
  * device) and launches it, (2) while it runs, admits queued requests in
- * arrival order as long as a resident slot and device memory (a footprint
+ * the configured order as long as a resident slot and device memory (a footprint
  * estimate against mem_budget_bytes) are free, assembling their A, and (3)
  * retires finished simulations: detector history and ledger are copied to
  * host and their device memory is freed.  A request submitted while others
@@ -484,6 +484,9 @@ typedef struct drts_server_stats {
     int64_t used_bytes, budget_bytes;
 } drts_server_stats;
 
+/* Create a server on the current device (cfg is copied; *out owns its
+ * streams and every request).  DRTS_EINVAL for a configuration out of range,
+ * DRTS_ECUDA if the device or its streams cannot be set up. */
 drts_status drts_server_create(const drts_server_config *cfg, drts_server **out);
 
 /* Queue one simulation: problem (copied; max_steps is set to n_steps), its
@@ -496,17 +499,28 @@ drts_status drts_server_submit(drts_server *srv, const drts_problem *prob, int32
                                const double *src_weight, int64_t t0, int32_t n_t,
                                const double *profile, int64_t n_steps, int64_t *request_id);
 
-/* One scheduling round (see above); *n_done = simulations retired. */
+/* One scheduling round (see above); *n_done = simulations retired.  A
+ * request whose assembly or result readout fails is marked DRTS_REQ_FAILED
+ * (drts_server_result then reports its error) and the others go on. */
 drts_status drts_server_tick(drts_server *srv, int32_t *n_done);
+
+/* State, sizes and host-clock timings of a request.  DRTS_EINVAL for an
+ * unknown id. */
 drts_status drts_server_poll(drts_server *srv, int64_t request_id, drts_request_info *out);
 
 /* Detector history [n_steps][n_patch] and ledger {sum x, injected, absorbed,
- * exited} of right-hand side rhs of a finished request (either may be NULL). */
+ * exited} of right-hand side rhs of a finished request (caller-owned host
+ * buffers, either may be NULL).  DRTS_ESTATE before the request is done,
+ * DRTS_EINVAL for an unknown id or rhs. */
 drts_status drts_server_result(drts_server *srv, int64_t request_id, int32_t rhs,
                                double *det_out, double *ledger_out);
+/* Forget a finished or failed request and its results (DRTS_ESTATE while it
+ * is queued or running, DRTS_EINVAL for an unknown id). */
 drts_status drts_server_release(drts_server *srv, int64_t request_id);
 drts_status drts_server_get_stats(const drts_server *srv, drts_server_stats *out);
+/* Text of the server's last error ("" for NULL); valid until the next call. */
 const char *drts_server_last_error(const drts_server *srv);
+/* Wait for the device, free every request and the server (NULL is ignored). */
 void drts_server_destroy(drts_server *srv);
 
 /* Free every device and host resource of ctx (NULL is ignored). */
