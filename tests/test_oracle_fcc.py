@@ -294,3 +294,25 @@ def test_planted_mistakes_are_caught(monkeypatch, plant):
         except AssertionError:
             failed += 1
     assert failed >= 1
+
+
+def test_any_direction_set_keeps_eq24_column_sums():
+    """The paper's own direction set (Lebedev points) is not carried here;
+    the oracle's stencil takes any unit vectors.  With 26 directions that do
+    not point at lattice sites, every source direction still sends out
+    exactly e^{-mu_a L} (Eq. 24) and g = 0 spreads the scattered share
+    evenly over the set."""
+    v = np.array([(x, y, z) for z in (-1, 0, 1) for y in (-1, 0, 1) for x in (-1, 0, 1)
+                  if (x, y, z) != (0, 0, 0)], dtype=np.float64)
+    dirs = v / np.linalg.norm(v, axis=1, keepdims=True)
+    mu_s, mu_a, s_mm = 6.0, 0.2, 0.1
+    W = fcc.stencil(mu_s, mu_a, 0.0, 1.0, s_mm, dirs)
+    tot = np.zeros(26)
+    into = np.zeros((26, 26))
+    for (n, _o, m), val in W.items():
+        tot[n] += val
+        into[n, m] += val
+    assert np.allclose(tot, math.exp(-mu_a * s_mm), rtol=1e-14, atol=0)
+    sc = (1.0 - math.exp(-mu_s * s_mm)) * math.exp(-mu_a * s_mm) / 26.0
+    un = math.exp(-mu_s * s_mm) * math.exp(-mu_a * s_mm)
+    assert np.allclose(into, sc + np.eye(26) * un, rtol=1e-13, atol=0)
