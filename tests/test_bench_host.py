@@ -47,3 +47,32 @@ def test_batched_launch_count():
     # no detector patches: no detector launch
     args.batched_kernel = "cuda"
     assert bench.batched_launches(args, {"variant": 1, "rhs_tile": 4}, _info(1, 1, 0), 6) == (1 + 2) * 5
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference (the oracle timed on the host cores) prints
+    exactly one JSON line with the keys of the benchmark contract."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload",
+                        "three_layers_16", "--steps", "2", "--warmup", "3"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["steps"] == 2 and d["warmup"] == 3 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    # fewer than three warm-up steps are raised to three (the timing rule)
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload",
+                        "three_layers_16", "--steps", "1", "--warmup", "1"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and json.loads(r.stdout.strip().splitlines()[-1])["warmup"] == 3
