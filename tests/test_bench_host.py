@@ -76,3 +76,18 @@ def test_reference_arm_prints_one_contract_line():
                         "three_layers_16", "--steps", "1", "--warmup", "1"],
                        cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and json.loads(r.stdout.strip().splitlines()[-1])["warmup"] == 3
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    """Under torchrun only rank 0 runs the reference arm; the other ranks
+    exit 0 without work or output."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="1", LOCAL_RANK="1", WORLD_SIZE="2")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload",
+                        "three_layers_16", "--steps", "1", "--warmup", "3", "--gpus", "2"],
+                       cwd=root, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip() == ""
