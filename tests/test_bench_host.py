@@ -91,3 +91,27 @@ def test_reference_arm_other_ranks_exit_quietly():
                        cwd=root, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_clock_summary_reads_nvidia_smi_rows():
+    cs = bench.ClockSampler(0)
+    assert cs.summary()["reasons"] == ["no samples"]
+    idle = ["0", "2070", "2070", "310.2", "0x0000000000000000", "Not Active", "Not Active",
+            "Not Active", "Not Active"]
+    capped = ["0", "1965", "2070", "1398.7", "0x0000000000000004", "Not Active", "Not Active",
+              "Not Active", "Active"]
+    cs.samples = [idle, capped, capped, ["0", "[N/A]", "[N/A]", "[N/A]", "[N/A]"]]
+    s = cs.summary()
+    assert s["sm_mhz"] == 1965.0 and s["sm_max_mhz"] == 2070.0      # median of the readable ones
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 4
+    hot = list(capped)
+    hot[7] = "Active"                                                # sw_thermal_slowdown
+    cs.samples = [hot]
+    assert cs.summary()["reasons"] == ["sw_power_cap", "sw_thermal_slowdown"]
+
+
+def test_peaks_prefer_the_measured_file(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6787.6}))
+    assert bench.peaks() == (6787.6, "measured")
