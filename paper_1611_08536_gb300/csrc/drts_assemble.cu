@@ -254,11 +254,6 @@ template <>
 __device__ __forceinline__ double to_store<double>(double v, float) { return v; }
 template <>
 __device__ __forceinline__ float to_store<float>(double v, float) { return __double2float_rn(v); }
-template <>
-__device__ __forceinline__ __half to_store<__half>(double v, float scale)
-{
-    return __double2half(v / double(scale));
-}
 
 // FP16 tier: each value v is stored as one of the two FP16 numbers lo <= v /
 // scale <= hi that bracket it - hi when the fraction (v/scale - lo) / (hi -
