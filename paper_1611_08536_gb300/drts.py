@@ -12,8 +12,6 @@ import os
 
 import numpy as np
 
-from . import inputs as _inputs
-
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libdrts.so")
 

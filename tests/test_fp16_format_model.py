@@ -12,7 +12,6 @@ target holds with the two-term values and fails without them."""
 import math
 
 import numpy as np
-import pytest
 import scipy.sparse as sp
 
 from paper_1611_08536_gb300 import inputs as I

@@ -2,7 +2,6 @@
 point detectors (sparse detector rows F of Eq. 27) in every step form, the
 sensor response of Eq. 27, the partial-path source column and the sub-step
 sources of Section 4.1, and their checkpoint / mode interplay."""
-import copy
 
 import numpy as np
 import pytest

@@ -5,7 +5,6 @@ rounding of the stored precision.  Time step: relative L1 of the state
 within the per-precision tolerance (FP64 1e-12; FP32 1e-5 per 1000 steps;
 FP16 row-scaled 1e-4 or the measured figure stated in the test).
 """
-import math
 
 import numpy as np
 import pytest

@@ -2,9 +2,6 @@
 mistake at a time (on the CPU) and at least one pin must fail.  Each check
 below is one of the pins of test_oracle_pins.py or test_oracle_extensions.py,
 run against the mutant."""
-import math
-
-import numpy as np
 import pytest
 
 from paper_1611_08536_gb300 import inputs as I
