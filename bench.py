@@ -120,15 +120,27 @@ def kernel_hash():
     return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
 
 
-def traffic_per_launch(workload_name, precision, nnz):
-    """DRAM bytes per step-kernel launch from a committed ncu capture, scaled to
-    this launch by nonzeros; None if absent or taken on another kernel source."""
+def traffic_captures():
+    """The committed ncu DRAM captures of the step kernel (one per precision
+    and launch variant), or [] when the file is absent."""
     if not os.path.exists(TRAFFIC_FILE):
-        return None
+        return []
     d = json.load(open(TRAFFIC_FILE))
-    if d.get("kernel_sha") != kernel_hash() or d.get("precision") != precision:
-        return None
-    return d["dram_bytes_per_nnz"] * nnz
+    return d.get("captures", [d])
+
+
+def traffic_per_launch(workload_name, precision, nnz, variant=None):
+    """DRAM bytes per step-kernel launch from a committed ncu capture of the
+    same precision and launch variant on the current kernel source, scaled to
+    this launch by nonzeros (traffic grows with the matrix); None when no
+    such capture exists."""
+    for d in traffic_captures():
+        if d.get("kernel_sha") != kernel_hash() or d.get("precision") != precision:
+            continue
+        if variant is not None and d.get("variant") is not None and int(d["variant"]) != int(variant):
+            continue
+        return d["dram_bytes_per_nnz"] * nnz
+    return None
 
 
 def algorithmic_bytes(info, precision):
@@ -234,7 +246,8 @@ def run_gpu(args):
     peak, peak_kind = peaks()
     alg = algorithmic_bytes(info, args.precision)
     achieved = alg / (ms_step * 1e-3) / 1e9
-    traffic = traffic_per_launch(args.workload, args.precision, info.nnz)
+    variant = tune["variant"] if tune else (args.variant if args.variant >= 0 else 0)
+    traffic = traffic_per_launch(args.workload, args.precision, info.nnz, variant)
     line = {
         "metric": METRIC, "value": round(gnnz, 3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -254,6 +267,9 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "peak_kind": peak_kind,
+                     "traffic_source": (f"ncu capture of launch variant {variant} at 48^3, "
+                                        "scaled to this launch by nonzeros")
+                     if traffic is not None else "no ncu capture of this kernel source and variant",
                      "algorithmic_bytes_per_launch": int(alg)},
         "gpu_launches": args.steps,
         "e2e": e2e,
@@ -264,11 +280,86 @@ def run_gpu(args):
     if rank == 0 and args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, args)
     ctx.close()
+    if ws == 1 and args.sub:
+        line.update(sub_lines(args, local))
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def measure_plain(workload_name, precision, steps, warmup, autotune, check=True, local=0):
+    """The plain single-right-hand-side step of another precision tier on a
+    workload, timed like the headline line (CUDA events over the timed
+    steps, autotuned launch), with its HBM roofline and sampled parity."""
+    import torch
+    from paper_1611_08536_gb300 import drts
+    stream = torch.cuda.current_stream()
+    prob, src = workload(workload_name, precision)
+    ctx = drts.Context(prob, max_steps=warmup + steps + 2, stream=stream.cuda_stream)
+    ctx.set_source(0, src)
+    tune = ctx.autotune(autotune) if autotune else None
+    info = ctx.info()
+    ctx.step_n(warmup)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ctx.step_n(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    parity = sampled_step_check(ctx, prob, None) if check else None
+    ctx.close()
+    peak, peak_kind = peaks()
+    alg = algorithmic_bytes(info, precision)
+    achieved = alg / (ms * 1e-3) / 1e9
+    variant = tune["variant"] if tune else 0
+    traffic = traffic_per_launch(workload_name, precision, info.nnz, variant)
+    return {
+        "workload": workload_name, "precision": precision, "steps": steps, "warmup": warmup,
+        "ms_per_step": round(ms, 4), "value": round(info.nnz / (ms * 1e-3) / 1e9, 3), "unit": UNIT,
+        "nnz": int(info.nnz), "nnz_stored": int(info.nnz_stored),
+        "matrix_GB": round(info.matrix_bytes / 1e9, 3), "launch": tune,
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": int(alg),
+                     "traffic_source": (f"ncu capture of launch variant {variant} at 48^3, "
+                                        "scaled to this launch by nonzeros")
+                     if traffic is not None else "no ncu capture of this kernel source and variant"},
+        "sampled_parity": parity, "gpu_launches": steps, "clocks": clk.summary(),
+    }
+
+
+def sub_lines(args, local):
+    """The metric's second half on the same box, after the headline: the
+    FP16-rowscale tier on the headline workload, the batched step of 64
+    right-hand sides sharing A (96^3 inclusions) against the plain
+    per-simulation step, and a served stream whose requests keep their full
+    step counts.  Each is a sub-object of the headline JSON line; a failure
+    is recorded there instead of ending the run."""
+    out = {}
+    jobs = []
+    if "fp16" in args.sub:
+        jobs.append(("fp16", lambda: measure_plain(args.workload, "fp16", args.steps, args.warmup,
+                                                    args.autotune, args.check, local)))
+    if "batched" in args.sub:
+        jobs.append(("batched", lambda: measure_batched(
+            types_ns(variant=-1, threads=0, blocks_per_sm=0, rhs_tile=0), args.sub_batched_workload, "fp32",
+            64, args.batched_kernel, args.sub_batched_steps, args.warmup, max(args.autotune, 1), 1500,
+            check=args.check, local=local)))
+    if "served" in args.sub:
+        jobs.append(("served", lambda: measure_served(args, args.sub_served_requests, 50.0, 1.0, 16, 20, 4,
+                                                       "fifo", baselines="estimate", local=local)))
+    for name, fn in jobs:
+        t = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as e:          # recorded in the line, never silently dropped
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = round(time.perf_counter() - t, 1)
+    return out
 
 
 def sampled_step_check(ctx, prob, args):
@@ -324,21 +415,62 @@ def cpu_baseline(prob, args, seconds=12.0):
     return out
 
 
-FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+def sm_max_mhz():
+    """Maximum SM clock: the measured file, else nvidia-smi, else the
+    GB300's 2070 MHz."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        v = json.load(open(p)).get("sm_max_mhz")
+        if v:
+            return float(v), "measured file"
+    try:
+        out = subprocess.run(["nvidia-smi", "--id=0", "--query-gpu=clocks.max.sm",
+                              "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                             timeout=5).stdout.strip()
+        return float(out.splitlines()[0]), "nvidia-smi"
+    except Exception:
+        return 2070.0, "nominal"
 
 
-def batched_roofline(args, flops, ms):
-    if args.batched_kernel == "tensor":
-        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
-            if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
-        ach = flops / (ms * 1e-3) / 1e12
-        return {"bound": "tensor", "achieved": round(ach, 2), "peak": p, "unit": "TFLOP/s",
-                "frac": round(ach / p, 4), "traffic": None,
-                "peak_kind": "measured bf16 (cuBLAS burst); kernel uses mma.sync, padded-block flops"}
-    ach = flops / (ms * 1e-3) / 1e12
-    return {"bound": "alu", "achieved": round(ach, 2), "peak": round(FP32_FMA_PEAK_TFLOPS, 1),
-            "unit": "TFLOP/s", "frac": round(ach / FP32_FMA_PEAK_TFLOPS, 4), "traffic": None,
-            "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+def fp32_fma_peak_tflops(sms, mhz):
+    """FP32 FMA peak of the CUDA cores: SMs x 128 FP32 lanes x 2 flop x clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def batched_bytes(info, precision, R):
+    """Algorithmic bytes of one batched step: A streamed once (values, 16-bit
+    codes, FP16 row scales) plus every right-hand side's state read and
+    written once."""
+    vb = {"fp32": 4, "fp64": 8, "fp16": 2}[precision]
+    sb = 8 if precision == "fp64" else 4
+    b = info.nnz_stored * (vb + 2) + 2 * info.n_states * R * sb
+    if precision == "fp16":
+        b += info.n_states * 4
+    return b
+
+
+def batched_roofline(flops, nbytes, ms, fma_peak, hbm_peak, kernel, tensor_peak=None):
+    """Roofline of the batched step on the method's work: 2 x nnz x R flops
+    (one multiply-add per nonzero and right-hand side) and its algorithmic
+    bytes.  The binding roof is the slower of the FP32 CUDA-core FMA roof and
+    the HBM roof; frac = that roof's time / the measured time."""
+    t_fma = flops / (fma_peak * 1e12)
+    t_hbm = nbytes / (hbm_peak * 1e9)
+    t = ms * 1e-3
+    if t_fma >= t_hbm:
+        out = {"bound": "alu", "achieved": round(flops / t / 1e12, 2), "peak": round(fma_peak, 1),
+               "unit": "TFLOP/s", "frac": round(t_fma / t, 4)}
+    else:
+        out = {"bound": "hbm", "achieved": round(nbytes / t / 1e9, 1), "peak": hbm_peak,
+               "unit": "GB/s", "frac": round(t_hbm / t, 4)}
+    out.update({"traffic": None, "flops_per_step": flops, "algorithmic_bytes_per_step": int(nbytes),
+                "fma_roof_ms": round(t_fma * 1e3, 3), "hbm_roof_ms": round(t_hbm * 1e3, 3),
+                "hbm_frac": round(t_hbm / t, 4), "fma_frac": round(t_fma / t, 4),
+                "peak_kind": "FP32 FMA derived from the device's SM count and maximum clock; "
+                             "HBM measured copy"})
+    if kernel == "tensor" and tensor_peak:
+        out["tensor_frac_method_flops"] = round(flops / t / 1e12 / tensor_peak, 5)
+    return out
 
 
 def batched_launches(args, tune, info, R):
@@ -356,103 +488,155 @@ def batched_launches(args, tune, info, R):
     return per * args.steps
 
 
+def measure_batched(args, workload_name, precision, R, kernel, steps, warmup, autotune,
+                    sim_steps, check=True, local=0):
+    """Batched step of R right-hand sides sharing A, timed with CUDA events;
+    the plain single-right-hand-side step of the same problem timed on the
+    same GPU; sampled per-right-hand-side parity of one more step."""
+    import copy
+    import numpy as np
+    import torch
+    from paper_1611_08536_gb300 import drts
+    stream = torch.cuda.current_stream()
+    prob, srcs = workload(workload_name, precision, R)
+    prob.batched_kernel = 1 if kernel == "tensor" else 0
+    ctx = drts.Context(prob, max_steps=warmup + steps + 2, stream=stream.cuda_stream)
+    for r, sr in enumerate(srcs):
+        ctx.set_source(r, sr)
+    if args.variant >= 0 or args.threads or args.blocks_per_sm or args.rhs_tile:
+        ctx.set_launch(args.blocks_per_sm, args.threads, args.rhs_tile, args.variant)
+    tune = ctx.autotune(autotune) if autotune else None
+    info = ctx.info()
+    ctx.step_n(warmup)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ctx.step_n(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    parity = None
+    if check:
+        # one more step from the current states (the delta sources are
+        # zero by now), checked row by row in FP64 on sampled planes
+        import oracle
+        rs = sorted({0, R // 2, R - 1})
+        xs = {r: ctx.read_state(r) for r in rs}
+        ctx.step_n(1)
+        ys = {r: ctx.read_state(r) for r in rs}
+        nz = prob.shape[2]
+        planes = sorted({0, nz // 2, nz - 1})
+        worst = 0.0
+        for z in planes:
+            c = oracle.assemble(prob, z, z + 1)
+            for r in rs:
+                yo = oracle.spmv(c, xs[r])
+                den = np.abs(yo).sum()
+                if den > 0:
+                    worst = max(worst, float(np.abs(ys[r][c.row0:c.row0 + c.n_rows] - yo).sum() / den))
+        parity = {"planes": planes, "rhs": rs, "rel_l1_one_step": worst}
+    ctx.close()
+    # the plain per-simulation step of the same problem
+    p1 = copy.copy(prob)
+    p1.n_rhs = 1
+    p1.batched_kernel = 0
+    c1 = drts.Context(p1, max_steps=warmup + steps, stream=stream.cuda_stream)
+    c1.set_source(0, srcs[0])
+    if autotune:
+        c1.autotune(autotune)
+    c1.step_n(warmup)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    c1.step_n(steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = ev0.elapsed_time(ev1) / steps
+    c1.close()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz, mhz_src = sm_max_mhz()
+    hbm, _ = peaks()
+    tensor_peak = None
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        tensor_peak = json.load(open(pk)).get("bf16_tflops")
+    flops = 2.0 * info.nnz * R
+    nbytes = batched_bytes(info, precision, R)
+    roof = batched_roofline(flops, nbytes, ms, fp32_fma_peak_tflops(sms, mhz), hbm, kernel, tensor_peak)
+    roof["peak_kind"] += f" ({sms} SMs, {mhz:.0f} MHz from {mhz_src})"
+    return {
+        "workload": workload_name, "rhs": R, "grid": list(prob.shape), "nnz": int(info.nnz),
+        "precision": precision, "batched_kernel": kernel, "launch": tune,
+        "ms_per_step": round(ms, 4), "nnz_rhs_per_s": round(info.nnz * R / (ms * 1e-3) / 1e9, 2),
+        "sims_per_s": round(R / (sim_steps * ms * 1e-3), 4),
+        "plain_single_rhs_ms_per_step": round(ms1, 4),
+        "plain_sims_per_s": round(1.0 / (sim_steps * ms1 * 1e-3), 4),
+        "speedup_vs_plain_per_simulation": round(R * ms1 / ms, 2),
+        "sim_steps": sim_steps, "roofline": roof, "sampled_parity": parity,
+        "gpu_launches": batched_launches(types_ns(batched_kernel=kernel, steps=steps), tune, info, R),
+        "clocks": clk.summary(),
+    }
+
+
+def types_ns(**kw):
+    import types
+    return types.SimpleNamespace(**kw)
+
+
 def run_batched(args):
     """Batched step: one pass over A serves R right-hand sides.  Reports
     nonzero-RHS products per second, simulations per second for a run of
     --sim-steps steps, and the plain single-RHS step of the same problem
     timed on the same GPU."""
-    import numpy as np
     import torch
-    from paper_1611_08536_gb300 import build, drts
+    from paper_1611_08536_gb300 import build
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     build.build()
-    stream = torch.cuda.current_stream()
-    prob, srcs = workload(args.workload, args.precision, args.rhs)
-    prob.batched_kernel = 1 if args.batched_kernel == "tensor" else 0
-    ctx = drts.Context(prob, max_steps=args.warmup + args.steps + 1, stream=stream.cuda_stream)
-    for r, sr in enumerate(srcs):
-        ctx.set_source(r, sr)
-    if args.variant >= 0 or args.threads or args.blocks_per_sm or args.rhs_tile:
-        ctx.set_launch(args.blocks_per_sm, args.threads, args.rhs_tile, args.variant)
-    tune = ctx.autotune(args.autotune) if args.autotune else None
-    info = ctx.info()
-    ctx.step_n(args.warmup)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        ctx.step_n(args.steps)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    ctx.close()
-    # the plain per-simulation step of the same problem
-    import copy
-    p1 = copy.copy(prob)
-    p1.n_rhs = 1
-    c1 = drts.Context(p1, max_steps=args.warmup + args.steps, stream=stream.cuda_stream)
-    c1.set_source(0, srcs[0])
-    if args.autotune:
-        c1.autotune(args.autotune)
-    c1.step_n(args.warmup)
-    torch.cuda.synchronize()
-    ev0.record(stream)
-    c1.step_n(args.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms1 = ev0.elapsed_time(ev1) / args.steps
-    c1.close()
-    R = args.rhs
-    flops = 2.0 * info.nnz * R * 2        # products + compensated accumulation
-    if args.batched_kernel == "tensor":
-        # tensor-core form: 27 padded 32x32 blocks per voxel, 5 bf16 MMA terms
-        rp = 8
-        while rp < R:
-            rp *= 2
-        flops = 2.0 * prob.n_voxels * 27 * 32 * 32 * rp * 5
+    m = measure_batched(args, args.workload, args.precision, args.rhs, args.batched_kernel, args.steps,
+                        args.warmup, args.autotune, args.sim_steps, check=args.check, local=local)
     line = {
         "metric": "DRTS batched step, nonzero x right-hand-side products per second",
-        "value": round(info.nnz * R / (ms * 1e-3) / 1e9, 2), "unit": "G nnz-rhs/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "value": m["nnz_rhs_per_s"], "unit": "G nnz-rhs/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f16-matrix/f32-state"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": args.workload, "rhs": R, "grid": list(prob.shape), "nnz": int(info.nnz),
-                   "batched_kernel": args.batched_kernel,
-                   "precision": args.precision, "launch": tune,
-                   "sims_per_s": round(R / (args.sim_steps * ms * 1e-3), 4),
-                   "plain_single_rhs_ms_per_step": round(ms1, 4),
-                   "plain_sims_per_s": round(1.0 / (args.sim_steps * ms1 * 1e-3), 4),
-                   "speedup_vs_plain_per_simulation": round(R * ms1 / ms, 2),
-                   "sim_steps": args.sim_steps},
-        "roofline": batched_roofline(args, flops, ms),
-        "gpu_launches": batched_launches(args, tune, info, R), "clocks": clk.summary(),
+        "config": {k: m[k] for k in ("workload", "rhs", "grid", "nnz", "batched_kernel", "precision",
+                                     "launch", "sims_per_s", "plain_single_rhs_ms_per_step",
+                                     "plain_sims_per_s", "speedup_vs_plain_per_simulation",
+                                     "sim_steps")},
+        "roofline": m["roofline"], "sampled_parity": m["sampled_parity"],
+        "gpu_launches": m["gpu_launches"], "clocks": m["clocks"],
     }
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
+def measure_served(args, n_requests, rate, step_scale, resident, tick_steps, streams, policy_name,
+                   baselines="run", local=0):
     """Served stream: seeded Poisson arrivals submitted in real time to the
-    continuous-batching server; reports sims/s and p50/p99 latency, next to
-    the same requests run one after another through plain contexts."""
+    continuous-batching server; sims/s and p50/p99 latency, next to the same
+    requests run without the server.  baselines = "run" runs every request
+    alone and every source as its own single-rhs simulation, one after
+    another; "estimate" times the single-rhs step once per grid side and
+    multiplies out (for requests with their full step counts, whose plain
+    runs would take minutes); "none" skips both."""
+    import copy
     import numpy as np
     import torch
-    from paper_1611_08536_gb300 import build, drts
+    from paper_1611_08536_gb300 import drts
     from paper_1611_08536_gb300 import inputs as I
-    torch.cuda.set_device(0)
-    build.build()
-    stream = I.served_stream(args.serve_requests, args.serve_rate, seed=4)
+    stream = I.served_stream(n_requests, rate, seed=4)
     for r in stream:
-        r.n_steps = max(1, int(round(r.n_steps * args.serve_step_scale)))
-    stats = None
+        r.n_steps = max(1, int(round(r.n_steps * step_scale)))
     lat, queue = [], []
-    policy = drts.SERVE_SHORTEST_FIRST if args.serve_policy == "shortest" else drts.SERVE_FIFO
-    with drts.Server(max_resident=args.serve_resident, steps_per_tick=args.serve_tick_steps,
-                     n_streams=args.serve_streams, policy=policy) as srv:
+    tick_host = []
+    policy = drts.SERVE_SHORTEST_FIRST if policy_name == "shortest" else drts.SERVE_FIFO
+    with drts.Server(max_resident=resident, steps_per_tick=tick_steps, n_streams=streams,
+                     policy=policy) as srv:
         t0 = time.perf_counter()
         ids, pending = [], list(stream)
-        with ClockSampler(0) as clk:
+        with ClockSampler(local) as clk:
             while pending or len(ids) == 0 or srv.stats()["completed"] + srv.stats()["failed"] < len(stream):
                 now = time.perf_counter() - t0
                 while pending and pending[0].arrival_s <= now:
@@ -462,64 +646,114 @@ def run_serve(args):
                 if st["resident"] == 0 and st["queued"] == 0 and pending:
                     time.sleep(min(0.01, max(0.0, pending[0].arrival_s - now)))
                     continue
+                tt = time.perf_counter()
                 srv.tick()
+                tick_host.append(time.perf_counter() - tt)
         makespan = time.perf_counter() - t0
         for rid in ids:
             inf = srv.poll(rid)
             lat.append(inf.latency_s)
             queue.append(inf.queue_s)
         stats = srv.stats()
-    # the same requests one after another, no batching or overlap
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    for r in (stream if args.serve_baselines else []):
-        with drts.Context(r.problem, max_steps=r.n_steps) as ctx:
-            for q, sr in enumerate(r.sources):
-                ctx.inject_source(q, sr.state, sr.weight, r.sources[0].t0, r.sources[0].profile)
-            ctx.step_n(r.n_steps)
-            ctx.read_detectors(0)
-    seq = time.perf_counter() - t1
-    # plain per-simulation SpMV: every source its own single-right-hand-side run
-    import copy
-    t2 = time.perf_counter()
-    n_single = 0
-    for r in (stream if args.serve_baselines else []):
-        p1 = copy.copy(r.problem)
-        p1.n_rhs = 1
-        for sr in r.sources:
-            with drts.Context(p1, max_steps=r.n_steps) as ctx:
-                ctx.inject_source(0, sr.state, sr.weight, r.sources[0].t0, r.sources[0].profile)
-                ctx.step_n(r.n_steps)
-                ctx.read_detectors(0)
-            n_single += 1
-    plain = time.perf_counter() - t2
     n = len(stream)
-    line = {
-        "metric": "DRTS served stream: simulations per second (continuous batching)",
-        "value": round(n / makespan, 4), "unit": "sims/s", "n_gpus": 1,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": "served_stream", "requests": n, "arrival_rate_per_s": args.serve_rate,
-                   "step_scale": args.serve_step_scale,
-                   "sides": list(I.SERVED_SIDES), "max_resident": args.serve_resident,
-                   "steps_per_tick": args.serve_tick_steps, "streams": args.serve_streams,
-                   "policy": args.serve_policy},
+    n_sims = sum(len(r.sources) for r in stream)
+    out = {
+        "workload": "served_stream", "requests": n, "simulations": n_sims,
+        "arrival_rate_per_s": rate, "step_scale": step_scale,
+        "steps": [r.n_steps for r in stream], "sides": [r.problem.shape[0] for r in stream],
+        "sources": [len(r.sources) for r in stream],
+        "max_resident": resident, "steps_per_tick": tick_steps, "streams": streams,
+        "policy": policy_name,
+        "requests_per_s": round(n / makespan, 4), "sims_per_s": round(n_sims / makespan, 4),
         "latency_s": {"p50": round(float(np.percentile(lat, 50)), 3),
                       "p99": round(float(np.percentile(lat, 99)), 3),
                       "max": round(float(np.max(lat)), 3)},
         "queue_s": {"p50": round(float(np.percentile(queue, 50)), 3),
                     "p99": round(float(np.percentile(queue, 99)), 3)},
         "makespan_s": round(makespan, 3),
-        "sequential_requests": {"requests_per_s": round(n / seq, 4), "seconds": round(seq, 3),
-                                "note": "each request alone, its sources batched"}
-        if args.serve_baselines else None,
-        "plain_per_simulation": {"simulations": n_single, "seconds": round(plain, 3),
-                                 "requests_per_s": round(n / plain, 4),
-                                 "note": "every source a separate single-rhs run, one after another"}
-        if args.serve_baselines else None,
-        "speedup_vs_plain_per_simulation": round(plain / makespan, 3) if args.serve_baselines else None,
+        "tick_wall_s": {"n": len(tick_host), "p50": round(float(np.percentile(tick_host, 50)), 5)
+                        if tick_host else None},
         "server_stats": stats, "clocks": clk.summary(),
     }
+    if baselines == "run":
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for r in stream:
+            with drts.Context(r.problem, max_steps=r.n_steps) as ctx:
+                for q, sr in enumerate(r.sources):
+                    ctx.inject_source(q, sr.state, sr.weight, r.sources[0].t0, r.sources[0].profile)
+                ctx.step_n(r.n_steps)
+                ctx.read_detectors(0)
+        seq = time.perf_counter() - t1
+        t2 = time.perf_counter()
+        for r in stream:
+            p1 = copy.copy(r.problem)
+            p1.n_rhs = 1
+            for sr in r.sources:
+                with drts.Context(p1, max_steps=r.n_steps) as ctx:
+                    ctx.inject_source(0, sr.state, sr.weight, r.sources[0].t0, r.sources[0].profile)
+                    ctx.step_n(r.n_steps)
+                    ctx.read_detectors(0)
+        plain = time.perf_counter() - t2
+        out["sequential_requests"] = {"requests_per_s": round(n / seq, 4), "seconds": round(seq, 3),
+                                      "note": "each request alone, its sources batched"}
+        out["plain_per_simulation"] = {"simulations": n_sims, "seconds": round(plain, 3),
+                                       "sims_per_s": round(n_sims / plain, 4),
+                                       "note": "every source a separate single-rhs run, one after another"}
+        out["speedup_vs_plain_per_simulation"] = round(plain / makespan, 3)
+    elif baselines == "estimate":
+        # single-rhs step time of each grid side (the requests' own media
+        # differ only in values, not in the matrix size), times steps x sources
+        ms_side = {}
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        cs = torch.cuda.current_stream()
+        for r in stream:
+            side = r.problem.shape[0]
+            if side in ms_side:
+                continue
+            p1 = copy.copy(r.problem)
+            p1.n_rhs = 1
+            with drts.Context(p1, max_steps=40, stream=cs.cuda_stream) as ctx:
+                ctx.inject_source(0, r.sources[0].state, r.sources[0].weight, r.sources[0].t0,
+                                  r.sources[0].profile)
+                ctx.autotune(2)
+                ctx.step_n(5)
+                torch.cuda.synchronize()
+                ev0.record(cs)
+                ctx.step_n(30)
+                ev1.record(cs)
+                torch.cuda.synchronize()
+                ms_side[side] = ev0.elapsed_time(ev1) / 30
+        plain = sum(ms_side[r.problem.shape[0]] * 1e-3 * r.n_steps * len(r.sources) for r in stream)
+        out["plain_per_simulation"] = {
+            "simulations": n_sims, "seconds_estimated": round(plain, 3),
+            "sims_per_s": round(n_sims / plain, 4),
+            "single_rhs_ms_per_step_by_side": {str(k): round(v, 4) for k, v in sorted(ms_side.items())},
+            "note": "every source as its own single-rhs simulation, one after another: the measured "
+                    "single-rhs step time of each grid side x steps x sources"}
+        out["speedup_vs_plain_per_simulation"] = round(plain / makespan, 3)
+    return out
+
+
+def run_serve(args):
+    """Served stream as its own benchmark line (see measure_served)."""
+    import torch
+    from paper_1611_08536_gb300 import build
+    torch.cuda.set_device(0)
+    build.build()
+    m = measure_served(args, args.serve_requests, args.serve_rate, args.serve_step_scale,
+                       args.serve_resident, args.serve_tick_steps, args.serve_streams, args.serve_policy,
+                       baselines="run" if args.serve_baselines else "none")
+    line = {
+        "metric": "DRTS served stream: simulations per second (continuous batching)",
+        "value": m["sims_per_s"], "unit": "sims/s", "n_gpus": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {k: m[k] for k in ("workload", "requests", "simulations", "arrival_rate_per_s",
+                                     "step_scale", "max_resident", "steps_per_tick", "streams",
+                                     "policy")},
+    }
+    line.update({k: v for k, v in m.items() if k not in line["config"]})
     print(json.dumps(line), flush=True)
 
 
@@ -657,9 +891,15 @@ def main():
     ap.add_argument("--point-detectors", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-check", dest="check", action="store_false")
+    ap.add_argument("--sub", default="fp16,batched,served",
+                    help="sub-lines of the default run (comma list of fp16, batched, served; '' = none)")
+    ap.add_argument("--sub-batched-workload", default="inclusions_96")
+    ap.add_argument("--sub-batched-steps", type=int, default=10)
+    ap.add_argument("--sub-served-requests", type=int, default=7)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    args.sub = [x for x in args.sub.split(",") if x]
     if args.impl == "reference":
         run_reference(args)
     elif args.serve:

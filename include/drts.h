@@ -408,23 +408,29 @@ drts_status drts_set_fault(drts_ctx *ctx, int32_t kind, int64_t arg);
 /*
  * Sum of x(t) of right-hand side rhs (the "sum of x" term of the ledger that
  * drts_read_detectors returns), written to out_device: one FP64 value in
- * device memory the caller owns.  The paper has no counterpart to this call;
- * it exists for callers that cannot allocate device memory when they need the
- * sum: work being recorded into a CUDA graph or stream capture (allocation
- * is not allowed there), real-time loops that must not wait on the
- * allocator, and processes whose device memory belongs to another runtime's
- * pool.  It allocates nothing: its per-block partial sums live in a static
+ * device memory the caller owns.  The paper has no counterpart to this call.
+ * drts_read_detectors allocates a small device buffer for the same sum; this
+ * call allocates nothing, for callers that cannot allocate device memory when
+ * they need the sum: real-time loops that must not wait on the allocator's
+ * locks or latency, and processes whose device memory is owned and budgeted
+ * by another runtime's pool.  Its per-block partial sums live in a static
  * device array of 4096 doubles (32 KiB) that every GPU which loads the
  * library keeps until the process exits.
  *   - Limit: at most 268,435,456 states (4096 blocks of 65,536); larger state
  *     vectors are rejected with DRTS_EINVAL.
  *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current) and caches it for the life of the process; make
+ *     that first call before any stream capture.  A device reset
+ *     (cudaDeviceReset) invalidates the cached address: do not call this
+ *     entry point on a device after resetting it.
  *   - Every call shares the array.  Calls on one stream are ordered; calls
  *     whose kernels overlap on the GPU (other streams, other contexts on the
  *     same device) race on it and may return wrong sums.
  *   - Asynchronous on the context stream; the result is deterministic (fixed
  *     reduction order) and equals the ledger's sum up to rounding order.
+ *   - DRTS_EUNSUPPORTED for a context of the tensor-core batched step
+ *     (batched_kernel DRTS_BATCHED_TENSOR with n_rhs > 1), whose state
+ *     layout this reduction does not read.
  */
 drts_status drts_state_sum_noalloc(drts_ctx *ctx, int32_t rhs, double *out_device);
 
@@ -460,6 +466,10 @@ typedef struct drts_server_config {
     int32_t steps_per_tick;          /* steps each resident simulation advances per tick */
     int32_t n_streams;               /* streams a tick's graph fans out over, 1..32 */
     int32_t policy;                  /* DRTS_SERVE_FIFO or DRTS_SERVE_SHORTEST_FIRST */
+    int32_t keep_state;              /* nonzero: keep each finished request's final state
+                                        x(n_steps) of every rhs on the host (FP64, canonical
+                                        order) for drts_server_result_state */
+    int32_t reserved;                /* must be 0 */
 } drts_server_config;
 
 #define DRTS_REQ_QUEUED 0
@@ -514,6 +524,13 @@ drts_status drts_server_poll(drts_server *srv, int64_t request_id, drts_request_
  * DRTS_EINVAL for an unknown id or rhs. */
 drts_status drts_server_result(drts_server *srv, int64_t request_id, int32_t rhs,
                                double *det_out, double *ledger_out);
+/* Final state x(n_steps) of right-hand side rhs of a finished request
+ * (n_states FP64 values in canonical order into caller-owned state_out),
+ * kept only when the server was created with keep_state set.  DRTS_ESTATE
+ * before the request is done or when states are not kept, DRTS_EINVAL for an
+ * unknown id, rhs or a NULL buffer. */
+drts_status drts_server_result_state(drts_server *srv, int64_t request_id, int32_t rhs,
+                                     double *state_out);
 /* Forget a finished or failed request and its results (DRTS_ESTATE while it
  * is queued or running, DRTS_EINVAL for an unknown id). */
 drts_status drts_server_release(drts_server *srv, int64_t request_id);

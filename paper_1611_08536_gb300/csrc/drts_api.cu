@@ -1178,7 +1178,7 @@ try {
 }
 
 drts_status drts_state_sum_noalloc(drts_ctx *c, int32_t rhs, double *out_device)
-{
+try {
     if (!c) return DRTS_EINVAL;
     if (rhs < 0 || rhs >= c->R || !out_device) return fail(c, DRTS_EINVAL, "bad arguments");
     if (c->tc) return fail(c, DRTS_EUNSUPPORTED, "not available for the tensor-core state layout");
@@ -1191,6 +1191,8 @@ drts_status drts_state_sum_noalloc(drts_ctx *c, int32_t rhs, double *out_device)
                                              c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "state_sum_noalloc");
     return DRTS_OK;
+} catch (...) {
+    return caught(c, "drts_state_sum_noalloc");
 }
 
 namespace {

@@ -3,12 +3,11 @@
 //
 // drts_read_detectors gets sum(x(t)) from a reduction whose result buffer it
 // allocates with cudaMallocAsync and fills with atomics.  Some callers cannot
-// call cudaMalloc at that point: code recording work into a CUDA graph or a
-// stream capture (allocation calls are not allowed while capturing), a
-// real-time loop that must not take the allocator's locks or latency, or a
-// process whose device memory is owned by another runtime's pool.  This entry
-// point computes the same sum into memory the caller already owns, keeping
-// its intermediate per-block partial sums in a fixed static device array.
+// call cudaMalloc at that point: a real-time loop that must not take the
+// allocator's locks or wait on its latency, or a process whose device memory
+// is owned and budgeted by another runtime's pool.  This entry point computes
+// the same sum into memory the caller already owns, keeping its intermediate
+// per-block partial sums in a fixed static device array.
 //
 // The array (kPartials doubles, 32 KiB) lives in every GPU that loads the
 // library until the process exits.  All calls share it, so two calls whose
@@ -68,7 +67,9 @@ __global__ void __launch_bounds__(kThreads) partials_sum_kernel(const double *pa
 }
 
 // Device address of g_partials for each device, looked up once per device
-// with that device current.  The host-side name of the array is only a
+// with that device current and kept for the life of the process (a device
+// reset would invalidate it; the header tells callers not to reset a device
+// they use this entry point on).  The host-side name of the array is only a
 // stand-in and must never be passed to a kernel.
 std::mutex g_mu;
 double *g_addr[64] = {};

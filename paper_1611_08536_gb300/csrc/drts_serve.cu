@@ -52,8 +52,14 @@ struct Request {
     int32_t n_patch = 0;
     std::vector<double> det;      // [rhs][n_steps][n_patch]
     std::vector<double> ledger;   // [rhs][4]
+    std::vector<double> final_x;  // [rhs][n_states] final states (keep_state only)
     Clock::time_point t_submit, t_admit, t_done;
     std::string error;
+    // states per rhs held in final_x (0 when not kept)
+    size_t state_n() const
+    {
+        return final_x.empty() ? 0 : final_x.size() / size_t(prob.n_rhs);
+    }
 };
 
 }  // namespace
@@ -132,6 +138,11 @@ drts_status retire(drts_server *s, Request &r)
     r.det.assign(size_t(R) * r.n_steps * std::max(info.n_patch, 0), 0.0);
     r.ledger.assign(size_t(R) * 4, 0.0);
     drts_status st = DRTS_OK;
+    if (s->cfg.keep_state) {
+        r.final_x.assign(size_t(R) * size_t(info.n_states), 0.0);
+        for (int q = 0; q < R && st == DRTS_OK; ++q)
+            st = drts_read_state(r.ctx, q, r.final_x.data() + size_t(q) * size_t(info.n_states));
+    }
     for (int q = 0; q < R && st == DRTS_OK; ++q)
         st = drts_read_detectors(r.ctx, q, 0, info.n_patch > 0 ? r.n_steps : 0,
                                  info.n_patch > 0 ? r.det.data() + size_t(q) * r.n_steps * info.n_patch : nullptr,
@@ -160,7 +171,7 @@ try {
     if (!cfg || !out) return DRTS_EINVAL;
     *out = nullptr;
     if (cfg->max_resident < 1 || cfg->max_resident > 256 || cfg->steps_per_tick < 1 || cfg->n_streams < 1 ||
-        cfg->n_streams > 32 || cfg->mem_budget_bytes < 0 ||
+        cfg->n_streams > 32 || cfg->mem_budget_bytes < 0 || cfg->reserved != 0 ||
         (cfg->policy != DRTS_SERVE_FIFO && cfg->policy != DRTS_SERVE_SHORTEST_FIRST))
         return DRTS_EINVAL;
     std::unique_ptr<drts_server> s(new drts_server);
@@ -375,6 +386,22 @@ try {
     return DRTS_OK;
 } catch (...) {
     return scaught(s, "drts_server_result");
+}
+
+drts_status drts_server_result_state(drts_server *s, int64_t id, int32_t rhs, double *state_out)
+try {
+    if (!s) return DRTS_EINVAL;
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return sfail(s, DRTS_EINVAL, "unknown request");
+    const Request &r = *it->second;
+    if (r.state != DRTS_REQ_DONE) return sfail(s, DRTS_ESTATE, r.error.empty() ? "request not done" : r.error);
+    if (rhs < 0 || rhs >= r.prob.n_rhs || !state_out) return sfail(s, DRTS_EINVAL, "bad rhs or NULL buffer");
+    if (r.state_n() == 0) return sfail(s, DRTS_ESTATE, "final states are kept only with keep_state");
+    const size_t n = r.state_n();
+    std::memcpy(state_out, r.final_x.data() + size_t(rhs) * n, n * sizeof(double));
+    return DRTS_OK;
+} catch (...) {
+    return scaught(s, "drts_server_result_state");
 }
 
 drts_status drts_server_release(drts_server *s, int64_t id)

@@ -74,7 +74,8 @@ class TuneResult(ctypes.Structure):
 class ServerConfig(ctypes.Structure):
     _fields_ = [("mem_budget_bytes", ctypes.c_int64), ("max_resident", ctypes.c_int32),
                 ("steps_per_tick", ctypes.c_int32), ("n_streams", ctypes.c_int32),
-                ("policy", ctypes.c_int32)]
+                ("policy", ctypes.c_int32), ("keep_state", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class RequestInfo(ctypes.Structure):
@@ -111,7 +112,8 @@ SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_dete
            "drts_column_info", "drts_get_info", "drts_host_tables", "drts_set_launch", "drts_destroy",
            "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_autotune",
            "drts_set_step_mode", "drts_server_create", "drts_server_submit", "drts_server_tick",
-           "drts_server_poll", "drts_server_result", "drts_server_release",
+           "drts_server_poll", "drts_server_result", "drts_server_result_state",
+           "drts_server_release",
            "drts_server_get_stats", "drts_server_last_error", "drts_server_destroy",
            "drts_checkpoint_size", "drts_checkpoint_save", "drts_checkpoint_load",
            "drts_set_point_detectors", "drts_read_point_detectors", "drts_sensor_response",
@@ -164,6 +166,7 @@ def load(path: str = LIB_PATH):
     lib.drts_server_tick.argtypes = [vp, ctypes.POINTER(i32)]
     lib.drts_server_poll.argtypes = [vp, i64, ctypes.POINTER(RequestInfo)]
     lib.drts_server_result.argtypes = [vp, i64, i32, vp, vp]
+    lib.drts_server_result_state.argtypes = [vp, i64, i32, vp]
     lib.drts_server_release.argtypes = [vp, i64]
     lib.drts_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     lib.drts_server_last_error.argtypes = [vp]
@@ -452,11 +455,13 @@ class Server:
     """Continuous-batching server of DRTS simulations (drts_server_*)."""
 
     def __init__(self, mem_budget_bytes=0, max_resident=16, steps_per_tick=10, n_streams=4,
-                 policy=0):
-        """policy: SERVE_FIFO (arrival order) or SERVE_SHORTEST_FIRST."""
+                 policy=0, keep_state=False):
+        """policy: SERVE_FIFO (arrival order) or SERVE_SHORTEST_FIRST;
+        keep_state: keep every finished request's final states for
+        ``result_state``."""
         self._lib = load()
         cfg = ServerConfig(int(mem_budget_bytes), int(max_resident), int(steps_per_tick),
-                           int(n_streams), int(policy))
+                           int(n_streams), int(policy), int(bool(keep_state)), 0)
         h = ctypes.c_void_p()
         st = self._lib.drts_server_create(ctypes.byref(cfg), ctypes.byref(h))
         if st != OK:
@@ -497,6 +502,15 @@ class Server:
         led = np.zeros(4, np.float64)
         self._check(self._lib.drts_server_result(self._h, int(rid), int(rhs), _ptr(det), _ptr(led)))
         return det[:, :info.n_patch], led
+
+    def result_state(self, rid, rhs=0, n_states=None):
+        """Final state x(n_steps) of right-hand side rhs (canonical order);
+        the server must keep states (``keep_state=True``)."""
+        if n_states is None:
+            raise ValueError("n_states is required (the problem's 26 * voxels)")
+        out = np.empty(int(n_states), np.float64)
+        self._check(self._lib.drts_server_result_state(self._h, int(rid), int(rhs), _ptr(out)))
+        return out
 
     def release(self, rid):
         self._check(self._lib.drts_server_release(self._h, int(rid)))

@@ -4,6 +4,8 @@ batched line claims."""
 import json
 import types
 
+import pytest
+
 import bench
 
 
@@ -115,3 +117,26 @@ def test_peaks_prefer_the_measured_file(tmp_path, monkeypatch):
     assert bench.peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6787.6}))
     assert bench.peaks() == (6787.6, "measured")
+
+
+def test_batched_roofline_counts_the_methods_work():
+    """The batched roofline counts 2 x nnz x R flops (one multiply-add per
+    nonzero and right-hand side, no compensation terms) and A once plus every
+    state read and written once; the binding roof is the slower of the FP32
+    FMA roof and the HBM roof, and the FMA peak follows the device's SM count."""
+    info = _info(4_799_000_000, 23_003_136)
+    R = 64
+    flops = 2.0 * info.nnz * R
+    nbytes = bench.batched_bytes(info, "fp32", R)
+    assert nbytes == info.nnz * 6 + 2 * info.n_states * R * 4
+    peak = bench.fp32_fma_peak_tflops(152, 2070.0)
+    assert peak == pytest.approx(80.55, rel=1e-3)
+    assert bench.fp32_fma_peak_tflops(148, 2070.0) < peak
+    r = bench.batched_roofline(flops, nbytes, 90.0, peak, 6787.6, "cuda")
+    assert r["bound"] == "alu"
+    assert r["frac"] == pytest.approx(flops / (peak * 1e12) / 0.090, rel=1e-3)
+    assert r["achieved"] == pytest.approx(flops / 0.090 / 1e12, rel=1e-3)
+    # a single right-hand side is HBM-bound
+    r1 = bench.batched_roofline(2.0 * info.nnz, bench.batched_bytes(info, "fp32", 1), 5.0, peak,
+                                6787.6, "cuda")
+    assert r1["bound"] == "hbm" and r1["unit"] == "GB/s"

@@ -144,3 +144,57 @@ def test_server_admission_policy(gpu, policy, order):
 def test_server_rejects_unknown_policy(gpu):
     with pytest.raises(gpu.DrtsError):
         gpu.Server(policy=7)
+
+
+def test_server_results_match_oracle(gpu, oracle_mod):
+    """Every source of every served request stays within relative L1 1e-4 of
+    the FP64 oracle (Eq. 26 stepped on the same problem, Eq. 27 detectors and
+    the energy ledger), with the requests overlapping on the device: three
+    resident slots, requests submitted while others run, the tick graph
+    fanned over three streams, and the batched step for the requests with
+    several sources."""
+    reqs = [I.served_request(17, i, sides=(8, 12, 16), steps=(100, 300), max_sources=6)
+            for i in range(6)]
+    assert any(len(r.sources) > 1 for r in reqs)
+    with gpu.Server(max_resident=3, steps_per_tick=25, n_streams=3, keep_state=True) as srv:
+        ids = [srv.submit(reqs[0].problem, reqs[0].sources, reqs[0].n_steps)]
+        srv.tick()
+        ids += [srv.submit(r.problem, r.sources, r.n_steps) for r in reqs[1:]]
+        for _ in range(1000):
+            srv.tick()
+            st = srv.stats()
+            if st["completed"] + st["failed"] == len(ids):
+                break
+        assert srv.stats()["completed"] == len(ids)
+        worst = 0.0
+        for rid, req in zip(ids, reqs):
+            prob = req.problem
+            csr = oracle_mod.assemble(prob)
+            colinfo = oracle_mod.column_info(prob)
+            prof = req.sources[0]
+            for r, s in enumerate(req.sources):
+                xo, deto, ledo = oracle_mod.run(prob, csr, req.n_steps,
+                                                (s.state, s.weight, prof.t0, prof.profile),
+                                                colinfo=colinfo)
+                x = srv.result_state(rid, r, n_states=prob.n_states)
+                det, led = srv.result(rid, r)
+                ex = rel_l1(x, xo)
+                ed = rel_l1(det, deto[:, :det.shape[1]])
+                worst = max(worst, ex, ed)
+                assert ex <= 1e-4, (rid, r, ex)
+                assert ed <= 1e-4, (rid, r, ed)
+                assert np.allclose(led, ledo, rtol=1e-4, atol=1e-12), (rid, r, led, ledo)
+        with pytest.raises(gpu.DrtsError):
+            srv.result_state(ids[0], len(reqs[0].sources), n_states=reqs[0].problem.n_states)
+    print(f"served vs oracle: worst relative L1 {worst:.2e}")
+
+
+def test_server_result_state_needs_keep_state(gpu):
+    req = small_stream(1, seed=9)[0]
+    with gpu.Server(max_resident=1, steps_per_tick=50, n_streams=1) as srv:
+        rid = srv.submit(req.problem, req.sources, req.n_steps)
+        while srv.stats()["completed"] < 1:
+            srv.tick()
+        with pytest.raises(gpu.DrtsError) as e:
+            srv.result_state(rid, 0, n_states=req.problem.n_states)
+        assert e.value.status == gpu.ESTATE
