@@ -26,9 +26,8 @@ struct drts_ctx {
     int64_t V = 0, n_states = 0;
     int K = 0, R = 1, n_patch = 0;
     int64_t rhs_stride = 0;              // elements between right-hand sides of a state buffer
-    bool tc = false;                     // tensor-core batched step, state X[v][r][32]
-    int tc_rp = 0;                       // its right-hand-side stride (multiple of 8)
-    void *tc_blocks = nullptr;
+    bool tc = false;                     // tensor-core batched step (8 KB bf16 state tile per voxel)
+    TcPlan tcp{};                        // its union-dense A
     uint8_t *d_src_voxel = nullptr;      // [V] voxels that receive a source term
     int64_t t = 0;
     std::string err;
@@ -281,7 +280,7 @@ StepArgs make_args(drts_ctx *c)
     a.V = c->V;
     a.R = c->R;
     a.rhs_stride = c->rhs_stride;
-    a.tc_blocks = static_cast<const uint4 *>(c->tc_blocks);
+    a.tcp = c->tcp;
     a.src_voxel = c->d_src_voxel;
     a.x = c->x; a.y = c->y;
     a.med = c->T.med;
@@ -304,7 +303,7 @@ StepArgs make_args(drts_ctx *c)
     a.err = c->d_err;
     a.spin_limit = c->spin_limit;
     a.fault_skip_chunk = c->fault_skip_chunk;
-    a.tc_rp = c->tc ? c->tc_rp : 0;
+    a.tcx = c->tc ? 1 : 0;
     a.pd.n_det = c->n_pdet;
     a.pd.off = c->d_pdet_off;
     a.pd.state = c->d_pdet_state;
@@ -327,7 +326,7 @@ cudaError_t launch_any_step(drts_ctx *c, const StepArgs &a)
     cudaError_t e = launch_point_detectors(a, c->stream);
     if (e != cudaSuccess) return e;
     if (c->R == 1) e = launch_step(a, c->variant, c->blocks, c->threads, c->stream);
-    else if (c->tc) e = launch_tc_step(a, c->tc_rp, c->rhs_tile, c->blocks, c->threads, true, c->stream);
+    else if (c->tc) e = launch_tc_step(a, true, c->stream);
     else e = launch_batched_step(a, c->R, c->rhs_tile, c->variant, c->blocks, c->threads, true, c->stream);
     if (e != cudaSuccess) return e;
     return launch_bulk_sources(a, c->stream);
@@ -341,7 +340,7 @@ int fit_blocks(drts_ctx *c, int threads, int variant, int rhs_tile)
     if (c->tc) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        return sms * tc_blocks_per_sm(c->tc_rp, threads, rhs_tile);
+        return sms * tc_blocks_per_sm();
     }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -359,6 +358,56 @@ cudaStream_t ctx_swap_stream(drts_ctx *c, cudaStream_t s)
     return old;
 }
 }  // namespace drts
+
+namespace {
+
+// Tensor-core batched step: the union of each block role's (n, m) positions
+// over all voxels (from the assembled sliced matrix), and A stored per voxel
+// and role at those positions as three bf16 terms (drts_tensor.cu).
+drts_status setup_tensor_core(drts_ctx *c)
+{
+    constexpr int kFlags = kOffs * kDirs * kDirs;
+    uint8_t *dflags = nullptr;
+    cudaError_t e = dalloc(c, &dflags, kFlags);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dflags, 0, kFlags, c->stream);
+    if (e == cudaSuccess) e = launch_tc_flags(c->A, c->V, dflags, c->stream);
+    std::vector<uint8_t> flags(kFlags, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flags.data(), dflags, kFlags, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core union pattern");
+    drelease(c, dflags);
+    std::vector<uint16_t> pos;
+    std::vector<int16_t> pidx(kFlags, -1);
+    TcPlan &P = c->tcp;
+    for (int d = 0; d < kOffs; ++d) {
+        P.role_off[d] = int(pos.size());
+        for (int m = 0; m < kDirs; ++m)
+            for (int n = 0; n < kDirs; ++n)
+                if (flags[size_t(d) * kDirs * kDirs + n * kDirs + m]) {
+                    pidx[size_t(d) * kDirs * kDirs + n * kDirs + m] = int16_t(pos.size());
+                    pos.push_back(uint16_t((n << 8) | m));
+                }
+    }
+    P.role_off[kOffs] = int(pos.size());
+    P.U = int(pos.size());
+    uint16_t *dpos = nullptr, *dAu = nullptr;
+    int16_t *dpidx = nullptr;
+    const size_t au_bytes = size_t(c->V) * 3 * size_t(P.U) * sizeof(uint16_t);
+    if ((e = upload(c, &dpos, pos)) != cudaSuccess || (e = upload(c, &dpidx, pidx)) != cudaSuccess ||
+        (e = dalloc(c, &dAu, au_bytes)) != cudaSuccess)
+        return cuda_fail(c, e, "tensor-core matrix allocation");
+    if ((e = cudaMemsetAsync(dAu, 0, au_bytes, c->stream)) != cudaSuccess ||
+        (e = launch_tc_convert(c->A, c->V, dpidx, P.U, dAu, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "tensor-core matrix conversion");
+    drelease(c, dpidx);
+    P.pos = dpos;
+    P.Au = dAu;
+    if (tc_blocks_per_sm() < 1) return fail(c, DRTS_ECUDA, "tensor-core step kernel does not fit on an SM");
+    return DRTS_OK;
+}
+
+}  // namespace
 
 void drts::set_global_error(const std::string &msg)
 {
@@ -388,7 +437,6 @@ try {
     c->R = prob->n_rhs;
     c->rhs_stride = c->n_states + 64;     // the tail keeps padding lanes in bounds
     c->tc = prob->n_rhs > 1 && prob->batched_kernel == DRTS_BATCHED_TENSOR;
-    c->tc_rp = c->tc ? tc_rhs_stride(c->R) : 0;
     if (prob->det_face != DRTS_FACE_NONE) c->n_patch = prob->det_nu * prob->det_nv;
 
     // a host allocation that throws below must not leak the partial context
@@ -505,19 +553,11 @@ try {
         c->special_permille = int(special * 1000 / c->V);
     }
     // state, ledger, detector history, sources
-    c->x_elems = c->tc ? c->V * c->tc_rp * 32 + 64
+    c->x_elems = c->tc ? int64_t(tcx_state_bytes(c->V) / 4)
                        : (c->R == 1 ? c->rhs_stride : c->rhs_stride * ((c->R + 3) / 4) * 4);
     if (c->tc) {
-        const size_t bb = size_t(c->V) * 27 * 6144;
-        if ((e = dalloc(c, &c->tc_blocks, bb)) != cudaSuccess) {
-            cuda_fail(c, e, "tensor-core block allocation");
-            return bail(DRTS_ENOMEM);
-        }
-        if ((e = cudaMemsetAsync(c->tc_blocks, 0, bb, c->stream)) != cudaSuccess ||
-            (e = launch_block_fill(T, c->tc_blocks, c->stream)) != cudaSuccess) {
-            cuda_fail(c, e, "tensor-core block fill");
-            return bail(DRTS_ECUDA);
-        }
+        st = setup_tensor_core(c);
+        if (st != DRTS_OK) return bail(st);
     }
     const size_t sb = size_t(c->x_elems) * state_elem_bytes(prob->precision);
     if ((e = dalloc(c, &c->x, sb)) != cudaSuccess || (e = dalloc(c, &c->y, sb)) != cudaSuccess ||
@@ -556,7 +596,7 @@ try {
         // this per problem)
         c->rhs_tile = c->R <= 4 ? 4 : 8;
     }
-    if (c->tc) c->rhs_tile = std::min(32, c->tc_rp);
+    if (c->tc) c->rhs_tile = kMaxRhs;      // all right-hand sides in one pass
     c->blocks = fit_blocks(c, c->threads, c->variant, c->rhs_tile);
     if (c->blocks < 1) {
         fail(c, DRTS_ECUDA, "step kernel does not fit on an SM");
@@ -688,7 +728,7 @@ try {
         double *tmp = nullptr;
         e = cudaMallocAsync(&tmp, sizeof(double), c->stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(tmp, 0, sizeof(double), c->stream);
-        if (e == cudaSuccess) e = (c->tc ? launch_tc_sum(c->x, c->V, c->tc_rp, rhs, tmp, c->stream)
+        if (e == cudaSuccess) e = (c->tc ? launch_tc_sum(c->x, c->V, rhs, tmp, c->stream)
                                       : launch_ledger_sum(rhs_view(c, c->x, rhs).base, c->prob.precision, c->n_states,
                                                           rhs_view(c, c->x, rhs).stride, 0, tmp, c->stream));
         if (e == cudaSuccess) e = cudaMemcpyAsync(ledger_out, tmp, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
@@ -709,7 +749,7 @@ try {
     double *tmp = nullptr;
     cudaError_t e = cudaMallocAsync(&tmp, sizeof(double) * c->n_states, c->stream);
     if (e == cudaSuccess)
-        e = c->tc ? launch_tc_to_canonical(c->x, c->V, c->tc_rp, rhs, tmp, c->stream)
+        e = c->tc ? launch_tc_to_canonical(c->x, c->V, rhs, tmp, c->stream)
                   : launch_to_canonical(rhs_view(c, c->x, rhs).base, c->prob.precision, c->V,
                                         rhs_view(c, c->x, rhs).stride, 0, tmp, c->stream);
     if (e == cudaSuccess)
@@ -730,7 +770,7 @@ try {
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(tmp, host_in, sizeof(double) * c->n_states, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
-        e = c->tc ? launch_tc_from_canonical(tmp, c->V, c->tc_rp, rhs, c->x, c->stream)
+        e = c->tc ? launch_tc_from_canonical(tmp, c->V, rhs, c->x, c->stream)
                   : launch_from_canonical(tmp, c->prob.precision, c->V, rhs_view(c, c->x, rhs).stride, 0,
                                           rhs_view(c, c->x, rhs).base, c->stream);
     if (tmp) cudaFreeAsync(tmp, c->stream);
@@ -864,9 +904,7 @@ try {
     if (c->R > 1 && rhs_tile != 0) {
         if (rhs_tile != 4 && rhs_tile != 8 && rhs_tile != 16 && rhs_tile != 32)
             return fail(c, DRTS_EINVAL, "rhs_tile must be 4, 8, 16 or 32");
-        if (c->tc && (rhs_tile < 8 || rhs_tile > c->tc_rp))
-            return fail(c, DRTS_EINVAL, "tensor-core rhs_tile must be 8..stride");
-        tile = rhs_tile;
+        tile = c->tc ? c->rhs_tile : rhs_tile;     // the tensor-core form takes all rhs at once
     }
     const int threads = threads_per_block ? threads_per_block : 256;
     const int var = variant < 0 ? c->variant : variant;
@@ -962,7 +1000,7 @@ try {
         for (int tile : {4, 8, 16, 32})
         for (int threads : {256, 128}) {
             if (c->R == 1 && tile != 4) continue;             // tile only matters when batched
-            if (c->tc && (tile < 8 || tile > c->tc_rp)) continue;
+            if (c->tc && (tile != 4 || threads != 256)) continue;      // one fixed shape
             if (c->R > 1 && tile > 4 && tile / 2 >= c->R) continue;   // tile far wider than R
             if (c->R > 1 && !c->tc && var == 2 && (tile != 4 || threads != 256)) continue;   // fixed shape
             const int fit = fit_blocks(c, threads, var, tile);
@@ -977,7 +1015,7 @@ try {
                 const int blocks = bps * sms;
                 auto run = [&]() {
                     if (c->R == 1) return launch_step(a, var, blocks, threads, c->stream);
-                    if (c->tc) return launch_tc_step(a, c->tc_rp, tile, blocks, threads, false, c->stream);
+                    if (c->tc) return launch_tc_step(a, false, c->stream);
                     return launch_batched_step(a, c->R, tile, var, blocks, threads, false, c->stream);
                 };
                 e = run();          // warm-up
@@ -1333,6 +1371,8 @@ try {
     if (n_entries < 0 || n_entries > kMaxSrc) return fail(c, DRTS_EINVAL, "n_entries must be 0..64");
     if (n_sub < 1 || n_sub > 64) return fail(c, DRTS_EINVAL, "n_sub must be 1..64");
     if (n_t < 0 || (n_t > 0 && n_entries > 0 && !profile)) return fail(c, DRTS_EINVAL, "bad profile");
+    if (c->tc && n_entries > 0)
+        return fail(c, DRTS_EUNSUPPORTED, "sub-step sources are not available with the tensor-core batched step");
     if (n_entries > 0 && (!state_idx || !weight)) return fail(c, DRTS_EINVAL, "NULL source arrays");
     drts_ctx::SubstepSource ss;
     const int ns = n_sub;

@@ -360,45 +360,6 @@ __global__ void fill_kernel(DevTables T, SlicedMatrix A)
     }
 }
 
-// Block-dense copy of A for the tensor-core batched step: for row voxel j
-// and neighbour offset d, the 26x26 block B[m][n] = A[(j,m), (j+d,n)] padded
-// to 32x32.  Each value (the FP32 value the sliced format stores) is split
-// exactly into three bf16 terms t0 + t1 + t2 (8 + 8 + 8 significant bits),
-// and the block is stored as twelve mma.m16n8k16 A fragments (m-tile,
-// k-tile, term), each 32 lanes x 16 bytes in register order (6 KB).
-struct BlockEmit {
-    uint16_t *blk;     // voxel j's blocks
-    int m;
-    __device__ void operator()(int code, double v)
-    {
-        const int d = code / kDirs, n = code % kDirs;
-        const int mt = m >> 4, rr = m & 15, kt = n >> 4, cc = n & 15;
-        const int lane = (rr & 7) * 4 + ((cc & 7) >> 1);
-        const int reg = (rr >> 3) + ((cc >> 3) << 1);
-        float rest = __double2float_rn(v);
-        for (int term = 0; term < 3; ++term) {
-            const __nv_bfloat16 b = __float2bfloat16_rn(rest);
-            rest = rest - __bfloat162float(b);             // exact in FP32
-            const int f = (mt * 2 + kt) * 3 + term;
-            const size_t half = ((size_t(d) * 12 + f) * 32 + lane) * 8 + reg * 2 + (cc & 1);
-            blk[half] = __bfloat16_as_ushort(b);
-        }
-    }
-};
-
-__global__ void block_fill_kernel(DevTables T, uint16_t *blocks)
-{
-    const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g >= T.V * kDirs) return;
-    const int64_t v = g / kDirs;
-    const int m = int(g % kDirs);
-    BlockEmit be;
-    be.blk = blocks + size_t(v) * 27 * 6144 / 2;
-    be.m = m;
-    const int x = int(v % T.nx), y = int(v / T.nx % T.ny), z = int(v / (int64_t(T.nx) * T.ny));
-    enumerate_row(T, x, y, z, m, be);
-}
-
 // Column `state` = (voxel i, direction n) of the matrix built from Tf: thread
 // g = d*26 + m evaluates the mass that (i, n) sends to (i + d, m), with the
 // same folding as the rows (plain rows need none: there folded_contribution
@@ -579,15 +540,6 @@ cudaError_t launch_source_column(const DevTables &Tf, int64_t state, double *out
     cudaError_t e = upload_dirs();
     if (e != cudaSuccess) return e;
     source_column_kernel<<<(kOffs * kDirs + 127) / 128, 128, 0, s>>>(Tf, state, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_block_fill(const DevTables &T, void *blocks, cudaStream_t s)
-{
-    cudaError_t e = upload_dirs();
-    if (e != cudaSuccess) return e;
-    const int th = 128;
-    block_fill_kernel<<<unsigned((T.V * kDirs + th - 1) / th), th, 0, s>>>(T, static_cast<uint16_t *>(blocks));
     return cudaGetLastError();
 }
 

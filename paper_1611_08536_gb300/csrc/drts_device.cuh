@@ -103,6 +103,15 @@ struct BulkSources {
     const double *prof_vals;
 };
 
+// Tensor-core batched step: A stored union-dense (per voxel, per block role
+// d, the values at the role's fixed (n, m) positions) as three bf16 terms.
+struct TcPlan {
+    int U;                      // union positions per voxel over all 27 roles
+    int role_off[28];           // role d owns positions [role_off[d], role_off[d+1])
+    const uint16_t *pos;        // [U] (n << 8) | m
+    const uint16_t *Au;         // [V][3][U] bf16 bits of a0, a1, a2
+};
+
 struct StepArgs {
     SlicedMatrix A;
     int nx, ny, nz;
@@ -125,11 +134,11 @@ struct StepArgs {
     const double *step_scale;  // [R] host-supplied source factors of this step, or null
     int rhs_tile;
     int *err;                  // set to 1 when a bounded device wait gives up
-    const uint4 *tc_blocks;    // tensor-core batched step: fragment blocks of A
+    TcPlan tcp;                // tensor-core batched step: union-dense A
     const uint8_t *src_voxel;  // [V] 1 where some source entry targets the voxel
     uint32_t spin_limit;       // polls before a device wait gives up
     int64_t fault_skip_chunk;  // tests only: chunk warp 0 never copies (-1 none)
-    int tc_rp;                 // > 0: tensor-core state layout X[(v*tc_rp + r)*32 + d]
+    int tcx;                   // 1: tensor-core state layout (8 KB bf16 (x0, x1) tile per voxel)
     PointDetectors pd;         // point detectors read from x (n_det = 0: none)
     BulkSources bulk;          // sub-step sources added to y (n_groups = 0: none)
 };
@@ -175,15 +184,18 @@ int batched_blocks_per_sm(int precision, int rhs_tile, int threads, int order);
 cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int order, int blocks, int threads,
                                 bool functionals, cudaStream_t s);
 
-// tensor-core batched step (drts_tensor.cu); state layout X[v][r][32]
-int tc_rhs_stride(int n_rhs);
-int tc_blocks_per_sm(int Rp, int threads, int tile);
-cudaError_t launch_tc_step(const StepArgs &a, int Rp, int tile, int blocks, int threads, bool functionals,
-                           cudaStream_t s);
-cudaError_t launch_tc_to_canonical(const void *x, int64_t V, int Rp, int r, double *out, cudaStream_t s);
-cudaError_t launch_tc_from_canonical(const double *in, int64_t V, int Rp, int r, void *x, cudaStream_t s);
-cudaError_t launch_tc_sum(const void *x, int64_t V, int Rp, int r, double *out, cudaStream_t s);
-cudaError_t launch_block_fill(const DevTables &T, void *blocks, cudaStream_t s);
+// tensor-core batched step (drts_tensor.cu): state tile per voxel of 64
+// right-hand sides of x0 and x1 (bf16, 8 KB); flags / convert build the
+// union-dense A from the sliced FP32 matrix
+size_t tcx_state_bytes(int64_t V);
+int tc_blocks_per_sm();
+cudaError_t launch_tc_flags(const SlicedMatrix &A, int64_t V, uint8_t *flags, cudaStream_t s);
+cudaError_t launch_tc_convert(const SlicedMatrix &A, int64_t V, const int16_t *pidx, int U, uint16_t *Au,
+                              cudaStream_t s);
+cudaError_t launch_tc_step(const StepArgs &a, bool functionals, cudaStream_t s);
+cudaError_t launch_tc_to_canonical(const void *x, int64_t V, int r, double *out, cudaStream_t s);
+cudaError_t launch_tc_from_canonical(const double *in, int64_t V, int r, void *x, cudaStream_t s);
+cudaError_t launch_tc_sum(const void *x, int64_t V, int r, double *out, cudaStream_t s);
 
 // Eq. 26/27 extensions (drts_functionals.cu): point detectors of x(t) (one
 // CTA per detector and rhs), sub-step sources added to y(t+1), and the

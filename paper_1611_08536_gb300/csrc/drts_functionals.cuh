@@ -2,17 +2,20 @@
 // kernels (drts_functionals.cu) and the persistent step kernel.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include "drts_device.cuh"
 
 namespace drts {
 namespace {
 
 // element offset of canonical state s of right-hand side r in a state buffer
+// (for the tensor-core layout: the bf16 element of x0; x1 is 512 further)
 __device__ __forceinline__ int64_t state_offset(const StepArgs &a, int64_t s, int r)
 {
     const int64_t v = s / kDirs;
     const int d = int(s - v * kDirs);
-    if (a.tc_rp > 0) return (v * a.tc_rp + r) * 32 + d;
+    if (a.tcx) return v * 4096 + (((d >> 3) * 16 + (r >> 3)) * 64) + (r & 7) * 8 + (d & 7);
     if (a.R == 1) return int64_t(d) * a.V + v;
     // batched: groups of four right-hand sides, the four values side by side
     return (int64_t(r >> 2) * a.rhs_stride + int64_t(d) * a.V + v) * 4 + (r & 3);
@@ -31,7 +34,13 @@ __device__ __forceinline__ void point_detector_block(const StepArgs &a, const XT
     double acc = 0.0;
     for (int64_t e = P.off[d] + threadIdx.x; e < e1; e += blockDim.x) {
         const int64_t o = state_offset(a, P.state[e], r);
-        const double xv = double(COHERENT ? __ldcg(x + o) : x[o]);
+        double xv;
+        if (a.tcx) {
+            const __nv_bfloat16 *xb = reinterpret_cast<const __nv_bfloat16 *>(x);
+            xv = double(__bfloat162float(xb[o])) + double(__bfloat162float(xb[o + 512]));
+        } else {
+            xv = double(COHERENT ? __ldcg(x + o) : x[o]);
+        }
         acc += P.w[e] * xv;
     }
     for (int k = 16; k > 0; k >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, k);

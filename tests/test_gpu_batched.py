@@ -133,3 +133,29 @@ def test_tensor_core_batched_same_alone_and_in_mix(gpu):
         x1, d1, _ = run_batched(gpu, p1, [srcs[r], srcs[(r + 1) % 6]], 25)
         assert rel_l1(xs[r], x1[0]) < 1e-6
         assert rel_l1(dets[r], d1[0]) < 1e-6
+
+
+def test_tensor_core_ragged_grid_and_rejections(gpu, oracle_mod):
+    """Tensor-core batched step on a ragged 5 x 7 x 3 grid with mirror and
+    Fresnel edges mixed through two media (every line of the sweep has
+    missing neighbour lines), 3 right-hand sides; sub-step sources are
+    rejected for this form."""
+    mov = np.zeros((3, 7, 5), np.uint8)
+    mov[:, 4:, :] = 1
+    prob = I.Problem((5, 7, 3), 0.1, [(8.0, 0.05, 0.85, 1.4), (12.0, 0.02, 0.9, 1.4)], mov, 1.0,
+                     I.FRESNEL, I.FP32, 3, I.FACE_PZ, 2, 3, "ragged_tc")
+    prob.batched_kernel = gpu.BATCHED_TENSOR
+    srcs = [I.Source(np.array([prob.state(1 + r, 2 + r, 0, I.direction_index(0, 0, 1))], np.int64),
+                     np.ones(1), 0, np.ones(1)) for r in range(3)]
+    steps = 60
+    csr = oracle_mod.assemble(prob)
+    xs, dets, leds = run_batched(gpu, prob, srcs, steps)
+    for r in range(3):
+        xo, deto, ledo = oracle_mod.run(prob, csr, steps, srcs[r].as_tuple())
+        assert rel_l1(xs[r], xo) < 1e-4, r
+        assert rel_l1(dets[r], deto) < 1e-4, r
+        assert np.allclose(leds[r], ledo, rtol=1e-4, atol=1e-12), (r, leds[r], ledo)
+    with gpu.Context(prob, max_steps=4) as ctx:
+        with pytest.raises(gpu.DrtsError) as e:
+            ctx.inject_source_substeps(0, [0], [1.0], 0, np.ones((1, 2)))
+        assert e.value.status == gpu.EUNSUPPORTED

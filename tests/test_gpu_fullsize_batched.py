@@ -14,13 +14,15 @@ PLANES = (0, 47, 95)
 RHS = (0, 31, 63)
 
 
-def test_batched_fullsize_one_step_sampled(oracle_mod):
+@pytest.mark.parametrize("kernel", [0, 1], ids=["cuda_cores", "tensor_cores"])
+def test_batched_fullsize_one_step_sampled(oracle_mod, kernel):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     from paper_1611_08536_gb300 import build, drts
     build.build()
     prob, _ = I.inclusions(96, n_rhs=64, precision=I.FP32)
+    prob.batched_kernel = kernel
     rng = np.random.default_rng(96)
     xs = {r: rng.random(prob.n_states) for r in RHS}
     with drts.Context(prob, max_steps=4) as ctx:
@@ -36,4 +38,7 @@ def test_batched_fullsize_one_step_sampled(oracle_mod):
         for r in RHS:
             yo = oracle_mod.spmv(c, xs[r])
             yg = ys[r][c.row0:c.row0 + c.n_rows]
-            assert np.abs(yg - yo).sum() / np.abs(yo).sum() < 1e-6, (z, r)
+            # tensor cores: the state is held as two block-floating bf16 terms
+            # (x0 on a grid shared by a voxel's directions, x1 its residual)
+            tol = 1e-6 if kernel == 0 else 2e-5
+            assert np.abs(yg - yo).sum() / np.abs(yo).sum() < tol, (z, r)

@@ -6,7 +6,9 @@ over a run, so each tier is checked at the length it is used for:
   * FP32 plain step, three layers at 48^3, 1000 steps: relative L1 <= 1e-5;
   * FP16-rowscale plain step, 24^3 inclusions, 1500 steps: <= 1e-4;
   * batched FP32 and batched FP16-rowscale, 24^3 inclusions x 8
-    right-hand sides, 1500 steps: <= 1e-4 for every checked right-hand side.
+    right-hand sides, 1500 steps: <= 1e-4 for every checked right-hand side;
+  * the tensor-core batched step (block-floating bf16 terms, tcgen05), the
+    same problem and length: <= 1e-4.
 Each test prints the measured error.
 """
 import numpy as np
@@ -71,9 +73,11 @@ def test_fp16_plain_inclusions_1500_steps(gpu, oracle_mod):
     assert np.allclose(led, ledo, rtol=1e-4, atol=1e-12)
 
 
-@pytest.mark.parametrize("precision", [I.FP32, I.FP16_ROWSCALE], ids=["fp32", "fp16"])
-def test_batched_inclusions_1500_steps(gpu, oracle_mod, precision):
+@pytest.mark.parametrize("precision,kernel", [(I.FP32, 0), (I.FP16_ROWSCALE, 0), (I.FP32, 1)],
+                         ids=["fp32", "fp16", "tensor"])
+def test_batched_inclusions_1500_steps(gpu, oracle_mod, precision, kernel):
     prob, srcs = I.inclusions(24, n_rhs=8, seed=3, precision=precision)
+    prob.batched_kernel = kernel
     steps = 1500
     csr = oracle_mod.assemble(prob)
     ci = oracle_mod.column_info(prob)
@@ -83,7 +87,7 @@ def test_batched_inclusions_1500_steps(gpu, oracle_mod, precision):
         ctx.step_n(steps)
         xs = [ctx.read_state(r) for r in range(8)]
         dets = [ctx.read_detectors(r) for r in range(8)]
-    name = "FP32" if precision == I.FP32 else "FP16-rowscale"
+    name = ("FP32" if precision == I.FP32 else "FP16-rowscale") + (" tensor-core" if kernel else "")
     for r in (0, 3, 5):
         xo, deto, ledo = oracle_mod.run(prob, csr, steps, srcs[r].as_tuple(), colinfo=ci)
         e = rel_l1(xs[r], xo)
