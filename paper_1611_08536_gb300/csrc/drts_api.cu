@@ -376,33 +376,49 @@ drts_status setup_tensor_core(drts_ctx *c)
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core union pattern");
     drelease(c, dflags);
+    // positions of each role in (m, n) order, padded to a multiple of 8 (16-byte
+    // arrays); a role's chunk is three fp16 arrays plus 32 exponent bytes
     std::vector<uint16_t> pos;
     std::vector<int16_t> pidx(kFlags, -1);
     TcPlan &P = c->tcp;
+    int64_t off = 0;
     for (int d = 0; d < kOffs; ++d) {
         P.role_off[d] = int(pos.size());
+        P.chunk_off[d] = int(off);
+        int np = 0;
         for (int m = 0; m < kDirs; ++m)
             for (int n = 0; n < kDirs; ++n)
                 if (flags[size_t(d) * kDirs * kDirs + n * kDirs + m]) {
-                    pidx[size_t(d) * kDirs * kDirs + n * kDirs + m] = int16_t(pos.size());
+                    pidx[size_t(d) * kDirs * kDirs + n * kDirs + m] = int16_t(np++);
                     pos.push_back(uint16_t((n << 8) | m));
                 }
+        while (np % 8) {
+            pos.push_back(uint16_t(31 << 8));         // padding: direction slot 31 of the tile is zero
+            ++np;
+        }
+        off += 6 * int64_t(np) + 32;
     }
     P.role_off[kOffs] = int(pos.size());
-    P.U = int(pos.size());
-    uint16_t *dpos = nullptr, *dAu = nullptr;
+    P.chunk_off[kOffs] = int(off);
+    P.voxel_bytes = off;
+    for (int L = 0; L < kOffs / 3; ++L)
+        if (P.chunk_off[3 * L + 3] - P.chunk_off[3 * L] > tc_stage_limit())
+            return fail(c, DRTS_EUNSUPPORTED, "tensor-core step: the matrix's block pattern needs more staging "
+                                              "than one tile slot holds");
+    uint16_t *dpos = nullptr;
     int16_t *dpidx = nullptr;
-    const size_t au_bytes = size_t(c->V) * 3 * size_t(P.U) * sizeof(uint16_t);
+    void *dAu = nullptr;
+    const size_t au_bytes = size_t(c->V) * size_t(P.voxel_bytes);
     if ((e = upload(c, &dpos, pos)) != cudaSuccess || (e = upload(c, &dpidx, pidx)) != cudaSuccess ||
         (e = dalloc(c, &dAu, au_bytes)) != cudaSuccess)
         return cuda_fail(c, e, "tensor-core matrix allocation");
+    P.pos = dpos;
+    P.Au = dAu;
     if ((e = cudaMemsetAsync(dAu, 0, au_bytes, c->stream)) != cudaSuccess ||
-        (e = launch_tc_convert(c->A, c->V, dpidx, P.U, dAu, c->stream)) != cudaSuccess ||
+        (e = launch_tc_convert(c->A, c->V, dpidx, P, dAu, c->stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "tensor-core matrix conversion");
     drelease(c, dpidx);
-    P.pos = dpos;
-    P.Au = dAu;
     if (tc_blocks_per_sm() < 1) return fail(c, DRTS_ECUDA, "tensor-core step kernel does not fit on an SM");
     return DRTS_OK;
 }

@@ -104,12 +104,16 @@ struct BulkSources {
 };
 
 // Tensor-core batched step: A stored union-dense (per voxel, per block role
-// d, the values at the role's fixed (n, m) positions) as three bf16 terms.
+// d, the values at the role's fixed (n, m) positions).  Voxel j's data is
+// voxel_bytes long; role d's chunk at chunk_off[d] holds three fp16 arrays
+// (a0, a1, a2) of the role's padded position count followed by 32 bytes of
+// row exponents (Ea + 160 per direction m).
 struct TcPlan {
-    int U;                      // union positions per voxel over all 27 roles
-    int role_off[28];           // role d owns positions [role_off[d], role_off[d+1])
-    const uint16_t *pos;        // [U] (n << 8) | m
-    const uint16_t *Au;         // [V][3][U] bf16 bits of a0, a1, a2
+    int role_off[28];           // role d owns positions [role_off[d], role_off[d+1]) (multiples of 8)
+    int chunk_off[28];          // byte offset of role d's chunk within a voxel
+    int64_t voxel_bytes;        // bytes per voxel (multiple of 16)
+    const uint16_t *pos;        // [role_off[27]] (n << 8) | m; padding entries (31 << 8)
+    const void *Au;             // [V][voxel_bytes]
 };
 
 struct StepArgs {
@@ -138,7 +142,7 @@ struct StepArgs {
     const uint8_t *src_voxel;  // [V] 1 where some source entry targets the voxel
     uint32_t spin_limit;       // polls before a device wait gives up
     int64_t fault_skip_chunk;  // tests only: chunk warp 0 never copies (-1 none)
-    int tcx;                   // 1: tensor-core state layout (8 KB bf16 (x0, x1) tile per voxel)
+    int tcx;                   // 1: tensor-core state layout (8 KB fp16 (x0, x1, Ex) tile per voxel)
     PointDetectors pd;         // point detectors read from x (n_det = 0: none)
     BulkSources bulk;          // sub-step sources added to y (n_groups = 0: none)
 };
@@ -188,10 +192,11 @@ cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int 
 // right-hand sides of x0 and x1 (bf16, 8 KB); flags / convert build the
 // union-dense A from the sliced FP32 matrix
 size_t tcx_state_bytes(int64_t V);
+int tc_stage_limit();
 int tc_blocks_per_sm();
 cudaError_t launch_tc_flags(const SlicedMatrix &A, int64_t V, uint8_t *flags, cudaStream_t s);
-cudaError_t launch_tc_convert(const SlicedMatrix &A, int64_t V, const int16_t *pidx, int U, uint16_t *Au,
-                              cudaStream_t s);
+cudaError_t launch_tc_convert(const SlicedMatrix &A, int64_t V, const int16_t *pidx, const TcPlan &P,
+                              void *Au, cudaStream_t s);
 cudaError_t launch_tc_step(const StepArgs &a, bool functionals, cudaStream_t s);
 cudaError_t launch_tc_to_canonical(const void *x, int64_t V, int r, double *out, cudaStream_t s);
 cudaError_t launch_tc_from_canonical(const double *in, int64_t V, int r, void *x, cudaStream_t s);

@@ -2,7 +2,7 @@
 // kernels (drts_functionals.cu) and the persistent step kernel.
 #pragma once
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "drts_device.cuh"
 
@@ -10,7 +10,7 @@ namespace drts {
 namespace {
 
 // element offset of canonical state s of right-hand side r in a state buffer
-// (for the tensor-core layout: the bf16 element of x0; x1 is 512 further)
+// (for the tensor-core layout: the fp16 element of x0; x1 is 512 further)
 __device__ __forceinline__ int64_t state_offset(const StepArgs &a, int64_t s, int r)
 {
     const int64_t v = s / kDirs;
@@ -36,8 +36,11 @@ __device__ __forceinline__ void point_detector_block(const StepArgs &a, const XT
         const int64_t o = state_offset(a, P.state[e], r);
         double xv;
         if (a.tcx) {
-            const __nv_bfloat16 *xb = reinterpret_cast<const __nv_bfloat16 *>(x);
-            xv = double(__bfloat162float(xb[o])) + double(__bfloat162float(xb[o + 512]));
+            // x0 + x1 scaled by 2^Ex, Ex stored at direction 26 of the x0 row
+            const __half *xh = reinterpret_cast<const __half *>(x);
+            const int64_t v = P.state[e] / kDirs;
+            const int ex = int(__half2float(xh[v * 4096 + ((3 * 16 + (r >> 3)) * 64) + (r & 7) * 8 + 2]));
+            xv = ldexp(double(__half2float(xh[o])) + double(__half2float(xh[o + 512])), ex);
         } else {
             xv = double(COHERENT ? __ldcg(x + o) : x[o]);
         }

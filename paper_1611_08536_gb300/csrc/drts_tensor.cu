@@ -9,41 +9,41 @@
 // that edge folding adds), so A is stored "union-dense": for every voxel and
 // role the values at U_d, zeros where that voxel has none.
 //
-// Number formats (rounding the dominant product only on exact grids):
+// Number formats (the dominant product is made exact):
 //   * The tensor cores truncate FP32 accumulation unless every product of an
-//     MMA lies on one grid; then the sum is exact.  So the dominant product is
-//     made exact: a0 = A rounded to 8 bits on a grid shared by a block row
-//     (quantum 2^(E-7), E = exponent of the row's largest value in the block)
-//     and x0 = X rounded to 8 bits on a grid shared by the 26 directions of one
-//     voxel and right-hand side; the products of one K = 32 block are integers
-//     times one quantum below 2^21, exact in FP32.
-//   * a1 = bf16(A - a0), a2 = bf16(A - a0 - a1) (A to ~25 bits: the stored FP32
-//     value exactly in all but the smallest entries of a row) and
-//     x1 = bf16(X - x0); the products with a1, a2 and x1 are 2^-7 of the result
-//     or smaller, so their truncation is below 2^-31 relative.
-//   * The state lives as the pair (x0, x1); every step writes it from the FP32
-//     result.  Each tile's products are drained from tensor memory into FP32
-//     sums on the CUDA cores (27 partials per output, plain round-to-nearest).
-//   A CPU emulation of these formats on the FP64 oracle's matrix stays within
-//   1.1e-5 relative L1 over 1500 steps (24^3 inclusions), below the 1e-4 bound.
+//     MMA lies on one grid; then the sum is exact.  A block row (voxel j, role
+//     d, direction m) is scaled by 2^-Ea (Ea from the row's largest value) so
+//     that a0 = rint(A 2^-Ea) is an integer of at most 256; a state row
+//     (voxel i, right-hand side r) likewise by 2^-Ex, x0 = rint(X 2^-Ex).  The
+//     products x0 a0 of one K = 32 block are integers below 2^21: exact.
+//   * a1 = fp16(A 2^-Ea - a0), a2 = fp16(A 2^-Ea - a0 - a1) (A to ~30 bits) and
+//     x1 = fp16(X 2^-Ex - x0) (11 bits of the residual); the products with
+//     a1, a2 and x1 are 2^-8 of the result or smaller, so their truncation is
+//     below 2^-32 relative.
+//   * The state lives as (x0, x1, Ex); every step writes it from the FP32
+//     result.  Each tile's products are drained from tensor memory, scaled by
+//     2^(Ex + Ea) and added into FP32 sums on the CUDA cores (27 partials per
+//     output, round to nearest).
 //
 // Kernel (one CTA per SM, persistent over output lines (y, z)): the state
 // tile of input voxel i (64 right-hand sides of x0 and of x1 = 128 rows,
-// 32 directions, bf16, 8 KB) feeds the three outputs on the output line whose
-// neighbour it is.  Input columns are swept along x: each of the <= 9 input
-// lines gives one tile per column.  Per tile:
-//   MMA1  D[0:192)  = [x0; x1] (128 x 32) x [a0 of 3 outputs | a1 of 3 outputs]
-//   MMA2  D[96:192) += [x0; x1] x [a2 of 3 outputs]
+// 32 directions, fp16, 8 KB, Ex of row r stored at direction 26 of row r)
+// feeds the three outputs on the output line whose neighbour it is.  Input
+// columns are swept along x; each of the <= 9 input lines gives one tile per
+// column.  The three outputs' 26 rows are packed into N = 80 columns
+// (column 26 bb + m for output c - 1 + bb).  Per tile:
+//   MMA1  D[0:160)  = [x0; x1] (128 x 32) x [a0 | a1]   (N = 160)
+//   MMA2  D[80:160) += [x0; x1] x [a2]                 (N = 80)
 // (two K = 16 steps each), D in tensor memory, fresh per tile, double-buffered.
-// Warp roles: warps 0-3 drain D (tcgen05.ld, lane quarter = warp) into FP32
-// sums of the three live outputs and write each finished output voxel's new
-// (x0, x1) tile; warp 4 issues the MMAs; warp 5 copies state tiles with
-// cp.async.bulk; warps 6-7 expand A's union-dense values into the B operand
-// tiles in shared memory.  B tiles are dedicated per input line role, whose
-// sparsity never changes, so only the values are rewritten.  Every wait is on
-// an mbarrier with a bounded poll count; a wait that runs out sets the
-// context's error word and the CTA winds down.
-#include <cuda_bf16.h>
+// Warp roles: warps 0-3 drain D (tcgen05.ld, lane quarter = warp) into the
+// FP32 sums of the three live outputs and write each finished output voxel's
+// new tile; warp 4 issues the MMAs; warp 5 copies each tile's state and A
+// chunks with cp.async.bulk into a ring of staging slots; warps 6-7 scatter
+// the staged A values into the B operand tiles.  B tiles are dedicated per
+// input line role, whose sparsity never changes, so only values are
+// rewritten.  Every wait is on an mbarrier with a bounded poll count; a wait
+// that runs out sets the context's error word and the CTA winds down.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "drts_device.cuh"
@@ -53,22 +53,31 @@ namespace drts {
 namespace {
 
 constexpr int kTcK = 32;                      // directions padded to the K extent
-constexpr int kXTileBytes = 8192;             // 128 rows x 32 directions x bf16
-constexpr int kXSlots = 4;
-constexpr int kB01 = 4 * 24 * 128;            // K 32 x N 192 (a0 | a1 of three outputs)
-constexpr int kB2 = 4 * 12 * 128;             // K 32 x N 96 (a2 of three outputs)
-constexpr int kBSlot = kB01 + kB2;
+constexpr int kN = 80;                        // three outputs x 26 rows, padded
+constexpr int kXTileBytes = 8192;             // 128 rows x 32 directions x fp16
+constexpr int kExpDir = 26;                   // direction slot holding Ex of a state row
+constexpr int kB01 = 4 * 20 * 128;            // K 32 x N 160 (a0 | a1)
+constexpr int kB2 = 4 * 10 * 128;             // K 32 x N 80 (a2)
+constexpr int kBScale = kN * 4;               // 2^Ea per packed column
+constexpr int kBSlot = 15744;                 // kB01 + kB2 + kBScale rounded to 128
 constexpr int kLines = 9;
-constexpr int kOffX = kLines * kBSlot;                    // 165,888
-constexpr int kOffXch = kOffX + kXSlots * kXTileBytes;    // 198,656
-constexpr int kOffBar = kOffXch + 64 * 32 * 4;            // 206,848
+constexpr int kAStageMax = 9216;              // A chunks of one tile
+constexpr int kRingSlot = kXTileBytes + kAStageMax;
+constexpr int kRing = 4;
+constexpr int kOffRing = kLines * kBSlot;                  // 141,696
+constexpr int kOffXch = kOffRing + kRing * kRingSlot;      // 211,328
+constexpr int kOffBar = kOffXch + kDirs * 64 * 4;          // 217,984
 constexpr int kSmemBytes = kOffBar + 512;
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 512;
-constexpr int kDCols = 192;
+constexpr int kDCols = 160;
+constexpr int kExpBias = 160;                 // A row exponents are stored as Ea + 160 (uint8)
+
+static_assert(kB01 + kB2 + kBScale <= kBSlot, "B slot");
+static_assert(kSmemBytes <= 232448, "shared memory");
 
 // barrier indices (8 bytes each at kOffBar)
-constexpr int kBarBFull = 0, kBarBEmpty = 9, kBarXFull = 18, kBarXEmpty = 22, kBarDFull = 26, kBarDEmpty = 28;
+constexpr int kBarBFull = 0, kBarBEmpty = 9, kBarRFull = 18, kBarREmpty = 22, kBarDFull = 26, kBarDEmpty = 28;
 constexpr int kNumBars = 30;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
@@ -86,13 +95,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
 }
 
-// kind::f16 instruction descriptor: bf16 A and B (K-major), FP32 D, M x N
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N)
+// kind::f16 instruction descriptor: fp16 A and B (K-major), FP32 D, M x N
+__device__ __forceinline__ uint32_t idesc_f16(int M, int N)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+    return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
@@ -147,20 +156,17 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
                  :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32])
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
 {
-    uint32_t r[32];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
                    "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                   "=r"(r[14]), "=r"(r[15])
                  : "r"(taddr));
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
@@ -176,29 +182,33 @@ __device__ __forceinline__ double tc_source_value(const StepArgs &a, const Sourc
     return 0.0;
 }
 
-// Split y into x0 (8 bits on the grid 2^(E-7) of the largest |y| of the tile
-// row, E its exponent) and x1 = bf16(y - x0); write the row pair (x0 in row
-// r, x1 in row 64 + r) of a state tile.
-__device__ __forceinline__ void write_state_row(__nv_bfloat16 *tile, int r, const float y[kDirs])
+// Write row pair r / 64 + r of a state tile from y: Ex from the largest |y|
+// (|y| 2^-Ex < 256), x0 = rint(y 2^-Ex) (exact in fp16), x1 = fp16(y 2^-Ex - x0),
+// Ex itself (an integer, exact in fp16) at direction 26 of row r.
+__device__ __forceinline__ void write_state_row(__half *tile, int r, const float y[kDirs])
 {
     float mx = 0.0f;
 #pragma unroll
     for (int m = 0; m < kDirs; ++m) mx = fmaxf(mx, fabsf(y[m]));
     int e = 0;
     frexpf(mx, &e);                                     // mx = f 2^e, f in [0.5, 1); e = 0 for mx = 0
+    const int ex = e - 8;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        __align__(16) __nv_bfloat16 h0[8], h1[8];
+        __align__(16) __half h0[8], h1[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int n = g * 8 + k;
             float x0 = 0.0f, x1 = 0.0f;
             if (n < kDirs) {
-                x0 = ldexpf(rintf(ldexpf(y[n], 8 - e)), e - 8);   // k 2^(e-8), |k| <= 256: exact
-                x1 = y[n] - x0;                                  // exact
+                const float ys = ldexpf(y[n], -ex);     // exact, |ys| < 256
+                x0 = rintf(ys);
+                x1 = ys - x0;                           // exact, |x1| <= 1/2
+            } else if (n == kExpDir) {
+                x0 = float(ex);
             }
-            h0[k] = __float2bfloat16_rn(x0);
-            h1[k] = __float2bfloat16_rn(x1);
+            h0[k] = __float2half_rn(x0);
+            h1[k] = __float2half_rn(x1);
         }
         *reinterpret_cast<uint4 *>(tile + xtile_elem(r, g * 8)) = *reinterpret_cast<const uint4 *>(h0);
         *reinterpret_cast<uint4 *>(tile + xtile_elem(64 + r, g * 8)) = *reinterpret_cast<const uint4 *>(h1);
@@ -206,27 +216,31 @@ __device__ __forceinline__ void write_state_row(__nv_bfloat16 *tile, int r, cons
 }
 
 struct EpiState {
-    float acc[3][kTcK];
+    float acc[3][kDirs];
 };
 
 // Add the drained tile (D buffer b) into the sums of the three outputs of
-// column c: output c - 1 + bb sits in slot (c - 1 + bb) mod 3 = (ROT + 2 + bb) % 3.
+// column c: packed column q = 26 bb + m belongs to output c - 1 + bb, whose
+// sums sit in slot (c - 1 + bb) mod 3 = (ROT + 2 + bb) % 3; scale 2^(Ex + Ea).
 template <int ROT>
-__device__ __forceinline__ void drain_tile(EpiState &s, uint32_t tmem_q, int b)
+__device__ __forceinline__ void drain_tile(EpiState &s, uint32_t tmem_q, int b, float qx, const float *qa)
 {
 #pragma unroll
-    for (int bb = 0; bb < 3; ++bb) {
-        float dF[32], dS[32];
-        tmem_ld32(tmem_q + uint32_t(b * kDCols + bb * 32), dF);
-        tmem_ld32(tmem_q + uint32_t(b * kDCols + 96 + bb * 32), dS);
+    for (int k = 0; k < 5; ++k) {
+        float dF[16], dS[16];
+        tmem_ld16(tmem_q + uint32_t(b * kDCols + 16 * k), dF);
+        tmem_ld16(tmem_q + uint32_t(b * kDCols + kN + 16 * k), dS);
         tmem_wait_ld();
-        constexpr int base = (ROT + 2) % 3;
-        const int slot = (base + bb) % 3;
 #pragma unroll
-        for (int m = 0; m < kTcK; ++m) {
-            if (slot == 0) s.acc[0][m] += dF[m] + dS[m];
-            else if (slot == 1) s.acc[1][m] += dF[m] + dS[m];
-            else s.acc[2][m] += dF[m] + dS[m];
+        for (int i = 0; i < 16; ++i) {
+            const int q = 16 * k + i;
+            if (q >= 3 * kDirs) continue;
+            const int bb = q / kDirs, m = q % kDirs;
+            const int slot = (ROT + 2 + bb) % 3;
+            const float v = (dF[i] + dS[i]) * (qx * qa[q]);
+            if (slot == 0) s.acc[0][m] += v;
+            else if (slot == 1) s.acc[1][m] += v;
+            else s.acc[2][m] += v;
         }
     }
 }
@@ -235,7 +249,7 @@ template <int SLOT>
 __device__ __forceinline__ void zero_slot(EpiState &s)
 {
 #pragma unroll
-    for (int m = 0; m < kTcK; ++m) s.acc[SLOT][m] = 0.0f;
+    for (int m = 0; m < kDirs; ++m) s.acc[SLOT][m] = 0.0f;
 }
 
 // Output voxel j (sums in slot SLOT) is complete: combine the x0-row and
@@ -265,7 +279,7 @@ __device__ __forceinline__ void finalize(EpiState &s, const StepArgs &a, float *
                     if (m == sm) y[m] += val;
             }
         }
-        __nv_bfloat16 *tile = static_cast<__nv_bfloat16 *>(a.y) + vox * (kXTileBytes / 2);
+        __half *tile = static_cast<__half *>(a.y) + vox * (kXTileBytes / 2);
         write_state_row(tile, rhs, y);
     }
     named_sync(1, 128);
@@ -283,12 +297,22 @@ __device__ __forceinline__ int line_roles(int y, int z, int ny, int nz, int *Ls)
     return n;
 }
 
-template <int ROT>
-__device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, int nL, uint32_t tmem_q,
-                                           uint32_t bars, int64_t &tau, volatile int *abort, volatile int *failed)
+__device__ __forceinline__ float state_scale(const __half *x, int64_t vi, int r)
 {
+    return ldexpf(1.0f, int(__half2float(x[vi * (kXTileBytes / 2) + xtile_elem(r, kExpDir)])));
+}
+
+template <int ROT>
+__device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, int c, int y, int z, const int *Ls,
+                                           int nL, uint32_t tmem_q, unsigned char *sm, uint32_t bars,
+                                           int64_t &tau, volatile int *abort, volatile int *failed, int rhs)
+{
+    const __half *x = static_cast<const __half *>(a.x);
     for (int li = 0; li < nL; ++li) {
+        const int L = Ls[li];
         const int b = int(tau & 1);
+        const int64_t vi = (int64_t(z + L / 3 - 1) * a.ny + (y + L % 3 - 1)) * a.nx + c;
+        const float qx = state_scale(x, vi, rhs);     // issued before the wait: its latency overlaps
         // every thread waits; a give-up anywhere is shared so the four warps agree
         if (!bar_wait(bars + 8 * (kBarDFull + b), uint32_t((tau >> 1) & 1), a.spin_limit, abort)) {
             *failed = 1;
@@ -298,9 +322,10 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, int n
         named_sync(1, 128);
         if (*failed) return false;
         tc_fence_after();
-        drain_tile<ROT>(s, tmem_q, b);
+        drain_tile<ROT>(s, tmem_q, b, qx, reinterpret_cast<const float *>(sm + L * kBSlot + kB01 + kB2));
         tc_fence_before();
         bar_arrive(bars + 8 * (kBarDEmpty + b));
+        bar_arrive(bars + 8 * (kBarBEmpty + L));       // the B slot's scales are read
         ++tau;
     }
     return true;
@@ -326,11 +351,11 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     if (tid == 0) {
         for (int L = 0; L < kLines; ++L) {
             bar_init(bars + 8 * (kBarBFull + L), 64);
-            bar_init(bars + 8 * (kBarBEmpty + L), 1);
+            bar_init(bars + 8 * (kBarBEmpty + L), 1 + 128);     // MMA done + epilogue read the scales
         }
-        for (int s = 0; s < kXSlots; ++s) {
-            bar_init(bars + 8 * (kBarXFull + s), 1);
-            bar_init(bars + 8 * (kBarXEmpty + s), 1);
+        for (int sl = 0; sl < kRing; ++sl) {
+            bar_init(bars + 8 * (kBarRFull + sl), 1);
+            bar_init(bars + 8 * (kBarREmpty + sl), 1 + 64);     // MMA read the state tile + A scattered
         }
         for (int b = 0; b < 2; ++b) {
             bar_init(bars + 8 * (kBarDFull + b), 1);
@@ -359,8 +384,9 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int m = 0; m < kTcK; ++m) s.acc[k][m] = 0.0f;
+            for (int m = 0; m < kDirs; ++m) s.acc[k][m] = 0.0f;
         const uint32_t tmem_q = tmem + (uint32_t(32 * warp) << 16);
+        const int rhs = lane + 32 * (warp & 1);
         int64_t tau = 0;
         bool ok = true;
         for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
@@ -371,20 +397,20 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             for (int c = 0; c < nx && ok; ++c) {
                 switch (c % 3) {
                 case 0:
-                    ok = epi_column<0>(s, a, nL, tmem_q, bars, tau, abort, failed);
+                    ok = epi_column<0>(s, a, c, y, z, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
                     if (!ok) break;
                     if (c >= 1) finalize<2>(s, a, xch, warp, lane, row0 + c - 1);
                     else zero_slot<2>(s);
                     if (c == nx - 1) { finalize<0>(s, a, xch, warp, lane, row0 + c); zero_slot<1>(s); }
                     break;
                 case 1:
-                    ok = epi_column<1>(s, a, nL, tmem_q, bars, tau, abort, failed);
+                    ok = epi_column<1>(s, a, c, y, z, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
                     if (!ok) break;
                     finalize<0>(s, a, xch, warp, lane, row0 + c - 1);
                     if (c == nx - 1) { finalize<1>(s, a, xch, warp, lane, row0 + c); zero_slot<2>(s); }
                     break;
                 default:
-                    ok = epi_column<2>(s, a, nL, tmem_q, bars, tau, abort, failed);
+                    ok = epi_column<2>(s, a, c, y, z, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
                     if (!ok) break;
                     finalize<1>(s, a, xch, warp, lane, row0 + c - 1);
                     if (c == nx - 1) { finalize<2>(s, a, xch, warp, lane, row0 + c); zero_slot<0>(s); }
@@ -395,8 +421,8 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     } else if (warp == 4) {
         // ---- MMA issue (one thread) ----
         if (lane == 0) {
-            const uint32_t id1 = idesc_bf16(128, 192), id2 = idesc_bf16(128, 96);
-            const uint32_t xs0 = smem_u32(sm + kOffX), bs0 = smem_u32(sm);
+            const uint32_t id1 = idesc_f16(128, 2 * kN), id2 = idesc_f16(128, kN);
+            const uint32_t ring0 = smem_u32(sm + kOffRing), bs0 = smem_u32(sm);
             int64_t tau = 0;
             int u[kLines] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
             bool ok = true;
@@ -407,21 +433,21 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                 for (int c = 0; c < nx && ok; ++c)
                     for (int li = 0; li < nL && ok; ++li) {
                         const int L = Ls[li];
-                        const int sx = int(tau % kXSlots), b = int(tau & 1);
-                        ok = bar_wait(bars + 8 * (kBarXFull + sx), uint32_t((tau / kXSlots) & 1), limit, abort) &&
+                        const int sr = int(tau % kRing), b = int(tau & 1);
+                        ok = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), limit, abort) &&
                              bar_wait(bars + 8 * (kBarBFull + L), uint32_t(u[L] & 1), limit, abort) &&
                              (tau < 2 || bar_wait(bars + 8 * (kBarDEmpty + b), uint32_t(((tau >> 1) - 1) & 1), limit, abort));
                         if (!ok) break;
                         tc_fence_after();
                         const uint32_t d = tmem + uint32_t(b * kDCols);
-                        const uint32_t xa = xs0 + sx * kXTileBytes, ba = bs0 + L * kBSlot;
+                        const uint32_t xa = ring0 + sr * kRingSlot, ba = bs0 + L * kBSlot;
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
                             const uint64_t ad = smem_desc(xa + kk * 4096, 2048, 128);
-                            mma_bf16(d, ad, smem_desc(ba + kk * 6144, 3072, 128), id1, kk);
-                            mma_bf16(d + 96, ad, smem_desc(ba + kB01 + kk * 3072, 1536, 128), id2, 1);
+                            mma_f16(d, ad, smem_desc(ba + kk * 5120, 2560, 128), id1, kk);
+                            mma_f16(d + kN, ad, smem_desc(ba + kB01 + kk * 2560, 1280, 128), id2, 1);
                         }
-                        mma_commit(bars + 8 * (kBarXEmpty + sx));
+                        mma_commit(bars + 8 * (kBarREmpty + sr));
                         mma_commit(bars + 8 * (kBarBEmpty + L));
                         mma_commit(bars + 8 * (kBarDFull + b));
                         ++u[L];
@@ -441,29 +467,50 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             }
         }
     } else if (warp == 5) {
-        // ---- state tile copies (one thread) ----
+        // ---- state tile and A chunk copies (one thread) ----
         if (lane == 0) {
-            const __nv_bfloat16 *x = static_cast<const __nv_bfloat16 *>(a.x);
-            const uint32_t xs0 = smem_u32(sm + kOffX);
+            const __half *x = static_cast<const __half *>(a.x);
+            const unsigned char *Au = reinterpret_cast<const unsigned char *>(P.Au);
+            const uint32_t ring0 = smem_u32(sm + kOffRing);
             int64_t tau = 0;
             bool ok = true;
             for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
                 const int y = int(line % ny), z = int(line / ny);
                 int Ls[kLines];
                 const int nL = line_roles(y, z, ny, nz, Ls);
+                const int64_t row0 = (int64_t(z) * ny + y) * nx;
                 for (int c = 0; c < nx && ok; ++c)
                     for (int li = 0; li < nL && ok; ++li) {
                         const int L = Ls[li];
-                        const int sx = int(tau % kXSlots);
-                        if (tau >= kXSlots &&
-                            !bar_wait(bars + 8 * (kBarXEmpty + sx), uint32_t(((tau / kXSlots) - 1) & 1), limit, abort)) {
+                        const int sr = int(tau % kRing);
+                        if (tau >= kRing &&
+                            !bar_wait(bars + 8 * (kBarREmpty + sr), uint32_t(((tau / kRing) - 1) & 1), limit, abort)) {
                             ok = false;
                             break;
                         }
                         const int64_t vi = (int64_t(z + L / 3 - 1) * ny + (y + L % 3 - 1)) * nx + c;
-                        bar_expect_tx(bars + 8 * (kBarXFull + sx), kXTileBytes);
-                        bulk_load(xs0 + sx * kXTileBytes, x + vi * (kXTileBytes / 2), kXTileBytes,
-                                  bars + 8 * (kBarXFull + sx));
+                        uint32_t bytes = kXTileBytes, stage = 0;
+                        int chunk_len[3];
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb) {
+                            const int d = 3 * L + 2 - bb;
+                            const int j = c - 1 + bb;
+                            chunk_len[bb] = (j >= 0 && j < nx) ? P.chunk_off[d + 1] - P.chunk_off[d] : 0;
+                            bytes += uint32_t(chunk_len[bb]);
+                        }
+                        const uint32_t slot = ring0 + sr * kRingSlot;
+                        const uint32_t fb = bars + 8 * (kBarRFull + sr);
+                        bar_expect_tx(fb, bytes);
+                        bulk_load(slot, x + vi * (kXTileBytes / 2), kXTileBytes, fb);
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb) {
+                            const int d = 3 * L + 2 - bb;
+                            if (chunk_len[bb] > 0)
+                                bulk_load(slot + kXTileBytes + stage,
+                                          Au + (row0 + c - 1 + bb) * P.voxel_bytes + P.chunk_off[d],
+                                          uint32_t(chunk_len[bb]), fb);
+                            stage += uint32_t(P.chunk_off[d + 1] - P.chunk_off[d]);
+                        }
                         ++tau;
                     }
             }
@@ -473,58 +520,67 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             }
         }
     } else {
-        // ---- B operand tiles from A's union-dense values (64 threads) ----
+        // ---- B operand tiles from the staged A chunks (64 threads) ----
         const int pt = tid - 192;
         int u[kLines] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        int64_t tau = 0;
         bool ok = true;
         for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
             const int y = int(line % ny), z = int(line / ny);
             int Ls[kLines];
             const int nL = line_roles(y, z, ny, nz, Ls);
-            const int64_t row0 = (int64_t(z) * ny + y) * nx;
             for (int c = 0; c < nx && ok; ++c)
                 for (int li = 0; li < nL && ok; ++li) {
                     const int L = Ls[li];
-                    if (u[L] >= 1) {
-                        if (!bar_wait(bars + 8 * (kBarBEmpty + L), uint32_t((u[L] - 1) & 1), limit, abort)) {
-                            failed[1] = 1;
-                            *abort = 1;
-                            atomicExch(a.err, 1);
-                        }
-                        named_sync(2, 64);
-                        if (failed[1]) {
-                            ok = false;
-                            break;
-                        }
+                    const int sr = int(tau % kRing);
+                    bool w = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), limit, abort);
+                    if (w && u[L] >= 1)
+                        w = bar_wait(bars + 8 * (kBarBEmpty + L), uint32_t((u[L] - 1) & 1), limit, abort);
+                    if (!w) {
+                        failed[1] = 1;
+                        *abort = 1;
+                        atomicExch(a.err, 1);
+                    }
+                    named_sync(2, 64);
+                    if (failed[1]) {
+                        ok = false;
+                        break;
                     }
                     unsigned char *slot = sm + L * kBSlot;
+                    float *scale = reinterpret_cast<float *>(slot + kB01 + kB2);
+                    const unsigned char *stage = sm + kOffRing + sr * kRingSlot + kXTileBytes;
 #pragma unroll 1
                     for (int bb = 0; bb < 3; ++bb) {
                         const int j = c - 1 + bb;
                         // input voxel (c, line L) is neighbour (1 - bb, L) of output j
-                        const int d = (L / 3) * 9 + (L % 3) * 3 + (2 - bb);
-                        const int p0 = P.role_off[d], p1 = P.role_off[d + 1];
+                        const int d = 3 * L + 2 - bb;
+                        const int p0 = P.role_off[d], np = P.role_off[d + 1] - p0;
                         const bool valid = j >= 0 && j < nx;
-                        const uint16_t *A0 = P.Au + (row0 + (valid ? j : 0)) * 3 * int64_t(P.U);
-                        for (int p = p0 + pt; p < p1; p += 64) {
-                            const uint32_t code = P.pos[p];
-                            const int n = int(code >> 8), m = int(code & 255);
-                            uint16_t v0 = 0, v1 = 0, v2 = 0;
+                        const __half *t0 = reinterpret_cast<const __half *>(stage);
+                        const unsigned char *ea = stage + 6 * np;
+                        for (int p = pt; p < np; p += 64) {
+                            const uint32_t code = P.pos[p0 + p];
+                            const int n = int(code >> 8), q = bb * kDirs + int(code & 255);
+                            __half v0 = __float2half_rn(0.0f), v1 = v0, v2 = v0;
                             if (valid) {
-                                v0 = A0[p];
-                                v1 = A0[P.U + p];
-                                v2 = A0[2 * P.U + p];
+                                v0 = t0[p];
+                                v1 = t0[np + p];
+                                v2 = t0[2 * np + p];
                             }
-                            const int q = bb * 4 + (m >> 3);
-                            const int within = (m & 7) * 16 + (n & 7) * 2;
-                            *reinterpret_cast<uint16_t *>(slot + ((n >> 3) * 24 + q) * 128 + within) = v0;
-                            *reinterpret_cast<uint16_t *>(slot + ((n >> 3) * 24 + 12 + q) * 128 + within) = v1;
-                            *reinterpret_cast<uint16_t *>(slot + kB01 + ((n >> 3) * 12 + q) * 128 + within) = v2;
+                            const int within = (q & 7) * 16 + (n & 7) * 2;
+                            *reinterpret_cast<__half *>(slot + ((n >> 3) * 20 + (q >> 3)) * 128 + within) = v0;
+                            *reinterpret_cast<__half *>(slot + ((n >> 3) * 20 + 10 + (q >> 3)) * 128 + within) = v1;
+                            *reinterpret_cast<__half *>(slot + kB01 + ((n >> 3) * 10 + (q >> 3)) * 128 + within) = v2;
                         }
+                        if (pt < kDirs) scale[bb * kDirs + pt] = valid ? ldexpf(1.0f, int(ea[pt]) - kExpBias) : 0.0f;
+                        if (valid) stage += P.chunk_off[d + 1] - P.chunk_off[d];
+                        else stage += P.chunk_off[d + 1] - P.chunk_off[d];
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_arrive(bars + 8 * (kBarBFull + L));
+                    bar_arrive(bars + 8 * (kBarREmpty + sr));
                     ++u[L];
+                    ++tau;
                 }
         }
     }
@@ -564,10 +620,11 @@ __global__ void tc_flags_kernel(SlicedMatrix A, int64_t V, uint8_t *flags)
     });
 }
 
-// Row (voxel j, direction m): per block role d the largest |value| fixes the
-// grid of a0; every value is split into a0 + a1 + a2 and stored at its union
-// position.
-__global__ void tc_convert_kernel(SlicedMatrix A, int64_t V, const int16_t *pidx, int U, uint16_t *Au)
+// Row (voxel j, direction m): per block role d, Ea from the row's largest
+// |value| in the block; every value v becomes a0 = rint(v 2^-Ea) (|a0| <= 256),
+// a1 = fp16(v 2^-Ea - a0), a2 = fp16(v 2^-Ea - a0 - a1), stored at its union
+// position in the role's chunk, and Ea + 160 in the chunk's exponent bytes.
+__global__ void tc_convert_kernel(SlicedMatrix A, int64_t V, const int16_t *pidx, TcPlan P, unsigned char *Au)
 {
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t q = g / kSlice;
@@ -582,7 +639,13 @@ __global__ void tc_convert_kernel(SlicedMatrix A, int64_t V, const int16_t *pidx
         const int d = code / kDirs;
         rmax[d] = fmaxf(rmax[d], fabsf(v));
     });
-    uint16_t *out = Au + j * 3 * int64_t(U);
+    unsigned char *vox = Au + j * P.voxel_bytes;
+    for (int d = 0; d < kOffs; ++d) {
+        int e = 0;
+        frexpf(rmax[d], &e);
+        const int np = P.role_off[d + 1] - P.role_off[d];
+        vox[P.chunk_off[d] + 6 * np + m] = uint8_t(e - 8 + kExpBias);
+    }
     for_row(A, q, lane, [&](int code, float v) {
         if (v == 0.0f) return;
         const int d = code / kDirs, n = code % kDirs;
@@ -590,32 +653,36 @@ __global__ void tc_convert_kernel(SlicedMatrix A, int64_t V, const int16_t *pidx
         if (p < 0) return;                      // cannot happen: the union covers every entry
         int e = 0;
         frexpf(rmax[d], &e);
-        const float a0 = ldexpf(rintf(ldexpf(v, 8 - e)), e - 8);
-        const float r1 = v - a0;
-        const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
-        const float r2 = r1 - __bfloat162float(b1);
-        out[p] = __bfloat16_as_ushort(__float2bfloat16_rn(a0));
-        out[U + p] = __bfloat16_as_ushort(b1);
-        out[2 * U + p] = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+        const float vs = ldexpf(v, 8 - e);      // exact, |vs| < 256
+        const float a0 = rintf(vs);
+        const float r1 = vs - a0;               // exact
+        const __half h1 = __float2half_rn(r1);
+        const float r2 = r1 - __half2float(h1); // exact
+        const int np = P.role_off[d + 1] - P.role_off[d];
+        __half *t = reinterpret_cast<__half *>(vox + P.chunk_off[d]);
+        t[p] = __float2half_rn(a0);
+        t[np + p] = h1;
+        t[2 * np + p] = __float2half_rn(r2);
     });
 }
 
 // ---- state layout helpers ----
 
-__device__ __forceinline__ double tcx_value(const __nv_bfloat16 *x, int64_t v, int n, int r)
+__device__ __forceinline__ double tcx_value(const __half *x, int64_t v, int n, int r)
 {
-    const __nv_bfloat16 *t = x + v * (kXTileBytes / 2);
-    return double(__bfloat162float(t[xtile_elem(r, n)])) + double(__bfloat162float(t[xtile_elem(64 + r, n)]));
+    const __half *t = x + v * (kXTileBytes / 2);
+    const double s = ldexp(1.0, int(__half2float(t[xtile_elem(r, kExpDir)])));
+    return (double(__half2float(t[xtile_elem(r, n)])) + double(__half2float(t[xtile_elem(64 + r, n)]))) * s;
 }
 
-__global__ void tcx_to_canonical_kernel(const __nv_bfloat16 *x, int64_t V, int r, double *out)
+__global__ void tcx_to_canonical_kernel(const __half *x, int64_t V, int r, double *out)
 {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= V * kDirs) return;
     out[s] = tcx_value(x, s / kDirs, int(s % kDirs), r);
 }
 
-__global__ void tcx_from_canonical_kernel(const double *in, int64_t V, int r, __nv_bfloat16 *x)
+__global__ void tcx_from_canonical_kernel(const double *in, int64_t V, int r, __half *x)
 {
     const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (v >= V) return;
@@ -624,7 +691,7 @@ __global__ void tcx_from_canonical_kernel(const double *in, int64_t V, int r, __
     write_state_row(x + v * (kXTileBytes / 2), r, y);
 }
 
-__global__ void tcx_sum_kernel(const __nv_bfloat16 *x, int64_t V, int r, double *out)
+__global__ void tcx_sum_kernel(const __half *x, int64_t V, int r, double *out)
 {
     double acc = 0.0;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < V * kDirs;
@@ -641,22 +708,20 @@ __global__ void tcx_sum_kernel(const __nv_bfloat16 *x, int64_t V, int r, double 
     }
 }
 
-// Ledger of X(t): one warp per voxel tile; lane k reads the 16-byte chunk k
-// of each 512-byte group (rows rho .. of one direction group), so a warp
-// reads the tile with coalesced loads; per right-hand side sums are
-// collected in shared memory.
+// Ledger of X(t): one warp per voxel tile, coalesced 16-byte chunks.  Chunk
+// ch (0..511) is row ch % 8 of core matrix ch / 8 = (direction group g, row
+// group h): rows rho = 8 h + ch % 8, directions 8 g .. 8 g + 7.  Lane l reads
+// chunks l + 32 k, whose right-hand side is l for even k and l + 32 for odd
+// k; its two row scales sit in chunks 12 and 13 (direction 26 of rows l, l + 32).
 __global__ void __launch_bounds__(256) tcx_ledger_kernel(StepArgs a)
 {
     __shared__ float red[2][64];
     for (int i = threadIdx.x; i < 128; i += blockDim.x) (&red[0][0])[i] = 0.0f;
     __syncthreads();
-    const __nv_bfloat16 *x = static_cast<const __nv_bfloat16 *>(a.x);
+    const __half *x = static_cast<const __half *>(a.x);
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
-    // chunk ch (0..511) of a tile is row ch % 8 of core matrix ch / 8 = (n group g, row
-    // group h) -> rows rho = 8 h + ch % 8, directions 8 g .. 8 g + 7.  Lane l reads
-    // chunks l + 32 k: its row's right-hand side rho & 63 depends only on k % 2.
     float ab[2] = {0.0f, 0.0f}, ex[2] = {0.0f, 0.0f};
     for (int64_t v = w0; v < a.V; v += nw) {
         const int k = a.med[v];
@@ -666,28 +731,36 @@ __global__ void __launch_bounds__(256) tcx_ledger_kernel(StepArgs a)
                          (xx == 0 ? 0 : (xx == a.nx - 1 ? 2 : 1));
         const double *et = a.tab.exit_total + (k * 27 + mask) * kDirs;
         const uint4 *t = reinterpret_cast<const uint4 *>(x + v * (kXTileBytes / 2));
+        float sc[2];
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+            const uint4 raw = t[lane + 32 * (12 + par)];
+            sc[par] = ldexpf(1.0f, int(__half2float(reinterpret_cast<const __half *>(&raw)[kExpDir - 24])));
+        }
+        float s[2] = {0.0f, 0.0f}, se[2] = {0.0f, 0.0f};
 #pragma unroll 4
         for (int kc = 0; kc < 16; ++kc) {
             const int ch = lane + 32 * kc;
             const int n0 = (ch >> 7) * 8;
             const uint4 raw = t[ch];
-            const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&raw);
-            float s = 0.0f, se = 0.0f;
+            const __half *h = reinterpret_cast<const __half *>(&raw);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int n = n0 + i;
                 if (n >= kDirs) continue;
-                const float xv = __bfloat162float(h[i]);
-                s += xv;
-                if (mask != 13) se += float(et[n]) * xv;
+                const float xv = __half2float(h[i]);
+                s[kc & 1] += xv;
+                if (mask != 13) se[kc & 1] += float(et[n]) * xv;
             }
-            ab[kc & 1] += abs_k * s;
-            ex[kc & 1] += se;
+        }
+#pragma unroll
+        for (int par = 0; par < 2; ++par) {
+            ab[par] += abs_k * s[par] * sc[par];
+            ex[par] += se[par] * sc[par];
         }
     }
     for (int par = 0; par < 2; ++par) {
-        const int ch = lane + 32 * par;
-        const int rr = (((ch >> 3) & 15) * 8 + (ch & 7)) & 63;
+        const int rr = lane + 32 * par;
         if (rr < a.R) {
             if (ab[par] != 0.0f) atomicAdd(&red[0][rr], ab[par]);
             if (ex[par] != 0.0f) atomicAdd(&red[1][rr], ex[par]);
@@ -717,7 +790,7 @@ __global__ void tcx_det_kernel(StepArgs a)
     const int Nu = N[ua], Nv = N[va];
     const int u0 = (pu * Nu + a.det_nu - 1) / a.det_nu, u1 = ((pu + 1) * Nu + a.det_nu - 1) / a.det_nu;
     const int v0 = (pv * Nv + a.det_nv - 1) / a.det_nv, v1 = ((pv + 1) * Nv + a.det_nv - 1) / a.det_nv;
-    const __nv_bfloat16 *x = static_cast<const __nv_bfloat16 *>(a.x);
+    const __half *x = static_cast<const __half *>(a.x);
     double sum = 0.0;
     for (int cv = v0; cv < v1; ++cv)
         for (int cu = u0; cu < u1; ++cu) {
@@ -749,6 +822,7 @@ int sm_count()
 }  // namespace
 
 size_t tcx_state_bytes(int64_t V) { return size_t(V) * kXTileBytes; }
+int tc_stage_limit() { return kAStageMax; }
 
 cudaError_t launch_tc_flags(const SlicedMatrix &A, int64_t V, uint8_t *flags, cudaStream_t s)
 {
@@ -757,11 +831,11 @@ cudaError_t launch_tc_flags(const SlicedMatrix &A, int64_t V, uint8_t *flags, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_convert(const SlicedMatrix &A, int64_t V, const int16_t *pidx, int U, uint16_t *Au,
-                              cudaStream_t s)
+cudaError_t launch_tc_convert(const SlicedMatrix &A, int64_t V, const int16_t *pidx, const TcPlan &P,
+                              void *Au, cudaStream_t s)
 {
     const int64_t n = A.n_slices * kSlice;
-    tc_convert_kernel<<<unsigned((n + 127) / 128), 128, 0, s>>>(A, V, pidx, U, Au);
+    tc_convert_kernel<<<unsigned((n + 127) / 128), 128, 0, s>>>(A, V, pidx, P, static_cast<unsigned char *>(Au));
     return cudaGetLastError();
 }
 
@@ -810,22 +884,21 @@ cudaError_t launch_tc_step(const StepArgs &a, bool functionals, cudaStream_t s)
 cudaError_t launch_tc_to_canonical(const void *x, int64_t V, int r, double *out, cudaStream_t s)
 {
     const int th = 256;
-    tcx_to_canonical_kernel<<<unsigned((V * kDirs + th - 1) / th), th, 0, s>>>(
-        static_cast<const __nv_bfloat16 *>(x), V, r, out);
+    tcx_to_canonical_kernel<<<unsigned((V * kDirs + th - 1) / th), th, 0, s>>>(static_cast<const __half *>(x), V,
+                                                                                r, out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_from_canonical(const double *in, int64_t V, int r, void *x, cudaStream_t s)
 {
     const int th = 128;
-    tcx_from_canonical_kernel<<<unsigned((V + th - 1) / th), th, 0, s>>>(in, V, r,
-                                                                        static_cast<__nv_bfloat16 *>(x));
+    tcx_from_canonical_kernel<<<unsigned((V + th - 1) / th), th, 0, s>>>(in, V, r, static_cast<__half *>(x));
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_sum(const void *x, int64_t V, int r, double *out, cudaStream_t s)
 {
-    tcx_sum_kernel<<<sm_count() * 2, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(x), V, r, out);
+    tcx_sum_kernel<<<sm_count() * 2, 256, 0, s>>>(static_cast<const __half *>(x), V, r, out);
     return cudaGetLastError();
 }
 
