@@ -401,6 +401,9 @@ drts_status setup_tensor_core(drts_ctx *c)
     P.role_off[kOffs] = int(pos.size());
     P.chunk_off[kOffs] = int(off);
     P.voxel_bytes = off;
+    if (P.role_off[kOffs] > tc_position_limit())
+        return fail(c, DRTS_EUNSUPPORTED, "tensor-core step: the matrix's block pattern has more positions than "
+                                          "the kernel's table holds");
     for (int L = 0; L < kOffs / 3; ++L)
         if (P.chunk_off[3 * L + 3] - P.chunk_off[3 * L] > tc_stage_limit())
             return fail(c, DRTS_EUNSUPPORTED, "tensor-core step: the matrix's block pattern needs more staging "

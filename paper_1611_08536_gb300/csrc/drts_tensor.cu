@@ -67,7 +67,10 @@ constexpr int kRing = 4;
 constexpr int kOffRing = kLines * kBSlot;                  // 141,696
 constexpr int kOffXch = kOffRing + kRing * kRingSlot;      // 211,328
 constexpr int kOffBar = kOffXch + kDirs * 64 * 4;          // 217,984
-constexpr int kSmemBytes = kOffBar + 512;
+constexpr int kOffPos = kOffBar + 512;                     // the union position table
+constexpr int kPosMax = 5888;                              // positions (padded) the table holds
+constexpr int kSmemBytes = kOffPos + kPosMax * 2;
+constexpr int kPrefetch = 8;                               // tiles whose data is pulled into L2 ahead
 constexpr int kThreads = 256;
 constexpr int kTmemCols = 512;
 constexpr int kDCols = 160;
@@ -148,6 +151,11 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint32_t
         if (*abort) return false;
     }
     return false;
+}
+
+__device__ __forceinline__ void l2_prefetch(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(src), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
@@ -297,23 +305,26 @@ __device__ __forceinline__ int line_roles(int y, int z, int ny, int nz, int *Ls)
     return n;
 }
 
-__device__ __forceinline__ float state_scale(const __half *x, int64_t vi, int r)
-{
-    return ldexpf(1.0f, int(__half2float(x[vi * (kXTileBytes / 2) + xtile_elem(r, kExpDir)])));
-}
-
 template <int ROT>
-__device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, int c, int y, int z, const int *Ls,
-                                           int nL, uint32_t tmem_q, unsigned char *sm, uint32_t bars,
-                                           int64_t &tau, volatile int *abort, volatile int *failed, int rhs)
+__device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, const int *Ls, int nL, uint32_t tmem_q,
+                                           unsigned char *sm, uint32_t bars, int64_t &tau, volatile int *abort,
+                                           volatile int *failed, int rhs)
 {
-    const __half *x = static_cast<const __half *>(a.x);
     for (int li = 0; li < nL; ++li) {
         const int L = Ls[li];
         const int b = int(tau & 1);
-        const int64_t vi = (int64_t(z + L / 3 - 1) * a.ny + (y + L % 3 - 1)) * a.nx + c;
-        const float qx = state_scale(x, vi, rhs);     // issued before the wait: its latency overlaps
+        const int sr = int(tau % kRing);
         // every thread waits; a give-up anywhere is shared so the four warps agree
+        float qx = 0.0f;
+        if (bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), a.spin_limit, abort)) {
+            // the state tile's row scale 2^Ex, from the staged copy
+            const __half *xt = reinterpret_cast<const __half *>(sm + kOffRing + sr * kRingSlot);
+            qx = ldexpf(1.0f, int(__half2float(xt[xtile_elem(rhs, kExpDir)])));
+        } else {
+            *failed = 1;
+            *abort = 1;
+            atomicExch(a.err, 1);
+        }
         if (!bar_wait(bars + 8 * (kBarDFull + b), uint32_t((tau >> 1) & 1), a.spin_limit, abort)) {
             *failed = 1;
             *abort = 1;
@@ -326,6 +337,7 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, int c
         tc_fence_before();
         bar_arrive(bars + 8 * (kBarDEmpty + b));
         bar_arrive(bars + 8 * (kBarBEmpty + L));       // the B slot's scales are read
+        bar_arrive(bars + 8 * (kBarREmpty + sr));      // the state tile's scales are read
         ++tau;
     }
     return true;
@@ -340,6 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     volatile int *abort = reinterpret_cast<volatile int *>(sm + kOffBar + 8 * kNumBars + 4);
     volatile int *failed = reinterpret_cast<volatile int *>(sm + kOffBar + 8 * kNumBars + 8);
     float *xch = reinterpret_cast<float *>(sm + kOffXch);
+    uint16_t *spos = reinterpret_cast<uint16_t *>(sm + kOffPos);
     const TcPlan &P = a.tcp;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int64_t n_lines = int64_t(ny) * nz;
@@ -348,6 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
 
     // B tiles start at zero; positions outside the union are never written
     for (int i = tid; i < kLines * kBSlot / 16; i += kThreads) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < P.role_off[kOffs]; i += kThreads) spos[i] = P.pos[i];
     if (tid == 0) {
         for (int L = 0; L < kLines; ++L) {
             bar_init(bars + 8 * (kBarBFull + L), 64);
@@ -355,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
         }
         for (int sl = 0; sl < kRing; ++sl) {
             bar_init(bars + 8 * (kBarRFull + sl), 1);
-            bar_init(bars + 8 * (kBarREmpty + sl), 1 + 64);     // MMA read the state tile + A scattered
+            bar_init(bars + 8 * (kBarREmpty + sl), 1 + 64 + 128);   // MMA + A scattered + scales read
         }
         for (int b = 0; b < 2; ++b) {
             bar_init(bars + 8 * (kBarDFull + b), 1);
@@ -397,20 +411,20 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             for (int c = 0; c < nx && ok; ++c) {
                 switch (c % 3) {
                 case 0:
-                    ok = epi_column<0>(s, a, c, y, z, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
+                    ok = epi_column<0>(s, a, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
                     if (!ok) break;
                     if (c >= 1) finalize<2>(s, a, xch, warp, lane, row0 + c - 1);
                     else zero_slot<2>(s);
                     if (c == nx - 1) { finalize<0>(s, a, xch, warp, lane, row0 + c); zero_slot<1>(s); }
                     break;
                 case 1:
-                    ok = epi_column<1>(s, a, c, y, z, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
+                    ok = epi_column<1>(s, a, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
                     if (!ok) break;
                     finalize<0>(s, a, xch, warp, lane, row0 + c - 1);
                     if (c == nx - 1) { finalize<1>(s, a, xch, warp, lane, row0 + c); zero_slot<2>(s); }
                     break;
                 default:
-                    ok = epi_column<2>(s, a, c, y, z, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
+                    ok = epi_column<2>(s, a, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
                     if (!ok) break;
                     finalize<1>(s, a, xch, warp, lane, row0 + c - 1);
                     if (c == nx - 1) { finalize<2>(s, a, xch, warp, lane, row0 + c); zero_slot<0>(s); }
@@ -479,6 +493,14 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                 int Ls[kLines];
                 const int nL = line_roles(y, z, ny, nz, Ls);
                 const int64_t row0 = (int64_t(z) * ny + y) * nx;
+                for (int c = 0; c < 3 && c < nx; ++c) {
+                    l2_prefetch(Au + (row0 + c) * P.voxel_bytes, uint32_t(P.voxel_bytes));
+                    for (int li = 0; li < nL && c < 2; ++li) {
+                        const int L = Ls[li];
+                        l2_prefetch(x + ((int64_t(z + L / 3 - 1) * ny + (y + L % 3 - 1)) * nx + c) * (kXTileBytes / 2),
+                                    kXTileBytes);
+                    }
+                }
                 for (int c = 0; c < nx && ok; ++c)
                     for (int li = 0; li < nL && ok; ++li) {
                         const int L = Ls[li];
@@ -498,6 +520,11 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                             chunk_len[bb] = (j >= 0 && j < nx) ? P.chunk_off[d + 1] - P.chunk_off[d] : 0;
                             bytes += uint32_t(chunk_len[bb]);
                         }
+                        // pull data two columns ahead into L2: the state tile of this line,
+                        // and once per column the whole A of the voxel three columns on
+                        if (c + 2 < nx) l2_prefetch(x + (vi + 2) * (kXTileBytes / 2), kXTileBytes);
+                        if (li == 0 && c + 3 < nx)
+                            l2_prefetch(Au + (row0 + c + 3) * P.voxel_bytes, uint32_t(P.voxel_bytes));
                         const uint32_t slot = ring0 + sr * kRingSlot;
                         const uint32_t fb = bars + 8 * (kBarRFull + sr);
                         bar_expect_tx(fb, bytes);
@@ -559,7 +586,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                         const __half *t0 = reinterpret_cast<const __half *>(stage);
                         const unsigned char *ea = stage + 6 * np;
                         for (int p = pt; p < np; p += 64) {
-                            const uint32_t code = P.pos[p0 + p];
+                            const uint32_t code = spos[p0 + p];
                             const int n = int(code >> 8), q = bb * kDirs + int(code & 255);
                             __half v0 = __float2half_rn(0.0f), v1 = v0, v2 = v0;
                             if (valid) {
@@ -823,6 +850,7 @@ int sm_count()
 
 size_t tcx_state_bytes(int64_t V) { return size_t(V) * kXTileBytes; }
 int tc_stage_limit() { return kAStageMax; }
+int tc_position_limit() { return kPosMax; }
 
 cudaError_t launch_tc_flags(const SlicedMatrix &A, int64_t V, uint8_t *flags, cudaStream_t s)
 {
