@@ -56,10 +56,15 @@ constexpr int kTcK = 32;                      // directions padded to the K exte
 constexpr int kN = 80;                        // three outputs x 26 rows, padded
 constexpr int kXTileBytes = 8192;             // 128 rows x 32 directions x fp16
 constexpr int kExpDir = 26;                   // direction slot holding Ex of a state row
-constexpr int kB01 = 4 * 20 * 128;            // K 32 x N 160 (a0 | a1)
-constexpr int kB2 = 4 * 10 * 128;             // K 32 x N 80 (a2)
+// B operand tiles, K-major core matrices; consecutive direction groups are
+// 16 bytes further apart than a whole group of core matrices, so the stores
+// of one direction row to different groups fall in different banks
+constexpr int kLbo01 = 20 * 128 + 16;         // K step of the (a0 | a1) tile, N 160
+constexpr int kLbo2 = 10 * 128 + 16;          // K step of the a2 tile, N 80
+constexpr int kB01 = 4 * kLbo01;              // K 32 x N 160 (a0 | a1)
+constexpr int kB2 = 4 * kLbo2;                // K 32 x N 80 (a2)
 constexpr int kBScale = kN * 4;               // 2^Ea per packed column
-constexpr int kBSlot = 15744;                 // kB01 + kB2 + kBScale rounded to 128
+constexpr int kBSlot = 15872;                 // kB01 + kB2 + kBScale rounded to 128
 constexpr int kLines = 9;
 constexpr int kAStageMax = 9216;              // A chunks of one tile
 constexpr int kRingSlot = kXTileBytes + kAStageMax;
@@ -458,8 +463,8 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
 #pragma unroll
                         for (int kk = 0; kk < 2; ++kk) {
                             const uint64_t ad = smem_desc(xa + kk * 4096, 2048, 128);
-                            mma_f16(d, ad, smem_desc(ba + kk * 5120, 2560, 128), id1, kk);
-                            mma_f16(d + kN, ad, smem_desc(ba + kB01 + kk * 2560, 1280, 128), id2, 1);
+                            mma_f16(d, ad, smem_desc(ba + kk * 2 * kLbo01, kLbo01, 128), id1, kk);
+                            mma_f16(d + kN, ad, smem_desc(ba + kB01 + kk * 2 * kLbo2, kLbo2, 128), id2, 1);
                         }
                         mma_commit(bars + 8 * (kBarREmpty + sr));
                         mma_commit(bars + 8 * (kBarBEmpty + L));
@@ -585,23 +590,33 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                         const bool valid = j >= 0 && j < nx;
                         const __half *t0 = reinterpret_cast<const __half *>(stage);
                         const unsigned char *ea = stage + 6 * np;
-                        for (int p = pt; p < np; p += 64) {
-                            const uint32_t code = spos[p0 + p];
-                            const int n = int(code >> 8), q = bb * kDirs + int(code & 255);
-                            __half v0 = __float2half_rn(0.0f), v1 = v0, v2 = v0;
-                            if (valid) {
-                                v0 = t0[p];
-                                v1 = t0[np + p];
-                                v2 = t0[2 * np + p];
+                        // four positions per iteration: their loads are issued before any store
+                        for (int p = pt; p < np; p += 4 * 64) {
+                            uint32_t code[4];
+                            __half v0[4], v1[4], v2[4];
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const int pk = p + 64 * k;
+                                code[k] = pk < np ? uint32_t(spos[p0 + pk]) : 0xFFFFu;
+                                v0[k] = v1[k] = v2[k] = __float2half_rn(0.0f);
+                                if (valid && pk < np) {
+                                    v0[k] = t0[pk];
+                                    v1[k] = t0[np + pk];
+                                    v2[k] = t0[2 * np + pk];
+                                }
                             }
-                            const int within = (q & 7) * 16 + (n & 7) * 2;
-                            *reinterpret_cast<__half *>(slot + ((n >> 3) * 20 + (q >> 3)) * 128 + within) = v0;
-                            *reinterpret_cast<__half *>(slot + ((n >> 3) * 20 + 10 + (q >> 3)) * 128 + within) = v1;
-                            *reinterpret_cast<__half *>(slot + kB01 + ((n >> 3) * 10 + (q >> 3)) * 128 + within) = v2;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                if (code[k] == 0xFFFFu) continue;
+                                const int n = int(code[k] >> 8), q = bb * kDirs + int(code[k] & 255);
+                                const int within = (q >> 3) * 128 + (q & 7) * 16 + (n & 7) * 2;
+                                *reinterpret_cast<__half *>(slot + (n >> 3) * kLbo01 + within) = v0[k];
+                                *reinterpret_cast<__half *>(slot + (n >> 3) * kLbo01 + 10 * 128 + within) = v1[k];
+                                *reinterpret_cast<__half *>(slot + kB01 + (n >> 3) * kLbo2 + within) = v2[k];
+                            }
                         }
                         if (pt < kDirs) scale[bb * kDirs + pt] = valid ? ldexpf(1.0f, int(ea[pt]) - kExpBias) : 0.0f;
-                        if (valid) stage += P.chunk_off[d + 1] - P.chunk_off[d];
-                        else stage += P.chunk_off[d + 1] - P.chunk_off[d];
+                        stage += P.chunk_off[d + 1] - P.chunk_off[d];
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     bar_arrive(bars + 8 * (kBarBFull + L));
