@@ -76,7 +76,8 @@ constexpr int kOffPos = kOffBar + 512;                     // the union position
 constexpr int kPosMax = 5888;                              // positions (padded) the table holds
 constexpr int kSmemBytes = kOffPos + kPosMax * 2;
 constexpr int kPrefetch = 8;                               // tiles whose data is pulled into L2 ahead
-constexpr int kThreads = 256;
+constexpr int kProducers = 128;               // threads expanding A into the B tiles (warps 6..9)
+constexpr int kThreads = 192 + kProducers;
 constexpr int kTmemCols = 512;
 constexpr int kDCols = 160;
 constexpr int kExpBias = 160;                 // A row exponents are stored as Ea + 160 (uint8)
@@ -348,7 +349,7 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, const
     return true;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
+__global__ void __maxnreg__(200) tcx_step_kernel(StepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -369,12 +370,12 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     for (int i = tid; i < P.role_off[kOffs]; i += kThreads) spos[i] = P.pos[i];
     if (tid == 0) {
         for (int L = 0; L < kLines; ++L) {
-            bar_init(bars + 8 * (kBarBFull + L), 64);
+            bar_init(bars + 8 * (kBarBFull + L), kProducers);
             bar_init(bars + 8 * (kBarBEmpty + L), 1 + 128);     // MMA done + epilogue read the scales
         }
         for (int sl = 0; sl < kRing; ++sl) {
             bar_init(bars + 8 * (kBarRFull + sl), 1);
-            bar_init(bars + 8 * (kBarREmpty + sl), 1 + 64 + 128);   // MMA + A scattered + scales read
+            bar_init(bars + 8 * (kBarREmpty + sl), 1 + kProducers + 128);   // MMA + A scattered + scales read
         }
         for (int b = 0; b < 2; ++b) {
             bar_init(bars + 8 * (kBarDFull + b), 1);
@@ -552,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             }
         }
     } else {
-        // ---- B operand tiles from the staged A chunks (64 threads) ----
+        // ---- B operand tiles from the staged A chunks (kProducers threads) ----
         const int pt = tid - 192;
         int u[kLines] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
         int64_t tau = 0;
@@ -573,7 +574,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                         *abort = 1;
                         atomicExch(a.err, 1);
                     }
-                    named_sync(2, 64);
+                    named_sync(2, kProducers);
                     if (failed[1]) {
                         ok = false;
                         break;
@@ -591,12 +592,12 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                         const __half *t0 = reinterpret_cast<const __half *>(stage);
                         const unsigned char *ea = stage + 6 * np;
                         // four positions per iteration: their loads are issued before any store
-                        for (int p = pt; p < np; p += 4 * 64) {
+                        for (int p = pt; p < np; p += 4 * kProducers) {
                             uint32_t code[4];
                             __half v0[4], v1[4], v2[4];
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
-                                const int pk = p + 64 * k;
+                                const int pk = p + kProducers * k;
                                 code[k] = pk < np ? uint32_t(spos[p0 + pk]) : 0xFFFFu;
                                 v0[k] = v1[k] = v2[k] = __float2half_rn(0.0f);
                                 if (valid && pk < np) {
