@@ -349,7 +349,7 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, const
     return true;
 }
 
-__global__ void __maxnreg__(200) tcx_step_kernel(StepArgs a)
+__global__ void __maxnreg__(192) tcx_step_kernel(StepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
