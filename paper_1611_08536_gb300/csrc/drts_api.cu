@@ -340,7 +340,7 @@ int fit_blocks(drts_ctx *c, int threads, int variant, int rhs_tile)
     if (c->tc) {
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        return sms * tc_blocks_per_sm();
+        return sms * tc_blocks_per_sm(nullptr);
     }
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -422,7 +422,8 @@ drts_status setup_tensor_core(drts_ctx *c)
         (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
         return cuda_fail(c, e, "tensor-core matrix conversion");
     drelease(c, dpidx);
-    if (tc_blocks_per_sm() < 1) return fail(c, DRTS_ECUDA, "tensor-core step kernel does not fit on an SM");
+    std::string why;
+    if (tc_blocks_per_sm(&why) < 1) return fail(c, DRTS_ECUDA, "tensor-core step kernel does not fit on an SM (" + why + ")");
     return DRTS_OK;
 }
 

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <string>
 
 #include "drts_internal.h"
 
@@ -194,7 +195,7 @@ cudaError_t launch_batched_step(const StepArgs &a, int n_rhs, int rhs_tile, int 
 size_t tcx_state_bytes(int64_t V);
 int tc_stage_limit();
 int tc_position_limit();
-int tc_blocks_per_sm();
+int tc_blocks_per_sm(std::string *why);
 cudaError_t launch_tc_flags(const SlicedMatrix &A, int64_t V, uint8_t *flags, cudaStream_t s);
 cudaError_t launch_tc_convert(const SlicedMatrix &A, int64_t V, const int16_t *pidx, const TcPlan &P,
                               void *Au, cudaStream_t s);

@@ -46,6 +46,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "drts_device.cuh"
 #include "drts_kernel_common.cuh"
 
@@ -76,7 +78,7 @@ constexpr int kOffPos = kOffBar + 512;                     // the union position
 constexpr int kPosMax = 5888;                              // positions (padded) the table holds
 constexpr int kSmemBytes = kOffPos + kPosMax * 2;
 constexpr int kPrefetch = 8;                               // tiles whose data is pulled into L2 ahead
-constexpr int kProducers = 128;               // threads expanding A into the B tiles (warps 6..9)
+constexpr int kProducers = 192;               // threads expanding A into the B tiles (warps 6..11)
 constexpr int kThreads = 192 + kProducers;
 constexpr int kTmemCols = 512;
 constexpr int kDCols = 160;
@@ -349,7 +351,7 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, const
     return true;
 }
 
-__global__ void __maxnreg__(192) tcx_step_kernel(StepArgs a)
+__global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
 {
     extern __shared__ __align__(1024) unsigned char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -883,25 +885,39 @@ cudaError_t launch_tc_convert(const SlicedMatrix &A, int64_t V, const int16_t *p
     return cudaGetLastError();
 }
 
-int tc_blocks_per_sm()
+int tc_blocks_per_sm(std::string *why)
 {
     static bool attr[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
         cudaGetLastError();
+        if (why) *why = "no current device";
         return 0;
     }
     if (!attr[dev]) {
-        if (cudaFuncSetAttribute(tcx_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) !=
-            cudaSuccess) {
+        const cudaError_t e = cudaFuncSetAttribute(tcx_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   kSmemBytes);
+        if (e != cudaSuccess) {
             cudaGetLastError();
+            if (why) *why = std::string("shared memory opt-in of ") + std::to_string(kSmemBytes) + " bytes: " +
+                            cudaGetErrorString(e);
             return 0;
         }
         attr[dev] = true;
     }
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tcx_step_kernel, kThreads, kSmemBytes) != cudaSuccess) {
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, tcx_step_kernel, kThreads, kSmemBytes);
+    if (e != cudaSuccess || n < 1) {
         cudaGetLastError();
+        if (why) {
+            cudaFuncAttributes fa{};
+            cudaFuncGetAttributes(&fa, tcx_step_kernel);
+            cudaGetLastError();
+            *why = std::string("occupancy ") + (e == cudaSuccess ? "0" : cudaGetErrorString(e)) + ": " +
+                   std::to_string(kThreads) + " threads x " + std::to_string(fa.numRegs) + " registers, " +
+                   std::to_string(kSmemBytes) + " + " + std::to_string(fa.sharedSizeBytes) +
+                   " bytes shared, kernel max threads " + std::to_string(fa.maxThreadsPerBlock);
+        }
         return 0;
     }
     return n;
@@ -918,7 +934,7 @@ cudaError_t launch_tc_step(const StepArgs &a, bool functionals, cudaStream_t s)
         tcx_ledger_kernel<<<unsigned(sm_count() * 4), 256, 0, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (tc_blocks_per_sm() < 1) return cudaErrorInvalidConfiguration;
+    if (tc_blocks_per_sm(nullptr) < 1) return cudaErrorInvalidConfiguration;
     const int64_t n_lines = int64_t(a.ny) * a.nz;
     const int grid = int(n_lines < sm_count() ? n_lines : sm_count());
     tcx_step_kernel<<<grid, kThreads, kSmemBytes, s>>>(a);
