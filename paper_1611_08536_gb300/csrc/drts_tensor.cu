@@ -82,14 +82,15 @@ constexpr int kProducers = 192;               // threads expanding A into the B 
 constexpr int kThreads = 192 + kProducers;
 constexpr int kTmemCols = 512;
 constexpr int kDCols = 160;
+constexpr int kDBufs = 3;                     // accumulator buffers in tensor memory (480 of 512 columns)
 constexpr int kExpBias = 160;                 // A row exponents are stored as Ea + 160 (uint8)
 
 static_assert(kB01 + kB2 + kBScale <= kBSlot, "B slot");
 static_assert(kSmemBytes <= 232448, "shared memory");
 
 // barrier indices (8 bytes each at kOffBar)
-constexpr int kBarBFull = 0, kBarBEmpty = 9, kBarRFull = 18, kBarREmpty = 22, kBarDFull = 26, kBarDEmpty = 28;
-constexpr int kNumBars = 30;
+constexpr int kBarBFull = 0, kBarBEmpty = 9, kBarRFull = 18, kBarREmpty = 22, kBarDFull = 26, kBarDEmpty = 29;
+constexpr int kNumBars = 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
@@ -320,7 +321,7 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, const
 {
     for (int li = 0; li < nL; ++li) {
         const int L = Ls[li];
-        const int b = int(tau & 1);
+        const int b = int(tau % kDBufs);
         const int sr = int(tau % kRing);
         // every thread waits; a give-up anywhere is shared so the four warps agree
         float qx = 0.0f;
@@ -328,12 +329,13 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, const
             // the state tile's row scale 2^Ex, from the staged copy
             const __half *xt = reinterpret_cast<const __half *>(sm + kOffRing + sr * kRingSlot);
             qx = ldexpf(1.0f, int(__half2float(xt[xtile_elem(rhs, kExpDir)])));
+            bar_arrive(bars + 8 * (kBarREmpty + sr));      // the state tile's scales are read
         } else {
             *failed = 1;
             *abort = 1;
             atomicExch(a.err, 1);
         }
-        if (!bar_wait(bars + 8 * (kBarDFull + b), uint32_t((tau >> 1) & 1), a.spin_limit, abort)) {
+        if (!bar_wait(bars + 8 * (kBarDFull + b), uint32_t((tau / kDBufs) & 1), a.spin_limit, abort)) {
             *failed = 1;
             *abort = 1;
             atomicExch(a.err, 1);
@@ -345,7 +347,6 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, const
         tc_fence_before();
         bar_arrive(bars + 8 * (kBarDEmpty + b));
         bar_arrive(bars + 8 * (kBarBEmpty + L));       // the B slot's scales are read
-        bar_arrive(bars + 8 * (kBarREmpty + sr));      // the state tile's scales are read
         ++tau;
     }
     return true;
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             bar_init(bars + 8 * (kBarRFull + sl), 1);
             bar_init(bars + 8 * (kBarREmpty + sl), 1 + kProducers + 128);   // MMA + A scattered + scales read
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kDBufs; ++b) {
             bar_init(bars + 8 * (kBarDFull + b), 1);
             bar_init(bars + 8 * (kBarDEmpty + b), 128);
         }
@@ -455,10 +456,11 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                 for (int c = 0; c < nx && ok; ++c)
                     for (int li = 0; li < nL && ok; ++li) {
                         const int L = Ls[li];
-                        const int sr = int(tau % kRing), b = int(tau & 1);
+                        const int sr = int(tau % kRing), b = int(tau % kDBufs);
                         ok = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), limit, abort) &&
                              bar_wait(bars + 8 * (kBarBFull + L), uint32_t(u[L] & 1), limit, abort) &&
-                             (tau < 2 || bar_wait(bars + 8 * (kBarDEmpty + b), uint32_t(((tau >> 1) - 1) & 1), limit, abort));
+                             (tau < kDBufs ||
+                              bar_wait(bars + 8 * (kBarDEmpty + b), uint32_t(((tau / kDBufs) - 1) & 1), limit, abort));
                         if (!ok) break;
                         tc_fence_after();
                         const uint32_t d = tmem + uint32_t(b * kDCols);
@@ -484,7 +486,8 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             if (tau > 0) {
                 const int64_t last = tau - 1;
                 uint32_t spins = 0;
-                while (!bar_test(bars + 8 * (kBarDFull + int(last & 1)), uint32_t((last >> 1) & 1)) && spins < limit)
+                while (!bar_test(bars + 8 * (kBarDFull + int(last % kDBufs)), uint32_t((last / kDBufs) & 1)) &&
+                       spins < limit)
                     ++spins;
             }
         }
