@@ -319,34 +319,43 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, const
                                            unsigned char *sm, uint32_t bars, int64_t &tau, volatile int *abort,
                                            volatile int *failed, int rhs)
 {
+    const bool leader = (threadIdx.x & 31) == 0;
     for (int li = 0; li < nL; ++li) {
         const int L = Ls[li];
         const int b = int(tau % kDBufs);
         const int sr = int(tau % kRing);
-        // every thread waits; a give-up anywhere is shared so the four warps agree
-        float qx = 0.0f;
-        if (bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), a.spin_limit, abort)) {
-            // the state tile's row scale 2^Ex, from the staged copy
-            const __half *xt = reinterpret_cast<const __half *>(sm + kOffRing + sr * kRingSlot);
-            qx = ldexpf(1.0f, int(__half2float(xt[xtile_elem(rhs, kExpDir)])));
-            bar_arrive(bars + 8 * (kBarREmpty + sr));      // the state tile's scales are read
-        } else {
+        // lane 0 of each warp waits; a give-up anywhere is shared so the four warps agree
+        if (leader && !bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), a.spin_limit, abort)) {
             *failed = 1;
             *abort = 1;
             atomicExch(a.err, 1);
         }
-        if (!bar_wait(bars + 8 * (kBarDFull + b), uint32_t((tau / kDBufs) & 1), a.spin_limit, abort)) {
-            *failed = 1;
-            *abort = 1;
-            atomicExch(a.err, 1);
+        __syncwarp();
+        float qx = 0.0f;
+        if (!*failed) {
+            // the state tile's row scale 2^Ex, from the staged copy
+            const __half *xt = reinterpret_cast<const __half *>(sm + kOffRing + sr * kRingSlot);
+            qx = ldexpf(1.0f, int(__half2float(xt[xtile_elem(rhs, kExpDir)])));
+        }
+        __syncwarp();
+        if (leader) {
+            bar_arrive(bars + 8 * (kBarREmpty + sr));  // this warp's scales are read
+            if (!*failed && !bar_wait(bars + 8 * (kBarDFull + b), uint32_t((tau / kDBufs) & 1), a.spin_limit, abort)) {
+                *failed = 1;
+                *abort = 1;
+                atomicExch(a.err, 1);
+            }
         }
         named_sync(1, 128);
         if (*failed) return false;
         tc_fence_after();
         drain_tile<ROT>(s, tmem_q, b, qx, reinterpret_cast<const float *>(sm + L * kBSlot + kB01 + kB2));
         tc_fence_before();
-        bar_arrive(bars + 8 * (kBarDEmpty + b));
-        bar_arrive(bars + 8 * (kBarBEmpty + L));       // the B slot's scales are read
+        __syncwarp();
+        if (leader) {
+            bar_arrive(bars + 8 * (kBarDEmpty + b));
+            bar_arrive(bars + 8 * (kBarBEmpty + L));   // the B slot's scales are read
+        }
         ++tau;
     }
     return true;
@@ -373,16 +382,16 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     for (int i = tid; i < P.role_off[kOffs]; i += kThreads) spos[i] = P.pos[i];
     if (tid == 0) {
         for (int L = 0; L < kLines; ++L) {
-            bar_init(bars + 8 * (kBarBFull + L), kProducers);
-            bar_init(bars + 8 * (kBarBEmpty + L), 1 + 128);     // MMA done + epilogue read the scales
+            bar_init(bars + 8 * (kBarBFull + L), 1);            // producers, after their own barrier
+            bar_init(bars + 8 * (kBarBEmpty + L), 1 + 4);       // MMA done + each epilogue warp read the scales
         }
         for (int sl = 0; sl < kRing; ++sl) {
             bar_init(bars + 8 * (kBarRFull + sl), 1);
-            bar_init(bars + 8 * (kBarREmpty + sl), 1 + kProducers + 128);   // MMA + A scattered + scales read
+            bar_init(bars + 8 * (kBarREmpty + sl), 1 + 1 + 4);  // MMA + A scattered + each epilogue warp
         }
         for (int b = 0; b < kDBufs; ++b) {
             bar_init(bars + 8 * (kBarDFull + b), 1);
-            bar_init(bars + 8 * (kBarDEmpty + b), 128);
+            bar_init(bars + 8 * (kBarDEmpty + b), 4);           // each epilogue warp
         }
         *abort = 0;
         failed[0] = 0;
@@ -571,13 +580,15 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                 for (int li = 0; li < nL && ok; ++li) {
                     const int L = Ls[li];
                     const int sr = int(tau % kRing);
-                    bool w = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), limit, abort);
-                    if (w && u[L] >= 1)
-                        w = bar_wait(bars + 8 * (kBarBEmpty + L), uint32_t((u[L] - 1) & 1), limit, abort);
-                    if (!w) {
-                        failed[1] = 1;
-                        *abort = 1;
-                        atomicExch(a.err, 1);
+                    if (lane == 0) {
+                        bool w = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), limit, abort);
+                        if (w && u[L] >= 1)
+                            w = bar_wait(bars + 8 * (kBarBEmpty + L), uint32_t((u[L] - 1) & 1), limit, abort);
+                        if (!w) {
+                            failed[1] = 1;
+                            *abort = 1;
+                            atomicExch(a.err, 1);
+                        }
                     }
                     named_sync(2, kProducers);
                     if (failed[1]) {
@@ -624,9 +635,14 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                         if (pt < kDirs) scale[bb * kDirs + pt] = valid ? ldexpf(1.0f, int(ea[pt]) - kExpBias) : 0.0f;
                         stage += P.chunk_off[d + 1] - P.chunk_off[d];
                     }
+                    // every producer's stores are made visible to the tensor cores, then
+                    // one thread signals for all of them
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bar_arrive(bars + 8 * (kBarBFull + L));
-                    bar_arrive(bars + 8 * (kBarREmpty + sr));
+                    named_sync(2, kProducers);
+                    if (pt == 0) {
+                        bar_arrive(bars + 8 * (kBarBFull + L));
+                        bar_arrive(bars + 8 * (kBarREmpty + sr));
+                    }
                     ++u[L];
                     ++tau;
                 }
