@@ -303,25 +303,29 @@ __device__ __forceinline__ void finalize(EpiState &s, const StepArgs &a, float *
     zero_slot<SLOT>(s);
 }
 
-// Valid input lines (dy, dz) of output line (y, z), in role order L = (dz+1)*3 + (dy+1).
-__device__ __forceinline__ int line_roles(int y, int z, int ny, int nz, int *Ls)
+// Valid input lines (dy, dz) of output line (y, z) as a bit mask over the
+// role order L = (dz+1)*3 + (dy+1).  (Masks, not arrays: small arrays indexed
+// at run time live in local memory, which the large shared-memory carve-out
+// leaves almost no L1 for.)
+__device__ __forceinline__ uint32_t line_mask(int y, int z, int ny, int nz)
 {
-    int n = 0;
+    uint32_t mask = 0;
+#pragma unroll
     for (int L = 0; L < kLines; ++L) {
         const int dy = L % 3 - 1, dz = L / 3 - 1;
-        if (y + dy >= 0 && y + dy < ny && z + dz >= 0 && z + dz < nz) Ls[n++] = L;
+        if (y + dy >= 0 && y + dy < ny && z + dz >= 0 && z + dz < nz) mask |= 1u << L;
     }
-    return n;
+    return mask;
 }
 
 template <int ROT>
-__device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, const int *Ls, int nL, uint32_t tmem_q,
+__device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, uint32_t lmask, uint32_t tmem_q,
                                            unsigned char *sm, uint32_t bars, int64_t &tau, volatile int *abort,
                                            volatile int *failed, int rhs)
 {
     const bool leader = (threadIdx.x & 31) == 0;
-    for (int li = 0; li < nL; ++li) {
-        const int L = Ls[li];
+    for (int L = 0; L < kLines; ++L) {
+        if (!((lmask >> L) & 1u)) continue;
         const int b = int(tau % kDBufs);
         const int sr = int(tau % kRing);
         // lane 0 of each warp waits; a give-up anywhere is shared so the four warps agree
@@ -371,6 +375,8 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     volatile int *failed = reinterpret_cast<volatile int *>(sm + kOffBar + 8 * kNumBars + 8);
     float *xch = reinterpret_cast<float *>(sm + kOffXch);
     uint16_t *spos = reinterpret_cast<uint16_t *>(sm + kOffPos);
+    int *s_roff = reinterpret_cast<int *>(sm + kOffBar + 288);      // role position offsets [28]
+    int *s_coff = s_roff + 28;                                       // role chunk byte offsets [28]
     const TcPlan &P = a.tcp;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int64_t n_lines = int64_t(ny) * nz;
@@ -380,6 +386,10 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     // B tiles start at zero; positions outside the union are never written
     for (int i = tid; i < kLines * kBSlot / 16; i += kThreads) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
     for (int i = tid; i < P.role_off[kOffs]; i += kThreads) spos[i] = P.pos[i];
+    for (int i = tid; i < 28; i += kThreads) {
+        s_roff[i] = P.role_off[i];
+        s_coff[i] = P.chunk_off[i];
+    }
     if (tid == 0) {
         for (int L = 0; L < kLines; ++L) {
             bar_init(bars + 8 * (kBarBFull + L), 1);            // producers, after their own barrier
@@ -423,26 +433,25 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
         bool ok = true;
         for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
             const int y = int(line % ny), z = int(line / ny);
-            int Ls[kLines];
-            const int nL = line_roles(y, z, ny, nz, Ls);
+            const uint32_t lmask = line_mask(y, z, ny, nz);
             const int64_t row0 = (int64_t(z) * ny + y) * nx;
             for (int c = 0; c < nx && ok; ++c) {
                 switch (c % 3) {
                 case 0:
-                    ok = epi_column<0>(s, a, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
+                    ok = epi_column<0>(s, a, lmask, tmem_q, sm, bars, tau, abort, failed, rhs);
                     if (!ok) break;
                     if (c >= 1) finalize<2>(s, a, xch, warp, lane, row0 + c - 1);
                     else zero_slot<2>(s);
                     if (c == nx - 1) { finalize<0>(s, a, xch, warp, lane, row0 + c); zero_slot<1>(s); }
                     break;
                 case 1:
-                    ok = epi_column<1>(s, a, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
+                    ok = epi_column<1>(s, a, lmask, tmem_q, sm, bars, tau, abort, failed, rhs);
                     if (!ok) break;
                     finalize<0>(s, a, xch, warp, lane, row0 + c - 1);
                     if (c == nx - 1) { finalize<1>(s, a, xch, warp, lane, row0 + c); zero_slot<2>(s); }
                     break;
                 default:
-                    ok = epi_column<2>(s, a, Ls, nL, tmem_q, sm, bars, tau, abort, failed, rhs);
+                    ok = epi_column<2>(s, a, lmask, tmem_q, sm, bars, tau, abort, failed, rhs);
                     if (!ok) break;
                     finalize<1>(s, a, xch, warp, lane, row0 + c - 1);
                     if (c == nx - 1) { finalize<2>(s, a, xch, warp, lane, row0 + c); zero_slot<0>(s); }
@@ -456,18 +465,17 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             const uint32_t id1 = idesc_f16(128, 2 * kN), id2 = idesc_f16(128, kN);
             const uint32_t ring0 = smem_u32(sm + kOffRing), bs0 = smem_u32(sm);
             int64_t tau = 0;
-            int u[kLines] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            uint32_t upar = 0;                      // parity of each B slot's uses
             bool ok = true;
             for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
                 const int y = int(line % ny), z = int(line / ny);
-                int Ls[kLines];
-                const int nL = line_roles(y, z, ny, nz, Ls);
+                const uint32_t lmask = line_mask(y, z, ny, nz);
                 for (int c = 0; c < nx && ok; ++c)
-                    for (int li = 0; li < nL && ok; ++li) {
-                        const int L = Ls[li];
+                    for (int L = 0; L < kLines && ok; ++L) {
+                        if (!((lmask >> L) & 1u)) continue;
                         const int sr = int(tau % kRing), b = int(tau % kDBufs);
                         ok = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), limit, abort) &&
-                             bar_wait(bars + 8 * (kBarBFull + L), uint32_t(u[L] & 1), limit, abort) &&
+                             bar_wait(bars + 8 * (kBarBFull + L), (upar >> L) & 1u, limit, abort) &&
                              (tau < kDBufs ||
                               bar_wait(bars + 8 * (kBarDEmpty + b), uint32_t(((tau / kDBufs) - 1) & 1), limit, abort));
                         if (!ok) break;
@@ -483,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                         mma_commit(bars + 8 * (kBarREmpty + sr));
                         mma_commit(bars + 8 * (kBarBEmpty + L));
                         mma_commit(bars + 8 * (kBarDFull + b));
-                        ++u[L];
+                        upar ^= 1u << L;
                         ++tau;
                     }
             }
@@ -510,20 +518,19 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             bool ok = true;
             for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
                 const int y = int(line % ny), z = int(line / ny);
-                int Ls[kLines];
-                const int nL = line_roles(y, z, ny, nz, Ls);
+                const uint32_t lmask = line_mask(y, z, ny, nz);
                 const int64_t row0 = (int64_t(z) * ny + y) * nx;
                 for (int c = 0; c < 3 && c < nx; ++c) {
                     l2_prefetch(Au + (row0 + c) * P.voxel_bytes, uint32_t(P.voxel_bytes));
-                    for (int li = 0; li < nL && c < 2; ++li) {
-                        const int L = Ls[li];
+                    for (int L = 0; L < kLines && c < 2; ++L) {
+                        if (!((lmask >> L) & 1u)) continue;
                         l2_prefetch(x + ((int64_t(z + L / 3 - 1) * ny + (y + L % 3 - 1)) * nx + c) * (kXTileBytes / 2),
                                     kXTileBytes);
                     }
                 }
                 for (int c = 0; c < nx && ok; ++c)
-                    for (int li = 0; li < nL && ok; ++li) {
-                        const int L = Ls[li];
+                    for (int L = 0; L < kLines && ok; ++L) {
+                        if (!((lmask >> L) & 1u)) continue;
                         const int sr = int(tau % kRing);
                         if (tau >= kRing &&
                             !bar_wait(bars + 8 * (kBarREmpty + sr), uint32_t(((tau / kRing) - 1) & 1), limit, abort)) {
@@ -537,13 +544,13 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                         for (int bb = 0; bb < 3; ++bb) {
                             const int d = 3 * L + 2 - bb;
                             const int j = c - 1 + bb;
-                            chunk_len[bb] = (j >= 0 && j < nx) ? P.chunk_off[d + 1] - P.chunk_off[d] : 0;
+                            chunk_len[bb] = (j >= 0 && j < nx) ? s_coff[d + 1] - s_coff[d] : 0;
                             bytes += uint32_t(chunk_len[bb]);
                         }
                         // pull data two columns ahead into L2: the state tile of this line,
                         // and once per column the whole A of the voxel three columns on
                         if (c + 2 < nx) l2_prefetch(x + (vi + 2) * (kXTileBytes / 2), kXTileBytes);
-                        if (li == 0 && c + 3 < nx)
+                        if (L == __ffs(lmask) - 1 && c + 3 < nx)
                             l2_prefetch(Au + (row0 + c + 3) * P.voxel_bytes, uint32_t(P.voxel_bytes));
                         const uint32_t slot = ring0 + sr * kRingSlot;
                         const uint32_t fb = bars + 8 * (kBarRFull + sr);
@@ -554,9 +561,9 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                             const int d = 3 * L + 2 - bb;
                             if (chunk_len[bb] > 0)
                                 bulk_load(slot + kXTileBytes + stage,
-                                          Au + (row0 + c - 1 + bb) * P.voxel_bytes + P.chunk_off[d],
+                                          Au + (row0 + c - 1 + bb) * P.voxel_bytes + s_coff[d],
                                           uint32_t(chunk_len[bb]), fb);
-                            stage += uint32_t(P.chunk_off[d + 1] - P.chunk_off[d]);
+                            stage += uint32_t(s_coff[d + 1] - s_coff[d]);
                         }
                         ++tau;
                     }
@@ -569,21 +576,20 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     } else {
         // ---- B operand tiles from the staged A chunks (kProducers threads) ----
         const int pt = tid - 192;
-        int u[kLines] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        uint32_t upar = 0, used = 0;            // parity of each B slot's uses, slots used
         int64_t tau = 0;
         bool ok = true;
         for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
             const int y = int(line % ny), z = int(line / ny);
-            int Ls[kLines];
-            const int nL = line_roles(y, z, ny, nz, Ls);
+            const uint32_t lmask = line_mask(y, z, ny, nz);
             for (int c = 0; c < nx && ok; ++c)
-                for (int li = 0; li < nL && ok; ++li) {
-                    const int L = Ls[li];
+                for (int L = 0; L < kLines && ok; ++L) {
+                    if (!((lmask >> L) & 1u)) continue;
                     const int sr = int(tau % kRing);
                     if (lane == 0) {
                         bool w = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), limit, abort);
-                        if (w && u[L] >= 1)
-                            w = bar_wait(bars + 8 * (kBarBEmpty + L), uint32_t((u[L] - 1) & 1), limit, abort);
+                        if (w && ((used >> L) & 1u))
+                            w = bar_wait(bars + 8 * (kBarBEmpty + L), ((upar >> L) & 1u) ^ 1u, limit, abort);
                         if (!w) {
                             failed[1] = 1;
                             *abort = 1;
@@ -603,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                         const int j = c - 1 + bb;
                         // input voxel (c, line L) is neighbour (1 - bb, L) of output j
                         const int d = 3 * L + 2 - bb;
-                        const int p0 = P.role_off[d], np = P.role_off[d + 1] - p0;
+                        const int p0 = s_roff[d], np = s_roff[d + 1] - p0;
                         const bool valid = j >= 0 && j < nx;
                         const __half *t0 = reinterpret_cast<const __half *>(stage);
                         const unsigned char *ea = stage + 6 * np;
@@ -633,7 +639,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                             }
                         }
                         if (pt < kDirs) scale[bb * kDirs + pt] = valid ? ldexpf(1.0f, int(ea[pt]) - kExpBias) : 0.0f;
-                        stage += P.chunk_off[d + 1] - P.chunk_off[d];
+                        stage += s_coff[d + 1] - s_coff[d];
                     }
                     // every producer's stores are made visible to the tensor cores, then
                     // one thread signals for all of them
@@ -643,7 +649,8 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                         bar_arrive(bars + 8 * (kBarBFull + L));
                         bar_arrive(bars + 8 * (kBarREmpty + sr));
                     }
-                    ++u[L];
+                    upar ^= 1u << L;
+                    used |= 1u << L;
                     ++tau;
                 }
         }
