@@ -199,6 +199,20 @@ __device__ __forceinline__ double tc_source_value(const StepArgs &a, const Sourc
     return 0.0;
 }
 
+// 2^k for -126 <= k <= 127 built from its bit pattern (exact), else 0 /
+// infinity-free fallbacks through two factors
+__device__ __forceinline__ float pow2f(int k)
+{
+    k = k < -126 ? -126 : (k > 127 ? 127 : k);
+    return __int_as_float((k + 127) << 23);
+}
+// y * 2^k exactly for |k| <= 252 (two power-of-two factors, no intermediate overflow)
+__device__ __forceinline__ float scale2(float y, int k)
+{
+    const int k1 = k / 2;
+    return (y * pow2f(k1)) * pow2f(k - k1);
+}
+
 // Write row pair r / 64 + r of a state tile from y: Ex from the largest |y|
 // (|y| 2^-Ex < 256), x0 = rint(y 2^-Ex) (exact in fp16), x1 = fp16(y 2^-Ex - x0),
 // Ex itself (an integer, exact in fp16) at direction 26 of row r.
@@ -218,7 +232,7 @@ __device__ __forceinline__ void write_state_row(__half *tile, int r, const float
             const int n = g * 8 + k;
             float x0 = 0.0f, x1 = 0.0f;
             if (n < kDirs) {
-                const float ys = ldexpf(y[n], -ex);     // exact, |ys| < 256
+                const float ys = scale2(y[n], -ex);     // exact, |ys| < 256
                 x0 = rintf(ys);
                 x1 = ys - x0;                           // exact, |x1| <= 1/2
             } else if (n == kExpDir) {
@@ -339,7 +353,7 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, uint3
         if (!*failed) {
             // the state tile's row scale 2^Ex, from the staged copy
             const __half *xt = reinterpret_cast<const __half *>(sm + kOffRing + sr * kRingSlot);
-            qx = ldexpf(1.0f, int(__half2float(xt[xtile_elem(rhs, kExpDir)])));
+            qx = scale2(1.0f, int(__half2float(xt[xtile_elem(rhs, kExpDir)])));
         }
         __syncwarp();
         if (leader) {
@@ -574,8 +588,10 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             }
         }
     } else {
-        // ---- B operand tiles from the staged A chunks (kProducers threads) ----
-        const int pt = tid - 192;
+        // ---- B operand tiles from the staged A chunks: producer warp w expands
+        // the tiles tau = w (mod kProducers / 32), one warp per tile, so several
+        // tiles are expanded at once ----
+        const int pw = warp - 6, npw = kProducers / 32;
         uint32_t upar = 0, used = 0;            // parity of each B slot's uses, slots used
         int64_t tau = 0;
         bool ok = true;
@@ -585,18 +601,22 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             for (int c = 0; c < nx && ok; ++c)
                 for (int L = 0; L < kLines && ok; ++L) {
                     if (!((lmask >> L) & 1u)) continue;
-                    const int sr = int(tau % kRing);
+                    const uint32_t par = (upar >> L) & 1u, was = (used >> L) & 1u;
+                    upar ^= 1u << L;
+                    used |= 1u << L;
+                    const int64_t tme = tau++;
+                    if (int(tme % npw) != pw) continue;
+                    const int sr = int(tme % kRing);
                     if (lane == 0) {
-                        bool w = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), limit, abort);
-                        if (w && ((used >> L) & 1u))
-                            w = bar_wait(bars + 8 * (kBarBEmpty + L), ((upar >> L) & 1u) ^ 1u, limit, abort);
+                        bool w = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tme / kRing) & 1), limit, abort);
+                        if (w && was) w = bar_wait(bars + 8 * (kBarBEmpty + L), par ^ 1u, limit, abort);
                         if (!w) {
                             failed[1] = 1;
                             *abort = 1;
                             atomicExch(a.err, 1);
                         }
                     }
-                    named_sync(2, kProducers);
+                    __syncwarp();
                     if (failed[1]) {
                         ok = false;
                         break;
@@ -604,7 +624,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                     unsigned char *slot = sm + L * kBSlot;
                     float *scale = reinterpret_cast<float *>(slot + kB01 + kB2);
                     const unsigned char *stage = sm + kOffRing + sr * kRingSlot + kXTileBytes;
-#pragma unroll 1
+#pragma unroll
                     for (int bb = 0; bb < 3; ++bb) {
                         const int j = c - 1 + bb;
                         // input voxel (c, line L) is neighbour (1 - bb, L) of output j
@@ -614,12 +634,12 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                         const __half *t0 = reinterpret_cast<const __half *>(stage);
                         const unsigned char *ea = stage + 6 * np;
                         // four positions per iteration: their loads are issued before any store
-                        for (int p = pt; p < np; p += 4 * kProducers) {
+                        for (int p = lane; p < np; p += 4 * 32) {
                             uint32_t code[4];
                             __half v0[4], v1[4], v2[4];
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
-                                const int pk = p + kProducers * k;
+                                const int pk = p + 32 * k;
                                 code[k] = pk < np ? uint32_t(spos[p0 + pk]) : 0xFFFFu;
                                 v0[k] = v1[k] = v2[k] = __float2half_rn(0.0f);
                                 if (valid && pk < np) {
@@ -638,20 +658,17 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                                 *reinterpret_cast<__half *>(slot + kB01 + (n >> 3) * kLbo2 + within) = v2[k];
                             }
                         }
-                        if (pt < kDirs) scale[bb * kDirs + pt] = valid ? ldexpf(1.0f, int(ea[pt]) - kExpBias) : 0.0f;
+                        if (lane < kDirs) scale[bb * kDirs + lane] = valid ? pow2f(int(ea[lane]) - kExpBias) : 0.0f;
                         stage += s_coff[d + 1] - s_coff[d];
                     }
-                    // every producer's stores are made visible to the tensor cores, then
-                    // one thread signals for all of them
+                    // this warp's stores are made visible to the tensor cores, then its
+                    // lane 0 signals the tile
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    named_sync(2, kProducers);
-                    if (pt == 0) {
+                    __syncwarp();
+                    if (lane == 0) {
                         bar_arrive(bars + 8 * (kBarBFull + L));
                         bar_arrive(bars + 8 * (kBarREmpty + sr));
                     }
-                    upar ^= 1u << L;
-                    used |= 1u << L;
-                    ++tau;
                 }
         }
     }
@@ -806,7 +823,7 @@ __global__ void __launch_bounds__(256) tcx_ledger_kernel(StepArgs a)
 #pragma unroll
         for (int par = 0; par < 2; ++par) {
             const uint4 raw = t[lane + 32 * (12 + par)];
-            sc[par] = ldexpf(1.0f, int(__half2float(reinterpret_cast<const __half *>(&raw)[kExpDir - 24])));
+            sc[par] = scale2(1.0f, int(__half2float(reinterpret_cast<const __half *>(&raw)[kExpDir - 24])));
         }
         float s[2] = {0.0f, 0.0f}, se[2] = {0.0f, 0.0f};
 #pragma unroll 4
