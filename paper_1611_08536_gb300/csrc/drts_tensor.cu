@@ -78,7 +78,7 @@ constexpr int kOffPos = kOffBar + 512;                     // the union position
 constexpr int kPosMax = 5888;                              // positions (padded) the table holds
 constexpr int kSmemBytes = kOffPos + kPosMax * 2;
 constexpr int kPrefetch = 8;                               // tiles whose data is pulled into L2 ahead
-constexpr int kProducers = 192;               // threads expanding A into the B tiles (warps 6..11)
+constexpr int kProducers = 128;               // threads expanding A into the B tiles (warps 6..9)
 constexpr int kThreads = 192 + kProducers;
 constexpr int kTmemCols = 512;
 constexpr int kDCols = 160;
@@ -87,6 +87,10 @@ constexpr int kExpBias = 160;                 // A row exponents are stored as E
 
 static_assert(kB01 + kB2 + kBScale <= kBSlot, "B slot");
 static_assert(kSmemBytes <= 232448, "shared memory");
+// producer warp w expands the tiles staged in ring slot w: its waits on that
+// slot's barriers then advance one phase at a time (an mbarrier parity wait
+// must never run two phases ahead)
+static_assert(kProducers / 32 == kRing, "one producer warp per staging slot");
 
 // barrier indices (8 bytes each at kOffBar)
 constexpr int kBarBFull = 0, kBarBEmpty = 9, kBarRFull = 18, kBarREmpty = 22, kBarDFull = 26, kBarDEmpty = 29;
@@ -589,8 +593,11 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
         }
     } else {
         // ---- B operand tiles from the staged A chunks: producer warp w expands
-        // the tiles tau = w (mod kProducers / 32), one warp per tile, so several
-        // tiles are expanded at once ----
+        // the tiles of ring slot w (tau = w mod 4), one warp per tile, so four
+        // tiles are expanded at once.  By the time its wait for the staged data
+        // succeeds, the loader has been released by the tile four back, hence
+        // the MMA and the epilogue have passed every earlier use of the tile's
+        // B slot: the slot's barrier is at most one phase behind. ----
         const int pw = warp - 6, npw = kProducers / 32;
         uint32_t upar = 0, used = 0;            // parity of each B slot's uses, slots used
         int64_t tau = 0;
