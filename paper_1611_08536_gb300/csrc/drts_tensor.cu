@@ -66,16 +66,17 @@ constexpr int kLbo2 = 10 * 128 + 16;          // K step of the a2 tile, N 80
 constexpr int kB01 = 4 * kLbo01;              // K 32 x N 160 (a0 | a1)
 constexpr int kB2 = 4 * kLbo2;                // K 32 x N 80 (a2)
 constexpr int kBScale = kN * 4;               // 2^Ea per packed column
-constexpr int kBSlot = 15872;                 // kB01 + kB2 + kBScale rounded to 128
+constexpr int kXScale = 64 * 4;               // 2^Ex of the tile's 64 state rows
+constexpr int kBSlot = 16128;                 // kB01 + kB2 + kBScale + kXScale rounded to 128
 constexpr int kLines = 9;
-constexpr int kAStageMax = 9216;              // A chunks of one tile
+constexpr int kAStageMax = 8960;              // A chunks of one tile
 constexpr int kRingSlot = kXTileBytes + kAStageMax;
 constexpr int kRing = 4;
-constexpr int kOffRing = kLines * kBSlot;                  // 141,696
-constexpr int kOffXch = kOffRing + kRing * kRingSlot;      // 211,328
-constexpr int kOffBar = kOffXch + kDirs * 64 * 4;          // 217,984
+constexpr int kOffRing = kLines * kBSlot;                  // 145,152
+constexpr int kOffXch = kOffRing + kRing * kRingSlot;      // 213,760
+constexpr int kOffBar = kOffXch + kDirs * 64 * 4;          // 220,416
 constexpr int kOffPos = kOffBar + 512;                     // the union position table
-constexpr int kPosMax = 5888;                              // positions (padded) the table holds
+constexpr int kPosMax = 5760;                              // positions (padded) the table holds
 constexpr int kSmemBytes = kOffPos + kPosMax * 2;
 constexpr int kPrefetch = 8;                               // tiles whose data is pulled into L2 ahead
 constexpr int kProducers = 128;               // threads expanding A into the B tiles (warps 6..9)
@@ -85,7 +86,7 @@ constexpr int kDCols = 160;
 constexpr int kDBufs = 3;                     // accumulator buffers in tensor memory (480 of 512 columns)
 constexpr int kExpBias = 160;                 // A row exponents are stored as Ea + 160 (uint8)
 
-static_assert(kB01 + kB2 + kBScale <= kBSlot, "B slot");
+static_assert(kB01 + kB2 + kBScale + kXScale <= kBSlot, "B slot");
 static_assert(kSmemBytes <= 232448, "shared memory");
 // producer warp w expands the tiles staged in ring slot w: its waits on that
 // slot's barriers then advance one phase at a time (an mbarrier parity wait
@@ -345,32 +346,17 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, uint3
     for (int L = 0; L < kLines; ++L) {
         if (!((lmask >> L) & 1u)) continue;
         const int b = int(tau % kDBufs);
-        const int sr = int(tau % kRing);
         // lane 0 of each warp waits; a give-up anywhere is shared so the four warps agree
-        if (leader && !bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), a.spin_limit, abort)) {
+        if (leader && !bar_wait(bars + 8 * (kBarDFull + b), uint32_t((tau / kDBufs) & 1), a.spin_limit, abort)) {
             *failed = 1;
             *abort = 1;
             atomicExch(a.err, 1);
         }
-        __syncwarp();
-        float qx = 0.0f;
-        if (!*failed) {
-            // the state tile's row scale 2^Ex, from the staged copy
-            const __half *xt = reinterpret_cast<const __half *>(sm + kOffRing + sr * kRingSlot);
-            qx = scale2(1.0f, int(__half2float(xt[xtile_elem(rhs, kExpDir)])));
-        }
-        __syncwarp();
-        if (leader) {
-            bar_arrive(bars + 8 * (kBarREmpty + sr));  // this warp's scales are read
-            if (!*failed && !bar_wait(bars + 8 * (kBarDFull + b), uint32_t((tau / kDBufs) & 1), a.spin_limit, abort)) {
-                *failed = 1;
-                *abort = 1;
-                atomicExch(a.err, 1);
-            }
-        }
         named_sync(1, 128);
         if (*failed) return false;
         tc_fence_after();
+        // the state rows' scales 2^Ex, copied into the B slot by its producer
+        const float qx = reinterpret_cast<const float *>(sm + L * kBSlot + kB01 + kB2 + kBScale)[rhs];
         drain_tile<ROT>(s, tmem_q, b, qx, reinterpret_cast<const float *>(sm + L * kBSlot + kB01 + kB2));
         tc_fence_before();
         __syncwarp();
@@ -415,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
         }
         for (int sl = 0; sl < kRing; ++sl) {
             bar_init(bars + 8 * (kBarRFull + sl), 1);
-            bar_init(bars + 8 * (kBarREmpty + sl), 1 + 1 + 4);  // MMA + A scattered + each epilogue warp
+            bar_init(bars + 8 * (kBarREmpty + sl), 1 + 1);      // MMA read the state tile + A scattered
         }
         for (int b = 0; b < kDBufs; ++b) {
             bar_init(bars + 8 * (kBarDFull + b), 1);
@@ -630,6 +616,13 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                     }
                     unsigned char *slot = sm + L * kBSlot;
                     float *scale = reinterpret_cast<float *>(slot + kB01 + kB2);
+                    {
+                        // the state tile's row scales, for the epilogue (rows r and r + 32)
+                        const __half *xt = reinterpret_cast<const __half *>(sm + kOffRing + sr * kRingSlot);
+                        float *xs = reinterpret_cast<float *>(slot + kB01 + kB2 + kBScale);
+                        xs[lane] = pow2f(int(__half2float(xt[xtile_elem(lane, kExpDir)])));
+                        xs[lane + 32] = pow2f(int(__half2float(xt[xtile_elem(lane + 32, kExpDir)])));
+                    }
                     const unsigned char *stage = sm + kOffRing + sr * kRingSlot + kXTileBytes;
 #pragma unroll
                     for (int bb = 0; bb < 3; ++bb) {
