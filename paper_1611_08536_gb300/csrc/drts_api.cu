@@ -377,7 +377,7 @@ drts_status setup_tensor_core(drts_ctx *c)
     if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core union pattern");
     drelease(c, dflags);
     // positions of each role in (m, n) order, padded to a multiple of 8 (16-byte
-    // arrays); a role's chunk is three fp16 arrays plus 32 exponent bytes
+    // arrays); a role's chunk is three bf16 arrays
     std::vector<uint16_t> pos;
     std::vector<int16_t> pidx(kFlags, -1);
     TcPlan &P = c->tcp;
@@ -396,7 +396,7 @@ drts_status setup_tensor_core(drts_ctx *c)
             pos.push_back(uint16_t(31 << 8));         // padding: direction slot 31 of the tile is zero
             ++np;
         }
-        off += 6 * int64_t(np) + 32;
+        off += 6 * int64_t(np);
     }
     P.role_off[kOffs] = int(pos.size());
     P.chunk_off[kOffs] = int(off);

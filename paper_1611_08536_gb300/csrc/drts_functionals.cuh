@@ -2,7 +2,7 @@
 // kernels (drts_functionals.cu) and the persistent step kernel.
 #pragma once
 
-#include <cuda_fp16.h>
+#include <cuda_bf16.h>
 
 #include "drts_device.cuh"
 
@@ -10,12 +10,13 @@ namespace drts {
 namespace {
 
 // element offset of canonical state s of right-hand side r in a state buffer
-// (for the tensor-core layout: the fp16 element of x0; x1 is 512 further)
+// (for the tensor-core layout: the bf16 element of x0 2^Ex; x1 is 512 further,
+// x2 1024)
 __device__ __forceinline__ int64_t state_offset(const StepArgs &a, int64_t s, int r)
 {
     const int64_t v = s / kDirs;
     const int d = int(s - v * kDirs);
-    if (a.tcx) return v * 4096 + (((d >> 3) * 16 + (r >> 3)) * 64) + (r & 7) * 8 + (d & 7);
+    if (a.tcx) return v * 6144 + (((d >> 3) * 24 + (r >> 3)) * 64) + (r & 7) * 8 + (d & 7);
     if (a.R == 1) return int64_t(d) * a.V + v;
     // batched: groups of four right-hand sides, the four values side by side
     return (int64_t(r >> 2) * a.rhs_stride + int64_t(d) * a.V + v) * 4 + (r & 3);
@@ -36,11 +37,10 @@ __device__ __forceinline__ void point_detector_block(const StepArgs &a, const XT
         const int64_t o = state_offset(a, P.state[e], r);
         double xv;
         if (a.tcx) {
-            // x0 + x1 scaled by 2^Ex, Ex stored at direction 26 of the x0 row
-            const __half *xh = reinterpret_cast<const __half *>(x);
-            const int64_t v = P.state[e] / kDirs;
-            const int ex = int(__half2float(xh[v * 4096 + ((3 * 16 + (r >> 3)) * 64) + (r & 7) * 8 + 2]));
-            xv = ldexp(double(__half2float(xh[o])) + double(__half2float(xh[o + 512])), ex);
+            // the value is the sum of its three bf16 terms
+            const __nv_bfloat16 *xh = reinterpret_cast<const __nv_bfloat16 *>(x);
+            xv = double(__bfloat162float(xh[o])) + double(__bfloat162float(xh[o + 512])) +
+                 double(__bfloat162float(xh[o + 1024]));
         } else {
             xv = double(COHERENT ? __ldcg(x + o) : x[o]);
         }

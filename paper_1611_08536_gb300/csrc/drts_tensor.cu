@@ -11,39 +11,53 @@
 //
 // Number formats (the dominant product is made exact):
 //   * The tensor cores truncate FP32 accumulation unless every product of an
-//     MMA lies on one grid; then the sum is exact.  A block row (voxel j, role
-//     d, direction m) is scaled by 2^-Ea (Ea from the row's largest value) so
+//     MMA output lies on one grid; then the sum is exact.  A block row (voxel
+//     j, role d, direction m) has an exponent Ea from its largest value, so
 //     that a0 = rint(A 2^-Ea) is an integer of at most 256; a state row
-//     (voxel i, right-hand side r) likewise by 2^-Ex, x0 = rint(X 2^-Ex).  The
-//     products x0 a0 of one K = 32 block are integers below 2^21: exact.
-//   * a1 = fp16(A 2^-Ea - a0), a2 = fp16(A 2^-Ea - a0 - a1) (A to ~30 bits) and
-//     x1 = fp16(X 2^-Ex - x0) (11 bits of the residual); the products with
-//     a1, a2 and x1 are 2^-8 of the result or smaller, so their truncation is
-//     below 2^-32 relative.
-//   * The state lives as (x0, x1, Ex); every step writes it from the FP32
-//     result.  Each tile's products are drained from tensor memory, scaled by
-//     2^(Ex + Ea) and added into FP32 sums on the CUDA cores (27 partials per
-//     output, round to nearest).
+//     (voxel i, right-hand side r) likewise Ex, x0 = rint(X 2^-Ex).  Both are
+//     stored in bf16 WITH their power-of-two scale (a0 2^Ea, x0 2^Ex: at most
+//     9 significant bits and the FP32 exponent range, so exact), hence every
+//     product of output (r, m) of one tile lies on the grid 2^(Ex + Ea) and
+//     their sum (below 2^21 grid units) is exact.  No scaling is left for the
+//     drain.
+//   * a1 = bf16(A - a0 2^Ea), a2 = bf16(A - a0 2^Ea - a1) (A to ~25 bits),
+//     x1 = bf16(X - x0 2^Ex), x2 = bf16(X - x0 2^Ex - x1) (X to ~25 bits, and
+//     to 16 bits for values far below their row's largest); their products
+//     are 2^-8 of the result or smaller and accumulate in a second tensor-
+//     memory sum, so their truncation is below 2^-32 relative.  Products of
+//     two residual terms below 2^-24 relative (x1 a2 and smaller) that no MMA
+//     forms for free are left out.
+//   * The state lives as (x0 2^Ex, x1, x2); every step writes it from the
+//     FP32 result.  Each tile's two sums are drained from tensor memory and
+//     added into FP32 sums on the CUDA cores (27 partials per output, round
+//     to nearest).  Rows whose largest |value| is below 2^-100 are stored as
+//     zero (the bf16 terms would otherwise fall below the normal range).
 //
 // Kernel (one CTA per SM, persistent over output lines (y, z)): the state
-// tile of input voxel i (64 right-hand sides of x0 and of x1 = 128 rows,
-// 32 directions, fp16, 8 KB, Ex of row r stored at direction 26 of row r)
-// feeds the three outputs on the output line whose neighbour it is.  Input
-// columns are swept along x; each of the <= 9 input lines gives one tile per
-// column.  The three outputs' 26 rows are packed into N = 80 columns
-// (column 26 bb + m for output c - 1 + bb).  Per tile:
-//   MMA1  D[0:160)  = [x0; x1] (128 x 32) x [a0 | a1]   (N = 160)
-//   MMA2  D[80:160) += [x0; x1] x [a2]                 (N = 80)
-// (two K = 16 steps each), D in tensor memory, fresh per tile, double-buffered.
-// Warp roles: warps 0-3 drain D (tcgen05.ld, lane quarter = warp) into the
-// FP32 sums of the three live outputs and write each finished output voxel's
-// new tile; warp 4 issues the MMAs; warp 5 copies each tile's state and A
-// chunks with cp.async.bulk into a ring of staging slots; warps 6-7 scatter
-// the staged A values into the B operand tiles.  B tiles are dedicated per
-// input line role, whose sparsity never changes, so only values are
-// rewritten.  Every wait is on an mbarrier with a bounded poll count; a wait
-// that runs out sets the context's error word and the CTA winds down.
-#include <cuda_fp16.h>
+// tile of input voxel i (x0, x1 and x2 of 64 right-hand sides, 32 directions,
+// bf16, 12 KB) feeds the three outputs on the output line whose neighbour it
+// is.  Input columns are swept along x; each of the <= 9 input lines gives
+// one tile per column.  The three outputs' 26 rows are packed into N = 80
+// columns (column 26 bb + m for output c - 1 + bb), and the B operand of a
+// line holds [a0 | a1 | a2] side by side (N = 240).  Per tile, with M = 128
+// rows and D fresh per tile in tensor memory (three buffers):
+//   MMA1  D[0:160)  = [x0; x1] x [a0 | a1]   (N = 160)
+//   MMA2  D[80:160) += [x0; x1] x [a2]       (N = 80)
+//   MMA3  D[80:160) += [x1; x2] x [a0]       (N = 80)
+// (two K = 16 steps each).  Right-hand side r then has x0 a0 exact in D row
+// r, columns 0-79, and every other term once in rows r and 64 + r, columns
+// 80-159 (row 64 + r of columns 0-79, x1 a0 again, is not read).  Warp roles:
+// warps 0-3 drain D (tcgen05.ld, lane quarter = warp) into the FP32 sums of
+// the three live outputs and write each finished output voxel's new tile;
+// warp 11 issues the MMAs; warp 7 copies each tile's state and A chunks with
+// cp.async.bulk into a ring of staging slots; warps 6-8 scatter the staged A
+// values into the B operand tiles through a table of shared-memory offsets
+// (one warp per tile).  B tiles are dedicated per input line role, whose
+// sparsity never changes, so only values are rewritten.  Every wait is on an
+// mbarrier with a bounded poll count (each poll may suspend the thread until
+// the phase completes or a short hardware time limit passes); a wait that
+// runs out sets the context's error word and the CTA winds down.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -54,56 +68,84 @@
 namespace drts {
 namespace {
 
-constexpr int kTcK = 32;                      // directions padded to the K extent
 constexpr int kN = 80;                        // three outputs x 26 rows, padded
-constexpr int kXTileBytes = 8192;             // 128 rows x 32 directions x fp16
-constexpr int kExpDir = 26;                   // direction slot holding Ex of a state row
-// B operand tiles, K-major core matrices; consecutive direction groups are
-// 16 bytes further apart than a whole group of core matrices, so the stores
-// of one direction row to different groups fall in different banks
-constexpr int kLbo01 = 20 * 128 + 16;         // K step of the (a0 | a1) tile, N 160
-constexpr int kLbo2 = 10 * 128 + 16;          // K step of the a2 tile, N 80
-constexpr int kB01 = 4 * kLbo01;              // K 32 x N 160 (a0 | a1)
-constexpr int kB2 = 4 * kLbo2;                // K 32 x N 80 (a2)
-constexpr int kBScale = kN * 4;               // 2^Ea per packed column
-constexpr int kXScale = 64 * 4;               // 2^Ex of the tile's 64 state rows
-constexpr int kBSlot = 16128;                 // kB01 + kB2 + kBScale + kXScale rounded to 128
+constexpr int kXTileBytes = 12288;            // 3 terms x 64 rows x 32 directions x bf16
+constexpr int kXGroup = 3072;                 // one direction group (8 directions) of a state tile
+// B operand tile of a tile: [a0 | a1 | a2] side by side, N = 240 (30 groups of
+// 8 columns), K-major core matrices; consecutive direction groups are 16
+// bytes further apart than a whole group of core matrices, so the stores of
+// one direction row to different groups fall in different banks
+constexpr int kLbo = 30 * 128 + 16;           // K step (8 directions) of the B tile
+constexpr int kA1Off = 10 * 128;              // a1 columns start 80 columns on
+constexpr int kA2Off = 20 * 128;              // a2 columns start 160 columns on
+constexpr int kBBytes = 15488;                // 4 K groups x kLbo, rounded to 128
 constexpr int kLines = 9;
-constexpr int kAStageMax = 8960;              // A chunks of one tile
-constexpr int kRingSlot = kXTileBytes + kAStageMax;
-constexpr int kRing = 4;
-constexpr int kOffRing = kLines * kBSlot;                  // 145,152
-constexpr int kOffXch = kOffRing + kRing * kRingSlot;      // 213,760
-constexpr int kOffBar = kOffXch + kDirs * 64 * 4;          // 220,416
-constexpr int kOffPos = kOffBar + 512;                     // the union position table
-constexpr int kPosMax = 5760;                              // positions (padded) the table holds
+// Tile slots: state tile + B tile, from the copy until the MMAs are done.
+// Staging slots: the tile's A chunks, from the copy until they are scattered.
+constexpr int kSlots = 6;
+constexpr int kSlotBytes = kXTileBytes + kBBytes;           // 27,776
+constexpr int kStages = 5;
+constexpr int kStageBytes = 8960;                           // A chunks of one tile
+constexpr int kOffStage = kSlots * kSlotBytes;              // 166,656
+constexpr int kOffXch = kOffStage + kStages * kStageBytes;  // 193,536
+constexpr int kOffBar = kOffXch + kDirs * 64 * 4;           // 200,192
+constexpr int kOffPos = kOffBar + 512;                      // the union offset table
+constexpr int kPosMax = 5760;                               // positions (padded) the table holds
 constexpr int kSmemBytes = kOffPos + kPosMax * 2;
-constexpr int kPrefetch = 8;                               // tiles whose data is pulled into L2 ahead
-constexpr int kProducers = 128;               // threads expanding A into the B tiles (warps 6..9)
-constexpr int kThreads = 192 + kProducers;
+// Warp roles.  A warp runs on scheduler warp % 4: one drain warp on each, the
+// two copy warps (alternate tiles) and the MMA warp on schedulers 2 and 3, the
+// five producers on the others' spare slots.
+constexpr int kWarpLoad0 = 7, kWarpLoad1 = 10, kWarpMma = 11;
+constexpr int kThreads = 12 * 32;
+// producer index of warps 4, 5, 6, 8, 9 (-1: no producer role)
+__device__ __forceinline__ int producer_of(int warp)
+{
+    return warp >= 4 && warp <= 6 ? warp - 4 : (warp == 8 || warp == 9 ? warp - 5 : -1);
+}
+static_assert(kStages == 5, "five producer warps, one per staging slot");
 constexpr int kTmemCols = 512;
 constexpr int kDCols = 160;
 constexpr int kDBufs = 3;                     // accumulator buffers in tensor memory (480 of 512 columns)
-constexpr int kExpBias = 160;                 // A row exponents are stored as Ea + 160 (uint8)
+constexpr int kTinyExp = -100;                // rows below 2^-100 are stored as zero
 
-static_assert(kB01 + kB2 + kBScale + kXScale <= kBSlot, "B slot");
+static_assert(4 * kLbo <= kBBytes && kBBytes % 128 == 0 && kSlotBytes % 128 == 0, "tile slot");
+static_assert(kStageBytes % 128 == 0, "staging slot");
 static_assert(kSmemBytes <= 232448, "shared memory");
-// producer warp w expands the tiles staged in ring slot w: its waits on that
-// slot's barriers then advance one phase at a time (an mbarrier parity wait
-// must never run two phases ahead)
-static_assert(kProducers / 32 == kRing, "one producer warp per staging slot");
+static_assert(kN % 8 == 0 && 3 * kN == 240, "B tile column groups");
+// Producer warp w expands the tiles staged in staging slot w, so its waits on
+// that slot's barrier advance one phase at a time (an mbarrier parity wait
+// must never run two phases ahead).  A tile slot is filled by different
+// producer warps in turn, but in order: the loader copies into a tile slot
+// only after the slot's previous MMAs, which waited for its previous B tile.
+static_assert(kStages <= kSlots, "a tile waits for its staging slot before its tile slot is reused");
 
 // barrier indices (8 bytes each at kOffBar)
-constexpr int kBarBFull = 0, kBarBEmpty = 9, kBarRFull = 18, kBarREmpty = 22, kBarDFull = 26, kBarDEmpty = 29;
-constexpr int kNumBars = 32;
+constexpr int kBarXFull = 0;                  // [kSlots] state tile copied (transaction count)
+constexpr int kBarBFull = 6;                  // [kSlots] B tile scattered
+constexpr int kBarSDone = 12;                 // [kSlots] the tile's MMAs are done (slot free, products ready)
+constexpr int kBarAFull = 18;                 // [kStages] A chunks copied (transaction count)
+constexpr int kBarAEmpty = 23;                // [kStages] A chunks scattered
+constexpr int kBarDEmpty = 28;                // [kDBufs] products drained
+constexpr int kNumBars = 31;
+static_assert(kBarBFull == kSlots && kBarAFull == 3 * kSlots && kBarDEmpty == kBarAFull + 2 * kStages &&
+              kBarDEmpty + kDBufs == kNumBars && 8 * kNumBars + 16 <= 288, "barrier layout");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return uint32_t(__cvta_generic_to_shared(p)); }
 
-// element offset of (row rho, direction n) in a state tile: K-major canonical
-// layout of 8x8 core matrices, core matrix (n/8, rho/8) at (n/8 * 16 + rho/8) * 64
+// element offset of (row rho, direction n) in a state tile, rho = 64 t + r for
+// term t of right-hand side r: K-major canonical layout of 8x8 core matrices,
+// core matrix (n/8, rho/8) at (n/8 * 24 + rho/8) * 64.  A direction group holds
+// the x0, x1 and x2 blocks one after the other, so rows [x0; x1] and rows
+// [x1; x2] are both 128-row operands with the same strides.
 __host__ __device__ __forceinline__ int xtile_elem(int rho, int n)
 {
-    return (((n >> 3) * 16 + (rho >> 3)) * 64) + (rho & 7) * 8 + (n & 7);
+    return (((n >> 3) * 24 + (rho >> 3)) * 64) + (rho & 7) * 8 + (n & 7);
+}
+
+// byte offset of (direction n, packed column q) in a line's B tile
+__device__ __forceinline__ int btile_byte(int n, int q)
+{
+    return (n >> 3) * kLbo + (q >> 3) * 128 + (q & 7) * 16 + (n & 7) * 2;
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
@@ -112,23 +154,26 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
            (uint64_t((sbo >> 4) & 0x3FFF) << 32) | (uint64_t(1) << 46);
 }
 
-// kind::f16 instruction descriptor: fp16 A and B (K-major), FP32 D, M x N
-__device__ __forceinline__ uint32_t idesc_f16(int M, int N)
+// kind::f16 instruction descriptor: bf16 A and B (K-major), FP32 D, M x N
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N)
 {
-    return (1u << 4) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+// The whole warp calls these with the same operands (they stay in uniform
+// registers); one elected lane issues the instruction.
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
 {
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+    asm volatile("{\n\t.reg .pred p, e;\n\tsetp.ne.b32 p, %4, 0;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
                  :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar)
 {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar)
-                 : "memory");
+    asm volatile("{\n\t.reg .pred e;\n\telect.sync _|e, 0xffffffff;\n\t"
+                 "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}"
+                 :: "r"(bar) : "memory");
 }
 
 __device__ __forceinline__ void bar_init(uint32_t bar, int count)
@@ -147,6 +192,19 @@ __device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes)
                  :: "r"(bar), "r"(bytes) : "memory");
 }
 
+// Whether the phase of the given parity has completed, without waiting.
+__device__ __forceinline__ bool bar_done(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// One poll of an mbarrier phase: the thread may be suspended until the phase
+// completes or a short hardware time limit passes, so a waiting warp takes
+// few issue slots from the warps that share its scheduler.
 __device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
@@ -160,9 +218,10 @@ __device__ __forceinline__ bool bar_test(uint32_t bar, uint32_t parity)
 // `limit` polls or when another role has flagged an abort.
 __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint32_t limit, volatile int *abort)
 {
+    if (bar_done(bar, parity)) return true;         // the common case costs one instruction
     for (uint32_t i = 0; i < limit; ++i) {
-        if (bar_test(bar, parity)) return true;
         if (*abort) return false;
+        if (bar_test(bar, parity)) return true;
     }
     return false;
 }
@@ -218,10 +277,11 @@ __device__ __forceinline__ float scale2(float y, int k)
     return (y * pow2f(k1)) * pow2f(k - k1);
 }
 
-// Write row pair r / 64 + r of a state tile from y: Ex from the largest |y|
-// (|y| 2^-Ex < 256), x0 = rint(y 2^-Ex) (exact in fp16), x1 = fp16(y 2^-Ex - x0),
-// Ex itself (an integer, exact in fp16) at direction 26 of row r.
-__device__ __forceinline__ void write_state_row(__half *tile, int r, const float y[kDirs])
+// Write the three rows r, 64 + r, 128 + r of a state tile from y: Ex from
+// the largest |y| (|y| 2^-Ex < 256), x0 = rint(y 2^-Ex) stored as x0 2^Ex
+// (bf16, exact), x1 = bf16(y - x0 2^Ex), x2 = bf16(y - x0 2^Ex - x1); a row
+// whose largest |y| is below 2^kTinyExp is stored as zero.
+__device__ __forceinline__ void write_state_row(__nv_bfloat16 *tile, int r, const float y[kDirs])
 {
     float mx = 0.0f;
 #pragma unroll
@@ -229,25 +289,25 @@ __device__ __forceinline__ void write_state_row(__half *tile, int r, const float
     int e = 0;
     frexpf(mx, &e);                                     // mx = f 2^e, f in [0.5, 1); e = 0 for mx = 0
     const int ex = e - 8;
+    const bool tiny = e <= kTinyExp;
 #pragma unroll
     for (int g = 0; g < 4; ++g) {
-        __align__(16) __half h0[8], h1[8];
+        __align__(16) __nv_bfloat16 h0[8], h1[8], h2[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int n = g * 8 + k;
-            float x0 = 0.0f, x1 = 0.0f;
-            if (n < kDirs) {
-                const float ys = scale2(y[n], -ex);     // exact, |ys| < 256
-                x0 = rintf(ys);
-                x1 = ys - x0;                           // exact, |x1| <= 1/2
-            } else if (n == kExpDir) {
-                x0 = float(ex);
+            float x0 = 0.0f, r1 = 0.0f;
+            if (n < kDirs && !tiny) {
+                x0 = scale2(rintf(scale2(y[n], -ex)), ex);   // both scalings exact, |rint| <= 256
+                r1 = y[n] - x0;                               // exact
             }
-            h0[k] = __float2half_rn(x0);
-            h1[k] = __float2half_rn(x1);
+            h0[k] = __float2bfloat16_rn(x0);                  // exact
+            h1[k] = __float2bfloat16_rn(r1);
+            h2[k] = __float2bfloat16_rn(r1 - __bfloat162float(h1[k]));   // the difference is exact
         }
         *reinterpret_cast<uint4 *>(tile + xtile_elem(r, g * 8)) = *reinterpret_cast<const uint4 *>(h0);
         *reinterpret_cast<uint4 *>(tile + xtile_elem(64 + r, g * 8)) = *reinterpret_cast<const uint4 *>(h1);
+        *reinterpret_cast<uint4 *>(tile + xtile_elem(128 + r, g * 8)) = *reinterpret_cast<const uint4 *>(h2);
     }
 }
 
@@ -255,30 +315,77 @@ struct EpiState {
     float acc[3][kDirs];
 };
 
-// Add the drained tile (D buffer b) into the sums of the three outputs of
-// column c: packed column q = 26 bb + m belongs to output c - 1 + bb, whose
-// sums sit in slot (c - 1 + bb) mod 3 = (ROT + 2 + bb) % 3; scale 2^(Ex + Ea).
-template <int ROT>
-__device__ __forceinline__ void drain_tile(EpiState &s, uint32_t tmem_q, int b, float qx, const float *qa)
+// Registers written by tcgen05.ld are defined only after tcgen05.wait::ld;
+// passing them through an empty asm after the wait keeps the compiler from
+// moving their uses above it.
+__device__ __forceinline__ void reg_fence(float (&v)[16])
+{
+    asm volatile("" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]),
+                 "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]),
+                 "+f"(v[14]), "+f"(v[15]));
+}
+
+// Add columns 16 k .. 16 k + 15 of the drained tile into the sums of the
+// three outputs of column c: packed column q = 26 bb + m belongs to output
+// c - 1 + bb, whose sums sit in slot (c - 1 + bb) mod 3 = (ROT + 2 + bb) % 3.
+// Column q of D holds the exact x0 a0 sum (lanes 0-63; lanes 64-127 hold x1
+// a0, which the residual sums count already, and pass zeros), column 80 + q
+// the residual terms' sum.
+template <int ROT, int K>
+__device__ __forceinline__ void add_part(EpiState &s, const float (&dF)[16], const float (&dS)[16])
 {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        float dF[16], dS[16];
-        tmem_ld16(tmem_q + uint32_t(b * kDCols + 16 * k), dF);
-        tmem_ld16(tmem_q + uint32_t(b * kDCols + kN + 16 * k), dS);
-        tmem_wait_ld();
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int q = 16 * k + i;
-            if (q >= 3 * kDirs) continue;
-            const int bb = q / kDirs, m = q % kDirs;
-            const int slot = (ROT + 2 + bb) % 3;
-            const float v = (dF[i] + dS[i]) * (qx * qa[q]);
-            if (slot == 0) s.acc[0][m] += v;
-            else if (slot == 1) s.acc[1][m] += v;
-            else s.acc[2][m] += v;
-        }
+    for (int i = 0; i < 16; ++i) {
+        const int q = 16 * K + i;
+        if (q >= 3 * kDirs) continue;
+        const int bb = q / kDirs, m = q % kDirs;
+        const int slot = (ROT + 2 + bb) % 3;
+        const float v = dF[i] + dS[i];
+        if (slot == 0) s.acc[0][m] += v;
+        else if (slot == 1) s.acc[1][m] += v;
+        else s.acc[2][m] += v;
     }
+}
+
+__device__ __forceinline__ void load_part(uint32_t tmem_b, int k, bool with_f, float (&dF)[16], float (&dS)[16])
+{
+    if (with_f) {
+        tmem_ld16(tmem_b + uint32_t(16 * k), dF);
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) dF[i] = 0.0f;
+    }
+    tmem_ld16(tmem_b + uint32_t(kN + 16 * k), dS);
+}
+
+__device__ __forceinline__ void wait_part(float (&dF)[16], float (&dS)[16])
+{
+    tmem_wait_ld();
+    reg_fence(dF);
+    reg_fence(dS);
+}
+
+// The five 16-column parts of a tile, software-pipelined: the loads of part
+// k + 1 are in flight while part k is added.
+template <int ROT>
+__device__ __forceinline__ void drain_tile(EpiState &s, uint32_t tmem_b, bool with_f)
+{
+    float f0[16], s0[16], f1[16], s1[16];
+    load_part(tmem_b, 0, with_f, f0, s0);
+    wait_part(f0, s0);
+    load_part(tmem_b, 1, with_f, f1, s1);
+    add_part<ROT, 0>(s, f0, s0);
+    wait_part(f1, s1);
+    load_part(tmem_b, 2, with_f, f0, s0);
+    add_part<ROT, 1>(s, f1, s1);
+    wait_part(f0, s0);
+    load_part(tmem_b, 3, with_f, f1, s1);
+    add_part<ROT, 2>(s, f0, s0);
+    wait_part(f1, s1);
+    load_part(tmem_b, 4, with_f, f0, s0);
+    add_part<ROT, 3>(s, f1, s1);
+    wait_part(f0, s0);
+    add_part<ROT, 4>(s, f0, s0);
 }
 
 template <int SLOT>
@@ -294,6 +401,8 @@ template <int SLOT>
 __device__ __forceinline__ void finalize(EpiState &s, const StepArgs &a, float *xch, int qd, int lane, int64_t vox)
 {
     const int rhs = lane + 32 * (qd & 1);
+    // the source flag is read before the barrier, which hides its latency
+    const bool has_src = qd < 2 && a.n_src > 0 && a.src_voxel[vox];
     if (qd >= 2) {
 #pragma unroll
         for (int m = 0; m < kDirs; ++m) xch[m * 64 + rhs] = s.acc[SLOT][m];
@@ -303,7 +412,7 @@ __device__ __forceinline__ void finalize(EpiState &s, const StepArgs &a, float *
         float y[kDirs];
 #pragma unroll
         for (int m = 0; m < kDirs; ++m) y[m] = s.acc[SLOT][m] + xch[m * 64 + rhs];
-        if (a.n_src > 0 && a.src_voxel[vox]) {
+        if (has_src) {
             for (int e = 0; e < a.n_src; ++e) {
                 const SourceEntry se = a.src[e];
                 const int64_t sv = (int64_t(se.slice) / kDirs) * kSlice + se.lane;
@@ -315,7 +424,7 @@ __device__ __forceinline__ void finalize(EpiState &s, const StepArgs &a, float *
                     if (m == sm) y[m] += val;
             }
         }
-        __half *tile = static_cast<__half *>(a.y) + vox * (kXTileBytes / 2);
+        __nv_bfloat16 *tile = static_cast<__nv_bfloat16 *>(a.y) + vox * (kXTileBytes / 2);
         write_state_row(tile, rhs, y);
     }
     named_sync(1, 128);
@@ -337,34 +446,36 @@ __device__ __forceinline__ uint32_t line_mask(int y, int z, int ny, int nz)
     return mask;
 }
 
+// Drain the tiles of input column c (one per valid input line, in line
+// order): each warp waits for the tile's products on its own (a warp-wide
+// poll, so its lanes agree), adds them into its sums and releases the buffer.
+// A tile's products are ready when its tile slot's MMAs are done; that
+// barrier cannot run a phase ahead of this wait, because the slot's next
+// tile needs the buffer that the drain of the tile after this one frees.
+struct EpiPos {
+    int sl, b;                                  // tile slot and accumulator buffer of the next tile
+    uint32_t sph;                               // phase parity of the slot's current round
+};
+
 template <int ROT>
 __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, uint32_t lmask, uint32_t tmem_q,
-                                           unsigned char *sm, uint32_t bars, int64_t &tau, volatile int *abort,
-                                           volatile int *failed, int rhs)
+                                           uint32_t bars, EpiPos &e, volatile int *abort, bool with_f)
 {
-    const bool leader = (threadIdx.x & 31) == 0;
     for (int L = 0; L < kLines; ++L) {
         if (!((lmask >> L) & 1u)) continue;
-        const int b = int(tau % kDBufs);
-        // lane 0 of each warp waits; a give-up anywhere is shared so the four warps agree
-        if (leader && !bar_wait(bars + 8 * (kBarDFull + b), uint32_t((tau / kDBufs) & 1), a.spin_limit, abort)) {
-            *failed = 1;
+        const int b = e.b;
+        if (!bar_wait(bars + 8 * (kBarSDone + e.sl), e.sph, a.spin_limit, abort)) {
             *abort = 1;
-            atomicExch(a.err, 1);
+            if ((threadIdx.x & 31) == 0) atomicExch(a.err, 1);
+            return false;
         }
-        named_sync(1, 128);
-        if (*failed) return false;
         tc_fence_after();
-        // the state rows' scales 2^Ex, copied into the B slot by its producer
-        const float qx = reinterpret_cast<const float *>(sm + L * kBSlot + kB01 + kB2 + kBScale)[rhs];
-        drain_tile<ROT>(s, tmem_q, b, qx, reinterpret_cast<const float *>(sm + L * kBSlot + kB01 + kB2));
+        drain_tile<ROT>(s, tmem_q + uint32_t(b * kDCols), with_f);
         tc_fence_before();
         __syncwarp();
-        if (leader) {
-            bar_arrive(bars + 8 * (kBarDEmpty + b));
-            bar_arrive(bars + 8 * (kBarBEmpty + L));   // the B slot's scales are read
-        }
-        ++tau;
+        if ((threadIdx.x & 31) == 0) bar_arrive(bars + 8 * (kBarDEmpty + b));
+        if (++e.b == kDBufs) e.b = 0;
+        if (++e.sl == kSlots) { e.sl = 0; e.sph ^= 1u; }
     }
     return true;
 }
@@ -376,7 +487,6 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     const uint32_t bars = smem_u32(sm + kOffBar);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(sm + kOffBar + 8 * kNumBars);
     volatile int *abort = reinterpret_cast<volatile int *>(sm + kOffBar + 8 * kNumBars + 4);
-    volatile int *failed = reinterpret_cast<volatile int *>(sm + kOffBar + 8 * kNumBars + 8);
     float *xch = reinterpret_cast<float *>(sm + kOffXch);
     uint16_t *spos = reinterpret_cast<uint16_t *>(sm + kOffPos);
     int *s_roff = reinterpret_cast<int *>(sm + kOffBar + 288);      // role position offsets [28]
@@ -387,33 +497,35 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     // an earlier launch gave up a wait: the state is already invalid, do nothing
     if (*reinterpret_cast<volatile int *>(a.err) != 0) return;
 
-    // B tiles start at zero; positions outside the union are never written
-    for (int i = tid; i < kLines * kBSlot / 16; i += kThreads) reinterpret_cast<uint4 *>(sm)[i] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < P.role_off[kOffs]; i += kThreads) spos[i] = P.pos[i];
+    // position (n, m) of role d = 3 L + 2 - bb lands in column q = 26 bb + m of
+    // line L's B tile: its byte offset there
+    for (int d = 0; d < kOffs; ++d) {
+        const int bb = 2 - d % 3;
+        for (int i = P.role_off[d] + tid; i < P.role_off[d + 1]; i += kThreads) {
+            const int code = P.pos[i];
+            spos[i] = uint16_t(btile_byte(code >> 8, bb * kDirs + (code & 255)));
+        }
+    }
     for (int i = tid; i < 28; i += kThreads) {
         s_roff[i] = P.role_off[i];
         s_coff[i] = P.chunk_off[i];
     }
     if (tid == 0) {
-        for (int L = 0; L < kLines; ++L) {
-            bar_init(bars + 8 * (kBarBFull + L), 1);            // producers, after their own barrier
-            bar_init(bars + 8 * (kBarBEmpty + L), 1 + 4);       // MMA done + each epilogue warp read the scales
+        for (int sl = 0; sl < kSlots; ++sl) {
+            bar_init(bars + 8 * (kBarXFull + sl), 1);           // the loader's expect_tx
+            bar_init(bars + 8 * (kBarBFull + sl), 1);           // the producer warp
+            bar_init(bars + 8 * (kBarSDone + sl), 1);          // the MMAs' commit
         }
-        for (int sl = 0; sl < kRing; ++sl) {
-            bar_init(bars + 8 * (kBarRFull + sl), 1);
-            bar_init(bars + 8 * (kBarREmpty + sl), 1 + 1);      // MMA read the state tile + A scattered
+        for (int st = 0; st < kStages; ++st) {
+            bar_init(bars + 8 * (kBarAFull + st), 1);           // the loader's expect_tx
+            bar_init(bars + 8 * (kBarAEmpty + st), 1);          // the producer warp
         }
-        for (int b = 0; b < kDBufs; ++b) {
-            bar_init(bars + 8 * (kBarDFull + b), 1);
-            bar_init(bars + 8 * (kBarDEmpty + b), 4);           // each epilogue warp
-        }
+        for (int b = 0; b < kDBufs; ++b) bar_init(bars + 8 * (kBarDEmpty + b), 4);   // each epilogue warp
         *abort = 0;
-        failed[0] = 0;
-        failed[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (warp == 4) {
+    if (warp == kWarpMma) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(tmem_slot)), "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -425,80 +537,94 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
     const uint32_t limit = a.spin_limit;
 
     if (warp < 4) {
-        // ---- epilogue: drain tiles, finish output voxels ----
+        // ---- epilogue: drain tiles, finish output voxels.  The four warps run
+        // the same loop to the end even after a failed wait (each later wait
+        // then fails at once), so their named barriers always pair up. ----
         EpiState s;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int m = 0; m < kDirs; ++m) s.acc[k][m] = 0.0f;
         const uint32_t tmem_q = tmem + (uint32_t(32 * warp) << 16);
-        const int rhs = lane + 32 * (warp & 1);
-        int64_t tau = 0;
-        bool ok = true;
-        for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
+        const bool with_f = warp < 2;
+        EpiPos ep{0, 0, 0u};
+        for (int64_t line = blockIdx.x; line < n_lines; line += gridDim.x) {
             const int y = int(line % ny), z = int(line / ny);
             const uint32_t lmask = line_mask(y, z, ny, nz);
             const int64_t row0 = (int64_t(z) * ny + y) * nx;
-            for (int c = 0; c < nx && ok; ++c) {
+            for (int c = 0; c < nx; ++c) {
                 switch (c % 3) {
                 case 0:
-                    ok = epi_column<0>(s, a, lmask, tmem_q, sm, bars, tau, abort, failed, rhs);
-                    if (!ok) break;
+                    epi_column<0>(s, a, lmask, tmem_q, bars, ep, abort, with_f);
                     if (c >= 1) finalize<2>(s, a, xch, warp, lane, row0 + c - 1);
                     else zero_slot<2>(s);
                     if (c == nx - 1) { finalize<0>(s, a, xch, warp, lane, row0 + c); zero_slot<1>(s); }
                     break;
                 case 1:
-                    ok = epi_column<1>(s, a, lmask, tmem_q, sm, bars, tau, abort, failed, rhs);
-                    if (!ok) break;
+                    epi_column<1>(s, a, lmask, tmem_q, bars, ep, abort, with_f);
                     finalize<0>(s, a, xch, warp, lane, row0 + c - 1);
                     if (c == nx - 1) { finalize<1>(s, a, xch, warp, lane, row0 + c); zero_slot<2>(s); }
                     break;
                 default:
-                    ok = epi_column<2>(s, a, lmask, tmem_q, sm, bars, tau, abort, failed, rhs);
-                    if (!ok) break;
+                    epi_column<2>(s, a, lmask, tmem_q, bars, ep, abort, with_f);
                     finalize<1>(s, a, xch, warp, lane, row0 + c - 1);
                     if (c == nx - 1) { finalize<2>(s, a, xch, warp, lane, row0 + c); zero_slot<0>(s); }
                     break;
                 }
             }
         }
-    } else if (warp == 4) {
-        // ---- MMA issue (one thread) ----
-        if (lane == 0) {
-            const uint32_t id1 = idesc_f16(128, 2 * kN), id2 = idesc_f16(128, kN);
-            const uint32_t ring0 = smem_u32(sm + kOffRing), bs0 = smem_u32(sm);
-            int64_t tau = 0;
-            uint32_t upar = 0;                      // parity of each B slot's uses
-            bool ok = true;
-            for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
-                const int y = int(line % ny), z = int(line / ny);
-                const uint32_t lmask = line_mask(y, z, ny, nz);
-                for (int c = 0; c < nx && ok; ++c)
-                    for (int L = 0; L < kLines && ok; ++L) {
-                        if (!((lmask >> L) & 1u)) continue;
-                        const int sr = int(tau % kRing), b = int(tau % kDBufs);
-                        ok = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tau / kRing) & 1), limit, abort) &&
-                             bar_wait(bars + 8 * (kBarBFull + L), (upar >> L) & 1u, limit, abort) &&
-                             (tau < kDBufs ||
-                              bar_wait(bars + 8 * (kBarDEmpty + b), uint32_t(((tau / kDBufs) - 1) & 1), limit, abort));
-                        if (!ok) break;
-                        tc_fence_after();
-                        const uint32_t d = tmem + uint32_t(b * kDCols);
-                        const uint32_t xa = ring0 + sr * kRingSlot, ba = bs0 + L * kBSlot;
+    } else if (warp == kWarpMma) {
+        // ---- MMA issue: the whole warp runs the loop in step (its values stay
+        // warp-uniform), lane 0 issues the MMAs and commits ----
+        const uint32_t id1 = idesc_bf16(128, 2 * kN), id2 = idesc_bf16(128, kN);
+        // operand descriptors of tile slot 0 for the two K halves; tile slot sl
+        // adds sl * kSlotBytes / 16 to their start-address field
+        const uint32_t x0a = smem_u32(sm), b0a = x0a + kXTileBytes;
+        uint64_t da01[2], da12[2], db0[2], db2[2];
 #pragma unroll
-                        for (int kk = 0; kk < 2; ++kk) {
-                            const uint64_t ad = smem_desc(xa + kk * 4096, 2048, 128);
-                            mma_f16(d, ad, smem_desc(ba + kk * 2 * kLbo01, kLbo01, 128), id1, kk);
-                            mma_f16(d + kN, ad, smem_desc(ba + kB01 + kk * 2 * kLbo2, kLbo2, 128), id2, 1);
-                        }
-                        mma_commit(bars + 8 * (kBarREmpty + sr));
-                        mma_commit(bars + 8 * (kBarBEmpty + L));
-                        mma_commit(bars + 8 * (kBarDFull + b));
-                        upar ^= 1u << L;
-                        ++tau;
+        for (int kk = 0; kk < 2; ++kk) {
+            // rows [x0; x1] and rows [x1; x2] of directions 16 kk .. 16 kk + 15
+            da01[kk] = smem_desc(x0a + kk * 2 * kXGroup, kXGroup, 128);
+            da12[kk] = smem_desc(x0a + kk * 2 * kXGroup + 1024, kXGroup, 128);
+            db0[kk] = smem_desc(b0a + kk * 2 * kLbo, kLbo, 128);
+            db2[kk] = smem_desc(b0a + kA2Off + kk * 2 * kLbo, kLbo, 128);
+        }
+        int64_t tau = 0;
+        int sl = 0, b = 0;
+        uint32_t sph = 0, dph = 0;                  // phase parity of the current slot / buffer round
+        bool ok = true;
+        for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
+            const int y = int(line % ny), z = int(line / ny);
+            const uint32_t lmask = line_mask(y, z, ny, nz);
+            for (int c = 0; c < nx && ok; ++c)
+                for (int L = 0; L < kLines && ok; ++L) {
+                    if (!((lmask >> L) & 1u)) continue;
+                    const uint32_t bx = bars + 8 * (kBarXFull + sl), bbf = bars + 8 * (kBarBFull + sl),
+                                   bde = bars + 8 * (kBarDEmpty + b);
+                    // the three conditions are tested at once; only a tile that is
+                    // not ready yet takes the polling path
+                    const bool r = bar_done(bx, sph) & bar_done(bbf, sph) & (tau < kDBufs || bar_done(bde, dph ^ 1u));
+                    if (!r)
+                        ok = bar_wait(bx, sph, limit, abort) && bar_wait(bbf, sph, limit, abort) &&
+                             (tau < kDBufs || bar_wait(bde, dph ^ 1u, limit, abort));
+                    ok = __all_sync(0xffffffffu, ok);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t d = tmem + uint32_t(b * kDCols);
+                    const uint64_t so = uint64_t(sl * (kSlotBytes >> 4));
+#pragma unroll
+                    for (int kk = 0; kk < 2; ++kk) {
+                        mma_bf16(d, da01[kk] + so, db0[kk] + so, id1, kk);          // [a0 | a1]
+                        mma_bf16(d + kN, da01[kk] + so, db2[kk] + so, id2, 1);      // a2
+                        mma_bf16(d + kN, da12[kk] + so, db0[kk] + so, id2, 1);      // a0 of x1, x2
                     }
-            }
+                    mma_commit(bars + 8 * (kBarSDone + sl));        // slot free, products ready
+                    ++tau;
+                    if (++sl == kSlots) { sl = 0; sph ^= 1u; }
+                    if (++b == kDBufs) { b = 0; dph ^= 1u; }
+                }
+        }
+        if (lane == 0) {
             if (!ok) {
                 *abort = 1;
                 atomicExch(a.err, 1);
@@ -507,86 +633,123 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             if (tau > 0) {
                 const int64_t last = tau - 1;
                 uint32_t spins = 0;
-                while (!bar_test(bars + 8 * (kBarDFull + int(last % kDBufs)), uint32_t((last / kDBufs) & 1)) &&
+                while (!bar_test(bars + 8 * (kBarSDone + int(last % kSlots)), uint32_t((last / kSlots) & 1)) &&
                        spins < limit)
                     ++spins;
             }
         }
-    } else if (warp == 5) {
-        // ---- state tile and A chunk copies (one thread) ----
-        if (lane == 0) {
-            const __half *x = static_cast<const __half *>(a.x);
-            const unsigned char *Au = reinterpret_cast<const unsigned char *>(P.Au);
-            const uint32_t ring0 = smem_u32(sm + kOffRing);
-            int64_t tau = 0;
-            bool ok = true;
-            for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
-                const int y = int(line % ny), z = int(line / ny);
-                const uint32_t lmask = line_mask(y, z, ny, nz);
-                const int64_t row0 = (int64_t(z) * ny + y) * nx;
-                for (int c = 0; c < 3 && c < nx; ++c) {
-                    l2_prefetch(Au + (row0 + c) * P.voxel_bytes, uint32_t(P.voxel_bytes));
-                    for (int L = 0; L < kLines && c < 2; ++L) {
-                        if (!((lmask >> L) & 1u)) continue;
-                        l2_prefetch(x + ((int64_t(z + L / 3 - 1) * ny + (y + L % 3 - 1)) * nx + c) * (kXTileBytes / 2),
+    } else if (warp == kWarpLoad0 || warp == kWarpLoad1) {
+        // ---- state tile and A chunk copies: two warps take alternate tiles.
+        // Lane 0 copies the state tile, lane 1 + 3 L + bb chunk bb of line L
+        // (its offsets held in registers), lanes 28-29 issue the L2 prefetches:
+        // each is one warp instruction with per-lane operands. ----
+        const int me = warp == kWarpLoad0 ? 0 : 1;
+        const __nv_bfloat16 *x = static_cast<const __nv_bfloat16 *>(a.x);
+        const unsigned char *Au = reinterpret_cast<const unsigned char *>(P.Au);
+        const uint32_t s0 = smem_u32(sm), st0 = smem_u32(sm + kOffStage);
+        const int64_t vb = P.voxel_bytes;
+        // this lane's chunk: line role my_l, output offset my_bb, role d = 3 L + 2 - bb
+        const int my_l = (lane - 1) / 3, my_bb = (lane - 1) % 3;
+        int my_len = 0, my_soff = 0, my_goff = 0;
+        if (lane >= 1 && lane <= 3 * kLines) {
+            const int d = 3 * my_l + 2 - my_bb;
+            my_soff = s_coff[3 * my_l + 3] - s_coff[d + 1];      // chunks sit in bb order
+            my_goff = s_coff[d];
+            my_len = s_coff[d + 1] - s_coff[d];
+        }
+        int64_t tau = 0;
+        int sl = 0, st = 0;
+        uint32_t sph = 0, stph = 0;                 // phase parity of the current slot / stage round
+        bool ok = true;
+        for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
+            const int y = int(line % ny), z = int(line / ny);
+            const uint32_t lmask = line_mask(y, z, ny, nz);
+            const int first_l = __ffs(lmask) - 1;
+            const int64_t row0 = (int64_t(z) * ny + y) * nx;
+            if (me == 0) {
+                // the line's first columns into L2: A of voxels 0-2, state tiles of columns 0-1
+                if (lane < 3 && lane < nx) l2_prefetch(Au + (row0 + lane) * vb, uint32_t(vb));
+                if (lane >= 3 && lane < 3 + 2 * kLines) {
+                    const int L = (lane - 3) % kLines, c = (lane - 3) / kLines;
+                    if (((lmask >> L) & 1u) && c < nx)
+                        l2_prefetch(x + ((int64_t(z + L / 3 - 1) * ny + (y + L % 3 - 1)) * nx + c) *
+                                            (kXTileBytes / 2),
                                     kXTileBytes);
-                    }
                 }
-                for (int c = 0; c < nx && ok; ++c)
-                    for (int L = 0; L < kLines && ok; ++L) {
-                        if (!((lmask >> L) & 1u)) continue;
-                        const int sr = int(tau % kRing);
-                        if (tau >= kRing &&
-                            !bar_wait(bars + 8 * (kBarREmpty + sr), uint32_t(((tau / kRing) - 1) & 1), limit, abort)) {
-                            ok = false;
-                            break;
-                        }
-                        const int64_t vi = (int64_t(z + L / 3 - 1) * ny + (y + L % 3 - 1)) * nx + c;
-                        uint32_t bytes = kXTileBytes, stage = 0;
-                        int chunk_len[3];
-#pragma unroll
-                        for (int bb = 0; bb < 3; ++bb) {
-                            const int d = 3 * L + 2 - bb;
-                            const int j = c - 1 + bb;
-                            chunk_len[bb] = (j >= 0 && j < nx) ? s_coff[d + 1] - s_coff[d] : 0;
-                            bytes += uint32_t(chunk_len[bb]);
-                        }
-                        // pull data two columns ahead into L2: the state tile of this line,
-                        // and once per column the whole A of the voxel three columns on
-                        if (c + 2 < nx) l2_prefetch(x + (vi + 2) * (kXTileBytes / 2), kXTileBytes);
-                        if (L == __ffs(lmask) - 1 && c + 3 < nx)
-                            l2_prefetch(Au + (row0 + c + 3) * P.voxel_bytes, uint32_t(P.voxel_bytes));
-                        const uint32_t slot = ring0 + sr * kRingSlot;
-                        const uint32_t fb = bars + 8 * (kBarRFull + sr);
-                        bar_expect_tx(fb, bytes);
-                        bulk_load(slot, x + vi * (kXTileBytes / 2), kXTileBytes, fb);
-#pragma unroll
-                        for (int bb = 0; bb < 3; ++bb) {
-                            const int d = 3 * L + 2 - bb;
-                            if (chunk_len[bb] > 0)
-                                bulk_load(slot + kXTileBytes + stage,
-                                          Au + (row0 + c - 1 + bb) * P.voxel_bytes + s_coff[d],
-                                          uint32_t(chunk_len[bb]), fb);
-                            stage += uint32_t(s_coff[d + 1] - s_coff[d]);
-                        }
-                        ++tau;
-                    }
             }
+            for (int c = 0; c < nx && ok; ++c)
+                for (int L = 0; L < kLines && ok; ++L) {
+                    if (!((lmask >> L) & 1u)) continue;
+                    const int tsl = sl, tst = st;
+                    const uint32_t tsph = sph, tstph = stph;
+                    const bool mine = (int(tau) & 1) == me;
+                    const bool reuse_s = tau >= kSlots, reuse_a = tau >= kStages;
+                    ++tau;
+                    if (++sl == kSlots) { sl = 0; sph ^= 1u; }
+                    if (++st == kStages) { st = 0; stph ^= 1u; }
+                    if (!mine) continue;
+                    // the tile slot's last MMAs and the staging slot's last scatter are done
+                    if (lane == 0)
+                        ok = (!reuse_s || bar_wait(bars + 8 * (kBarSDone + tsl), tsph ^ 1u, limit, abort)) &&
+                             (!reuse_a || bar_wait(bars + 8 * (kBarAEmpty + tst), tstph ^ 1u, limit, abort));
+                    ok = __shfl_sync(0xffffffffu, ok, 0);
+                    if (!ok) break;
+                    const int64_t vi = (int64_t(z + L / 3 - 1) * ny + (y + L % 3 - 1)) * nx + c;
+                    const uint32_t xb = bars + 8 * (kBarXFull + tsl), ab = bars + 8 * (kBarAFull + tst);
+                    // chunk bb of output c - 1 + bb exists inside the line only
+                    const bool valid = my_l == L && c - 1 + my_bb >= 0 && c - 1 + my_bb < nx;
+                    const int len = valid ? my_len : 0;
+                    int bytes = __shfl_sync(0xffffffffu, len, 1 + 3 * L) + __shfl_sync(0xffffffffu, len, 2 + 3 * L) +
+                                __shfl_sync(0xffffffffu, len, 3 + 3 * L);
+                    if (lane == 0) {
+                        bar_expect_tx(xb, kXTileBytes);
+                        bar_expect_tx(ab, uint32_t(bytes));
+                    }
+                    __syncwarp();
+                    uint32_t dst = st0 + tst * kStageBytes + my_soff, cb = ab, cl = uint32_t(len);
+                    const void *src = Au + (row0 + c - 1 + my_bb) * vb + my_goff;
+                    if (lane == 0) {
+                        dst = s0 + tsl * kSlotBytes;
+                        src = x + vi * (kXTileBytes / 2);
+                        cl = kXTileBytes;
+                        cb = xb;
+                    }
+                    if (cl > 0) bulk_load(dst, src, cl, cb);
+                    // data ahead into L2: this line's state tile two columns on and,
+                    // once per column, the whole A of the voxel three columns on
+                    const void *pf = x + (vi + 2) * (kXTileBytes / 2);
+                    uint32_t pl = (lane == 28 && c + 2 < nx) ? kXTileBytes : 0;
+                    if (lane == 29) {
+                        pf = Au + (row0 + c + 3) * vb;
+                        pl = (L == first_l && c + 3 < nx) ? uint32_t(vb) : 0;
+                    }
+                    if (pl > 0) l2_prefetch(pf, pl);
+                }
+        }
+        if (lane == 0) {
             if (!ok) {
                 *abort = 1;
                 atomicExch(a.err, 1);
             }
+            // after a failed wait anywhere, copies this warp issued may never be
+            // consumed: give them time to land (they cannot stall) before the
+            // block exits
+            if (*abort) {
+                uint64_t t0, t1;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+                do {
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+                } while (t1 - t0 < 1000000u);
+            }
         }
-    } else {
+    } else if (producer_of(warp) >= 0) {
         // ---- B operand tiles from the staged A chunks: producer warp w expands
-        // the tiles of ring slot w (tau = w mod 4), one warp per tile, so four
-        // tiles are expanded at once.  By the time its wait for the staged data
-        // succeeds, the loader has been released by the tile four back, hence
-        // the MMA and the epilogue have passed every earlier use of the tile's
-        // B slot: the slot's barrier is at most one phase behind. ----
-        const int pw = warp - 6, npw = kProducers / 32;
-        uint32_t upar = 0, used = 0;            // parity of each B slot's uses, slots used
-        int64_t tau = 0;
+        // the tiles of staging slot w (tau = w mod kStages), one warp per tile,
+        // so kStages tiles are expanded at once.  The tile's slot is free: the loader
+        // waited for its last MMAs before the copies this warp waits for. ----
+        const int pw = producer_of(warp);
+        int sl = 0, st = 0;
+        uint32_t stph = 0;                          // phase parity of the current stage round
         bool ok = true;
         for (int64_t line = blockIdx.x; line < n_lines && ok; line += gridDim.x) {
             const int y = int(line % ny), z = int(line / ny);
@@ -594,87 +757,71 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
             for (int c = 0; c < nx && ok; ++c)
                 for (int L = 0; L < kLines && ok; ++L) {
                     if (!((lmask >> L) & 1u)) continue;
-                    const uint32_t par = (upar >> L) & 1u, was = (used >> L) & 1u;
-                    upar ^= 1u << L;
-                    used |= 1u << L;
-                    const int64_t tme = tau++;
-                    if (int(tme % npw) != pw) continue;
-                    const int sr = int(tme % kRing);
-                    if (lane == 0) {
-                        bool w = bar_wait(bars + 8 * (kBarRFull + sr), uint32_t((tme / kRing) & 1), limit, abort);
-                        if (w && was) w = bar_wait(bars + 8 * (kBarBEmpty + L), par ^ 1u, limit, abort);
-                        if (!w) {
-                            failed[1] = 1;
-                            *abort = 1;
-                            atomicExch(a.err, 1);
-                        }
-                    }
-                    __syncwarp();
-                    if (failed[1]) {
+                    const int tsl = sl, tst = st;
+                    const uint32_t tph = stph;
+                    if (++sl == kSlots) sl = 0;
+                    if (++st == kStages) { st = 0; stph ^= 1u; }
+                    if (tst != pw) continue;
+                    if (!bar_wait(bars + 8 * (kBarAFull + pw), tph, limit, abort)) {
+                        *abort = 1;
+                        if (lane == 0) atomicExch(a.err, 1);
                         ok = false;
                         break;
                     }
-                    unsigned char *slot = sm + L * kBSlot;
-                    float *scale = reinterpret_cast<float *>(slot + kB01 + kB2);
-                    {
-                        // the state tile's row scales, for the epilogue (rows r and r + 32)
-                        const __half *xt = reinterpret_cast<const __half *>(sm + kOffRing + sr * kRingSlot);
-                        float *xs = reinterpret_cast<float *>(slot + kB01 + kB2 + kBScale);
-                        xs[lane] = pow2f(int(__half2float(xt[xtile_elem(lane, kExpDir)])));
-                        xs[lane + 32] = pow2f(int(__half2float(xt[xtile_elem(lane + 32, kExpDir)])));
-                    }
-                    const unsigned char *stage = sm + kOffRing + sr * kRingSlot + kXTileBytes;
+                    unsigned char *btile = sm + tsl * kSlotBytes + kXTileBytes;
+                    // positions outside this line's union are zero
+                    for (int i = lane; i < kBBytes / 16; i += 32)
+                        reinterpret_cast<uint4 *>(btile)[i] = make_uint4(0, 0, 0, 0);
+                    __syncwarp();
+                    const unsigned char *stage = sm + kOffStage + pw * kStageBytes;
 #pragma unroll
                     for (int bb = 0; bb < 3; ++bb) {
-                        const int j = c - 1 + bb;
-                        // input voxel (c, line L) is neighbour (1 - bb, L) of output j
+                        // input voxel (c, line L) is neighbour (1 - bb, L) of output c - 1 + bb
                         const int d = 3 * L + 2 - bb;
                         const int p0 = s_roff[d], np = s_roff[d + 1] - p0;
-                        const bool valid = j >= 0 && j < nx;
-                        const __half *t0 = reinterpret_cast<const __half *>(stage);
-                        const unsigned char *ea = stage + 6 * np;
-                        // four positions per iteration: their loads are issued before any store
+                        const uint16_t *t = reinterpret_cast<const uint16_t *>(stage);
+                        stage += s_coff[d + 1] - s_coff[d];
+                        // an output outside the line: its chunk was not copied and its
+                        // columns stay zero
+                        const int j = c - 1 + bb;
+                        if (j < 0 || j >= nx) continue;
+                        // four positions per lane and pass: all loads before the stores
                         for (int p = lane; p < np; p += 4 * 32) {
-                            uint32_t code[4];
-                            __half v0[4], v1[4], v2[4];
+                            uint32_t off[4];
+                            uint16_t v0[4], v1[4], v2[4];
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
                                 const int pk = p + 32 * k;
-                                code[k] = pk < np ? uint32_t(spos[p0 + pk]) : 0xFFFFu;
-                                v0[k] = v1[k] = v2[k] = __float2half_rn(0.0f);
-                                if (valid && pk < np) {
-                                    v0[k] = t0[pk];
-                                    v1[k] = t0[np + pk];
-                                    v2[k] = t0[2 * np + pk];
-                                }
+                                const bool in = pk < np;
+                                off[k] = in ? uint32_t(spos[p0 + pk]) : 0xFFFFFFFFu;
+                                v0[k] = in ? t[pk] : uint16_t(0);
+                                v1[k] = in ? t[np + pk] : uint16_t(0);
+                                v2[k] = in ? t[2 * np + pk] : uint16_t(0);
                             }
 #pragma unroll
                             for (int k = 0; k < 4; ++k) {
-                                if (code[k] == 0xFFFFu) continue;
-                                const int n = int(code[k] >> 8), q = bb * kDirs + int(code[k] & 255);
-                                const int within = (q >> 3) * 128 + (q & 7) * 16 + (n & 7) * 2;
-                                *reinterpret_cast<__half *>(slot + (n >> 3) * kLbo01 + within) = v0[k];
-                                *reinterpret_cast<__half *>(slot + (n >> 3) * kLbo01 + 10 * 128 + within) = v1[k];
-                                *reinterpret_cast<__half *>(slot + kB01 + (n >> 3) * kLbo2 + within) = v2[k];
+                                if (off[k] == 0xFFFFFFFFu) continue;
+                                unsigned char *e = btile + off[k];
+                                *reinterpret_cast<uint16_t *>(e) = v0[k];
+                                *reinterpret_cast<uint16_t *>(e + kA1Off) = v1[k];
+                                *reinterpret_cast<uint16_t *>(e + kA2Off) = v2[k];
                             }
                         }
-                        if (lane < kDirs) scale[bb * kDirs + lane] = valid ? pow2f(int(ea[lane]) - kExpBias) : 0.0f;
-                        stage += s_coff[d + 1] - s_coff[d];
                     }
                     // this warp's stores are made visible to the tensor cores, then its
-                    // lane 0 signals the tile
+                    // lane 0 signals the tile and frees the staging slot
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     __syncwarp();
                     if (lane == 0) {
-                        bar_arrive(bars + 8 * (kBarBFull + L));
-                        bar_arrive(bars + 8 * (kBarREmpty + sr));
+                        bar_arrive(bars + 8 * (kBarBFull + tsl));
+                        bar_arrive(bars + 8 * (kBarAEmpty + pw));
                     }
                 }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == kWarpMma) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kTmemCols));
     }
@@ -709,9 +856,11 @@ __global__ void tc_flags_kernel(SlicedMatrix A, int64_t V, uint8_t *flags)
 }
 
 // Row (voxel j, direction m): per block role d, Ea from the row's largest
-// |value| in the block; every value v becomes a0 = rint(v 2^-Ea) (|a0| <= 256),
-// a1 = fp16(v 2^-Ea - a0), a2 = fp16(v 2^-Ea - a0 - a1), stored at its union
-// position in the role's chunk, and Ea + 160 in the chunk's exponent bytes.
+// |value| in the block (a0 = rint(v 2^-Ea) then has |a0| <= 256); every value
+// v becomes a0 2^Ea, a1 = bf16(v - a0 2^Ea) and a2 = bf16(v - a0 2^Ea - a1),
+// stored as bf16 at its union position in the role's chunk (three arrays of
+// np values).  A block row whose largest |value| is below 2^kTinyExp is
+// stored as zero.
 __global__ void tc_convert_kernel(SlicedMatrix A, int64_t V, const int16_t *pidx, TcPlan P, unsigned char *Au)
 {
     const int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -728,12 +877,6 @@ __global__ void tc_convert_kernel(SlicedMatrix A, int64_t V, const int16_t *pidx
         rmax[d] = fmaxf(rmax[d], fabsf(v));
     });
     unsigned char *vox = Au + j * P.voxel_bytes;
-    for (int d = 0; d < kOffs; ++d) {
-        int e = 0;
-        frexpf(rmax[d], &e);
-        const int np = P.role_off[d + 1] - P.role_off[d];
-        vox[P.chunk_off[d] + 6 * np + m] = uint8_t(e - 8 + kExpBias);
-    }
     for_row(A, q, lane, [&](int code, float v) {
         if (v == 0.0f) return;
         const int d = code / kDirs, n = code % kDirs;
@@ -741,36 +884,36 @@ __global__ void tc_convert_kernel(SlicedMatrix A, int64_t V, const int16_t *pidx
         if (p < 0) return;                      // cannot happen: the union covers every entry
         int e = 0;
         frexpf(rmax[d], &e);
-        const float vs = ldexpf(v, 8 - e);      // exact, |vs| < 256
-        const float a0 = rintf(vs);
-        const float r1 = vs - a0;               // exact
-        const __half h1 = __float2half_rn(r1);
-        const float r2 = r1 - __half2float(h1); // exact
+        if (e <= kTinyExp) return;
+        const float a0 = scale2(rintf(scale2(v, 8 - e)), e - 8);   // exact, |rint| <= 256
+        const float r1 = v - a0;                // exact
+        const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(h1);  // exact
         const int np = P.role_off[d + 1] - P.role_off[d];
-        __half *t = reinterpret_cast<__half *>(vox + P.chunk_off[d]);
-        t[p] = __float2half_rn(a0);
+        __nv_bfloat16 *t = reinterpret_cast<__nv_bfloat16 *>(vox + P.chunk_off[d]);
+        t[p] = __float2bfloat16_rn(a0);         // exact
         t[np + p] = h1;
-        t[2 * np + p] = __float2half_rn(r2);
+        t[2 * np + p] = __float2bfloat16_rn(r2);
     });
 }
 
 // ---- state layout helpers ----
 
-__device__ __forceinline__ double tcx_value(const __half *x, int64_t v, int n, int r)
+__device__ __forceinline__ double tcx_value(const __nv_bfloat16 *x, int64_t v, int n, int r)
 {
-    const __half *t = x + v * (kXTileBytes / 2);
-    const double s = ldexp(1.0, int(__half2float(t[xtile_elem(r, kExpDir)])));
-    return (double(__half2float(t[xtile_elem(r, n)])) + double(__half2float(t[xtile_elem(64 + r, n)]))) * s;
+    const __nv_bfloat16 *t = x + v * (kXTileBytes / 2);
+    return double(__bfloat162float(t[xtile_elem(r, n)])) + double(__bfloat162float(t[xtile_elem(64 + r, n)])) +
+           double(__bfloat162float(t[xtile_elem(128 + r, n)]));
 }
 
-__global__ void tcx_to_canonical_kernel(const __half *x, int64_t V, int r, double *out)
+__global__ void tcx_to_canonical_kernel(const __nv_bfloat16 *x, int64_t V, int r, double *out)
 {
     const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (s >= V * kDirs) return;
     out[s] = tcx_value(x, s / kDirs, int(s % kDirs), r);
 }
 
-__global__ void tcx_from_canonical_kernel(const double *in, int64_t V, int r, __half *x)
+__global__ void tcx_from_canonical_kernel(const double *in, int64_t V, int r, __nv_bfloat16 *x)
 {
     const int64_t v = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (v >= V) return;
@@ -779,7 +922,7 @@ __global__ void tcx_from_canonical_kernel(const double *in, int64_t V, int r, __
     write_state_row(x + v * (kXTileBytes / 2), r, y);
 }
 
-__global__ void tcx_sum_kernel(const __half *x, int64_t V, int r, double *out)
+__global__ void tcx_sum_kernel(const __nv_bfloat16 *x, int64_t V, int r, double *out)
 {
     double acc = 0.0;
     for (int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; s < V * kDirs;
@@ -797,16 +940,16 @@ __global__ void tcx_sum_kernel(const __half *x, int64_t V, int r, double *out)
 }
 
 // Ledger of X(t): one warp per voxel tile, coalesced 16-byte chunks.  Chunk
-// ch (0..511) is row ch % 8 of core matrix ch / 8 = (direction group g, row
-// group h): rows rho = 8 h + ch % 8, directions 8 g .. 8 g + 7.  Lane l reads
-// chunks l + 32 k, whose right-hand side is l for even k and l + 32 for odd
-// k; its two row scales sit in chunks 12 and 13 (direction 26 of rows l, l + 32).
+// ch (0..767) is row ch % 8 of core matrix ch / 8 = 24 g + h (direction group
+// g, row group h): row rho = 8 h + ch % 8, directions 8 g .. 8 g + 7.  Lane l
+// reads chunks l + 32 k, k = 0..23: row l + 32 (k mod 6) of group k / 6, the
+// x0, x1 and x2 rows of right-hand side l for even k and l + 32 for odd k.
 __global__ void __launch_bounds__(256) tcx_ledger_kernel(StepArgs a)
 {
     __shared__ float red[2][64];
     for (int i = threadIdx.x; i < 128; i += blockDim.x) (&red[0][0])[i] = 0.0f;
     __syncthreads();
-    const __half *x = static_cast<const __half *>(a.x);
+    const __nv_bfloat16 *x = static_cast<const __nv_bfloat16 *>(a.x);
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -819,32 +962,26 @@ __global__ void __launch_bounds__(256) tcx_ledger_kernel(StepArgs a)
                          (xx == 0 ? 0 : (xx == a.nx - 1 ? 2 : 1));
         const double *et = a.tab.exit_total + (k * 27 + mask) * kDirs;
         const uint4 *t = reinterpret_cast<const uint4 *>(x + v * (kXTileBytes / 2));
-        float sc[2];
-#pragma unroll
-        for (int par = 0; par < 2; ++par) {
-            const uint4 raw = t[lane + 32 * (12 + par)];
-            sc[par] = scale2(1.0f, int(__half2float(reinterpret_cast<const __half *>(&raw)[kExpDir - 24])));
-        }
         float s[2] = {0.0f, 0.0f}, se[2] = {0.0f, 0.0f};
-#pragma unroll 4
-        for (int kc = 0; kc < 16; ++kc) {
+#pragma unroll 6
+        for (int kc = 0; kc < 24; ++kc) {
             const int ch = lane + 32 * kc;
-            const int n0 = (ch >> 7) * 8;
+            const int n0 = (kc / 6) * 8;
             const uint4 raw = t[ch];
-            const __half *h = reinterpret_cast<const __half *>(&raw);
+            const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&raw);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 const int n = n0 + i;
                 if (n >= kDirs) continue;
-                const float xv = __half2float(h[i]);
+                const float xv = __bfloat162float(h[i]);
                 s[kc & 1] += xv;
                 if (mask != 13) se[kc & 1] += float(et[n]) * xv;
             }
         }
 #pragma unroll
         for (int par = 0; par < 2; ++par) {
-            ab[par] += abs_k * s[par] * sc[par];
-            ex[par] += se[par] * sc[par];
+            ab[par] += abs_k * s[par];
+            ex[par] += se[par];
         }
     }
     for (int par = 0; par < 2; ++par) {
@@ -878,7 +1015,7 @@ __global__ void tcx_det_kernel(StepArgs a)
     const int Nu = N[ua], Nv = N[va];
     const int u0 = (pu * Nu + a.det_nu - 1) / a.det_nu, u1 = ((pu + 1) * Nu + a.det_nu - 1) / a.det_nu;
     const int v0 = (pv * Nv + a.det_nv - 1) / a.det_nv, v1 = ((pv + 1) * Nv + a.det_nv - 1) / a.det_nv;
-    const __half *x = static_cast<const __half *>(a.x);
+    const __nv_bfloat16 *x = static_cast<const __nv_bfloat16 *>(a.x);
     double sum = 0.0;
     for (int cv = v0; cv < v1; ++cv)
         for (int cu = u0; cu < u1; ++cu) {
@@ -910,7 +1047,7 @@ int sm_count()
 }  // namespace
 
 size_t tcx_state_bytes(int64_t V) { return size_t(V) * kXTileBytes; }
-int tc_stage_limit() { return kAStageMax; }
+int tc_stage_limit() { return kStageBytes; }
 int tc_position_limit() { return kPosMax; }
 
 cudaError_t launch_tc_flags(const SlicedMatrix &A, int64_t V, uint8_t *flags, cudaStream_t s)
@@ -987,7 +1124,7 @@ cudaError_t launch_tc_step(const StepArgs &a, bool functionals, cudaStream_t s)
 cudaError_t launch_tc_to_canonical(const void *x, int64_t V, int r, double *out, cudaStream_t s)
 {
     const int th = 256;
-    tcx_to_canonical_kernel<<<unsigned((V * kDirs + th - 1) / th), th, 0, s>>>(static_cast<const __half *>(x), V,
+    tcx_to_canonical_kernel<<<unsigned((V * kDirs + th - 1) / th), th, 0, s>>>(static_cast<const __nv_bfloat16 *>(x), V,
                                                                                 r, out);
     return cudaGetLastError();
 }
@@ -995,13 +1132,13 @@ cudaError_t launch_tc_to_canonical(const void *x, int64_t V, int r, double *out,
 cudaError_t launch_tc_from_canonical(const double *in, int64_t V, int r, void *x, cudaStream_t s)
 {
     const int th = 128;
-    tcx_from_canonical_kernel<<<unsigned((V + th - 1) / th), th, 0, s>>>(in, V, r, static_cast<__half *>(x));
+    tcx_from_canonical_kernel<<<unsigned((V + th - 1) / th), th, 0, s>>>(in, V, r, static_cast<__nv_bfloat16 *>(x));
     return cudaGetLastError();
 }
 
 cudaError_t launch_tc_sum(const void *x, int64_t V, int r, double *out, cudaStream_t s)
 {
-    tcx_sum_kernel<<<sm_count() * 2, 256, 0, s>>>(static_cast<const __half *>(x), V, r, out);
+    tcx_sum_kernel<<<sm_count() * 2, 256, 0, s>>>(static_cast<const __nv_bfloat16 *>(x), V, r, out);
     return cudaGetLastError();
 }
 
