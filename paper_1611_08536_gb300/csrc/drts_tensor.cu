@@ -226,6 +226,15 @@ __device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint32_t
     return false;
 }
 
+// The same wait for a whole warp: every lane polls, then a warp vote makes
+// the outcome uniform and brings the lanes back in step.  (Lanes that poll on
+// their own can leave a wait at different times; a warp split that way must
+// not reach an .aligned tcgen05 instruction, which needs every lane in step.)
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint32_t limit, volatile int *abort)
+{
+    return __all_sync(0xffffffffu, bar_wait(bar, parity, limit, abort));
+}
+
 __device__ __forceinline__ void l2_prefetch(const void *src, uint32_t bytes)
 {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(src), "r"(bytes) : "memory");
@@ -464,11 +473,12 @@ __device__ __forceinline__ bool epi_column(EpiState &s, const StepArgs &a, uint3
     for (int L = 0; L < kLines; ++L) {
         if (!((lmask >> L) & 1u)) continue;
         const int b = e.b;
-        if (!bar_wait(bars + 8 * (kBarSDone + e.sl), e.sph, a.spin_limit, abort)) {
+        if (!warp_wait(bars + 8 * (kBarSDone + e.sl), e.sph, a.spin_limit, abort)) {
             *abort = 1;
             if ((threadIdx.x & 31) == 0) atomicExch(a.err, 1);
             return false;
         }
+        __syncwarp();
         tc_fence_after();
         drain_tile<ROT>(s, tmem_q + uint32_t(b * kDCols), with_f);
         tc_fence_before();
@@ -607,7 +617,7 @@ __global__ void __launch_bounds__(kThreads, 1) tcx_step_kernel(StepArgs a)
                     if (!r)
                         ok = bar_wait(bx, sph, limit, abort) && bar_wait(bbf, sph, limit, abort) &&
                              (tau < kDBufs || bar_wait(bde, dph ^ 1u, limit, abort));
-                    ok = __all_sync(0xffffffffu, ok);
+                    ok = __all_sync(0xffffffffu, ok);           // uniform, lanes in step for elect.sync
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t d = tmem + uint32_t(b * kDCols);
