@@ -478,10 +478,12 @@ def batched_launches(args, tune, info, R):
     detector readout (when there are patches), the ledger reduction and the
     product (one launch per tile of right-hand sides, one for the
     shared-memory-halo order and the tensor-core form)."""
+    per = (1 if info.n_patch > 0 else 0) + 1
+    if args.batched_kernel == "tensor":
+        return (per + 1) * args.steps
     if tune is None:
         return None
-    per = (1 if info.n_patch > 0 else 0) + 1
-    if args.batched_kernel == "tensor" or tune["variant"] == 2:
+    if tune["variant"] == 2:
         per += 1
     else:
         per += -(-R // tune["rhs_tile"])
@@ -885,7 +887,8 @@ def main():
     ap.add_argument("--no-serve-baselines", dest="serve_baselines", action="store_false",
                     help="skip the one-after-another and per-simulation baseline runs")
     ap.add_argument("--sim-steps", type=int, default=1500, help="steps per simulation for sims/s")
-    ap.add_argument("--batched-kernel", default="cuda", choices=["cuda", "tensor"])
+    ap.add_argument("--batched-kernel", default="tensor", choices=["cuda", "tensor"],
+                    help="batched product: tcgen05 tensor-core form (default) or CUDA-core form")
     ap.add_argument("--functionals", action="store_true",
                     help="cost of point detectors and sub-step sources on the workload")
     ap.add_argument("--point-detectors", type=int, default=256)
