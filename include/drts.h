@@ -559,8 +559,9 @@ const char *drts_last_error(const drts_ctx *ctx);
  * fastest; state index site*12 + d.  One step moves light 2dr (all media
  * share one refractive index: there is no interface folding), and the edges
  * are open: mass whose target site lies outside the box leaves.  The matrix
- * follows Eq. 18-21 and 23 as on the voxel grid.  Only the host assembly
- * exists so far; the device step for this partition is not built.
+ * follows Eq. 18-21 and 23 as on the voxel grid.  drts_fcc_host_rows is the
+ * host assembly (FP64 rows); drts_fcc_assemble and the calls after it run the
+ * step on the device.
  */
 typedef struct drts_fcc_problem {
     int32_t nx, ny, nz;              /* integer box; nx even, ny, nz >= 1 */
@@ -579,6 +580,71 @@ typedef struct drts_fcc_problem {
  */
 drts_status drts_fcc_host_rows(const drts_fcc_problem *prob, int64_t row_begin, int64_t row_end,
                                int64_t *row_ptr, int32_t *col, double *val, int64_t cap);
+
+/*
+ * ---- The step on the close-packed partition, on the device ----
+ *
+ * The same Eq. 26 step x(t+1) = A x(t) + s(t) (x(0) = 0) on the close-packed
+ * sites, with A of Eq. 18-21 and 23 assembled on the device: the host builds
+ * only each medium's FP64 stencil (transition weights by lattice offset and
+ * direction pair); device kernels count, lay out (SELL-32 slices of 32
+ * consecutive sites of one direction, 16-bit codes offset*12 + n) and fill
+ * the rows, each row's entries in ascending column order.  Values and state
+ * in FP64 (DRTS_FP64) or FP32 (DRTS_FP32).  All calls are on the stream given
+ * to drts_fcc_assemble; those that return host data synchronise it.
+ */
+typedef struct drts_fcc_ctx drts_fcc_ctx;
+
+typedef struct drts_fcc_info {
+    int64_t n_sites;
+    int64_t n_states;                /* n_sites * 12 */
+    int64_t nnz;                     /* stored nonzeros */
+    int64_t slots;                   /* entries including slice padding */
+    int32_t n_offsets;               /* lattice offsets of the stencil (the site itself included) */
+    int32_t precision;
+    int64_t t;                       /* steps taken */
+    int64_t matrix_bytes;            /* values + codes on the device */
+} drts_fcc_info;
+
+/*
+ * Validates prob (as drts_fcc_host_rows), assembles A on the device and
+ * returns a context with x = 0, t = 0.  precision: DRTS_FP64 or DRTS_FP32
+ * (DRTS_EUNSUPPORTED otherwise).  cuda_stream: a cudaStream_t or NULL for the
+ * default stream.  Host inputs are read during the call only.  DRTS_EINVAL /
+ * DRTS_ENOMEM / DRTS_ECUDA with a message in drts_last_error(NULL).
+ */
+drts_status drts_fcc_assemble(const drts_fcc_problem *prob, int32_t precision, void *cuda_stream,
+                              drts_fcc_ctx **out);
+
+/*
+ * The source term s(t) of Eq. 26: s(t) = P(t) sum_e weights[e] e_{states[e]}
+ * with P(t) = profile[t - t0] for t0 <= t < t0 + n_t, else 0 (t counts the
+ * steps taken; step t adds s(t)).  states index n_sites * 12 (site * 12 + d),
+ * at most 64 entries; the arrays are copied.  Replaces an earlier source.
+ */
+drts_status drts_fcc_set_source(drts_fcc_ctx *ctx, int32_t n, const int64_t *states, const double *weights,
+                                int64_t t0, int32_t n_t, const double *profile);
+
+/* n steps of Eq. 26 on the context's stream (asynchronous). */
+drts_status drts_fcc_step_n(drts_fcc_ctx *ctx, int64_t n);
+
+/* x(t) in state order (site * 12 + d) as FP64, host_out [n_states], caller-owned. */
+drts_status drts_fcc_read_state(drts_fcc_ctx *ctx, double *host_out);
+
+/*
+ * Rows [row_begin, row_end) (state order) of the assembled A read back from
+ * the device as CSR: row_ptr [row_end - row_begin + 1] relative to
+ * row_begin, col / val [cap] (caller-owned; val in FP64 whatever the stored
+ * precision).  DRTS_EINVAL for a bad range or a cap below the entry count
+ * (row_ptr is filled either way).
+ */
+drts_status drts_fcc_read_rows(drts_fcc_ctx *ctx, int64_t row_begin, int64_t row_end, int64_t *row_ptr,
+                               int32_t *col, double *val, int64_t cap);
+
+drts_status drts_fcc_get_info(const drts_fcc_ctx *ctx, drts_fcc_info *out);
+
+/* Frees the context (NULL is a no-op); the stream is drained first. */
+drts_status drts_fcc_destroy(drts_fcc_ctx *ctx);
 
 #ifdef __cplusplus
 }

@@ -29,6 +29,7 @@ SOURCES = {
     "drts_tensor.cu": [],
     "drts_functionals.cu": [],
     "drts_fcc.cpp": [],
+    "drts_fcc_step.cu": [],
 }
 
 

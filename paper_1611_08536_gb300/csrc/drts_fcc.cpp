@@ -27,8 +27,6 @@
 namespace drts {
 namespace {
 
-constexpr int kFccDirs = 12;
-
 struct Vec3 {
     double x, y, z;
 };
@@ -161,6 +159,50 @@ drts_status fcc_fail(const std::string &m)
 }
 
 }  // namespace
+
+drts_status fcc_validate(const drts_fcc_problem *p)
+{
+    if (!p) return fcc_fail("problem is NULL");
+    if (p->nx < 2 || p->ny < 1 || p->nz < 1 || (p->nx & 1)) return fcc_fail("nx must be even and >= 2, ny, nz >= 1");
+    if (!(p->spacing_mm > 0.0)) return fcc_fail("spacing_mm must be > 0");
+    if (p->n_media < 1 || p->n_media > 255 || !p->media || !p->medium_of_site)
+        return fcc_fail("n_media must be 1..255 with media and medium_of_site");
+    const int64_t n_sites = int64_t(p->nx) * p->ny * p->nz / 2;
+    if (n_sites * kFccDirs >= (int64_t(1) << 31)) return fcc_fail("more than 2^31 states");
+    for (int k = 0; k < p->n_media; ++k) {
+        const drts_medium &m = p->media[k];
+        if (!(m.n > 0.0) || m.mu_s < 0.0 || m.mu_a < 0.0 || !(m.g > -1.0 && m.g < 1.0))
+            return fcc_fail("medium " + std::to_string(k) + " out of range");
+        if (m.n != p->media[0].n) return fcc_fail("all media need one refractive index (no interface folding)");
+    }
+    for (int64_t v = 0; v < n_sites; ++v)
+        if (p->medium_of_site[v] >= p->n_media) return fcc_fail("medium index out of range");
+    return DRTS_OK;
+}
+
+// The stencils of all media on one list of lattice offsets (the union of
+// the offsets any medium reaches, plus the site itself, which the device
+// step uses for padding entries): W[k][o][n][m].
+void fcc_tables(const drts_fcc_problem &p, FccTables &T)
+{
+    std::vector<FccStencil> S;
+    for (int k = 0; k < p.n_media; ++k) S.push_back(fcc_stencil(p.media[k], p.spacing_mm));
+    T.off.clear();
+    T.off.push_back({0, 0, 0});
+    for (const FccStencil &Sk : S)
+        for (const auto &o : Sk.off)
+            if (std::find(T.off.begin(), T.off.end(), o) == T.off.end()) T.off.push_back(o);
+    const size_t no = T.off.size();
+    T.W.assign(size_t(p.n_media) * no * kFccDirs * kFccDirs, 0.0);
+    for (int k = 0; k < p.n_media; ++k)
+        for (size_t o = 0; o < S[size_t(k)].off.size(); ++o) {
+            const size_t u = size_t(std::find(T.off.begin(), T.off.end(), S[size_t(k)].off[o]) - T.off.begin());
+            for (int n = 0; n < kFccDirs; ++n)
+                for (int m = 0; m < kFccDirs; ++m)
+                    T.W[((size_t(k) * no + u) * kFccDirs + n) * kFccDirs + m] = S[size_t(k)].at(o, n, m);
+        }
+}
+
 }  // namespace drts
 
 using namespace drts;
@@ -170,22 +212,9 @@ extern "C" {
 drts_status drts_fcc_host_rows(const drts_fcc_problem *p, int64_t row_begin, int64_t row_end,
                                int64_t *row_ptr, int32_t *col, double *val, int64_t cap)
 try {
-    if (!p) return fcc_fail("problem is NULL");
-    if (p->nx < 2 || p->ny < 1 || p->nz < 1 || (p->nx & 1)) return fcc_fail("nx must be even and >= 2, ny, nz >= 1");
-    if (!(p->spacing_mm > 0.0)) return fcc_fail("spacing_mm must be > 0");
-    if (p->n_media < 1 || p->n_media > 255 || !p->media || !p->medium_of_site)
-        return fcc_fail("n_media must be 1..255 with media and medium_of_site");
-    const int64_t n_sites = int64_t(p->nx) * p->ny * p->nz / 2;
-    const int64_t n_states = n_sites * kFccDirs;
-    if (n_states >= (int64_t(1) << 31)) return fcc_fail("more than 2^31 states");
-    for (int k = 0; k < p->n_media; ++k) {
-        const drts_medium &m = p->media[k];
-        if (!(m.n > 0.0) || m.mu_s < 0.0 || m.mu_a < 0.0 || !(m.g > -1.0 && m.g < 1.0))
-            return fcc_fail("medium " + std::to_string(k) + " out of range");
-        if (m.n != p->media[0].n) return fcc_fail("all media need one refractive index (no interface folding)");
-    }
-    for (int64_t v = 0; v < n_sites; ++v)
-        if (p->medium_of_site[v] >= p->n_media) return fcc_fail("medium index out of range");
+    const drts_status st = fcc_validate(p);
+    if (st != DRTS_OK) return st;
+    const int64_t n_states = int64_t(p->nx) * p->ny * p->nz / 2 * kFccDirs;
     if (row_begin < 0 || row_end < row_begin || row_end > n_states || !row_ptr) return fcc_fail("bad row range");
 
     std::vector<FccStencil> S;

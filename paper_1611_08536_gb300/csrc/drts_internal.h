@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <array>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -29,6 +30,18 @@ constexpr int kGroup = 4;         // entries per lane per vector load
 constexpr int kCenterCode = 13 * kDirs;  // offset (0,0,0), direction 0: padding
 constexpr int kMaxRhs = 64;
 constexpr int kMaxSrc = 64;
+
+// Close-packed (FCC) partition: 12 nearest-neighbour directions.
+constexpr int kFccDirs = 12;
+
+// Stencils of every medium of a close-packed problem on one list of lattice
+// offsets (offset 0 is the site itself): W[k][o][n][m], FP64, host-built.
+struct FccTables {
+    std::vector<std::array<int, 3>> off;
+    std::vector<double> W;
+};
+drts_status fcc_validate(const drts_fcc_problem *p);   // DRTS_EINVAL with a message
+void fcc_tables(const drts_fcc_problem &p, FccTables &T);
 
 // Lattice direction table (state order of Eq. 22).
 struct Directions {

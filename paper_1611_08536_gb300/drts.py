@@ -118,7 +118,8 @@ SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_dete
            "drts_checkpoint_size", "drts_checkpoint_save", "drts_checkpoint_load",
            "drts_set_point_detectors", "drts_read_point_detectors", "drts_sensor_response",
            "drts_source_column", "drts_inject_source_substeps", "drts_substep_count",
-           "drts_fcc_host_rows"]
+           "drts_fcc_host_rows", "drts_fcc_assemble", "drts_fcc_set_source", "drts_fcc_step_n",
+           "drts_fcc_read_state", "drts_fcc_read_rows", "drts_fcc_get_info", "drts_fcc_destroy"]
 
 _lib = None
 
@@ -145,6 +146,13 @@ def load(path: str = LIB_PATH):
     lib.drts_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.drts_host_tables.argtypes = [ctypes.POINTER(ProblemC), i32, vp, vp, vp, vp]
     lib.drts_fcc_host_rows.argtypes = [ctypes.POINTER(FccProblemC), i64, i64, vp, vp, vp, i64]
+    lib.drts_fcc_assemble.argtypes = [ctypes.POINTER(FccProblemC), i32, vp, ctypes.POINTER(vp)]
+    lib.drts_fcc_set_source.argtypes = [vp, i32, vp, vp, i64, i32, vp]
+    lib.drts_fcc_step_n.argtypes = [vp, i64]
+    lib.drts_fcc_read_state.argtypes = [vp, vp]
+    lib.drts_fcc_read_rows.argtypes = [vp, i64, i64, vp, vp, vp, i64]
+    lib.drts_fcc_get_info.argtypes = [vp, ctypes.POINTER(FccInfo)]
+    lib.drts_fcc_destroy.argtypes = [vp]
     lib.drts_set_launch.argtypes = [vp, i32, i32, i32, i32]
     lib.drts_state_sum_noalloc.argtypes = [vp, i32, vp]
     lib.drts_set_fault.argtypes = [vp, i32, i64]
@@ -227,6 +235,86 @@ def fcc_host_rows(shape, spacing_mm, media, medium_of_site, row_begin=0, row_end
         raise DrtsError(st, lib.drts_last_error(None).decode())
     nnz = int(rp[-1])
     return rp, col[:nnz].copy(), val[:nnz].copy()
+
+
+class FccInfo(ctypes.Structure):
+    _fields_ = [("n_sites", ctypes.c_int64), ("n_states", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("slots", ctypes.c_int64), ("n_offsets", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("t", ctypes.c_int64), ("matrix_bytes", ctypes.c_int64)]
+
+
+class FccContext:
+    """The Eq. 26 step on the close-packed partition, assembled and run on the
+    device (drts_fcc_assemble ... drts_fcc_destroy); marshalling only."""
+
+    def __init__(self, shape, spacing_mm, media, medium_of_site, precision=FP32, stream=None):
+        self._lib = load()
+        nx, ny, nz = shape
+        self.shape = tuple(shape)
+        self.n_states = nx * ny * nz // 2 * 12
+        med = (Medium * len(media))(*[Medium(*m) for m in media])
+        mos = np.ascontiguousarray(medium_of_site, dtype=np.uint8).ravel()
+        p = FccProblemC(nx, ny, nz, float(spacing_mm), len(media), med, _ptr(mos))
+        h = ctypes.c_void_p()
+        st = self._lib.drts_fcc_assemble(ctypes.byref(p), int(precision), ctypes.c_void_p(stream), ctypes.byref(h))
+        if st != OK:
+            raise DrtsError(st, self._lib.drts_last_error(None).decode())
+        self._h = h
+
+    def _check(self, st):
+        if st != OK:
+            raise DrtsError(st, self._lib.drts_last_error(None).decode())
+
+    def set_source(self, states, weights, profile, t0=0):
+        st_ = np.ascontiguousarray(states, dtype=np.int64)
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        pr = np.ascontiguousarray(profile, dtype=np.float64)
+        self._check(self._lib.drts_fcc_set_source(self._h, len(st_), _ptr(st_), _ptr(w), int(t0), len(pr),
+                                                  _ptr(pr)))
+
+    def step_n(self, n):
+        self._check(self._lib.drts_fcc_step_n(self._h, int(n)))
+
+    def read_state(self):
+        out = np.empty(self.n_states, np.float64)
+        self._check(self._lib.drts_fcc_read_state(self._h, _ptr(out)))
+        return out
+
+    def read_rows(self, row_begin=0, row_end=None, cap=None):
+        if row_end is None:
+            row_end = self.n_states
+        n = row_end - row_begin
+        rp = np.zeros(max(n, 0) + 1, np.int64)
+        if cap is None:
+            cap = 200 * max(n, 0) + 16
+        col = np.empty(cap, np.int32)
+        val = np.empty(cap, np.float64)
+        self._check(self._lib.drts_fcc_read_rows(self._h, int(row_begin), int(row_end), _ptr(rp), _ptr(col),
+                                                 _ptr(val), int(cap)))
+        nnz = int(rp[-1])
+        return rp, col[:nnz].copy(), val[:nnz].copy()
+
+    def info(self):
+        i = FccInfo()
+        self._check(self._lib.drts_fcc_get_info(self._h, ctypes.byref(i)))
+        return i
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.drts_fcc_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def problem_struct(prob, max_steps=0):
