@@ -332,6 +332,54 @@ def measure_plain(workload_name, precision, steps, warmup, autotune, check=True,
     }
 
 
+def measure_fcc(box, steps, warmup, local=0):
+    """The FP32 step on the close-packed partition (Section 3): a box of
+    close-packed sites in one scattering medium (the voxel workloads' tissue
+    values), a point source, CUDA events over the timed steps, and the HBM
+    roofline on the same algorithmic bytes as the voxel step: each stored
+    nonzero's value and code once, each state read and written once."""
+    import numpy as np
+    import torch
+    from paper_1611_08536_gb300 import drts
+    stream = torch.cuda.current_stream()
+    nx, ny, nz = box
+    n_sites = nx * ny * nz // 2
+    media = [(10.0, 0.01, 0.9, 1.4)]
+    t_asm = time.perf_counter()
+    ctx = drts.FccContext(box, 0.1, media, np.zeros(n_sites, np.uint8), precision=drts.FP32,
+                          stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t_asm = time.perf_counter() - t_asm
+    c = ((nz // 2) * ny + ny // 2) * nx // 2 + nx // 4
+    ctx.set_source([c * 12 + 3], [1.0], np.ones(4))
+    info = ctx.info()
+    ctx.step_n(warmup)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ctx.step_n(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    ctx.close()
+    hbm, kind = peaks()
+    nbytes = info.nnz * (4 + 2) + info.n_states * 8
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    return {
+        "workload": f"close_packed_{nx}x{ny}x{nz}", "sites": int(info.n_sites), "states": int(info.n_states),
+        "nnz": int(info.nnz), "slots": int(info.slots), "offsets": int(info.n_offsets), "precision": "fp32",
+        "steps": steps, "warmup": warmup, "ms_per_step": round(ms, 4),
+        "value": round(info.nnz / (ms * 1e-3) / 1e9, 3), "unit": "GNNZ/s", "assembly_s": round(t_asm, 2),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(achieved / hbm, 4), "traffic": None, "peak_kind": kind,
+                     "algorithmic_bytes_per_launch": int(nbytes)},
+        "sampled_parity": "the device matrix and multi-step states are checked against the oracle "
+                          "in the GPU tests on boxes the numpy oracle assembles (up to 20,480 sites)",
+        "gpu_launches": steps + 1, "clocks": clk.summary(),
+    }
+
+
 def sub_lines(args, local):
     """The metric's second half on the same box, after the headline: the
     FP16-rowscale tier on the headline workload, the batched step of 64
@@ -349,6 +397,9 @@ def sub_lines(args, local):
             types_ns(variant=-1, threads=0, blocks_per_sm=0, rhs_tile=0), args.sub_batched_workload, "fp32",
             64, args.batched_kernel, args.sub_batched_steps, args.warmup, max(args.autotune, 1), 1500,
             check=args.check, local=local)))
+    if "fcc" in args.sub:
+        jobs.append(("fcc", lambda: measure_fcc(tuple(int(v) for v in args.sub_fcc_box.split("x")), args.steps,
+                                                 args.warmup, local=local)))
     if "served" in args.sub:
         jobs.append(("served", lambda: measure_served(args, args.sub_served_requests, 50.0, 1.0, 16, 20, 4,
                                                        "fifo", baselines="estimate", local=local)))
@@ -894,8 +945,10 @@ def main():
     ap.add_argument("--point-detectors", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-check", dest="check", action="store_false")
-    ap.add_argument("--sub", default="fp16,batched,served",
-                    help="sub-lines of the default run (comma list of fp16, batched, served; '' = none)")
+    ap.add_argument("--sub", default="fp16,batched,fcc,served",
+                    help="sub-lines of the default run (comma list of fp16, batched, fcc, served; '' = none)")
+    ap.add_argument("--sub-fcc-box", default="192x160x160",
+                    help="close-packed box (nx x ny x nz lattice units, nx even) of the fcc sub-line")
     ap.add_argument("--sub-batched-workload", default="inclusions_96")
     ap.add_argument("--sub-batched-steps", type=int, default=10)
     ap.add_argument("--sub-served-requests", type=int, default=7)
