@@ -726,7 +726,15 @@ def measure_served(args, n_requests, rate, step_scale, resident, tick_steps, str
         "makespan_s": round(makespan, 3),
         "tick_wall_s": {"n": len(tick_host), "p50": round(float(np.percentile(tick_host, 50)), 5)
                         if tick_host else None},
-        "server_stats": stats, "clocks": clk.summary(),
+        "server_stats": stats,
+        "tick_graph_host_ms": {
+            "updated_in_place": round(1e3 * (stats["host_graph_s"] - stats["host_instantiate_s"])
+                                      / max(stats["graph_updates"], 1), 4),
+            "instantiated": round(1e3 * stats["host_instantiate_s"] / max(stats["graph_instantiations"], 1), 4),
+            "updates": stats["graph_updates"], "instantiations": stats["graph_instantiations"],
+            "note": "host time to capture the tick's launches and update the kept executable graph, against "
+                    "capture + instantiate (what every tick paid when each tick instantiated its graph)"},
+        "clocks": clk.summary(),
     }
     if baselines == "run":
         torch.cuda.synchronize()

@@ -492,6 +492,12 @@ typedef struct drts_server_stats {
     int64_t submitted, admitted, completed, failed, ticks, graph_launches;
     int32_t resident, queued;
     int64_t used_bytes, budget_bytes;
+    /* the tick graph: ticks whose executable graph was updated in place
+     * (same launches, new parameters), ticks that instantiated a new one,
+     * host seconds spent capturing and updating / instantiating in all
+     * ticks, and the part of it in the ticks that instantiated */
+    int64_t graph_updates, graph_instantiations;
+    double host_graph_s, host_instantiate_s;
 } drts_server_stats;
 
 /* Create a server on the current device (cfg is copied; *out owns its

@@ -6,7 +6,10 @@
 //   2. advances every resident simulation by up to steps_per_tick steps:
 //      all their step launches are captured into one CUDA graph whose
 //      branches fan out over n_streams streams, so the kernels of different
-//      simulations overlap on the device, and the graph is launched once;
+//      simulations overlap on the device, and the graph is launched once.
+//      The executable graph is kept: a tick whose launches match the
+//      previous one (same simulations and step counts, new parameters)
+//      updates it in place instead of instantiating a new one;
 //   3. retires finished simulations (detector history and ledger copied to
 //      host, device memory freed), which frees room for the next admissions.
 // Requests that arrive while others run are admitted at the next tick.
@@ -75,6 +78,7 @@ struct drts_server {
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> ev;
     cudaEvent_t fork = nullptr;
+    cudaGraphExec_t exec = nullptr;    // the tick graph, kept across ticks
     std::string err;
     drts_server_stats stats{};
 };
@@ -245,8 +249,8 @@ try {
     // 1. the steps of every resident simulation, captured in one graph
     std::vector<int64_t> running;
     for (int64_t id : s->resident) running.push_back(id);
-    cudaGraphExec_t exec = nullptr;
     if (!running.empty()) {
+        const Clock::time_point t_graph = Clock::now();
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(s->main, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) e = cudaEventRecord(s->fork, s->main);
@@ -271,11 +275,34 @@ try {
             if (graph) cudaGraphDestroy(graph);
             return sfail(s, st, "tick: step launch failed during capture");
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+        // the previous tick's executable graph takes the new parameters when
+        // the launches are the same (same simulations, same step counts);
+        // otherwise a new one is instantiated
+        if (e == cudaSuccess && s->exec) {
+            cudaGraphExecUpdateResultInfo ui{};
+            if (cudaGraphExecUpdate(s->exec, graph, &ui) == cudaSuccess) {
+                s->stats.graph_updates++;
+            } else {
+                cudaGetLastError();
+                cudaGraphExecDestroy(s->exec);
+                s->exec = nullptr;
+            }
+        }
+        bool instantiated = false;
+        if (e == cudaSuccess && !s->exec) {
+            e = cudaGraphInstantiate(&s->exec, graph, 0);
+            if (e == cudaSuccess) s->stats.graph_instantiations++;
+            else s->exec = nullptr;
+            instantiated = true;
+        }
         if (graph) cudaGraphDestroy(graph);
-        if (e == cudaSuccess) e = cudaGraphLaunch(exec, s->main);
+        const double host_s = std::chrono::duration<double>(Clock::now() - t_graph).count();
+        s->stats.host_graph_s += host_s;
+        if (instantiated) s->stats.host_instantiate_s += host_s;
+        if (e == cudaSuccess) e = cudaGraphLaunch(s->exec, s->main);
         if (e != cudaSuccess) {
-            if (exec) cudaGraphExecDestroy(exec);
+            if (s->exec) cudaGraphExecDestroy(s->exec);
+            s->exec = nullptr;
             return sfail(s, DRTS_ECUDA, std::string("tick graph: ") + cudaGetErrorString(e));
         }
         s->stats.ticks++;
@@ -323,7 +350,6 @@ try {
     }
     // 3. wait for the tick, retire finished simulations
     cudaError_t e = cudaStreamSynchronize(s->main);
-    if (exec) cudaGraphExecDestroy(exec);
     if (e != cudaSuccess) return sfail(s, DRTS_ECUDA, std::string("tick: ") + cudaGetErrorString(e));
     std::vector<int64_t> keep;
     for (int64_t id : running) {
@@ -445,6 +471,7 @@ void drts_server_destroy(drts_server *s)
         cudaEventDestroy(s->ev[i]);
     }
     cudaEventDestroy(s->fork);
+    if (s->exec) cudaGraphExecDestroy(s->exec);
     cudaStreamDestroy(s->main);
     cudaStreamDestroy(s->admit);
     delete s;

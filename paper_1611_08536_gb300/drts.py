@@ -89,7 +89,9 @@ class ServerStats(ctypes.Structure):
                 ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("ticks", ctypes.c_int64), ("graph_launches", ctypes.c_int64),
                 ("resident", ctypes.c_int32), ("queued", ctypes.c_int32),
-                ("used_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64)]
+                ("used_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
+                ("graph_updates", ctypes.c_int64), ("graph_instantiations", ctypes.c_int64),
+                ("host_graph_s", ctypes.c_double), ("host_instantiate_s", ctypes.c_double)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}

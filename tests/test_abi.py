@@ -81,7 +81,7 @@ print(st, h.value is None, lib.drts_last_error(None).decode())
 
 STRUCTS = [("Medium", "drts_medium"), ("ProblemC", "drts_problem"), ("Info", "drts_info"),
            ("TuneResult", "drts_tune_result"), ("ServerConfig", "drts_server_config"),
-           ("RequestInfo", "drts_request_info"), ("ServerStats", "drts_server_stats"),
+           ("RequestInfo", "drts_request_info"), ("ServerStats", "drts_server_stats"), ("FccInfo", "drts_fcc_info"),
            ("FccProblemC", "drts_fcc_problem")]
 
 

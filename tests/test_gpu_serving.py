@@ -63,6 +63,10 @@ def test_server_results_equal_alone_and_admit_while_running(gpu):
         st = srv.stats()
         assert st["completed"] == len(ids) and st["failed"] == 0
         assert seen_mixed                           # continuous batching, not one batch
+        # every tick launched one graph; ticks with the same resident set
+        # updated the kept executable graph instead of instantiating one
+        assert st["graph_updates"] + st["graph_instantiations"] == st["graph_launches"]
+        assert st["graph_updates"] >= 1 and st["host_graph_s"] > 0.0
         for rid, req in zip(ids, reqs):
             alone = run_alone(gpu, req)
             for r in range(len(req.sources)):
