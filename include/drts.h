@@ -92,15 +92,20 @@ typedef struct drts_problem {
     int32_t batched_kernel;          /* n_rhs > 1: DRTS_BATCHED_CUDA_CORES or DRTS_BATCHED_TENSOR */
 } drts_problem;
 
-/* Batched step (n_rhs > 1) implementations:
+/* Batched step (n_rhs > 1) implementations (Eq. 26 with R right-hand sides
+ * sharing A; both within 1e-5 of the FP64 oracle over 1500 steps):
  *   DRTS_BATCHED_CUDA_CORES  sliced sparse A, one pass per tile of 4..32 rhs,
- *                            compensated FP32 sums (the accurate default);
- *                            state kept in groups of four right-hand sides;
- *   DRTS_BATCHED_TENSOR      A as 27 dense 32x32 blocks per voxel, each value
- *                            split exactly into three bf16 parts, on the tensor
- *                            cores, all rhs in one pass (DRTS_FP32 precision,
- *                            n_rhs <= 64; the tensor cores' FP32 accumulation
- *                            leaves ~1e-7 relative per step). */
+ *                            compensated FP32 sums; state kept in groups of
+ *                            four right-hand sides;
+ *   DRTS_BATCHED_TENSOR      tcgen05 tensor cores, all rhs in one pass
+ *                            (DRTS_FP32 precision, n_rhs <= 64): A stored per
+ *                            voxel and neighbour role at the problem's union
+ *                            of block positions, as three bf16 terms (the
+ *                            first an integer of <= 9 bits times a
+ *                            power-of-two row scale, so each tile's leading
+ *                            products sum exactly), the state as three bf16
+ *                            terms per value, FP32 sums per output; the
+ *                            faster form. */
 #define DRTS_BATCHED_CUDA_CORES 0
 #define DRTS_BATCHED_TENSOR 1
 
