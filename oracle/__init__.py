@@ -84,6 +84,7 @@ class _Problem(ctypes.Structure):
         ("boundary", ctypes.c_int32),
         ("det_face", ctypes.c_int32),
         ("det_nu", ctypes.c_int32), ("det_nv", ctypes.c_int32),
+        ("interface", ctypes.c_int32),
     ]
 
 
@@ -166,7 +167,8 @@ class Problem:
                           _ptr(self.keep[2]), _ptr(self.keep[3]),
                           _ptr(self.keep[4]), float(prob.n_outside),
                           int(prob.boundary), int(prob.det_face),
-                          int(prob.det_nu), int(prob.det_nv))
+                          int(prob.det_nu), int(prob.det_nv),
+                          int(getattr(prob, "interface", 0)))
         self.shape = (nx, ny, nz)
         self.n_states = nx * ny * nz * NDIR
 

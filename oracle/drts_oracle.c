@@ -17,7 +17,8 @@
  *   - the state vector of Eq. 22 and the system matrix of Eq. 23, built by
  *     scattering every source state's contributions into target rows;
  *   - boundary and interface reflection / refraction, Section 4.2, in the
- *     first-order reading stated at orc_fold();
+ *     first-order reading stated at orc_fold(), or, for layered media, the
+ *     two-step crossing of the planar interfaces (build_two_step());
  *   - the step J(t+dt) = A J(t) + B P(t) of Eq. 26 and the detector
  *     functional of Eq. 27 (exit mass through a face patch).
  *
@@ -58,6 +59,7 @@ typedef struct {
     int32_t boundary;         /* 0 open, 1 mirror, 2 fresnel */
     int32_t det_face;         /* 0..5 = -x,+x,-y,+y,-z,+z; -1 for none */
     int32_t det_nu, det_nv;   /* detector patch grid on that face */
+    int32_t interface;        /* 0 first-order folding (R6); 1 planar two-step (R19) */
 } orc_problem;
 
 /* one raw contribution of a source state: target offset o, direction m */
@@ -259,6 +261,217 @@ static void free_stencil(orc_stencil *S)
     for (int n = 0; n < NDIR; ++n) free(S->e[n]);
 }
 
+/* ------------------------------------------------------------------------ */
+/* Planar interfaces crossed in two steps (Section 4.2; reading R19)         */
+
+static inline int64_t vox(const orc_problem *P, int x, int y, int z);
+
+/* Spread mass w over the lattice points closer than h to the segment [A, B]
+ * (a point when A = B), weights (h - d) / sum (Eq. 18/19), into entries of
+ * source direction n with target direction m. */
+static void spread(orc_stencil *S, int n, int cap, const double A[3], const double B[3], int m, double w)
+{
+    if (!(w > 0.0)) return;
+    double wsum = 0.0, wr[125];
+    int oo[125][3], cnt = 0;
+    for (int z = -2; z <= 2; ++z) for (int y = -2; y <= 2; ++y) for (int x = -2; x <= 2; ++x) {
+        double p[3] = {x, y, z};
+        double dd = seg_dist(p, A, B);
+        if (dd * dd < 1.0 - TIE_MARGIN) {
+            oo[cnt][0] = x; oo[cnt][1] = y; oo[cnt][2] = z;
+            wr[cnt] = 1.0 - dd; wsum += wr[cnt]; ++cnt;
+        }
+    }
+    for (int q = 0; q < cnt; ++q) {
+        if (abs(oo[q][0]) > 1 || abs(oo[q][1]) > 1 || abs(oo[q][2]) > 1) abort();
+        add_entry(S, n, cap, oo[q], m, wr[q] / wsum * w);
+    }
+}
+
+/* A Dirac source of mass `mass` at point C (units of h) moving along unit
+ * vector D for the path l (units of h) in a medium (mu_s, mu_a, phase row
+ * grow[m] for scattering out of D): Eq. 18 for the unscattered share, landing
+ * around C + l D in the directions dir[0..nd) with weights dw, Eq. 19 for the
+ * scattered share around [C + l S_m, C + l D] into every m. */
+static void dirac_step(orc_stencil *S, int n, int cap, const double C[3], const double D[3], double l,
+                       double mu_s, double mu_a, double h, const double grow[NDIR], const int *dir,
+                       const double *dw, int nd, double mass)
+{
+    double B[3] = {C[0] + l * D[0], C[1] + l * D[1], C[2] + l * D[2]};
+    double un = mass * exp(-(mu_s + mu_a) * l * h);
+    for (int q = 0; q < nd; ++q) spread(S, n, cap, B, B, dir[q], un * dw[q]);
+    double sc = mass * (1.0 - exp(-mu_s * l * h)) * exp(-mu_a * l * h);
+    if (sc > 0.0)
+        for (int m = 0; m < NDIR; ++m) {
+            double A[3] = {C[0] + l * DIRS[m][0], C[1] + l * DIRS[m][1], C[2] + l * DIRS[m][2]};
+            spread(S, n, cap, A, B, m, sc * grow[m]);
+        }
+}
+
+/*
+ * Contributions of a source in medium k1 whose direction n reaches the plane
+ * to a layer of medium k2 (another refractive index) half a voxel away, for
+ * every n with S_nz != 0 and crossing fraction tc = 1/2 / (lambda_1 |S_nz|)
+ * below 1 (active[n] = 1), split into entries that fold as usual (S1) and
+ * entries that meet no further interface (S0):
+ *  - S1: photons scattered before the crossing point, at a fraction s in
+ *    [0, tc) of the step, land around the segment from lambda_1 S_m (s = 0)
+ *    to lambda_1 (tc S_n + (1 - tc) S_m) (s = tc) in direction m, with the
+ *    scattering probability of the path tc L_1 and the absorption of the
+ *    whole step in medium 1 (Eq. 10 over the first part);
+ *  - S0: the unscattered share exp(-(mu_s + mu_a) tc L_1) reaches C = tc L_1
+ *    S_n and becomes two Dirac sources: R (unpolarised Fresnel at the true
+ *    incidence angle) reflected along S_n with its z component reversed for
+ *    the rest of the step in medium 1, 1 - R refracted by Snell's law for the
+ *    rest of the step in medium 2 (path (1 - tc) L_2); the refracted
+ *    direction's state is shared between the two lattice directions of its
+ *    azimuth whose polar angles bracket its own, linearly in the angle (the
+ *    normal +-z, the incident direction's angle, the horizontal).
+ */
+static int build_two_step(const orc_problem *P, int k1, int k2, orc_stencil *S1, orc_stencil *S0, int active[NDIR])
+{
+    const int cap = 27 * NDIR;
+    double nmin = min_index(P), h = P->h;
+    double n1 = P->n[k1], n2 = P->n[k2];
+    double l1 = nmin / n1, l2 = nmin / n2;
+    double G1[NDIR][NDIR];
+    hg_table(P->g[k1], G1);
+    for (int n = 0; n < NDIR; ++n) {
+        S1->count[n] = S0->count[n] = 0;
+        S1->e[n] = (orc_entry *)malloc(sizeof(orc_entry) * cap);
+        S0->e[n] = (orc_entry *)malloc(sizeof(orc_entry) * cap);
+        if (!S1->e[n] || !S0->e[n]) return -1;
+        active[n] = 0;
+        double sz = DIRS[n][2];
+        if (sz == 0.0) continue;
+        double tc = 0.5 / (l1 * fabs(sz));
+        if (!(tc < 1.0)) continue;
+        active[n] = 1;
+        int sg = sz > 0.0 ? 1 : -1;
+        /* scattered before C */
+        double p1 = (1.0 - exp(-P->mu_s[k1] * tc * l1 * h)) * exp(-P->mu_a[k1] * l1 * h);
+        if (p1 > 0.0)
+            for (int m = 0; m < NDIR; ++m) {
+                double A[3] = {l1 * DIRS[m][0], l1 * DIRS[m][1], l1 * DIRS[m][2]};
+                double B[3];
+                for (int a = 0; a < 3; ++a) B[a] = l1 * (tc * DIRS[n][a] + (1.0 - tc) * DIRS[m][a]);
+                spread(S1, n, cap, A, B, m, p1 * G1[n][m]);
+            }
+        /* unscattered to C, then reflected and refracted */
+        double p0 = exp(-(P->mu_s[k1] + P->mu_a[k1]) * tc * l1 * h);
+        double C[3] = {tc * l1 * DIRS[n][0], tc * l1 * DIRS[n][1], tc * l1 * DIRS[n][2]};
+        double cos_i = fabs(sz);
+        double R = orc_fresnel(cos_i, n1, n2);
+#ifdef PLANT_TWO_STEP_NO_FLIP
+        int nr = n;
+#else
+        int nr = DIRI[(-DIRV[n][2] + 1) * 9 + (DIRV[n][1] + 1) * 3 + (DIRV[n][0] + 1)];
+#endif
+        double wr1 = 1.0;
+        dirac_step(S0, n, cap, C, DIRS[nr], (1.0 - tc) * l1, P->mu_s[k1], P->mu_a[k1], h, G1[nr], &nr, &wr1, 1,
+                   p0 * R);
+        if (R < 1.0) {
+            double sin_i = sqrt(1.0 - cos_i * cos_i);
+#ifdef PLANT_SNELL_INVERTED
+            double sin_t = n2 / n1 * sin_i;
+            if (sin_t > 1.0) sin_t = 1.0;
+#else
+            double sin_t = n1 / n2 * sin_i;
+#endif
+            double cos_t = sqrt(1.0 - sin_t * sin_t);
+            double D[3] = {0.0, 0.0, sg * cos_t};
+            int dir[2];
+            double dw[2];
+            int nd = 1;
+            dir[0] = n;
+            dw[0] = 1.0;
+            if (sin_i > 0.0) {
+                double hl = sqrt(DIRS[n][0] * DIRS[n][0] + DIRS[n][1] * DIRS[n][1]);
+                D[0] = sin_t * DIRS[n][0] / hl;
+                D[1] = sin_t * DIRS[n][1] / hl;
+                double th_i = atan2(sin_i, cos_i), th_t = atan2(sin_t, cos_t);
+                int axis = DIRI[(sg + 1) * 9 + 1 * 3 + 1];
+                int horiz = DIRI[1 * 9 + (DIRV[n][1] + 1) * 3 + (DIRV[n][0] + 1)];
+                double half_pi = 2.0 * atan(1.0);
+                if (th_t <= th_i) {
+                    dir[0] = n;    dw[0] = th_t / th_i;
+                    dir[1] = axis; dw[1] = 1.0 - dw[0];
+                } else {
+                    dir[0] = n;     dw[0] = (half_pi - th_t) / (half_pi - th_i);
+                    dir[1] = horiz; dw[1] = 1.0 - dw[0];
+                }
+                nd = 2;
+            }
+            /* phase row for scattering out of the refracted direction */
+            double grow[NDIR], gsum = 0.0;
+            for (int m = 0; m < NDIR; ++m) {
+                grow[m] = hg(P->g[k2], D[0] * DIRS[m][0] + D[1] * DIRS[m][1] + D[2] * DIRS[m][2]);
+                gsum += grow[m];
+            }
+            for (int m = 0; m < NDIR; ++m) grow[m] /= gsum;
+#ifdef PLANT_TWO_STEP_PATH_MEDIUM1
+            dirac_step(S0, n, cap, C, D, (1.0 - tc) * l1, P->mu_s[k2], P->mu_a[k2], h, grow, dir, dw, nd,
+                       p0 * (1.0 - R));
+#else
+            dirac_step(S0, n, cap, C, D, (1.0 - tc) * l2, P->mu_s[k2], P->mu_a[k2], h, grow, dir, dw, nd,
+                       p0 * (1.0 - R));
+#endif
+        }
+    }
+    return 0;
+}
+
+/* Two-step tables of every ordered pair of media with different indices
+ * (built on first use; NULL entries elsewhere). */
+typedef struct {
+    int K;
+    orc_stencil *S1, *S0;    /* [K*K] */
+    int *active;             /* [K*K][NDIR] */
+    int *built;              /* [K*K] */
+} orc_two_step;
+
+static orc_two_step *two_step_new(const orc_problem *P)
+{
+    if (!P->interface) return NULL;
+    orc_two_step *T = (orc_two_step *)calloc(1, sizeof(orc_two_step));
+    int K = P->n_media;
+    T->K = K;
+    T->S1 = (orc_stencil *)calloc((size_t)K * K, sizeof(orc_stencil));
+    T->S0 = (orc_stencil *)calloc((size_t)K * K, sizeof(orc_stencil));
+    T->active = (int *)calloc((size_t)K * K * NDIR, sizeof(int));
+    T->built = (int *)calloc((size_t)K * K, sizeof(int));
+    return T;
+}
+
+static void two_step_free(orc_two_step *T)
+{
+    if (!T) return;
+    for (int q = 0; q < T->K * T->K; ++q)
+        if (T->built[q]) { free_stencil(&T->S1[q]); free_stencil(&T->S0[q]); }
+    free(T->S1); free(T->S0); free(T->active); free(T->built); free(T);
+}
+
+/* The two-step tables for source (voxel i of medium k, direction n), or 0
+ * when that state crosses no planar interface within the step. */
+static int two_step_for(const orc_problem *P, orc_two_step *T, const int i[3], int k, int n,
+                        const orc_stencil **S1, const orc_stencil **S0)
+{
+    if (!T || DIRV[n][2] == 0) return 0;
+    int zn = i[2] + DIRV[n][2];
+    if (zn < 0 || zn >= P->nz) return 0;
+    int k2 = P->medium[vox(P, i[0], i[1], zn)];
+    if (P->n[k2] == P->n[k]) return 0;
+    int q = k * T->K + k2;
+    if (!T->built[q]) {
+        if (build_two_step(P, k, k2, &T->S1[q], &T->S0[q], T->active + (size_t)q * NDIR)) abort();
+        T->built[q] = 1;
+    }
+    if (!T->active[(size_t)q * NDIR + n]) return 0;
+    *S1 = &T->S1[q];
+    *S0 = &T->S0[q];
+    return 1;
+}
+
 static inline int64_t vox(const orc_problem *P, int x, int y, int z)
 {
     return ((int64_t)z * P->ny + y) * P->nx + x;
@@ -304,10 +517,12 @@ typedef struct {
  *    the source medium throughout.
  *
  * Writes up to two in-grid outputs; exit[f] receives the mass that leaves
- * through face f = 2*axis + (high side).
+ * through face f = 2*axis + (high side).  no_interface skips the interface
+ * part (the second part of a two-step crossing, which meets no further
+ * interface within the step).
  */
 static int orc_fold(const orc_problem *P, const int i[3], int k, const orc_entry *e,
-                    orc_out out[2], double exit[6])
+                    orc_out out[2], double exit[6], int no_interface)
 {
     int N[3] = {P->nx, P->ny, P->nz};
     int t[3] = {i[0] + e->o[0], i[1] + e->o[1], i[2] + e->o[2]};
@@ -338,7 +553,7 @@ static int orc_fold(const orc_problem *P, const int i[3], int k, const orc_entry
     }
     if (w == 0.0) return 0;
 
-    if (!ghost && (e->o[0] || e->o[1] || e->o[2])) {
+    if (!ghost && !no_interface && (e->o[0] || e->o[1] || e->o[2])) {
         double ni = P->n[k];
         double nt = nidx(P, t[0], t[1], t[2]);
         if (nt != ni) {
@@ -399,6 +614,13 @@ static int check_problem(const orc_problem *P)
     if (P->n_media < 1 || P->n_media > 256) return -1;
     if ((int64_t)P->nx * P->ny * P->nz * NDIR >= ((int64_t)1 << 31)) return -1;
     for (int k = 0; k < P->n_media; ++k) if (P->n[k] <= 0.0) return -1;
+    if (P->interface != 0 && P->interface != 1) return -1;
+    if (P->interface == 1)              /* planar interfaces: one medium per z layer */
+        for (int z = 0; z < P->nz; ++z) {
+            int k0 = P->medium[vox(P, 0, 0, z)];
+            for (int y = 0; y < P->ny; ++y) for (int x = 0; x < P->nx; ++x)
+                if (P->medium[vox(P, x, y, z)] != k0) return -1;
+        }
     return 0;
 }
 
@@ -411,6 +633,7 @@ orc_csr *orc_assemble(const orc_problem *P, int z0, int z1)
     if (check_problem(P) || z0 < 0 || z1 > P->nz || z0 >= z1) return NULL;
     orc_stencil *S = (orc_stencil *)calloc(P->n_media, sizeof(orc_stencil));
     for (int k = 0; k < P->n_media; ++k) build_stencil(P, k, &S[k]);
+    orc_two_step *TS = two_step_new(P);
 
     int64_t plane_rows = (int64_t)P->nx * P->ny * NDIR;
     orc_csr *C = (orc_csr *)calloc(1, sizeof(orc_csr));
@@ -434,9 +657,13 @@ orc_csr *orc_assemble(const orc_problem *P, int z0, int z1)
                 int k = P->medium[vox(P, xs, ys, zs)];
                 for (int n = 0; n < NDIR; ++n) {
                     int32_t col = (int32_t)(vox(P, xs, ys, zs) * NDIR + n);
-                    for (int q = 0; q < S[k].count[n]; ++q) {
+                    const orc_stencil *S1 = &S[k], *S0 = NULL;
+                    two_step_for(P, TS, i, k, n, &S1, &S0);
+                    int n1 = S1->count[n], n0 = S0 ? S0->count[n] : 0;
+                    for (int q = 0; q < n1 + n0; ++q) {
                         orc_out out[2]; double ex[6] = {0};
-                        int no = orc_fold(P, i, k, &S[k].e[n][q], out, ex);
+                        int no = q < n1 ? orc_fold(P, i, k, &S1->e[n][q], out, ex, 0)
+                                        : orc_fold(P, i, k, &S0->e[n][q - n1], out, ex, 1);
                         for (int u = 0; u < no; ++u) {
                             if (out[u].t[2] != zt) continue;
                             if (nt >= tcap) {
@@ -491,6 +718,7 @@ orc_csr *orc_assemble(const orc_problem *P, int z0, int z1)
     free(T); free(T2); free(cnt);
     for (int k = 0; k < P->n_media; ++k) free_stencil(&S[k]);
     free(S);
+    two_step_free(TS);
     return C;
 }
 
@@ -523,6 +751,7 @@ int orc_column_info(const orc_problem *P, double *absorb, double *exit_total,
     if (check_problem(P)) return -1;
     orc_stencil *S = (orc_stencil *)calloc(P->n_media, sizeof(orc_stencil));
     for (int k = 0; k < P->n_media; ++k) build_stencil(P, k, &S[k]);
+    orc_two_step *TS = two_step_new(P);
     double nmin = min_index(P);
     int N[3] = {P->nx, P->ny, P->nz};
     int fa = P->det_face >= 0 ? P->det_face / 2 : -1;
@@ -540,12 +769,24 @@ int orc_column_info(const orc_problem *P, double *absorb, double *exit_total,
         }
         for (int n = 0; n < NDIR; ++n) {
             double ex[6] = {0, 0, 0, 0, 0, 0};
-            for (int q = 0; q < S[k].count[n]; ++q) {
+            const orc_stencil *S1 = &S[k], *S0 = NULL;
+            two_step_for(P, TS, i, k, n, &S1, &S0);
+            for (int q = 0; q < S1->count[n]; ++q) {
                 orc_out out[2];
-                orc_fold(P, i, k, &S[k].e[n][q], out, ex);
+                orc_fold(P, i, k, &S1->e[n][q], out, ex, 0);
+            }
+            for (int q = 0; S0 && q < S0->count[n]; ++q) {
+                orc_out out[2];
+                orc_fold(P, i, k, &S0->e[n][q], out, ex, 1);
             }
             int64_t s = v * NDIR + n;
             absorb[s] = 1.0 - exp(-P->mu_a[k] * L);
+            if (S0) {   /* a two-step crossing: whatever the raw entries do not carry is absorbed */
+                double kept = 0.0;
+                for (int q = 0; q < S1->count[n]; ++q) kept += S1->e[n][q].w;
+                for (int q = 0; q < S0->count[n]; ++q) kept += S0->e[n][q].w;
+                absorb[s] = 1.0 - kept;
+            }
             exit_total[s] = ex[0] + ex[1] + ex[2] + ex[3] + ex[4] + ex[5];
             exit_det[s] = P->det_face >= 0 ? ex[P->det_face] : 0.0;
             det_patch[s] = patch;
@@ -553,6 +794,7 @@ int orc_column_info(const orc_problem *P, double *absorb, double *exit_total,
     }
     for (int k = 0; k < P->n_media; ++k) free_stencil(&S[k]);
     free(S);
+    two_step_free(TS);
     return 0;
 }
 
@@ -725,7 +967,7 @@ int orc_source_column(const orc_problem *P, int64_t state, double frac, int32_t 
     double ex[6] = {0, 0, 0, 0, 0, 0};
     for (int q = 0; q < S.count[n]; ++q) {
         orc_out out[2];
-        int no = orc_fold(P, i, k, &S.e[n][q], out, ex);
+        int no = orc_fold(P, i, k, &S.e[n][q], out, ex, 0);
         for (int u = 0; u < no; ++u) {
             ts[nt] = vox(P, out[u].t[0], out[u].t[1], out[u].t[2]) * NDIR + out[u].m;
             tw[nt] = out[u].w;

@@ -47,6 +47,11 @@ def direction_vector(d: int):
     return (q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1)
 
 
+# interface treatment (Section 4.2): per-contribution first-order folding, or
+# the two-step crossing of planar interfaces (layered media only)
+INTERFACE_FIRST_ORDER, INTERFACE_TWO_STEP = 0, 1
+
+
 @dataclasses.dataclass
 class Problem:
     shape: tuple                   # (nx, ny, nz)
@@ -62,6 +67,7 @@ class Problem:
     det_nv: int = 16
     name: str = ""
     batched_kernel: int = 0        # 0 CUDA cores, 1 tensor cores (n_rhs > 1)
+    interface: int = 0             # INTERFACE_FIRST_ORDER or INTERFACE_TWO_STEP (layered media)
 
     @property
     def n_voxels(self) -> int:

@@ -1,18 +1,20 @@
 """The pins catch plausible mistakes: the oracle is rebuilt with one planted
 mistake at a time (on the CPU) and at least one pin must fail.  Each check
-below is one of the pins of test_oracle_pins.py or test_oracle_extensions.py,
-run against the mutant."""
+below is one of the pins of test_oracle_pins.py, test_oracle_extensions.py,
+test_oracle_symmetry.py or test_oracle_two_step.py, run against the mutant."""
 import pytest
 
 from paper_1611_08536_gb300 import inputs as I
 from tests import test_oracle_extensions as ext
 from tests import test_oracle_pins as pins
 from tests import test_oracle_symmetry as sym
+from tests import test_oracle_two_step as two
 
 PLANTS = ["PLANT_DROP_UNSCATTERED", "PLANT_ABSORB_ONCE", "PLANT_SEGMENT_SIGN",
           "PLANT_HG_UNNORMALISED", "PLANT_MIRROR_INDEX", "PLANT_FRESNEL_SWAP",
           "PLANT_WRONG_DIRECTION_INDEX", "PLANT_POINT_OFF_BY_ONE", "PLANT_SENSOR_LAG_SIGN",
-          "PLANT_SOURCE_FULL_PATH", "PLANT_HIGH_FACE_NO_FLIP"]
+          "PLANT_SOURCE_FULL_PATH", "PLANT_HIGH_FACE_NO_FLIP",
+          "PLANT_SNELL_INVERTED", "PLANT_TWO_STEP_PATH_MEDIUM1", "PLANT_TWO_STEP_NO_FLIP"]
 
 CHECKS = [
     pins.test_axis_direction_single_target,
@@ -32,6 +34,11 @@ CHECKS = [
     ext.test_sensor_delayed_impulse_shifts,
     lambda o: ext.test_source_column_axis_closed_form(o, 0.25),
     lambda o: sym.test_homogeneous_cube_has_the_48_symmetries(o, I.MIRROR),
+    two.test_mass_and_fresnel_share_oblique,
+    two.test_snell_angle_of_the_transmitted_split,
+    two.test_scattering_free_beam_lands_around_the_two_step_points,
+    two.test_normal_incidence,
+    two.test_absorption_along_the_two_path_pieces,
 ]
 
 
