@@ -45,9 +45,12 @@ def test_batched_launch_count():
     assert bench.batched_launches(args, {"variant": 2, "rhs_tile": 4}, info, 64) == 3 * 5
     args.batched_kernel = "tensor"
     assert bench.batched_launches(args, {"variant": 0, "rhs_tile": 16}, info, 64) == 3 * 5
+    # the tensor-core form needs no tuning record to count its launches
+    assert bench.batched_launches(args, None, info, 64) == 3 * 5
+    # the CUDA-core form without a tuning record has no known count
+    args.batched_kernel = "cuda"
     assert bench.batched_launches(args, None, info, 64) is None
     # no detector patches: no detector launch
-    args.batched_kernel = "cuda"
     assert bench.batched_launches(args, {"variant": 1, "rhs_tile": 4}, _info(1, 1, 0), 6) == (1 + 2) * 5
 
 
