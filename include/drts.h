@@ -52,6 +52,19 @@ typedef int32_t drts_status;
 #define DRTS_MIRROR 1        /* mass is reflected back (closed box) */
 #define DRTS_FRESNEL 2       /* unpolarised Fresnel split against n_outside */
 
+/* treatment of a change of refractive index inside the grid (Section 4.2) */
+#define DRTS_INTERFACE_FIRST_ORDER 0  /* each raw target folded once: the Fresnel share at
+                                         the lattice direction's angle is reflected, the rest
+                                         transmitted without a change of direction; the step
+                                         keeps the source medium throughout */
+#define DRTS_INTERFACE_TWO_STEP 1     /* planar interfaces normal to z (one medium per z
+                                         layer): a state whose direction reaches the plane
+                                         half a voxel away within the step travels in two
+                                         parts, splitting at the crossing point into the
+                                         Fresnel share reflected at the true incidence angle
+                                         and the share refracted by Snell's law, which
+                                         finishes the step in the other medium at its speed */
+
 /* storage / arithmetic precision of the time step */
 #define DRTS_FP64 0          /* A, state and accumulation in FP64 */
 #define DRTS_FP32 1          /* A and state in FP32, FP32 accumulation */
@@ -90,6 +103,11 @@ typedef struct drts_problem {
     int32_t det_nu, det_nv;          /* detector patch grid on that face */
     int64_t max_steps;               /* detector history capacity in steps */
     int32_t batched_kernel;          /* n_rhs > 1: DRTS_BATCHED_CUDA_CORES or DRTS_BATCHED_TENSOR */
+    int32_t interface;               /* DRTS_INTERFACE_FIRST_ORDER or DRTS_INTERFACE_TWO_STEP;
+                                        TWO_STEP needs one medium per z layer (else
+                                        DRTS_EINVAL).  Sub-step source columns
+                                        (drts_source_column, drts_inject_source_substeps)
+                                        use the first-order fold in both modes. */
 } drts_problem;
 
 /* Batched step (n_rhs > 1) implementations (Eq. 26 with R right-hand sides
@@ -217,8 +235,10 @@ drts_status drts_sensor_response(drts_ctx *ctx, int32_t rhs, int32_t which, int6
  * it leaves the centre of voxel i in direction n (state_idx = i*26 + n) and
  * travels only the fraction frac (0 < frac <= 1) of the step's path L_k:
  * Eq. 18/19/21 evaluated for the path frac * L_k, folded at the domain edge
- * and at interfaces as the system matrix is.  frac = 1 is column state_idx
- * of A; as frac -> 0 the population stays in state_idx.  Writes the target
+ * and at interfaces as the first-order system matrix is.  frac = 1 is
+ * column state_idx of A under DRTS_INTERFACE_FIRST_ORDER (under TWO_STEP
+ * the columns of crossing states differ); as frac -> 0 the population stays
+ * in state_idx.  Writes the target
  * states (ascending) and values to host arrays of capacity cap; *count
  * receives the number of targets (DRTS_EINVAL, with *count set, if it
  * exceeds cap) and, if exit_mass is not NULL, *exit_mass the mass that
@@ -314,6 +334,26 @@ drts_status drts_get_info(const drts_ctx *ctx, drts_info *out);
  */
 drts_status drts_host_tables(const drts_problem *prob, int32_t medium, double *stencil_out,
                              double *exit_total_out, double *exit_det_out, float *dir_scale_out);
+
+/*
+ * Host-built two-step entries of a DRTS_INTERFACE_TWO_STEP problem (Section
+ * 4.2, planar interface crossed in two parts), computed without a device: a
+ * state in a voxel of medium k1 whose z neighbour layer holds medium k2.
+ * Outputs are caller-owned, any may be NULL:
+ *   cross_out [26]: 1 when direction n reaches the plane between the layers
+ *                   within the step (those states use the entries below
+ *                   instead of medium k1's stencil), else 0;
+ *   fold_out  [26][27][26]: mass scattered before the plane, by target
+ *                   offset o and direction m (folded at edges and interfaces
+ *                   as the stencil is);
+ *   edge_out  [26][27][26]: mass reflected or refracted at the plane (folded
+ *                   at the grid edge only).
+ * DRTS_EINVAL for a problem drts_assemble would reject, interface !=
+ * DRTS_INTERFACE_TWO_STEP, or media k1, k2 that do not meet across a z plane
+ * with different refractive indices.
+ */
+drts_status drts_two_step_tables(const drts_problem *prob, int32_t k1, int32_t k2, uint8_t *cross_out,
+                                 double *fold_out, double *edge_out);
 
 /* Set the launch shape of the step kernel (0 = library default): blocks per
  * SM (must fit), threads per block (multiple of 32, <= 256), right-hand sides

@@ -111,6 +111,7 @@ def _bind(path):
     lib.orc_source_column.argtypes = [P, ctypes.c_int64, ctypes.c_double,
                                       ctypes.c_int32, vp, vp, vp]
     lib.orc_raw_stencil.argtypes = [P, ctypes.c_int, vp]
+    lib.orc_two_step_stencil.argtypes = [P, ctypes.c_int, ctypes.c_int, vp, vp, vp]
     lib.orc_fresnel.restype = ctypes.c_double
     lib.orc_fresnel.argtypes = [ctypes.c_double] * 3
     lib.orc_direction.argtypes = [ctypes.c_int, vp]
@@ -319,6 +320,19 @@ def raw_stencil(prob, k: int) -> np.ndarray:
     if lib.orc_raw_stencil(ctypes.byref(P.s), int(k), _ptr(W)):
         raise ValueError("oracle: invalid problem")
     return W
+
+
+def two_step_stencil(prob, k1: int, k2: int):
+    """Two-step entries of a source in medium k1 next to a z layer of medium
+    k2: (S1, S0, active) with S1/S0[n][o][m] dense and active[n] in {0, 1}."""
+    lib = _load()
+    P = prob if isinstance(prob, Problem) else Problem(prob)
+    S1 = np.empty((NDIR, 27, NDIR), np.float64)
+    S0 = np.empty((NDIR, 27, NDIR), np.float64)
+    act = np.empty(NDIR, np.int32)
+    if lib.orc_two_step_stencil(ctypes.byref(P.s), int(k1), int(k2), _ptr(S1), _ptr(S0), _ptr(act)):
+        raise ValueError("oracle: invalid problem or medium pair")
+    return S1, S0, act
 
 
 def fresnel(cos_i: float, n1: float, n2: float) -> float:

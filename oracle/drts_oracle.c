@@ -906,6 +906,38 @@ int orc_raw_stencil(const orc_problem *P, int k, double *W)
     return 0;
 }
 
+/* Dense two-step entries of a source in medium k1 next to a z layer of
+ * medium k2 (another refractive index): S1[n][o][m] (folded like the usual
+ * entries), S0[n][o][m] (folded at the grid edge only) and active[n] (S_n
+ * reaches the plane within the step); test access to build_two_step(). */
+int orc_two_step_stencil(const orc_problem *P, int k1, int k2, double *S1, double *S0, int32_t *active)
+{
+    init_dirs();
+    if (check_problem(P) || k1 < 0 || k1 >= P->n_media || k2 < 0 || k2 >= P->n_media) return -1;
+    if (P->n[k1] == P->n[k2]) return -1;
+    orc_stencil A, B;
+    int act[NDIR];
+    if (build_two_step(P, k1, k2, &A, &B, act)) return -1;
+    memset(S1, 0, sizeof(double) * NDIR * 27 * NDIR);
+    memset(S0, 0, sizeof(double) * NDIR * 27 * NDIR);
+    for (int n = 0; n < NDIR; ++n) {
+        active[n] = act[n];
+        for (int q = 0; q < A.count[n]; ++q) {
+            const orc_entry *e = &A.e[n][q];
+            int o = (e->o[2] + 1) * 9 + (e->o[1] + 1) * 3 + (e->o[0] + 1);
+            S1[((int64_t)n * 27 + o) * NDIR + e->m] += e->w;
+        }
+        for (int q = 0; q < B.count[n]; ++q) {
+            const orc_entry *e = &B.e[n][q];
+            int o = (e->o[2] + 1) * 9 + (e->o[1] + 1) * 3 + (e->o[0] + 1);
+            S0[((int64_t)n * 27 + o) * NDIR + e->m] += e->w;
+        }
+    }
+    free_stencil(&A);
+    free_stencil(&B);
+    return 0;
+}
+
 /*
  * Sensor response of Eq. 27: a sensor integrates the photons reaching it with
  * an impulse response h over a window of +-w steps around t,

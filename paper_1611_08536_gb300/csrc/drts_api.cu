@@ -40,7 +40,10 @@ struct drts_ctx {
     int64_t x_elems = 0;
     double *ledger = nullptr;            // [R][4]
     double *det = nullptr;               // [R][max_steps][n_patch]
-    double *d_absorb = nullptr, *d_exit_tot = nullptr, *d_exit_det = nullptr;
+    double *d_absorb = nullptr, *d_exit_tot = nullptr, *d_exit_det = nullptr;   // per ledger class
+    double *d_absorb_dir = nullptr;      // [C][26] two-step interfaces, else null
+    uint8_t *d_cls = nullptr;            // [V] ledger class of each voxel (= d_med without two-step)
+    std::vector<uint8_t> cls_host;       // [V] host copy (two-step interfaces only; else med_host)
     SourceEntry *d_src = nullptr;
     SourceProfile *d_prof = nullptr;
     double *d_prof_vals = nullptr;
@@ -198,6 +201,15 @@ drts_status validate(const drts_problem *p)
         return fail(nullptr, DRTS_EINVAL, "bad batched_kernel");
     if (p->batched_kernel == DRTS_BATCHED_TENSOR && p->n_rhs > 1 && p->precision != DRTS_FP32)
         return fail(nullptr, DRTS_EUNSUPPORTED, "the tensor-core batched step runs FP32 problems");
+    if (p->interface != DRTS_INTERFACE_FIRST_ORDER && p->interface != DRTS_INTERFACE_TWO_STEP)
+        return fail(nullptr, DRTS_EINVAL, "bad interface");
+    if (p->interface == DRTS_INTERFACE_TWO_STEP) {
+        // planar interfaces normal to z: one medium per z layer
+        const int64_t layer = int64_t(p->nx) * p->ny;
+        for (int64_t v = 0; v < V; ++v)
+            if (p->medium_of_voxel[v] != p->medium_of_voxel[v - v % layer])
+                return fail(nullptr, DRTS_EINVAL, "two-step interfaces need one medium per z layer");
+    }
     return DRTS_OK;
 }
 
@@ -283,8 +295,9 @@ StepArgs make_args(drts_ctx *c)
     a.tcp = c->tcp;
     a.src_voxel = c->d_src_voxel;
     a.x = c->x; a.y = c->y;
-    a.med = c->T.med;
+    a.cls = c->d_cls;
     a.tab.absorb = c->d_absorb;
+    a.tab.absorb_dir = c->d_absorb_dir;
     a.tab.exit_total = c->d_exit_tot;
     a.tab.exit_det = c->d_exit_det;
     a.det_face = c->prob.det_face;
@@ -492,9 +505,9 @@ try {
         (e = upload(c, &dnr, H.nref)) != cudaSuccess ||
         (e = upload(c, &dmed, med)) != cudaSuccess ||
         (e = dalloc(c, &dplain, size_t(c->V))) != cudaSuccess ||
-        (e = upload(c, &c->d_absorb, H.absorb)) != cudaSuccess ||
-        (e = upload(c, &c->d_exit_tot, H.exit_total)) != cudaSuccess ||
-        (e = upload(c, &c->d_exit_det, H.exit_det)) != cudaSuccess) {
+        (e = upload(c, &c->d_absorb, H.led_absorb)) != cudaSuccess ||
+        (e = upload(c, &c->d_exit_tot, H.led_exit_total)) != cudaSuccess ||
+        (e = upload(c, &c->d_exit_det, H.led_exit_det)) != cudaSuccess) {
         cuda_fail(c, e, "table upload");
         return bail(e == cudaErrorMemoryAllocation ? DRTS_ENOMEM : DRTS_ECUDA);
     }
@@ -504,7 +517,28 @@ try {
     T.W = dW; T.tmpl_off = dto; T.tmpl_n = dtn; T.tmpl_val = dtv;
     T.r_edge = dre; T.r_int = dri; T.nref = dnr; T.med = dmed; T.plain = dplain;
     c->d_med = dmed;
+    c->d_cls = dmed;
     c->med_host = med;
+    if (prob->interface == DRTS_INTERFACE_TWO_STEP) {
+        // pair tables for the assembler, per-layer ledger classes for the step
+        const int64_t layer = int64_t(prob->nx) * prob->ny;
+        c->cls_host.resize(size_t(c->V));
+        for (int64_t v = 0; v < c->V; ++v) c->cls_host[size_t(v)] = H.class_of_layer[size_t(v / layer)];
+        int32_t *dps = nullptr;
+        uint8_t *dcr = nullptr;
+        double *dw2f = nullptr, *dw2n = nullptr;
+        if ((e = upload(c, &dps, H.pair_slot)) != cudaSuccess ||
+            (H.n_pairs > 0 && ((e = upload(c, &dcr, H.cross)) != cudaSuccess ||
+                               (e = upload(c, &dw2f, H.W2f)) != cudaSuccess ||
+                               (e = upload(c, &dw2n, H.W2n)) != cudaSuccess)) ||
+            (e = upload(c, &c->d_absorb_dir, H.led_absorb_dir)) != cudaSuccess ||
+            (e = upload(c, &c->d_cls, c->cls_host)) != cudaSuccess) {
+            cuda_fail(c, e, "two-step table upload");
+            return bail(e == cudaErrorMemoryAllocation ? DRTS_ENOMEM : DRTS_ECUDA);
+        }
+        T.interface = DRTS_INTERFACE_TWO_STEP;
+        T.pair_slot = dps; T.cross = dcr; T.W2f = dw2f; T.W2n = dw2n;
+    }
 
     // slices and counts
     SlicedMatrix &A = c->A;
@@ -862,27 +896,53 @@ try {
     return caught(nullptr, "drts_host_tables");
 }
 
+drts_status drts_two_step_tables(const drts_problem *prob, int32_t k1, int32_t k2, uint8_t *cross_out,
+                                 double *fold_out, double *edge_out)
+try {
+    drts_status st = validate(prob);
+    if (st != DRTS_OK) return st;
+    if (prob->interface != DRTS_INTERFACE_TWO_STEP)
+        return fail(nullptr, DRTS_EINVAL, "interface is not DRTS_INTERFACE_TWO_STEP");
+    if (k1 < 0 || k1 >= prob->n_media || k2 < 0 || k2 >= prob->n_media)
+        return fail(nullptr, DRTS_EINVAL, "medium out of range");
+    HostTables H;
+    const std::string err = build_host_tables(*prob, H);
+    if (!err.empty()) return fail(nullptr, DRTS_EINVAL, err);
+    const int q = H.pair_slot[size_t(k1) * prob->n_media + k2];
+    if (q < 0) return fail(nullptr, DRTS_EINVAL, "the media do not meet across a z plane with different indices");
+    const size_t nw = size_t(kDirs) * kOffs * kDirs;
+    if (cross_out) std::memcpy(cross_out, H.cross.data() + size_t(q) * kDirs, kDirs);
+    if (fold_out) std::memcpy(fold_out, H.W2f.data() + size_t(q) * nw, nw * sizeof(double));
+    if (edge_out) std::memcpy(edge_out, H.W2n.data() + size_t(q) * nw, nw * sizeof(double));
+    return DRTS_OK;
+} catch (...) {
+    return caught(nullptr, "drts_two_step_tables");
+}
+
 drts_status drts_column_info(drts_ctx *c, double *absorb, double *exit_total, double *exit_det)
 try {
     if (!c) return DRTS_EINVAL;
-    // host evaluation of the per-(medium, face mask, direction) tables over
-    // the medium map (a one-off readout, not part of the step)
-    std::vector<uint8_t> med(size_t(c->V));
-    cudaError_t e = cudaMemcpyAsync(med.data(), c->T.med, size_t(c->V), cudaMemcpyDeviceToHost, c->stream);
+    // host evaluation of the per-(ledger class, face mask, direction) tables
+    // the step reads, over the class map on the device (a one-off readout,
+    // not part of the step)
+    std::vector<uint8_t> cls(size_t(c->V));
+    cudaError_t e = cudaMemcpyAsync(cls.data(), c->d_cls, size_t(c->V), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "column_info");
+    const HostTables &H = c->host;
     const int nx = c->prob.nx, ny = c->prob.ny, nz = c->prob.nz;
     for (int64_t v = 0; v < c->V; ++v) {
         const int x = int(v % nx), y = int(v / nx % ny), z = int(v / (int64_t(nx) * ny));
         const int b[3] = {x == 0 ? 0 : (x == nx - 1 ? 2 : 1), y == 0 ? 0 : (y == ny - 1 ? 2 : 1),
                           z == 0 ? 0 : (z == nz - 1 ? 2 : 1)};
         const int mask = b[2] * 9 + b[1] * 3 + b[0];
-        const int k = med[size_t(v)];
+        const int k = cls[size_t(v)];
         for (int d = 0; d < kDirs; ++d) {
             const size_t ti = (size_t(k) * 27 + mask) * kDirs + d;
-            if (absorb) absorb[v * kDirs + d] = c->host.absorb[k];
-            if (exit_total) exit_total[v * kDirs + d] = c->host.exit_total[ti];
-            if (exit_det) exit_det[v * kDirs + d] = c->host.exit_det[ti];
+            if (absorb)
+                absorb[v * kDirs + d] = H.led_absorb_dir.empty() ? H.led_absorb[k] : H.led_absorb_dir[k * kDirs + d];
+            if (exit_total) exit_total[v * kDirs + d] = H.led_exit_total[ti];
+            if (exit_det) exit_det[v * kDirs + d] = H.led_exit_det[ti];
         }
     }
     return DRTS_OK;
@@ -1265,6 +1325,7 @@ drts_status source_column_host(drts_ctx *c, int64_t state, double frac,
     HostTables tf;
     drts_problem p = c->prob;
     p.media = c->media.data();
+    p.interface = DRTS_INTERFACE_FIRST_ORDER;   // sub-step columns use the first-order fold
     const std::string terr = build_host_tables(p, tf, frac);
     if (!terr.empty()) return fail(c, DRTS_EINVAL, terr);
     double *dW = nullptr, *dout = nullptr;
@@ -1275,6 +1336,7 @@ drts_status source_column_host(drts_ctx *c, int64_t state, double frac,
         e = cudaMemcpyAsync(dW, tf.W.data(), tf.W.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
     DevTables Tf = c->T;
     Tf.W = dW;
+    Tf.interface = DRTS_INTERFACE_FIRST_ORDER;
     if (e == cudaSuccess) e = launch_source_column(Tf, state, dout, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out.data(), dout, out.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream);

@@ -13,6 +13,12 @@
 //    reach (j, m) directly (possibly weakened by an interface transmission),
 //    by Fresnel reflection at an interface from the voxel across it, or by
 //    mirroring from outside the grid.
+//  * With planar two-step interfaces, a source state whose direction reaches
+//    the plane to the next z layer within the step uses that medium pair's
+//    two-step entries instead of its medium's stencil: one part folds as
+//    above, the part that already crossed (or reflected) at the plane folds
+//    at the grid edge only.  Rows up to two layers from an index change are
+//    therefore never plain.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -58,9 +64,24 @@ __device__ __forceinline__ int vox_of(const DevTables &T, int x, int y, int z)
     return (z * T.ny + y) * T.nx + x;
 }
 
-__device__ __forceinline__ double Wat(const DevTables &T, int k, int n, int o, int m)
+constexpr size_t kStencil = size_t(kDirs) * kOffs * kDirs;   // one [26][27][26] raw stencil
+
+// entry (n, o, m) of the raw stencil S ([26][27][26])
+__device__ __forceinline__ double Wat(const double *S, int n, int o, int m)
 {
-    return __ldg(&T.W[((size_t(k) * kDirs + n) * kOffs + o) * kDirs + m]);
+    return __ldg(&S[(n * kOffs + o) * kDirs + m]);
+}
+
+// Two-step slot of source (voxel i of medium k, direction n): the pair
+// (k, medium of the z layer S_n points to) when the indices differ and S_n
+// reaches the plane between the layers within the step, else -1.
+__device__ __forceinline__ int crossing_slot(const DevTables &T, const int i[3], int k, int n)
+{
+    if (!T.interface || c_dir[n][2] == 0) return -1;
+    const int zn = i[2] + c_dir[n][2];
+    if (zn < 0 || zn >= T.nz) return -1;
+    const int p = __ldg(&T.pair_slot[k * T.K + T.med[vox_of(T, i[0], i[1], zn)]]);
+    return p >= 0 && T.cross[p * kDirs + n] ? p : -1;
 }
 
 // incidence class of direction m on the face normal to axis a
@@ -95,16 +116,27 @@ __device__ int normal_axis(const DevTables &T, const int i[3], const int o[3], d
 }
 
 // Mass that state (i, n) of medium k sends to (j, m) in one step, for a row
-// voxel j that needs edge or interface folding.
+// voxel j that needs edge or interface folding.  The raw entries are the
+// medium's stencil, or for a two-step crossing state the pair's entries that
+// fold at edges and interfaces (S) plus those that fold at the grid edge
+// only (S0).
 __device__ double folded_contribution(const DevTables &T, const int i[3], int k, double ni,
                                       int n, const int j[3], int kj, double nj, int m)
 {
     const int N[3] = {T.nx, T.ny, T.nz};
+    const double *S = T.W + size_t(k) * kStencil;
+    const double *S0 = nullptr;
+    const int slot = crossing_slot(T, i, k, n);
+    if (slot >= 0) {
+        S = T.W2f + size_t(slot) * kStencil;
+        S0 = T.W2n + size_t(slot) * kStencil;
+    }
     double sum = 0.0;
     // (1) raw target (j, m): direct, or transmitted through an interface
     {
         const int o[3] = {j[0] - i[0], j[1] - i[1], j[2] - i[2]};
-        const double w = Wat(T, k, n, offset_index(o[0], o[1], o[2]), m);
+        if (S0) sum += Wat(S0, n, offset_index(o[0], o[1], o[2]), m);
+        const double w = Wat(S, n, offset_index(o[0], o[1], o[2]), m);
         if (w > 0.0) {
             double f = 1.0;
             if ((o[0] | o[1] | o[2]) != 0 && nj != ni) {
@@ -129,7 +161,7 @@ __device__ double folded_contribution(const DevTables &T, const int i[3], int k,
             if (normal_axis(T, i, o, ni) != a) continue;
             const int mr = flip_dir(m, 1 << a);
             if (c_dir[mr][a] * s <= 0) continue;
-            const double w = Wat(T, k, n, offset_index(o[0], o[1], o[2]), mr);
+            const double w = Wat(S, n, offset_index(o[0], o[1], o[2]), mr);
             if (w > 0.0) sum += w * __ldg(&T.r_int[(size_t(k) * T.K + kt) * 4 + inc_class(mr, a)]);
         }
     }
@@ -144,7 +176,8 @@ __device__ double folded_contribution(const DevTables &T, const int i[3], int k,
             t[a] = (G >> a & 1) ? (j[a] == 0 ? -1 : N[a]) : j[a];
         const int o[3] = {t[0] - i[0], t[1] - i[1], t[2] - i[2]};
         const int mr = flip_dir(m, G);
-        const double w = Wat(T, k, n, offset_index(o[0], o[1], o[2]), mr);
+        const int oi = offset_index(o[0], o[1], o[2]);
+        const double w = Wat(S, n, oi, mr) + (S0 ? Wat(S0, n, oi, mr) : 0.0);
         if (w <= 0.0) continue;
         double f = 1.0;
         for (int a = 0; a < 3; ++a)
@@ -200,6 +233,10 @@ __global__ void classify_kernel(DevTables T, uint8_t *plain)
             const int u = vox_of(T, x + d % 3 - 1, y + d / 3 % 3 - 1, z + d / 9 - 1);
             if (T.nref[T.med[u]] != n0) ok = 0;
         }
+        // two-step interfaces: a source one layer above or below crosses when
+        // the layer beyond it (two from the row) has another index
+        for (int dz = -2; dz <= 2 && ok && T.interface; dz += 4)
+            if (z + dz >= 0 && z + dz < T.nz && T.nref[T.med[vox_of(T, x, y, z + dz)]] != n0) ok = 0;
     }
     plain[v] = ok;
 }

@@ -435,8 +435,8 @@ __global__ void __launch_bounds__(256) ledger_kernel(StepArgs a)
         if (xs == 0.0f) continue;
         const int d = int(i / a.V);
         const int64_t v = i - int64_t(d) * a.V;
-        const int k = a.med[v];
-        ab += float(a.tab.absorb[k]) * xs;
+        const int k = a.cls[v];
+        ab += float(a.tab.absorb_dir ? a.tab.absorb_dir[k * kDirs + d] : a.tab.absorb[k]) * xs;
         const int xx = int(v % a.nx), yy = int(v / a.nx % a.ny), zz = int(v / (int64_t(a.nx) * a.ny));
         const int mask = (zz == 0 ? 0 : (zz == a.nz - 1 ? 2 : 1)) * 9 +
                          (yy == 0 ? 0 : (yy == a.ny - 1 ? 2 : 1)) * 3 + (xx == 0 ? 0 : (xx == a.nx - 1 ? 2 : 1));
@@ -484,7 +484,7 @@ __global__ void det_kernel(StepArgs a)
             c[ua] = cu;
             c[va] = cv;
             const int64_t v = (int64_t(c[2]) * a.ny + c[1]) * a.nx + c[0];
-            const int k = a.med[v];
+            const int k = a.cls[v];
             const int mask = (c[2] == 0 ? 0 : (c[2] == a.nz - 1 ? 2 : 1)) * 9 +
                              (c[1] == 0 ? 0 : (c[1] == a.ny - 1 ? 2 : 1)) * 3 +
                              (c[0] == 0 ? 0 : (c[0] == a.nx - 1 ? 2 : 1));

@@ -27,6 +27,12 @@ struct DevTables {
     const uint8_t *med;         // [V] medium of each voxel
     const uint8_t *plain;       // [V] 1 when the voxel's rows need no folding
     const float *dir_scale;     // [26] FP16 tier row scale by direction (or null)
+    // planar two-step interface crossing (DRTS_INTERFACE_TWO_STEP; else 0 / null)
+    int interface;
+    const int32_t *pair_slot;   // [K][K] slot of (source medium, medium of the next z layer), or -1
+    const uint8_t *cross;       // [P][26] direction n reaches the plane within the step
+    const double *W2f;          // [P][26][27][26] crossing entries folded at edges and interfaces
+    const double *W2n;          // [P][26][27][26] crossing entries folded at the grid edge only
 };
 
 // Sliced storage of A: slice q = voxel block b (32 voxels) * 26 + direction
@@ -62,11 +68,14 @@ struct SourceProfile {
     int32_t pad0, pad1;
 };
 
-// Column functionals of one step (per medium / face mask / direction).
+// Column functionals of one step (per ledger class / face mask / direction;
+// the class of a voxel is its medium, or with two-step interfaces the class
+// of its z layer).
 struct StepTables {
-    const double *absorb;      // [K]
-    const double *exit_total;  // [K][27][26]
-    const double *exit_det;    // [K][27][26]
+    const double *absorb;      // [C] absorbed fraction of a state
+    const double *absorb_dir;  // [C][26] per direction, or null when absorb[C] holds for all
+    const double *exit_total;  // [C][27][26]
+    const double *exit_det;    // [C][27][26]
 };
 
 // Sparse detector rows F of Eq. 27 (point detectors): the entries of
@@ -125,7 +134,7 @@ struct StepArgs {
     int64_t rhs_stride;        // elements between right-hand sides of a state buffer
     const void *x;             // state at t, layout [r*rhs_stride + n*V + v]
     void *y;                   // state at t+1
-    const uint8_t *med;
+    const uint8_t *cls;        // [V] ledger class of each voxel (StepTables)
     StepTables tab;
     int det_face, det_nu, det_nv, n_patch;
     double *det;               // det[r][t_hist][patch] base, or null

@@ -87,11 +87,35 @@ struct HostTables {
     std::vector<double> exit_det;   // [k][27][26]
     std::vector<float> dir_scale;   // [26] FP16 tier: row scale of direction m (power of two)
     int n_template_entries_max = 0;
+
+    // Planar two-step interface crossing (DRTS_INTERFACE_TWO_STEP, Section
+    // 4.2): the ordered medium pairs (k1 of a source voxel, k2 of the z layer
+    // next to it) with different refractive indices that meet in the grid,
+    // and for each pair the raw entries of every direction that reaches the
+    // plane between them within the step.
+    int n_pairs = 0;
+    std::vector<int32_t> pair_slot; // [K][K] slot of (k1, k2), or -1
+    std::vector<uint8_t> cross;     // [P][26] 1: direction n reaches the plane within the step
+    std::vector<double> W2f;        // [P][26][27][26] raw entries folded at edges and interfaces
+    std::vector<double> W2n;        // [P][26][27][26] raw entries folded at the grid edge only
+
+    // Ledger classes of the column functionals (absorbed and exiting mass of
+    // a state in one step): class = medium, or with two-step interfaces one
+    // class per distinct (medium, pair above, pair below) of a z layer.
+    int n_classes = 0;
+    std::vector<uint8_t> class_of_layer;  // [nz] (two-step interfaces only; else class = medium)
+    std::vector<double> led_absorb;       // [C] absorbed fraction of a non-crossing state
+    std::vector<double> led_absorb_dir;   // [C][26] per direction (two-step interfaces only)
+    std::vector<double> led_exit_total;   // [C][27][26] as exit_total, per class
+    std::vector<double> led_exit_det;     // [C][27][26] as exit_det, per class
 };
 
 // path_frac scales every medium's path L_k (1 for the system matrix; a
 // fraction of the step for sources emitted within it, Section 4.1)
 std::string build_host_tables(const drts_problem &p, HostTables &t, double path_frac = 1.0);
+// the two-step interface part of build_host_tables (problem already validated
+// to one medium per z layer); fills pair_slot .. W2n and the ledger classes
+std::string build_two_step_tables(const drts_problem &p, HostTables &t);
 
 // Record the message drts_last_error(NULL) returns on this thread (calls
 // that have no context).

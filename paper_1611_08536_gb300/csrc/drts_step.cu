@@ -211,8 +211,8 @@ __device__ __forceinline__ void row_epilogue(const StepArgs &a, const StepShared
         if (sh.src[e].slice == q && sh.src[e].lane == lane) acc += AT(sh.src_val[e]);
     y[row] = XT(acc);
     const AT xs = AT(COHERENT ? __ldcg(x + row) : x[row]);
-    const int k = a.med[v];
-    ab_lane += AT(a.tab.absorb[k]) * xs;
+    const int k = a.cls[v];
+    ab_lane += AT(a.tab.absorb_dir ? a.tab.absorb_dir[k * kDirs + m] : a.tab.absorb[k]) * xs;
     const int nxy = a.nx * a.ny;
     const int xx = int(v % a.nx), yy = int(v / a.nx % a.ny), zz = int(v / nxy);
     const int bx = xx == 0 ? 0 : (xx == a.nx - 1 ? 2 : 1);

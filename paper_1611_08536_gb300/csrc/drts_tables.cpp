@@ -121,7 +121,265 @@ void diffuse_round_fp32(const double *W, double *out)
     }
 }
 
+// Mass of one raw column Wn[o][m] (a state of a medium with edge
+// reflectances r_edge[4], in a voxel with face mask `mask`) that leaves the
+// grid in one step, and the part of it through the detector face: a raw
+// target outside the grid along axis a (x, then y, then z) keeps R and lets
+// 1 - R out through that face (Section 4.2 edge reading).
+void column_exit(const double *Wn, const double *r_edge, int mask, int det_face, double &tot, double &det)
+{
+    const Directions &D = dirs();
+    const int b[3] = {mask % 3, mask / 3 % 3, mask / 9};
+    tot = 0.0;
+    det = 0.0;
+    for (int o = 0; o < kOffs; ++o) {
+        const int ov[3] = {o % 3 - 1, o / 3 % 3 - 1, o / 9 - 1};
+        for (int m = 0; m < kDirs; ++m) {
+            double w = Wn[o * kDirs + m];
+            if (w <= 0.0) continue;
+            for (int a = 0; a < 3; ++a) {
+                const bool out_lo = b[a] == 0 && ov[a] == -1;
+                const bool out_hi = b[a] == 2 && ov[a] == 1;
+                if (!out_lo && !out_hi) continue;
+                const int c = D.v[m][a] != 0 ? D.nnzc[m] : 0;
+                const double R = r_edge[c];
+                const double leave = w * (1.0 - R);
+                tot += leave;
+                if (det_face == 2 * a + (out_hi ? 1 : 0)) det += leave;
+                w *= R;
+            }
+        }
+    }
+}
+
+// Henyey-Greenstein weights of the 26 lattice directions for scattering out
+// of the unit vector u, normalised over the lattice (the discrete kernel of
+// Section 5, here also for a direction that is not a lattice one).
+void phase_row(double g, const double u[3], double out[kDirs])
+{
+    const Directions &D = dirs();
+    double sum = 0.0;
+    for (int m = 0; m < kDirs; ++m) {
+        const double mu = u[0] * D.u[m][0] + u[1] * D.u[m][1] + u[2] * D.u[m][2];
+        const double den = 1.0 + g * g - 2.0 * g * mu;
+        out[m] = (1.0 - g * g) / (den * std::sqrt(den));
+        sum += out[m];
+    }
+    for (int m = 0; m < kDirs; ++m) out[m] /= sum;
+}
+
+// Mass w landing around the segment [a, b] (points in units of h, a point
+// when a == b) in direction m, shared over the lattice offsets by the
+// weights of Eq. 18/19, added to the raw column Wn[o][m].
+void deposit(double *Wn, const double a[3], const double b[3], int m, double w)
+{
+    if (!(w > 0.0)) return;
+    double wo[kOffs];
+    segment_weights(a, b, wo);
+    for (int o = 0; o < kOffs; ++o)
+        if (wo[o] > 0.0) Wn[o * kDirs + m] += wo[o] * w;
+}
+
+// One free flight (Eq. 9-12 and 18/19 for a population that starts at the
+// point c instead of a voxel centre): mass `mass` leaves c along the unit
+// vector u for the path l (units of h) in medium md.  The unscattered share
+// lands around c + l u, divided over the lattice states st[0..ns) by the
+// shares sh; the scattered share lands around [c + l S_m, c + l u] in every
+// direction m, weighted by the phase row ph.
+void flight(double *Wn, const double c[3], const double u[3], double l, double h, const drts_medium &md,
+            const double ph[kDirs], const int *st, const double *sh, int ns, double mass)
+{
+    const Directions &D = dirs();
+    const double end[3] = {c[0] + l * u[0], c[1] + l * u[1], c[2] + l * u[2]};
+    const double keep = mass * std::exp(-(md.mu_s + md.mu_a) * l * h);
+    for (int q = 0; q < ns; ++q) deposit(Wn, end, end, st[q], keep * sh[q]);
+    const double scat = mass * (1.0 - std::exp(-md.mu_s * l * h)) * std::exp(-md.mu_a * l * h);
+    if (scat > 0.0)
+        for (int m = 0; m < kDirs; ++m) {
+            const double a[3] = {c[0] + l * D.u[m][0], c[1] + l * D.u[m][1], c[2] + l * D.u[m][2]};
+            deposit(Wn, a, end, m, scat * ph[m]);
+        }
+}
+
+// Raw column of a state of direction n in a voxel of medium k1 whose z
+// neighbour layer holds medium k2 (another refractive index), when S_n
+// reaches the plane between them, half a voxel away, within the step
+// (Section 4.2, planar interface crossed in two parts).  With lambda_1 the
+// path of a whole step in medium 1 (units of h), the plane is met at the
+// fraction tc = 1/2 / (lambda_1 |S_nz|) of the step; tc >= 1 returns false
+// (no crossing).  Writes
+//  * Wf: the share scattered before the plane.  A photon scattered at the
+//    fraction s < tc into m ends the step at lambda_1 (s S_n + (1 - s) S_m):
+//    a segment from lambda_1 S_m to lambda_1 (tc S_n + (1 - tc) S_m), with
+//    the scattering probability of the path tc L_1 and the absorption of the
+//    whole step in medium 1.  These entries meet the interface again in the
+//    assembler's fold.
+//  * Wn: the unscattered share exp(-(mu_s1 + mu_a1) tc L_1) at the crossing
+//    point C = tc lambda_1 S_n.  The Fresnel share R at the true incidence
+//    angle continues in medium 1 along S_n with z reversed; the rest is
+//    refracted by Snell's law (sin t = n1/n2 sin i, same azimuth) and
+//    continues in medium 2 for (1 - tc) of a step at medium 2's speed.  The
+//    refracted direction is not a lattice direction: its population goes to
+//    the two lattice directions of its azimuth whose polar angles bracket
+//    its own (the normal and S_n, or S_n and the horizontal), linearly in the
+//    polar angle.  These entries meet no further interface in the step.
+// Snell's law cannot give total reflection here: tc < 1 needs lambda_1 |S_nz|
+// > 1/2, so n1 < 2 n_min |S_nz| <= 2 n2 |S_nz|, and sin t = n1/n2 sin i < 1
+// follows from 4 cos^2 i sin^2 i <= 1.
+bool two_step_column(const drts_problem &p, double nmin, int k1, int k2, int n, double *Wf, double *Wn)
+{
+    const Directions &D = dirs();
+    if (D.v[n][2] == 0) return false;
+    const drts_medium &m1 = p.media[k1], &m2 = p.media[k2];
+    const double lam1 = nmin / m1.n, lam2 = nmin / m2.n;
+    const double ci = std::fabs(D.u[n][2]);            // cosine of incidence on the plane
+    const double tc = 0.5 / (lam1 * ci);
+    if (!(tc < 1.0)) return false;
+    const double h = p.voxel_mm;
+    const double zs = D.v[n][2] > 0 ? 1.0 : -1.0;
+
+    // scattered before the plane
+    double ph1[kDirs];
+    phase_row(m1.g, D.u[n], ph1);
+    const double p_scat = (1.0 - std::exp(-m1.mu_s * tc * lam1 * h)) * std::exp(-m1.mu_a * lam1 * h);
+    if (p_scat > 0.0)
+        for (int m = 0; m < kDirs; ++m) {
+            const double a[3] = {lam1 * D.u[m][0], lam1 * D.u[m][1], lam1 * D.u[m][2]};
+            double b[3];
+            for (int c = 0; c < 3; ++c) b[c] = lam1 * (tc * D.u[n][c] + (1.0 - tc) * D.u[m][c]);
+            deposit(Wf, a, b, m, p_scat * ph1[m]);
+        }
+
+    // unscattered up to the crossing point, then reflected and refracted
+    const double p_keep = std::exp(-(m1.mu_s + m1.mu_a) * tc * lam1 * h);
+    const double C[3] = {tc * lam1 * D.u[n][0], tc * lam1 * D.u[n][1], tc * lam1 * D.u[n][2]};
+    const double R = fresnel(ci, m1.n, m2.n);
+    const int nr = D.index_of[offset_index(D.v[n][0], D.v[n][1], -D.v[n][2])];
+    double phr[kDirs];
+    phase_row(m1.g, D.u[nr], phr);
+    const double one = 1.0;
+    flight(Wn, C, D.u[nr], (1.0 - tc) * lam1, h, m1, phr, &nr, &one, 1, p_keep * R);
+    if (R < 1.0) {
+        const double si = std::sqrt(1.0 - ci * ci);
+        const double st = m1.n / m2.n * si;
+        const double ct = std::sqrt(1.0 - st * st);
+        double u[3] = {0.0, 0.0, zs * ct};
+        int states[2] = {n, n};
+        double share[2] = {1.0, 0.0};
+        int ns = 1;
+        if (si > 0.0) {
+            const double hor = std::sqrt(D.u[n][0] * D.u[n][0] + D.u[n][1] * D.u[n][1]);
+            u[0] = st * D.u[n][0] / hor;
+            u[1] = st * D.u[n][1] / hor;
+            const double th_i = std::atan2(si, ci), th_t = std::atan2(st, ct);
+            const double right = 1.57079632679489661923;   // pi / 2
+            if (th_t <= th_i) {            // between the normal and S_n
+                states[1] = D.index_of[offset_index(0, 0, D.v[n][2])];
+                share[0] = th_t / th_i;
+            } else {                       // between S_n and the horizontal
+                states[1] = D.index_of[offset_index(D.v[n][0], D.v[n][1], 0)];
+                share[0] = (right - th_t) / (right - th_i);
+            }
+            share[1] = 1.0 - share[0];
+            ns = 2;
+        }
+        double ph2[kDirs];
+        phase_row(m2.g, u, ph2);
+        flight(Wn, C, u, (1.0 - tc) * lam2, h, m2, ph2, states, share, ns, p_keep * (1.0 - R));
+    }
+    return true;
+}
+
 }  // namespace
+
+// Two-step tables of every medium pair that meets across a z plane, and the
+// ledger classes of the layers (problems validated to one medium per layer).
+std::string build_two_step_tables(const drts_problem &p, HostTables &t)
+{
+    const int K = p.n_media;
+    const int64_t layer = int64_t(p.nx) * p.ny;
+    double nmin = p.media[0].n;
+    for (int k = 1; k < K; ++k) nmin = std::fmin(nmin, p.media[k].n);
+    std::vector<int> kz(size_t(p.nz));
+    for (int z = 0; z < p.nz; ++z) kz[size_t(z)] = p.medium_of_voxel[int64_t(z) * layer];
+
+    const size_t blk = size_t(kDirs) * kOffs * kDirs;
+    t.pair_slot.assign(size_t(K) * K, -1);
+    t.n_pairs = 0;
+    std::vector<std::pair<int, int>> pairs;
+    for (int z = 0; z + 1 < p.nz; ++z) {
+        const int a = kz[size_t(z)], b = kz[size_t(z) + 1];
+        if (p.media[a].n == p.media[b].n) continue;
+        for (const auto &pr : {std::make_pair(a, b), std::make_pair(b, a)})
+            if (t.pair_slot[size_t(pr.first) * K + pr.second] < 0) {
+                t.pair_slot[size_t(pr.first) * K + pr.second] = int32_t(pairs.size());
+                pairs.push_back(pr);
+            }
+    }
+    t.n_pairs = int(pairs.size());
+    t.cross.assign(size_t(t.n_pairs) * kDirs, 0);
+    t.W2f.assign(size_t(t.n_pairs) * blk, 0.0);
+    t.W2n.assign(size_t(t.n_pairs) * blk, 0.0);
+    for (int q = 0; q < t.n_pairs; ++q)
+        for (int n = 0; n < kDirs; ++n) {
+            const size_t off = size_t(q) * blk + size_t(n) * kOffs * kDirs;
+            t.cross[size_t(q) * kDirs + n] =
+                two_step_column(p, nmin, pairs[size_t(q)].first, pairs[size_t(q)].second, n, &t.W2f[off],
+                                &t.W2n[off]);
+        }
+
+    // ledger classes: (medium, slot of the pair above, slot of the pair below)
+    std::vector<std::array<int, 3>> keys;
+    t.class_of_layer.assign(size_t(p.nz), 0);
+    for (int z = 0; z < p.nz; ++z) {
+        const int k = kz[size_t(z)];
+        const int up = z + 1 < p.nz ? t.pair_slot[size_t(k) * K + kz[size_t(z) + 1]] : -1;
+        const int dn = z > 0 ? t.pair_slot[size_t(k) * K + kz[size_t(z) - 1]] : -1;
+        const std::array<int, 3> key = {k, up, dn};
+        size_t c = 0;
+        while (c < keys.size() && keys[c] != key) ++c;
+        if (c == keys.size()) {
+            if (keys.size() == 255)
+                return "two-step interfaces: more than 255 distinct (medium, neighbour layers) classes";
+            keys.push_back(key);
+        }
+        t.class_of_layer[size_t(z)] = uint8_t(c);
+    }
+    const int C = int(keys.size());
+    t.n_classes = C;
+    t.led_absorb.assign(size_t(C), 0.0);
+    t.led_absorb_dir.assign(size_t(C) * kDirs, 0.0);
+    t.led_exit_total.assign(size_t(C) * 27 * kDirs, 0.0);
+    t.led_exit_det.assign(size_t(C) * 27 * kDirs, 0.0);
+    std::vector<double> col(size_t(kOffs) * kDirs);
+    for (int c = 0; c < C; ++c) {
+        const int k = keys[size_t(c)][0];
+        t.led_absorb[size_t(c)] = t.absorb[size_t(k)];
+        for (int n = 0; n < kDirs; ++n) {
+            const Directions &D = dirs();
+            const int slot = D.v[n][2] > 0 ? keys[size_t(c)][1] : (D.v[n][2] < 0 ? keys[size_t(c)][2] : -1);
+            const bool crossing = slot >= 0 && t.cross[size_t(slot) * kDirs + n];
+            double kept = 0.0;
+            if (crossing) {
+                const size_t off = size_t(slot) * blk + size_t(n) * kOffs * kDirs;
+                for (size_t e = 0; e < col.size(); ++e) {
+                    col[e] = t.W2f[off + e] + t.W2n[off + e];
+                    kept += col[e];
+                }
+            } else {
+                std::copy_n(&t.W[size_t(k) * blk + size_t(n) * kOffs * kDirs], col.size(), col.begin());
+            }
+            // a crossing state keeps what its raw entries carry; the rest is absorbed
+            t.led_absorb_dir[size_t(c) * kDirs + n] = crossing ? 1.0 - kept : t.absorb[size_t(k)];
+            for (int mask = 0; mask < 27; ++mask) {
+                const size_t ti = (size_t(c) * 27 + mask) * kDirs + n;
+                column_exit(col.data(), &t.r_edge[size_t(k) * 4], mask, p.det_face, t.led_exit_total[ti],
+                            t.led_exit_det[ti]);
+            }
+        }
+    }
+    return std::string();
+}
 
 std::string build_host_tables(const drts_problem &p, HostTables &t, double path_frac)
 {
@@ -242,39 +500,28 @@ std::string build_host_tables(const drts_problem &p, HostTables &t, double path_
                 t.r_int[(size_t(k) * K + k2) * 4 + c] = fresnel(class_cos(c), p.media[k].n, p.media[k2].n);
         }
 
-    // exit fractions per (medium, face mask, direction): a raw target outside
-    // the grid along axis a (x, then y, then z) keeps R and lets 1 - R out
-    // through that face (Section 4.2 edge reading)
+    // exit fractions per (medium, face mask, direction)
     t.exit_total.assign(size_t(K) * 27 * kDirs, 0.0);
     t.exit_det.assign(size_t(K) * 27 * kDirs, 0.0);
     for (int k = 0; k < K; ++k) {
         const double *Wk = &t.W[size_t(k) * kDirs * kOffs * kDirs];
-        for (int mask = 0; mask < 27; ++mask) {
-            const int b[3] = {mask % 3, mask / 3 % 3, mask / 9};
+        for (int mask = 0; mask < 27; ++mask)
             for (int n = 0; n < kDirs; ++n) {
-                double tot = 0.0, det = 0.0;
-                for (int o = 0; o < kOffs; ++o) {
-                    const int ov[3] = {o % 3 - 1, o / 3 % 3 - 1, o / 9 - 1};
-                    for (int m = 0; m < kDirs; ++m) {
-                        double w = Wk[(n * kOffs + o) * kDirs + m];
-                        if (w <= 0.0) continue;
-                        for (int a = 0; a < 3; ++a) {
-                            const bool out_lo = b[a] == 0 && ov[a] == -1;
-                            const bool out_hi = b[a] == 2 && ov[a] == 1;
-                            if (!out_lo && !out_hi) continue;
-                            const int c = D.v[m][a] != 0 ? D.nnzc[m] : 0;
-                            const double R = t.r_edge[k * 4 + c];
-                            const double leave = w * (1.0 - R);
-                            tot += leave;
-                            if (p.det_face == 2 * a + (out_hi ? 1 : 0)) det += leave;
-                            w *= R;
-                        }
-                    }
-                }
-                t.exit_total[(size_t(k) * 27 + mask) * kDirs + n] = tot;
-                t.exit_det[(size_t(k) * 27 + mask) * kDirs + n] = det;
+                const size_t ti = (size_t(k) * 27 + mask) * kDirs + n;
+                column_exit(&Wk[size_t(n) * kOffs * kDirs], &t.r_edge[k * 4], mask, p.det_face,
+                            t.exit_total[ti], t.exit_det[ti]);
             }
-        }
+    }
+
+    if (p.interface == DRTS_INTERFACE_TWO_STEP && path_frac == 1.0) {
+        const std::string err = build_two_step_tables(p, t);
+        if (!err.empty()) return err;
+    } else {
+        // one ledger class per medium
+        t.n_classes = K;
+        t.led_absorb = t.absorb;
+        t.led_exit_total = t.exit_total;
+        t.led_exit_det = t.exit_det;
     }
     return std::string();
 }

@@ -965,8 +965,10 @@ __global__ void __launch_bounds__(256) tcx_ledger_kernel(StepArgs a)
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
     float ab[2] = {0.0f, 0.0f}, ex[2] = {0.0f, 0.0f};
     for (int64_t v = w0; v < a.V; v += nw) {
-        const int k = a.med[v];
+        const int k = a.cls[v];
         const float abs_k = float(a.tab.absorb[k]);
+        // two-step interfaces: absorption per direction (s then sums it, not x)
+        const double *ad = a.tab.absorb_dir ? a.tab.absorb_dir + k * kDirs : nullptr;
         const int xx = int(v % a.nx), yy = int(v / a.nx % a.ny), zz = int(v / (int64_t(a.nx) * a.ny));
         const int mask = (zz == 0 ? 0 : (zz == a.nz - 1 ? 2 : 1)) * 9 + (yy == 0 ? 0 : (yy == a.ny - 1 ? 2 : 1)) * 3 +
                          (xx == 0 ? 0 : (xx == a.nx - 1 ? 2 : 1));
@@ -984,13 +986,13 @@ __global__ void __launch_bounds__(256) tcx_ledger_kernel(StepArgs a)
                 const int n = n0 + i;
                 if (n >= kDirs) continue;
                 const float xv = __bfloat162float(h[i]);
-                s[kc & 1] += xv;
+                s[kc & 1] += ad ? float(ad[n]) * xv : xv;
                 if (mask != 13) se[kc & 1] += float(et[n]) * xv;
             }
         }
 #pragma unroll
         for (int par = 0; par < 2; ++par) {
-            ab[par] += abs_k * s[par];
+            ab[par] += ad ? s[par] : abs_k * s[par];
             ex[par] += se[par];
         }
     }
@@ -1034,7 +1036,7 @@ __global__ void tcx_det_kernel(StepArgs a)
             c[ua] = cu;
             c[va] = cv;
             const int64_t v = (int64_t(c[2]) * a.ny + c[1]) * a.nx + c[0];
-            const int k = a.med[v];
+            const int k = a.cls[v];
             const int mask = (c[2] == 0 ? 0 : (c[2] == a.nz - 1 ? 2 : 1)) * 9 +
                              (c[1] == 0 ? 0 : (c[1] == a.ny - 1 ? 2 : 1)) * 3 +
                              (c[0] == 0 ? 0 : (c[0] == a.nx - 1 ? 2 : 1));

@@ -52,6 +52,7 @@ class ProblemC(ctypes.Structure):
         ("det_nu", ctypes.c_int32), ("det_nv", ctypes.c_int32),
         ("max_steps", ctypes.c_int64),
         ("batched_kernel", ctypes.c_int32),
+        ("interface", ctypes.c_int32),
     ]
 
 
@@ -111,7 +112,7 @@ class Info(ctypes.Structure):
 
 SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_detectors",
            "drts_read_state", "drts_write_state", "drts_run_host", "drts_export_rows",
-           "drts_column_info", "drts_get_info", "drts_host_tables", "drts_set_launch", "drts_destroy",
+           "drts_column_info", "drts_get_info", "drts_host_tables", "drts_two_step_tables", "drts_set_launch", "drts_destroy",
            "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_autotune",
            "drts_set_step_mode", "drts_server_create", "drts_server_submit", "drts_server_tick",
            "drts_server_poll", "drts_server_result", "drts_server_result_state",
@@ -147,6 +148,7 @@ def load(path: str = LIB_PATH):
     lib.drts_column_info.argtypes = [vp, vp, vp, vp]
     lib.drts_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     lib.drts_host_tables.argtypes = [ctypes.POINTER(ProblemC), i32, vp, vp, vp, vp]
+    lib.drts_two_step_tables.argtypes = [ctypes.POINTER(ProblemC), i32, i32, vp, vp, vp]
     lib.drts_fcc_host_rows.argtypes = [ctypes.POINTER(FccProblemC), i64, i64, vp, vp, vp, i64]
     lib.drts_fcc_assemble.argtypes = [ctypes.POINTER(FccProblemC), i32, vp, ctypes.POINTER(vp)]
     lib.drts_fcc_set_source.argtypes = [vp, i32, vp, vp, i64, i32, vp]
@@ -212,6 +214,21 @@ def host_tables(prob, medium):
     if st != OK:
         raise DrtsError(st, lib.drts_last_error(None).decode())
     return W, ex, ed, sc
+
+
+def two_step_tables(prob, k1, k2):
+    """Host-built two-step entries of a planar-interface problem, computed
+    without a device (drts_two_step_tables): (cross[26], fold[26][27][26],
+    edge[26][27][26]) for a state of medium k1 next to a z layer of k2."""
+    lib = load()
+    ps = problem_struct(prob, 0)
+    cross = np.empty(26, np.uint8)
+    fold = np.empty((26, 27, 26), np.float64)
+    edge = np.empty((26, 27, 26), np.float64)
+    st = lib.drts_two_step_tables(ctypes.byref(ps), int(k1), int(k2), _ptr(cross), _ptr(fold), _ptr(edge))
+    if st != OK:
+        raise DrtsError(st, lib.drts_last_error(None).decode())
+    return cross, fold, edge
 
 
 def fcc_host_rows(shape, spacing_mm, media, medium_of_site, row_begin=0, row_end=None, cap=None):
@@ -327,7 +344,8 @@ def problem_struct(prob, max_steps=0):
     s = ProblemC(nx, ny, nz, float(prob.voxel_mm), len(prob.media), media, _ptr(mov),
                  float(prob.n_outside), int(prob.boundary), int(prob.precision),
                  int(prob.n_rhs), int(prob.det_face), int(prob.det_nu),
-                 int(prob.det_nv), int(max_steps), int(getattr(prob, "batched_kernel", 0)))
+                 int(prob.det_nv), int(max_steps), int(getattr(prob, "batched_kernel", 0)),
+                 int(getattr(prob, "interface", 0)))
     s._keep = (media, mov)
     return s
 
