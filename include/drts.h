@@ -420,7 +420,9 @@ typedef struct drts_tune_result {
 /*
  * Pick the fastest launch of the step for this context by timing every
  * variant, block size and blocks-per-SM choice that fits (trial_steps timed
- * launches each, CUDA events on the context stream) and apply it.  The state,
+ * launches each, CUDA events on the context stream; the four fastest are then
+ * timed twice more, alternately, over 3 x trial_steps launches, and the best
+ * of those repeats wins) and apply it.  The state,
  * t, detectors and ledger are left unchanged (the trial steps write the spare
  * state buffer and a scratch ledger).  Results are cached per (grid,
  * precision, rhs, SM count, stored entries) in the process and, when the environment
@@ -433,10 +435,12 @@ drts_status drts_autotune(drts_ctx *ctx, int32_t trial_steps, drts_tune_result *
  * Host-side fault injection for testing the failure paths (no GPU fault is
  * ever caused).  kind:
  *   DRTS_FAULT_NONE        clear everything below;
- *   DRTS_FAULT_SKIP_COPY   the bulk-copy step variants never issue copy number
- *                          arg of the first warp, so that warp's bounded wait
- *                          runs out; the step then reports DRTS_ETIMEOUT at the
- *                          next synchronising call and the context stays usable;
+ *   DRTS_FAULT_SKIP_COPY   the bulk-copy step variants (3-6, one right-hand
+ *                          side; DRTS_ESTATE for any other launch) never issue
+ *                          copy number arg of the first warp, so that warp's
+ *                          bounded wait runs out; the step then reports
+ *                          DRTS_ETIMEOUT at the next synchronising call and the
+ *                          context stays usable;
  *   DRTS_FAULT_SPIN_LIMIT  polls before a device-side wait gives up (arg,
  *                          1..2^30; default 2^22);
  *   DRTS_FAULT_SKIP_BARRIER in persistent mode the first block never arrives

@@ -57,7 +57,6 @@ struct drts_ctx {
     int64_t fault_skip_chunk = -1;
     int fault_skip_barrier = 0;
     int step_mode = DRTS_STEP_LAUNCH;
-    int persist_blocks = 0;
     unsigned *d_bar = nullptr;           // grid barrier of the persistent kernel
     int special_permille = 0;
     std::vector<drts_medium> media;      // the problem's media (partial-path tables)
@@ -710,8 +709,15 @@ try {
         if (c->n_bulk_groups > 0)
             return fail(c, DRTS_EUNSUPPORTED, "sub-step sources need the launch step mode");
         StepArgs a = make_args(c);
+        // the launch path's split variants (two or four warps per slice) carry over
+        int split = c->variant == 10 ? 2 : (c->variant == 11 ? 4 : 1);
+        if (c->threads / 32 < split) split = 1;
+        // as many blocks as the launch path uses, when they can all be resident
+        int blocks = persistent_blocks(c->prob.precision, c->threads, split);
+        if (blocks < 1) return fail(c, DRTS_EUNSUPPORTED, "persistent kernel does not fit");
+        if (c->blocks > 0 && c->blocks < blocks) blocks = c->blocks;
         cudaError_t e = launch_persistent(a, c->y, n_steps, c->det, c->prob.max_steps, c->d_bar,
-                                          c->fault_skip_barrier, c->persist_blocks, c->threads, c->stream);
+                                          c->fault_skip_barrier, blocks, c->threads, split, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "persistent launch");
         if (n_steps & 1) std::swap(c->x, c->y);
         c->t += n_steps;
@@ -1075,6 +1081,30 @@ try {
     drts_tune_result best{};
     best.ms_per_step = 1e30;
     int tried = 0;
+    // mean ms per step of one candidate over `steps` launches after one warm-up
+    auto time_candidate = [&](const drts_tune_result &r, int steps, double &per) -> cudaError_t {
+        StepArgs a = make_args(c);
+        a.det = nullptr;
+        a.ledger = scratch_ledger;
+        a.n_src = 0;
+        const int blocks = r.blocks_per_sm * sms;
+        auto run = [&]() {
+            if (c->R == 1) return launch_step(a, r.variant, blocks, r.threads, c->stream);
+            if (c->tc) return launch_tc_step(a, false, c->stream);
+            return launch_batched_step(a, c->R, r.rhs_tile > 0 ? r.rhs_tile : 4, r.variant, blocks, r.threads, false,
+                                       c->stream);
+        };
+        cudaError_t err = run();          // warm-up
+        if (err == cudaSuccess) err = cudaEventRecord(e0, c->stream);
+        for (int i = 0; i < steps && err == cudaSuccess; ++i) err = run();
+        if (err == cudaSuccess) err = cudaEventRecord(e1, c->stream);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+        per = double(ms) / steps;
+        return err;
+    };
+    std::vector<drts_tune_result> cand;
     const int n_var = c->R == 1 ? kStepVariants : (c->tc ? 1 : kBatchedOrders);
     for (int var = 0; var < n_var && e == cudaSuccess; ++var)
         for (int tile : {4, 8, 16, 32})
@@ -1088,35 +1118,37 @@ try {
             const int fit_per_sm = fit / sms;
             for (int bps : {fit_per_sm, fit_per_sm / 2}) {
                 if (bps < 1 || (bps == fit_per_sm / 2 && bps == fit_per_sm)) continue;
-                StepArgs a = make_args(c);
-                a.det = nullptr;
-                a.ledger = scratch_ledger;
-                a.n_src = 0;
-                const int blocks = bps * sms;
-                auto run = [&]() {
-                    if (c->R == 1) return launch_step(a, var, blocks, threads, c->stream);
-                    if (c->tc) return launch_tc_step(a, false, c->stream);
-                    return launch_batched_step(a, c->R, tile, var, blocks, threads, false, c->stream);
-                };
-                e = run();          // warm-up
-                if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-                for (int i = 0; i < trial_steps && e == cudaSuccess; ++i) e = run();
-                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
-                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-                float ms = 0.0f;
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                drts_tune_result r{};
+                r.variant = var;
+                r.threads = threads;
+                r.blocks_per_sm = bps;
+                r.rhs_tile = c->R > 1 ? tile : 0;
+                e = time_candidate(r, trial_steps, r.ms_per_step);
                 if (e != cudaSuccess) break;
                 ++tried;
-                const double per = double(ms) / trial_steps;
-                if (per < best.ms_per_step) {
-                    best.ms_per_step = per;
-                    best.variant = var;
-                    best.threads = threads;
-                    best.blocks_per_sm = bps;
-                    best.rhs_tile = c->R > 1 ? tile : 0;
-                }
+                cand.push_back(r);
             }
         }
+    // single short trials are noisy on a shared machine: the fastest few are
+    // timed again, alternately, over three times the steps, and the best of
+    // those repeats decides
+    if (e == cudaSuccess && !cand.empty()) {
+        std::stable_sort(cand.begin(), cand.end(),
+                         [](const drts_tune_result &x, const drts_tune_result &y) { return x.ms_per_step < y.ms_per_step; });
+        const size_t top = std::min<size_t>(cand.size(), 4);
+        std::vector<double> rt(top, 1e30);
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep)
+            for (size_t i = 0; i < top && e == cudaSuccess; ++i) {
+                double per = 0.0;
+                e = time_candidate(cand[i], 3 * trial_steps, per);
+                rt[i] = std::min(rt[i], per);
+            }
+        for (size_t i = 0; i < top; ++i)
+            if (rt[i] < best.ms_per_step) {
+                best = cand[i];
+                best.ms_per_step = rt[i];
+            }
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     if (scratch_ledger) cudaFree(scratch_ledger);
@@ -1255,9 +1287,8 @@ try {
     if (mode == DRTS_STEP_PERSISTENT) {
         if (c->R != 1) return fail(c, DRTS_EUNSUPPORTED, "persistent mode steps one right-hand side");
         if (c->n_bulk_groups > 0) return fail(c, DRTS_EUNSUPPORTED, "sub-step sources need the launch step mode");
-        const int blocks = persistent_blocks(c->prob.precision, c->threads);
+        const int blocks = persistent_blocks(c->prob.precision, c->threads, 1);
         if (blocks < 1) return fail(c, DRTS_EUNSUPPORTED, "cooperative launch not available");
-        c->persist_blocks = blocks;
         c->step_mode = mode;
         return DRTS_OK;
     }
@@ -1281,7 +1312,8 @@ try {
         return DRTS_OK;
     case DRTS_FAULT_SKIP_COPY:
         if (arg < 0) return fail(c, DRTS_EINVAL, "chunk index must be >= 0");
-        if (c->variant < 3) return fail(c, DRTS_ESTATE, "the registers variants have no copies to skip");
+        if (c->R != 1 || c->variant < 3 || c->variant > 6)
+            return fail(c, DRTS_ESTATE, "only the bulk-copy step variants (3-6) have copies to skip");
         c->fault_skip_chunk = arg;
         return DRTS_OK;
     case DRTS_FAULT_SPIN_LIMIT:

@@ -177,10 +177,12 @@ cudaError_t launch_count_export(const SlicedMatrix &A, int64_t V, int64_t row_be
 cudaError_t launch_step(const StepArgs &a, int variant, int blocks, int threads, cudaStream_t s);
 int step_default_blocks(int precision, int R, int threads, int variant);
 constexpr int kStepVariants = 12;
-// persistent multi-step kernel (cooperative launch, bounded grid barrier)
-int persistent_blocks(int precision, int threads);
+// persistent multi-step kernel (cooperative launch, bounded grid barrier);
+// split = warps per slice (1, 2 or 4)
+int persistent_blocks(int precision, int threads, int split);
 cudaError_t launch_persistent(const StepArgs &a, void *other, int64_t n_steps, double *det_base, int64_t max_steps,
-                              unsigned *bar, int fault_skip_barrier, int blocks, int threads, cudaStream_t s);
+                              unsigned *bar, int fault_skip_barrier, int blocks, int threads, int split,
+                              cudaStream_t s);
 cudaError_t launch_to_canonical(const void *x, int precision, int64_t V, int R, int r,
                                 double *out, cudaStream_t s);
 cudaError_t launch_from_canonical(const double *in, int precision, int64_t V, int R, int r,

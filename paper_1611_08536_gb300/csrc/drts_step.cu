@@ -507,17 +507,25 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned nblocks, ui
     return s_ok != 0;
 }
 
-template <class VT, class XT, class AT>
+// matrix groups the persistent kernel keeps in flight per lane (the launch
+// path's best registers variant at full size prefetches two)
+constexpr int kPersistDepth = 2;
+
+// K > 1: as the split variants, K warps share each slice (grids too small to
+// give every warp slot a slice), the parts meeting in shared memory in part
+// order.
+template <class VT, class XT, class AT, int K>
 __global__ void __launch_bounds__(256) persistent_kernel(StepArgs a0, void *other, int64_t n_steps,
                                                          double *det_base, int64_t max_steps, unsigned *bar,
                                                          int fault_skip_barrier)
 {
     __shared__ StepShared sh;
     __shared__ double pd_red[32];
+    __shared__ AT part[K > 1 ? 8 : 1][kSlice];
     step_delta(a0, sh);
     const VT *__restrict__ vals = static_cast<const VT *>(a0.A.vals);
     const uint16_t *__restrict__ codes = a0.A.codes;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t warp0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
     for (int64_t k = 0; k < n_steps; ++k) {
@@ -533,14 +541,49 @@ __global__ void __launch_bounds__(256) persistent_kernel(StepArgs a0, void *othe
             for (int d = blockIdx.x; d < a.pd.n_det; d += gridDim.x)
                 point_detector_block<XT, true>(a, x, 0, d, pd_red);
         AT ab_lane = 0, ex_lane = 0;
-        for (int64_t q = warp0; q < a.A.n_slices; q += nwarps) {
-            const int64_t b = q / kDirs;
-            const int m = int(q - b * kDirs);
-            const int64_t v = b * kSlice + lane;
-            const int len4 = a.A.slice_len4[q];
-            const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
-            const AT acc = row_dot<VT, XT, AT, 1, true>(vals, codes, base, len4, x, v, sh.delta);
-            row_epilogue<XT, AT, true>(a, sh, q, lane, v, m, acc, ab_lane, ex_lane);
+        if constexpr (K == 1) {
+            for (int64_t q = warp0; q < a.A.n_slices; q += nwarps) {
+                const int64_t b = q / kDirs;
+                const int m = int(q - b * kDirs);
+                const int64_t v = b * kSlice + lane;
+                const int len4 = a.A.slice_len4[q];
+                const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
+                const AT acc = row_dot<VT, XT, AT, kPersistDepth, true>(vals, codes, base, len4, x, v, sh.delta);
+                row_epilogue<XT, AT, true>(a, sh, q, lane, v, m, acc, ab_lane, ex_lane);
+            }
+        } else {
+            const int per_cta = (blockDim.x >> 5) / K;
+            const int kk = warp % K, slot = warp / K;
+            const int64_t span = int64_t(gridDim.x) * per_cta;
+            const int64_t rounds = (a.A.n_slices + span - 1) / span;
+            for (int64_t rd = 0; rd < rounds; ++rd) {
+                const int64_t q = (rd * gridDim.x + blockIdx.x) * per_cta + slot;
+                const bool live = slot < per_cta && q < a.A.n_slices;
+                AT acc = 0;
+                int64_t v = 0;
+                int m = 0;
+                if (live) {
+                    const int64_t b = q / kDirs;
+                    m = int(q - b * kDirs);
+                    v = b * kSlice + lane;
+                    const int len4 = a.A.slice_len4[q];
+                    const int chunk = (len4 + K - 1) / K;
+                    const int g0 = kk * chunk < len4 ? kk * chunk : len4;
+                    const int g1 = g0 + chunk < len4 ? g0 + chunk : len4;
+                    const int64_t base =
+                        a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup + int64_t(g0) * (kSlice * kGroup);
+                    acc = row_dot<VT, XT, AT, kPersistDepth, true>(vals, codes, base, g1 - g0, x, v, sh.delta);
+                }
+                part[warp][lane] = acc;
+                __syncthreads();
+                if (live && kk == 0) {
+                    AT sum = part[warp][lane];
+#pragma unroll
+                    for (int j = 1; j < K; ++j) sum += part[warp + j][lane];
+                    row_epilogue<XT, AT, true>(a, sh, q, lane, v, m, sum, ab_lane, ex_lane);
+                }
+                __syncthreads();
+            }
         }
         step_finish(a, sh, ab_lane, ex_lane);
         if (k + 1 < n_steps &&
@@ -897,7 +940,8 @@ struct PipeLaunch {
 
 // Variant table: 0-2 registers path with prefetch depth 1, 2, 3;
 // 3-6 bulk-copy path with stage shapes (G groups, S stages) = (8,3), (4,3),
-// (4,4), (2,6).
+// (4,4), (2,6); 7-8 state halo in shared memory; 9 both streams pipelined;
+// 10-11 two or four warps per slice.
 template <class VT, class XT, class AT>
 struct Variants {
     static int per_sm(int variant, int threads)
@@ -957,11 +1001,11 @@ int step_default_blocks(int precision, int R, int threads, int variant)
 }
 
 namespace {
-template <class VT, class XT, class AT>
+template <class VT, class XT, class AT, int K>
 int persistent_fit(int threads)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, persistent_kernel<VT, XT, AT>, threads, 0) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, persistent_kernel<VT, XT, AT, K>, threads, 0) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -969,43 +1013,62 @@ int persistent_fit(int threads)
 }
 
 template <class VT, class XT, class AT>
+int persistent_fit_k(int threads, int split)
+{
+    return split == 4 ? persistent_fit<VT, XT, AT, 4>(threads)
+         : split == 2 ? persistent_fit<VT, XT, AT, 2>(threads)
+                      : persistent_fit<VT, XT, AT, 1>(threads);
+}
+
+template <class VT, class XT, class AT, int K>
 cudaError_t persistent_launch(const StepArgs &a, void *other, int64_t n_steps, double *det_base,
                               int64_t max_steps, unsigned *bar, int fault, int blocks, int threads,
                               cudaStream_t s)
 {
     StepArgs a0 = a;
     void *args[] = {&a0, &other, &n_steps, &det_base, &max_steps, &bar, &fault};
-    return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(persistent_kernel<VT, XT, AT>), dim3(blocks),
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(persistent_kernel<VT, XT, AT, K>), dim3(blocks),
                                        dim3(threads), args, 0, s);
+}
+
+template <class VT, class XT, class AT>
+cudaError_t persistent_launch_k(int split, const StepArgs &a, void *other, int64_t n_steps, double *det_base,
+                                int64_t max_steps, unsigned *bar, int fault, int blocks, int threads, cudaStream_t s)
+{
+    if (split == 4)
+        return persistent_launch<VT, XT, AT, 4>(a, other, n_steps, det_base, max_steps, bar, fault, blocks, threads, s);
+    if (split == 2)
+        return persistent_launch<VT, XT, AT, 2>(a, other, n_steps, det_base, max_steps, bar, fault, blocks, threads, s);
+    return persistent_launch<VT, XT, AT, 1>(a, other, n_steps, det_base, max_steps, bar, fault, blocks, threads, s);
 }
 }  // namespace
 
-int persistent_blocks(int precision, int threads)
+int persistent_blocks(int precision, int threads, int split)
 {
     int dev = 0, sms = 0, coop = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (!coop) return 0;
-    const int per = precision == DRTS_FP64 ? persistent_fit<double, double, double>(threads)
-                  : precision == DRTS_FP32 ? persistent_fit<float, float, float>(threads)
-                                           : persistent_fit<__half, float, float>(threads);
+    const int per = precision == DRTS_FP64 ? persistent_fit_k<double, double, double>(threads, split)
+                  : precision == DRTS_FP32 ? persistent_fit_k<float, float, float>(threads, split)
+                                           : persistent_fit_k<__half, float, float>(threads, split);
     return per * sms;
 }
 
 cudaError_t launch_persistent(const StepArgs &a, void *other, int64_t n_steps, double *det_base, int64_t max_steps,
-                              unsigned *bar, int fault_skip_barrier, int blocks, int threads, cudaStream_t s)
+                              unsigned *bar, int fault_skip_barrier, int blocks, int threads, int split, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     if (a.A.precision == DRTS_FP64)
-        return persistent_launch<double, double, double>(a, other, n_steps, det_base, max_steps, bar,
-                                                         fault_skip_barrier, blocks, threads, s);
+        return persistent_launch_k<double, double, double>(split, a, other, n_steps, det_base, max_steps, bar,
+                                                           fault_skip_barrier, blocks, threads, s);
     if (a.A.precision == DRTS_FP32)
-        return persistent_launch<float, float, float>(a, other, n_steps, det_base, max_steps, bar,
-                                                      fault_skip_barrier, blocks, threads, s);
-    return persistent_launch<__half, float, float>(a, other, n_steps, det_base, max_steps, bar,
-                                                   fault_skip_barrier, blocks, threads, s);
+        return persistent_launch_k<float, float, float>(split, a, other, n_steps, det_base, max_steps, bar,
+                                                        fault_skip_barrier, blocks, threads, s);
+    return persistent_launch_k<__half, float, float>(split, a, other, n_steps, det_base, max_steps, bar,
+                                                     fault_skip_barrier, blocks, threads, s);
 }
 
 cudaError_t launch_step(const StepArgs &a, int variant, int blocks, int threads, cudaStream_t s)

@@ -343,6 +343,25 @@ def test_persistent_fp64_300_steps(gpu, oracle_mod):
     assert np.allclose(led, ledo, rtol=1e-11)
 
 
+@pytest.mark.parametrize("variant,threads", [(10, 256), (10, 64), (11, 256), (11, 128)])
+def test_persistent_split_slices(gpu, oracle_mod, variant, threads):
+    """After a split launch variant (two or four warps per slice) the
+    persistent kernel splits its slices the same way."""
+    prob, src = I.fresnel_cube(12, precision=I.FP64)
+    csr = oracle_mod.assemble(prob)
+    xo, deto, ledo = oracle_mod.run(prob, csr, 40, src.as_tuple())
+    with gpu.Context(prob, max_steps=40) as ctx:
+        ctx.set_launch(0, threads, 0, variant)
+        ctx.set_step_mode(gpu.STEP_PERSISTENT)
+        ctx.set_source(0, src)
+        ctx.step_n(40)
+        x = ctx.read_state()
+        det, led = ctx.read_detectors()
+    assert rel_l1(x, xo) < 1e-12
+    assert rel_l1(det, deto) < 1e-12
+    assert np.allclose(led, ledo, rtol=1e-11)
+
+
 def test_persistent_mixed_with_launches(gpu, oracle_mod):
     prob, src = I.three_layers(16, precision=I.FP32)
     csr = oracle_mod.assemble(prob)
