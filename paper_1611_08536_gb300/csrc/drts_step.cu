@@ -349,6 +349,62 @@ __global__ void __launch_bounds__(256) step_kernel(StepArgs a)
     step_finish(a, sh, ab_lane, ex_lane);
 }
 
+// Variants 12-13: the registers path (one group in flight) with 32-bit
+// slice, voxel and state indices.  A row streams from its own base
+// pointers, so a group's address is one wide multiply-add, and a gather's
+// index is one 32-bit add (states < 2^31, checked at launch).  Fewer
+// instructions per nonzero and fewer live registers than variant 0; the
+// block is held to 40 registers (six 256-thread CTAs per SM) or to 32
+// (eight: every warp slot of the SM), trading spills for occupancy.
+template <class VT, class XT, class AT>
+__device__ __forceinline__ AT row_dot_lean(const VT *__restrict__ vrow, const uint16_t *__restrict__ crow, int len4,
+                                           const XT *__restrict__ x, int vi, const int32_t *s_delta)
+{
+    constexpr int kStride = kSlice * kGroup;
+    RawGroup<VT> nxt;
+    Acc<AT> acc;
+    if (len4 > 0) load_raw(vrow, crow, 0, nxt);
+    for (int g = 0; g < len4; ++g) {
+        const RawGroup<VT> cur = nxt;
+        if (g + 1 < len4) load_raw(vrow, crow, (g + 1) * kStride, nxt);
+        AT w[4];
+        unpack(cur, w);
+        const int c0 = int(cur.c.x & 0xffffu), c1 = int(cur.c.x >> 16);
+        const int c2 = int(cur.c.y & 0xffffu), c3 = int(cur.c.y >> 16);
+        const AT p0 = w[0] * AT(__ldg(x + (vi + s_delta[c0])));
+        const AT p1 = w[1] * AT(__ldg(x + (vi + s_delta[c1])));
+        const AT p2 = w[2] * AT(__ldg(x + (vi + s_delta[c2])));
+        const AT p3 = w[3] * AT(__ldg(x + (vi + s_delta[c3])));
+        acc.add((p0 + p1) + (p2 + p3));
+    }
+    return acc.value();
+}
+
+template <class VT, class XT, class AT, int MINB>
+__global__ void __launch_bounds__(256, MINB) step_kernel_lean(StepArgs a)
+{
+    __shared__ StepShared sh;
+    step_prologue(a, sh);
+    const XT *__restrict__ x = static_cast<const XT *>(a.x);
+    const VT *__restrict__ vals = static_cast<const VT *>(a.A.vals);
+    const uint16_t *__restrict__ codes = a.A.codes;
+    const int lane = threadIdx.x & 31;
+    const int warp0 = int((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = int((gridDim.x * blockDim.x) >> 5);
+    const int n_slices = int(a.A.n_slices);
+    AT ab_lane = 0, ex_lane = 0;
+    for (int q = warp0; q < n_slices; q += nwarps) {
+        const int b = q / kDirs;
+        const int m = q - b * kDirs;
+        const int vi = b * kSlice + lane;
+        const int len4 = a.A.slice_len4[q];
+        const int64_t base = a.A.slice_ptr[q] * (kSlice * kGroup) + lane * kGroup;
+        const AT acc = row_dot_lean<VT, XT, AT>(vals + base, codes + base, len4, x, vi, sh.delta);
+        row_epilogue<XT, AT>(a, sh, q, lane, vi, m, acc, ab_lane, ex_lane);
+    }
+    step_finish(a, sh, ab_lane, ex_lane);
+}
+
 // Variants 10-11: K warps per slice (K = 2, 4).  On small grids a slice
 // per warp leaves most warp slots empty and each warp walks ~50 groups of
 // its row one after another; splitting every slice's groups into K
@@ -901,6 +957,23 @@ struct SplitLaunch {
     }
 };
 
+template <class VT, class XT, class AT, int MINB>
+struct LeanLaunch {
+    static int per_sm(int threads)
+    {
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel_lean<VT, XT, AT, MINB>, threads, 0);
+        return n;
+    }
+    static cudaError_t launch(const StepArgs &a, int blocks, int threads, cudaStream_t s)
+    {
+        // 32-bit indices: slices, voxels and states below 2^31
+        if (a.A.n_slices >= (int64_t(1) << 31) || a.V * kDirs >= (int64_t(1) << 31)) return cudaErrorInvalidValue;
+        step_kernel_lean<VT, XT, AT, MINB><<<blocks, threads, 0, s>>>(a);
+        return cudaGetLastError();
+    }
+};
+
 template <class VT, class XT, class AT, int W>
 struct HaloLaunch {
     static int per_sm(int threads)
@@ -941,7 +1014,8 @@ struct PipeLaunch {
 // Variant table: 0-2 registers path with prefetch depth 1, 2, 3;
 // 3-6 bulk-copy path with stage shapes (G groups, S stages) = (8,3), (4,3),
 // (4,4), (2,6); 7-8 state halo in shared memory; 9 both streams pipelined;
-// 10-11 two or four warps per slice.
+// 10-11 two or four warps per slice; 12-13 registers path with 32-bit
+// indices at six or eight CTAs per SM.
 template <class VT, class XT, class AT>
 struct Variants {
     static int per_sm(int variant, int threads)
@@ -959,6 +1033,8 @@ struct Variants {
         case 9: return PipeLaunch<VT, XT, AT>::per_sm(threads);
         case 10: return SplitLaunch<VT, XT, AT, 2>::per_sm(threads);
         case 11: return SplitLaunch<VT, XT, AT, 4>::per_sm(threads);
+        case 12: return LeanLaunch<VT, XT, AT, 6>::per_sm(threads);
+        case 13: return LeanLaunch<VT, XT, AT, 8>::per_sm(threads);
         }
         return 0;
     }
@@ -977,6 +1053,8 @@ struct Variants {
         case 9: return PipeLaunch<VT, XT, AT>::launch(a, blocks, threads, s);
         case 10: return SplitLaunch<VT, XT, AT, 2>::launch(a, blocks, threads, s);
         case 11: return SplitLaunch<VT, XT, AT, 4>::launch(a, blocks, threads, s);
+        case 12: return LeanLaunch<VT, XT, AT, 6>::launch(a, blocks, threads, s);
+        case 13: return LeanLaunch<VT, XT, AT, 8>::launch(a, blocks, threads, s);
         }
         return cudaErrorInvalidValue;
     }
