@@ -950,11 +950,19 @@ __global__ void tcx_sum_kernel(const __nv_bfloat16 *x, int64_t V, int r, double 
 }
 
 // Ledger of X(t): one warp per voxel tile, coalesced 16-byte chunks.  Chunk
-// ch (0..767) is row ch % 8 of core matrix ch / 8 = 24 g + h (direction group
-// g, row group h): row rho = 8 h + ch % 8, directions 8 g .. 8 g + 7.  Lane l
-// reads chunks l + 32 k, k = 0..23: row l + 32 (k mod 6) of group k / 6, the
-// x0, x1 and x2 rows of right-hand side l for even k and l + 32 for odd k.
-__global__ void __launch_bounds__(256) tcx_ledger_kernel(StepArgs a)
+// ch (0..767) of a tile holds directions 8 g .. 8 g + 7 of row rho, with
+// ch = 192 g + rho (rho = 64 term + r).  Lane l reads chunks l + 32 k,
+// k = 0..23: direction group g = k / 6, row l + 32 (k mod 6), i.e. the x0,
+// x1 and x2 rows of right-hand side l for even k and l + 32 for odd k.  All
+// 24 loads of a tile are issued before any is used (12 KB per warp in
+// flight).  Interior voxels with one absorption coefficient need only each
+// right-hand side's sum over directions; boundary voxels (exit weights per
+// direction) and per-direction absorption take the weighted form, which
+// reads the tile's chunks a second time from cache.
+__device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+__global__ void __launch_bounds__(256, 2) tcx_ledger_kernel(StepArgs a)
 {
     __shared__ float red[2][64];
     for (int i = threadIdx.x; i < 128; i += blockDim.x) (&red[0][0])[i] = 0.0f;
@@ -963,37 +971,58 @@ __global__ void __launch_bounds__(256) tcx_ledger_kernel(StepArgs a)
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (int64_t(gridDim.x) * blockDim.x) >> 5;
+    const int64_t nxy = int64_t(a.nx) * a.ny;
     float ab[2] = {0.0f, 0.0f}, ex[2] = {0.0f, 0.0f};
     for (int64_t v = w0; v < a.V; v += nw) {
+        const uint4 *t = reinterpret_cast<const uint4 *>(x + v * (kXTileBytes / 2));
+        uint4 raw[24];
+#pragma unroll
+        for (int kc = 0; kc < 24; ++kc) raw[kc] = __ldcs(t + lane + 32 * kc);
         const int k = a.cls[v];
-        const float abs_k = float(a.tab.absorb[k]);
         // two-step interfaces: absorption per direction (s then sums it, not x)
         const double *ad = a.tab.absorb_dir ? a.tab.absorb_dir + k * kDirs : nullptr;
-        const int xx = int(v % a.nx), yy = int(v / a.nx % a.ny), zz = int(v / (int64_t(a.nx) * a.ny));
+        const int zz = int(v / nxy), rem = int(v - zz * nxy);
+        const int yy = rem / a.nx, xx = rem - yy * a.nx;
         const int mask = (zz == 0 ? 0 : (zz == a.nz - 1 ? 2 : 1)) * 9 + (yy == 0 ? 0 : (yy == a.ny - 1 ? 2 : 1)) * 3 +
                          (xx == 0 ? 0 : (xx == a.nx - 1 ? 2 : 1));
-        const double *et = a.tab.exit_total + (k * 27 + mask) * kDirs;
-        const uint4 *t = reinterpret_cast<const uint4 *>(x + v * (kXTileBytes / 2));
-        float s[2] = {0.0f, 0.0f}, se[2] = {0.0f, 0.0f};
-#pragma unroll 6
-        for (int kc = 0; kc < 24; ++kc) {
-            const int ch = lane + 32 * kc;
-            const int n0 = (kc / 6) * 8;
-            const uint4 raw = t[ch];
-            const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&raw);
+        if (!ad && mask == 13) {
+            float s[2] = {0.0f, 0.0f};
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int n = n0 + i;
-                if (n >= kDirs) continue;
-                const float xv = __bfloat162float(h[i]);
-                s[kc & 1] += ad ? float(ad[n]) * xv : xv;
-                if (mask != 13) se[kc & 1] += float(et[n]) * xv;
+            for (int kc = 0; kc < 24; ++kc) {
+                const uint4 w = raw[kc];
+                float cs = bf16_lo(w.x) + bf16_hi(w.x);         // directions 8 g, 8 g + 1
+                if (kc < 18)                                     // g < 3: all eight are directions
+                    cs += (bf16_lo(w.y) + bf16_hi(w.y)) + ((bf16_lo(w.z) + bf16_hi(w.z)) + (bf16_lo(w.w) + bf16_hi(w.w)));
+                s[kc & 1] += cs;
             }
-        }
+            const float abs_k = float(a.tab.absorb[k]);
+            ab[0] += abs_k * s[0];
+            ab[1] += abs_k * s[1];
+        } else {
+            const double *et = a.tab.exit_total + (k * 27 + mask) * kDirs;
+            const float abs_k = float(a.tab.absorb[k]);
+            float s[2] = {0.0f, 0.0f}, se[2] = {0.0f, 0.0f};
+            // the tile's chunks again (from cache): indexing the register
+            // copy with a loop counter would move it to local memory
+#pragma unroll 1
+            for (int kc = 0; kc < 24; ++kc) {
+                const int n0 = (kc / 6) * 8;
+                const uint4 w = __ldg(t + lane + 32 * kc);
+                const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-        for (int par = 0; par < 2; ++par) {
-            ab[par] += ad ? s[par] : abs_k * s[par];
-            ex[par] += se[par];
+                for (int i = 0; i < 8; ++i) {
+                    const int n = n0 + i;
+                    if (n >= kDirs) continue;
+                    const float xv = (i & 1) ? bf16_hi(wd[i >> 1]) : bf16_lo(wd[i >> 1]);
+                    s[kc & 1] += ad ? float(ad[n]) * xv : xv;
+                    if (mask != 13) se[kc & 1] += float(et[n]) * xv;
+                }
+            }
+#pragma unroll
+            for (int par = 0; par < 2; ++par) {
+                ab[par] += ad ? s[par] : abs_k * s[par];
+                ex[par] += se[par];
+            }
         }
     }
     for (int par = 0; par < 2; ++par) {
@@ -1123,7 +1152,7 @@ cudaError_t launch_tc_step(const StepArgs &a, bool functionals, cudaStream_t s)
             tcx_det_kernel<<<a.n_patch, kMaxRhs, 0, s>>>(a);
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
-        tcx_ledger_kernel<<<unsigned(sm_count() * 4), 256, 0, s>>>(a);
+        tcx_ledger_kernel<<<unsigned(sm_count() * 2), 256, 0, s>>>(a);     // two resident per SM
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (tc_blocks_per_sm(nullptr) < 1) return cudaErrorInvalidConfiguration;
