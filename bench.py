@@ -191,12 +191,14 @@ def run_gpu(args):
     info = ctx.info()
     ctx.set_source(0, src)
     tune = None
-    if args.step_mode == "persistent":
-        ctx.set_step_mode(drts.STEP_PERSISTENT)
     if args.blocks_per_sm or args.threads or args.variant >= 0:
         ctx.set_launch(args.blocks_per_sm, args.threads, 0, args.variant)
-    elif args.autotune and args.step_mode == "launch":
+    elif args.autotune:
+        # the persistent mode keeps the tuned launch's block size, grid and
+        # warps per slice
         tune = ctx.autotune(args.autotune)
+    if args.step_mode == "persistent":
+        ctx.set_step_mode(drts.STEP_PERSISTENT)
 
     ctx.step_n(args.warmup)
     torch.cuda.synchronize()
@@ -271,7 +273,8 @@ def run_gpu(args):
                                         "scaled to this launch by nonzeros")
                      if traffic is not None else "no ncu capture of this kernel source and variant",
                      "algorithmic_bytes_per_launch": int(alg)},
-        "gpu_launches": args.steps,
+        # one cooperative launch runs all timed steps in the persistent mode
+        "gpu_launches": 1 if args.step_mode == "persistent" else args.steps,
         "e2e": e2e,
         "clocks": clk.summary(),
     }

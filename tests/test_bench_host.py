@@ -26,14 +26,28 @@ def test_algorithmic_bytes_per_precision():
 
 
 def test_traffic_follows_kernel_source():
-    d = json.load(open(bench.TRAFFIC_FILE))
+    """Each committed capture scales to a launch by nonzeros when it was
+    taken on the current kernel source, for its own precision and variant;
+    no capture, no traffic figure."""
     nnz = 11429626472
-    if d["kernel_sha"] == bench.kernel_hash():
-        t = bench.traffic_per_launch("three_layers_128", d["precision"], nnz)
+    caps = bench.traffic_captures()
+    assert caps
+    for d in caps:
+        if d["kernel_sha"] != bench.kernel_hash():
+            assert bench.traffic_per_launch("three_layers_128", d["precision"], nnz, d["variant"]) is None or any(
+                c["kernel_sha"] == bench.kernel_hash() and c["precision"] == d["precision"]
+                and c["variant"] == d["variant"] for c in caps)
+            continue
+        t = bench.traffic_per_launch("three_layers_128", d["precision"], nnz, d["variant"])
         assert t == d["dram_bytes_per_nnz"] * nnz
-        # the capture's bytes per nonzero are the algorithmic ones plus padding
-        assert 6.0 < d["dram_bytes_per_nnz"] < 6.5
+        # bytes per nonzero: the algorithmic ones plus slice padding (FP32:
+        # 4 B value + 2 B code; FP16: 2 + 2 B and the second terms of split
+        # values, per nonzero of the matrix)
+        lo, hi = {"fp32": (6.0, 6.5), "fp16": (4.0, 4.5)}[d["precision"]]
+        assert lo < d["dram_bytes_per_nnz"] < hi
     assert bench.traffic_per_launch("three_layers_128", "fp64", nnz) is None
+    # a variant without a capture has no traffic figure
+    assert bench.traffic_per_launch("three_layers_128", "fp32", nnz, 5) is None
 
 
 def test_batched_launch_count():
