@@ -367,7 +367,8 @@ drts_status drts_two_step_tables(const drts_problem *prob, int32_t k1, int32_t k
  * warps per slice, each summing a contiguous part of the rows, for grids too
  * small to give every warp slot a slice; 12-13 = registers path with one
  * group in flight and 32-bit slice, voxel and state indices, compiled for six
- * or eight 256-thread blocks per SM).  For a batched
+ * or eight 256-thread blocks per SM; 14 = eight warps per slice, blocks of
+ * 256 threads).  For a batched
  * context on the CUDA cores the variant is the slice order: 0 = warps
  * stride over all slices, 1 = block-major (one CTA works through all 26
  * direction slices of a voxel block), 2 = block-major with the block's x

@@ -710,7 +710,7 @@ try {
             return fail(c, DRTS_EUNSUPPORTED, "sub-step sources need the launch step mode");
         StepArgs a = make_args(c);
         // the launch path's split variants (two or four warps per slice) carry over
-        int split = c->variant == 10 ? 2 : (c->variant == 11 ? 4 : 1);
+        int split = c->variant == 10 ? 2 : (c->variant == 11 ? 4 : (c->variant == 14 ? 8 : 1));
         if (c->threads / 32 < split) split = 1;
         // as many blocks as the launch path uses, when they can all be resident
         int blocks = persistent_blocks(c->prob.precision, c->threads, split);

@@ -174,12 +174,12 @@ cudaError_t launch_count_export(const SlicedMatrix &A, int64_t V, int64_t row_be
 // shared-memory x-halo paths with 13 or 26 warps (nx a multiple of 32), 9
 // registers path with matrix and gather streams both pipelined, 10-11 two
 // or four warps per slice (small grids), 12-13 registers path with 32-bit
-// indices held to six or eight CTAs per SM
+// indices held to six or eight CTAs per SM, 14 eight warps per slice
 cudaError_t launch_step(const StepArgs &a, int variant, int blocks, int threads, cudaStream_t s);
 int step_default_blocks(int precision, int R, int threads, int variant);
-constexpr int kStepVariants = 14;
+constexpr int kStepVariants = 15;
 // persistent multi-step kernel (cooperative launch, bounded grid barrier);
-// split = warps per slice (1, 2 or 4)
+// split = warps per slice (1, 2, 4 or 8)
 int persistent_blocks(int precision, int threads, int split);
 cudaError_t launch_persistent(const StepArgs &a, void *other, int64_t n_steps, double *det_base, int64_t max_steps,
                               unsigned *bar, int fault_skip_barrier, int blocks, int threads, int split,

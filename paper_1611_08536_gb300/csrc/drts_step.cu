@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(256, MINB) step_kernel_lean(StepArgs a)
     step_finish(a, sh, ab_lane, ex_lane);
 }
 
-// Variants 10-11: K warps per slice (K = 2, 4).  On small grids a slice
+// Variants 10-11 and 14: K warps per slice (K = 2, 4, 8).  On small grids a slice
 // per warp leaves most warp slots empty and each warp walks ~50 groups of
 // its row one after another; splitting every slice's groups into K
 // contiguous parts run by K warps of the CTA multiplies the matrix loads in
@@ -1015,7 +1015,7 @@ struct PipeLaunch {
 // 3-6 bulk-copy path with stage shapes (G groups, S stages) = (8,3), (4,3),
 // (4,4), (2,6); 7-8 state halo in shared memory; 9 both streams pipelined;
 // 10-11 two or four warps per slice; 12-13 registers path with 32-bit
-// indices at six or eight CTAs per SM.
+// indices at six or eight CTAs per SM; 14 eight warps per slice.
 template <class VT, class XT, class AT>
 struct Variants {
     static int per_sm(int variant, int threads)
@@ -1035,6 +1035,7 @@ struct Variants {
         case 11: return SplitLaunch<VT, XT, AT, 4>::per_sm(threads);
         case 12: return LeanLaunch<VT, XT, AT, 6>::per_sm(threads);
         case 13: return LeanLaunch<VT, XT, AT, 8>::per_sm(threads);
+        case 14: return SplitLaunch<VT, XT, AT, 8>::per_sm(threads);
         }
         return 0;
     }
@@ -1055,6 +1056,7 @@ struct Variants {
         case 11: return SplitLaunch<VT, XT, AT, 4>::launch(a, blocks, threads, s);
         case 12: return LeanLaunch<VT, XT, AT, 6>::launch(a, blocks, threads, s);
         case 13: return LeanLaunch<VT, XT, AT, 8>::launch(a, blocks, threads, s);
+        case 14: return SplitLaunch<VT, XT, AT, 8>::launch(a, blocks, threads, s);
         }
         return cudaErrorInvalidValue;
     }
@@ -1093,7 +1095,8 @@ int persistent_fit(int threads)
 template <class VT, class XT, class AT>
 int persistent_fit_k(int threads, int split)
 {
-    return split == 4 ? persistent_fit<VT, XT, AT, 4>(threads)
+    return split == 8 ? persistent_fit<VT, XT, AT, 8>(threads)
+         : split == 4 ? persistent_fit<VT, XT, AT, 4>(threads)
          : split == 2 ? persistent_fit<VT, XT, AT, 2>(threads)
                       : persistent_fit<VT, XT, AT, 1>(threads);
 }
@@ -1113,6 +1116,8 @@ template <class VT, class XT, class AT>
 cudaError_t persistent_launch_k(int split, const StepArgs &a, void *other, int64_t n_steps, double *det_base,
                                 int64_t max_steps, unsigned *bar, int fault, int blocks, int threads, cudaStream_t s)
 {
+    if (split == 8)
+        return persistent_launch<VT, XT, AT, 8>(a, other, n_steps, det_base, max_steps, bar, fault, blocks, threads, s);
     if (split == 4)
         return persistent_launch<VT, XT, AT, 4>(a, other, n_steps, det_base, max_steps, bar, fault, blocks, threads, s);
     if (split == 2)

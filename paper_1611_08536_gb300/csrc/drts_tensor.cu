@@ -1002,20 +1002,29 @@ __global__ void __launch_bounds__(256, 2) tcx_ledger_kernel(StepArgs a)
             const double *et = a.tab.exit_total + (k * 27 + mask) * kDirs;
             const float abs_k = float(a.tab.absorb[k]);
             float s[2] = {0.0f, 0.0f}, se[2] = {0.0f, 0.0f};
-            // the tile's chunks again (from cache): indexing the register
-            // copy with a loop counter would move it to local memory
+            // per direction group: its eight weights once, then its six chunks
+            // (the tile's chunks again, from cache: indexing the register copy
+            // with a loop counter would move it to local memory)
 #pragma unroll 1
-            for (int kc = 0; kc < 24; ++kc) {
-                const int n0 = (kc / 6) * 8;
-                const uint4 w = __ldg(t + lane + 32 * kc);
-                const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+            for (int g = 0; g < 4; ++g) {
+                float wa[8], we[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    const int n = n0 + i;
-                    if (n >= kDirs) continue;
-                    const float xv = (i & 1) ? bf16_hi(wd[i >> 1]) : bf16_lo(wd[i >> 1]);
-                    s[kc & 1] += ad ? float(ad[n]) * xv : xv;
-                    if (mask != 13) se[kc & 1] += float(et[n]) * xv;
+                    const int n = 8 * g + i;
+                    wa[i] = n < kDirs ? (ad ? float(ad[n]) : 1.0f) : 0.0f;
+                    we[i] = n < kDirs && mask != 13 ? float(et[n]) : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < 6; ++j) {
+                    const uint4 w = __ldg(t + lane + 32 * (6 * g + j));
+                    const uint32_t wd[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        if (8 * g + i >= kDirs) continue;       // padding columns of the last group
+                        const float xv = (i & 1) ? bf16_hi(wd[i >> 1]) : bf16_lo(wd[i >> 1]);
+                        s[j & 1] += wa[i] * xv;
+                        se[j & 1] += we[i] * xv;
+                    }
                 }
             }
 #pragma unroll

@@ -226,7 +226,7 @@ def test_run_host_matches_step_n(gpu):
     assert rel_l1(det[:, 0, :], da) < 1e-6
 
 
-@pytest.mark.parametrize("variant", list(range(14)))
+@pytest.mark.parametrize("variant", list(range(15)))
 @pytest.mark.parametrize("precision", [I.FP64, I.FP32, I.FP16_ROWSCALE])
 def test_step_variants_agree(gpu, oracle_mod, variant, precision):
     """Every launch variant of the step computes the same step (32 x 14 x 14
@@ -256,10 +256,10 @@ def test_step_variants_agree(gpu, oracle_mod, variant, precision):
 
 
 @pytest.mark.parametrize("variant,threads", [(9, 256), (10, 256), (10, 96), (11, 256), (11, 128), (12, 256),
-                                            (13, 96)])
+                                            (13, 96), (14, 256)])
 def test_step_variants_ragged_grid(gpu, oracle_mod, variant, threads):
     """The register variants that take any grid (pipelined, two and four
-    warps per slice, 32-bit indices) on a 13 x 11 x 9 FP64 grid whose 32-voxel blocks wrap
+    and eight warps per slice, 32-bit indices) on a 13 x 11 x 9 FP64 grid whose 32-voxel blocks wrap
     across x rows, with detector and ledger, including block shapes whose
     warp count is not a multiple of the warps per slice."""
     prob, _ = I.three_layers(9, precision=I.FP64)
@@ -316,7 +316,7 @@ def test_autotune_keeps_state_and_parity(gpu, oracle_mod):
         before = ctx.read_state()
         r = ctx.autotune(2)
         # 16^3: the halo variants (7, 8: whole 32-voxel x-runs only) do not apply
-        assert 0 <= r["variant"] < 14 and r["variant"] not in (7, 8)
+        assert 0 <= r["variant"] < 15 and r["variant"] not in (7, 8)
         assert r["candidates"] > 0 and r["ms_per_step"] > 0
         assert np.array_equal(ctx.read_state(), before)
         det, led = ctx.read_detectors()
@@ -344,9 +344,9 @@ def test_persistent_fp64_300_steps(gpu, oracle_mod):
     assert np.allclose(led, ledo, rtol=1e-11)
 
 
-@pytest.mark.parametrize("variant,threads", [(10, 256), (10, 64), (11, 256), (11, 128)])
+@pytest.mark.parametrize("variant,threads", [(10, 256), (10, 64), (11, 256), (11, 128), (14, 256)])
 def test_persistent_split_slices(gpu, oracle_mod, variant, threads):
-    """After a split launch variant (two or four warps per slice) the
+    """After a split launch variant (two, four or eight warps per slice) the
     persistent kernel splits its slices the same way."""
     prob, src = I.fresnel_cube(12, precision=I.FP64)
     csr = oracle_mod.assemble(prob)
