@@ -249,7 +249,9 @@ def run_gpu(args):
     alg = algorithmic_bytes(info, args.precision)
     achieved = alg / (ms_step * 1e-3) / 1e9
     variant = tune["variant"] if tune else (args.variant if args.variant >= 0 else 0)
-    traffic = traffic_per_launch(args.workload, args.precision, info.nnz, variant)
+    # the captures are of the launch-per-step kernels, not of the persistent one
+    traffic = (traffic_per_launch(args.workload, args.precision, info.nnz, variant)
+               if args.step_mode == "launch" else None)
     line = {
         "metric": METRIC, "value": round(gnnz, 3), "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
