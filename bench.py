@@ -809,7 +809,8 @@ def run_serve(args):
     build.build()
     m = measure_served(args, args.serve_requests, args.serve_rate, args.serve_step_scale,
                        args.serve_resident, args.serve_tick_steps, args.serve_streams, args.serve_policy,
-                       baselines="run" if args.serve_baselines else "none")
+                       baselines=("estimate" if args.serve_estimate_baselines
+                                  else "run" if args.serve_baselines else "none"))
     line = {
         "metric": "DRTS served stream: simulations per second (continuous batching)",
         "value": m["sims_per_s"], "unit": "sims/s", "n_gpus": 1,
@@ -950,6 +951,9 @@ def main():
                     help="admission order of queued requests")
     ap.add_argument("--no-serve-baselines", dest="serve_baselines", action="store_false",
                     help="skip the one-after-another and per-simulation baseline runs")
+    ap.add_argument("--serve-estimate-baselines", action="store_true",
+                    help="estimate the per-simulation baseline from the single-rhs step timed once per "
+                         "grid side (for requests with their full step counts)")
     ap.add_argument("--sim-steps", type=int, default=1500, help="steps per simulation for sims/s")
     ap.add_argument("--batched-kernel", default="tensor", choices=["cuda", "tensor"],
                     help="batched product: tcgen05 tensor-core form (default) or CUDA-core form")
