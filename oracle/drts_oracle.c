@@ -124,8 +124,16 @@ static double seg_dist(const double p[3], const double a[3], const double b[3])
 /* Henyey-Greenstein phase value for cos(angle) = mu */
 static double hg(double g, double mu)
 {
+#ifndef PLANT_HG_SIGN
     double den = 1.0 + g * g - 2.0 * g * mu;
+#else
+    double den = 1.0 + g * g + 2.0 * g * mu;
+#endif
+#ifndef PLANT_HG_EXPONENT
     return (1.0 - g * g) / (den * sqrt(den));
+#else
+    return (1.0 - g * g) / den;
+#endif
 }
 
 /* Unpolarised Fresnel reflectance, Section 4.2 (reflection and refraction at a

@@ -141,6 +141,61 @@ def test_hg_forward_bias_monotone(oracle_mod):
         if c[a + 1] > c[a] + 1e-12:
             assert s[a + 1] > s[a]
 
+
+def _scattered_shares(oracle_mod, g, mu_s=5.0, h=0.1):
+    """share[n][m]: the scattered part of W[n] summed over targets, per
+    outgoing direction m (no absorption), normalised to sum 1 per n."""
+    W = oracle_mod.raw_stencil(_prob(4, [(mu_s, 0.0, g, 1.0)], h=h), 0)
+    out = np.zeros((26, 26))
+    for n in range(26):
+        sh = W[n].sum(axis=0)
+        sh[n] -= math.exp(-mu_s * h)          # the unscattered share stays in n
+        out[n] = sh / sh.sum()
+    return out
+
+
+def _unit(d):
+    v = np.array(I.direction_vector(d), dtype=float)
+    return v / np.linalg.norm(v)
+
+
+def test_hg_sign_of_g_reverses_directions(oracle_mod):
+    """The Henyey-Greenstein phase function depends on g and cos(theta) only
+    through g cos(theta) and g^2 (Section 2, HG), so p(cos; -g) = p(-cos; g);
+    the 26 lattice directions are symmetric under S -> -S, so the discrete
+    kernel satisfies share_{-g}(n -> m) = share_g(n -> -m) exactly."""
+    for g in (0.3, 0.9):
+        a, b = _scattered_shares(oracle_mod, g), _scattered_shares(oracle_mod, -g)
+        for n in range(26):
+            for m in range(26):
+                opp = D(*(-c for c in I.direction_vector(m)))
+                assert b[n, m] == pytest.approx(a[n, opp], rel=1e-12, abs=1e-15)
+
+
+def test_hg_mean_cosine_slope_is_one(oracle_mod):
+    """HG expands in Legendre polynomials as sum_l (2l + 1) g^l P_l(cos) / 4pi.
+    Over the 26 lattice directions sum_m P_1 = sum_m P_2 = sum_m P_3 = 0 and
+    sum_m (n.m)^2 = 26/3 for every unit n (cubic symmetry: sum_m m m^T =
+    26/3 I), so the discrete kernel's mean cosine is g (1 + O(g^2)) for every
+    incoming direction.  A wrong exponent, a missing normalisation of the
+    lattice vectors or a sign error changes the slope."""
+    g = 1e-3
+    share = _scattered_shares(oracle_mod, g)
+    for n in range(26):
+        un = _unit(n)
+        mean_cos = sum(share[n, m] * float(un @ _unit(m)) for m in range(26))
+        assert mean_cos / g == pytest.approx(1.0, abs=1e-4), (n, mean_cos / g)
+
+
+def test_hg_forward_limit(oracle_mod):
+    """As g -> 1 the HG lobe collapses onto the incoming direction: at
+    g = 0.999 its value there exceeds its value 45 degrees off by a factor of
+    about 4e8, so all but ~1e-8 of the scattered share stays in n."""
+    share = _scattered_shares(oracle_mod, 0.999)
+    for n in range(26):
+        assert share[n, n] > 1.0 - 1e-6
+        assert share[n, n] < 1.0
+
 # --------------------------------------------------------------------------
 # Properties listed under Eq. 24
 

@@ -14,7 +14,8 @@ PLANTS = ["PLANT_DROP_UNSCATTERED", "PLANT_ABSORB_ONCE", "PLANT_SEGMENT_SIGN",
           "PLANT_HG_UNNORMALISED", "PLANT_MIRROR_INDEX", "PLANT_FRESNEL_SWAP",
           "PLANT_WRONG_DIRECTION_INDEX", "PLANT_POINT_OFF_BY_ONE", "PLANT_SENSOR_LAG_SIGN",
           "PLANT_SOURCE_FULL_PATH", "PLANT_HIGH_FACE_NO_FLIP",
-          "PLANT_SNELL_INVERTED", "PLANT_TWO_STEP_PATH_MEDIUM1", "PLANT_TWO_STEP_NO_FLIP"]
+          "PLANT_SNELL_INVERTED", "PLANT_TWO_STEP_PATH_MEDIUM1", "PLANT_TWO_STEP_NO_FLIP",
+          "PLANT_HG_SIGN", "PLANT_HG_EXPONENT"]
 
 CHECKS = [
     pins.test_axis_direction_single_target,
@@ -22,6 +23,8 @@ CHECKS = [
     pins.test_unscattered_survival_factor,
     pins.test_perpendicular_scatter_four_points,
     pins.test_isotropic_kernel_uniform,
+    pins.test_hg_mean_cosine_slope_is_one,
+    pins.test_hg_forward_limit,
     lambda o: pins.test_interior_column_sums_equal_absorption_survival(o, 10.0, 0.01, 0.9),
     pins.test_mirror_columns_sum_to_survival_everywhere,
     pins.test_energy_conservation_mirror_with_interface,
