@@ -65,6 +65,24 @@ typedef int32_t drts_status;
                                          and the share refracted by Snell's law, which
                                          finishes the step in the other medium at its speed */
 
+/* weights of the outgoing lattice directions in the discrete
+ * Henyey-Greenstein kernel (Section 2, the scattering kernel g(S, S') on the
+ * partition of directions of Section 3):
+ *   DRTS_HG_EQUAL       G[n][m] = p(S_n . S_m) / sum_m' p(S_n . S_m'): every
+ *                       lattice direction counts alike (the default);
+ *   DRTS_HG_QUADRATURE  each direction also weighted by its share of the
+ *                       sphere, G[n][m] = w_m p(S_n . S_m) / sum_m' w_m'
+ *                       p(S_n . S_m'), with w = 1/21 per axis, 4/105 per face
+ *                       diagonal and 9/280 per body diagonal: the 26
+ *                       directions with these weights integrate every
+ *                       polynomial of degree <= 7 on the sphere exactly, so
+ *                       the kernel's mean cosine is g up to the HG terms of
+ *                       degree 7 and above.  The paper gives its directions
+ *                       as quadrature points (Lebedev) without saying whether
+ *                       the kernel carries their weights. */
+#define DRTS_HG_EQUAL 0
+#define DRTS_HG_QUADRATURE 1
+
 /* storage / arithmetic precision of the time step */
 #define DRTS_FP64 0          /* A, state and accumulation in FP64 */
 #define DRTS_FP32 1          /* A and state in FP32, FP32 accumulation */
@@ -108,6 +126,7 @@ typedef struct drts_problem {
                                         DRTS_EINVAL).  Sub-step source columns
                                         (drts_source_column, drts_inject_source_substeps)
                                         use the first-order fold in both modes. */
+    int32_t direction_weights;       /* DRTS_HG_EQUAL (0) or DRTS_HG_QUADRATURE */
 } drts_problem;
 
 /* Batched step (n_rhs > 1) implementations (Eq. 26 with R right-hand sides

@@ -86,6 +86,7 @@ class _Problem(ctypes.Structure):
         ("det_face", ctypes.c_int32),
         ("det_nu", ctypes.c_int32), ("det_nv", ctypes.c_int32),
         ("interface", ctypes.c_int32),
+        ("direction_weights", ctypes.c_int32),
     ]
 
 
@@ -170,7 +171,8 @@ class Problem:
                           _ptr(self.keep[4]), float(prob.n_outside),
                           int(prob.boundary), int(prob.det_face),
                           int(prob.det_nu), int(prob.det_nv),
-                          int(getattr(prob, "interface", 0)))
+                          int(getattr(prob, "interface", 0)),
+                          int(getattr(prob, "direction_weights", 0)))
         self.shape = (nx, ny, nz)
         self.n_states = nx * ny * nz * NDIR
 

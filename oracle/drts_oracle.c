@@ -60,6 +60,7 @@ typedef struct {
     int32_t det_face;         /* 0..5 = -x,+x,-y,+y,-z,+z; -1 for none */
     int32_t det_nu, det_nv;   /* detector patch grid on that face */
     int32_t interface;        /* 0 first-order folding (R6); 1 planar two-step (R19) */
+    int32_t direction_weights; /* 0 every direction alike (R7); 1 quadrature shares (R7 variant) */
 } orc_problem;
 
 /* one raw contribution of a source state: target offset o, direction m */
@@ -154,15 +155,39 @@ double orc_fresnel(double cos_i, double n1, double n2)
     return 0.5 * (rs * rs + rp * rp);
 }
 
+/* Share of the unit sphere carried by lattice direction m when the kernel
+ * weights directions as quadrature points (reading R7, variant): the unique
+ * weights, equal within each class of the cube's symmetry (6 axes, 12 face
+ * diagonals, 8 body diagonals), that integrate every polynomial of degree
+ * <= 7 on the sphere exactly (odd ones vanish by the central symmetry).  Written from the class sizes and the sphere averages
+ * <1> = 1, <x^2 y^2 z^2> = 1/105, <x^2 y^2> = 1/15 (solved in that order):
+ * body diagonals (|x y z| = 1/sqrt(27)) carry 8 c / 27 = 1/105, face
+ * diagonals (x^2 y^2 = 1/4 for 4 of 12) b + 8 c / 9 = 1/15, axes the rest. */
+static double quadrature_share(int m)
+{
+    int k = (DIRV[m][0] != 0) + (DIRV[m][1] != 0) + (DIRV[m][2] != 0);
+    double c = 27.0 / (8.0 * 105.0);
+    double b = 1.0 / 15.0 - 8.0 * c / 9.0;
+    double a = (1.0 - 12.0 * b - 8.0 * c) / 6.0;
+    return k == 1 ? a : (k == 2 ? b : c);
+}
+
+static double direction_weight(int mode, int m)
+{
+    return mode == 1 ? quadrature_share(m) : 1.0;
+}
+
 /* Discrete Henyey-Greenstein kernel g(S_n, S_m), normalised over the 26
- * directions for each incoming n (the probability kernel of Eq. 1/19). */
-static void hg_table(double g, double G[NDIR][NDIR])
+ * directions for each incoming n (the probability kernel of Eq. 1/19);
+ * mode 1 weights each outgoing direction by its quadrature share. */
+static void hg_table(double g, int mode, double G[NDIR][NDIR])
 {
     for (int n = 0; n < NDIR; ++n) {
         double sum = 0.0;
         for (int m = 0; m < NDIR; ++m) {
             double mu = DIRS[n][0] * DIRS[m][0] + DIRS[n][1] * DIRS[m][1] + DIRS[n][2] * DIRS[m][2];
             G[n][m] = hg(g, mu);
+            if (mode == 1) G[n][m] *= direction_weight(mode, m);
             sum += G[n][m];
         }
 #ifndef PLANT_HG_UNNORMALISED
@@ -204,7 +229,7 @@ static int build_stencil_frac(const orc_problem *P, int k, double frac, orc_sten
 #endif
     double f1 = (1.0 - surv_s) * surv_a;          /* Eq. 10 */
     double G[NDIR][NDIR];
-    hg_table(P->g[k], G);
+    hg_table(P->g[k], P->direction_weights, G);
 
     for (int n = 0; n < NDIR; ++n) {
         S->count[n] = 0;
@@ -343,7 +368,7 @@ static int build_two_step(const orc_problem *P, int k1, int k2, orc_stencil *S1,
     double n1 = P->n[k1], n2 = P->n[k2];
     double l1 = nmin / n1, l2 = nmin / n2;
     double G1[NDIR][NDIR];
-    hg_table(P->g[k1], G1);
+    hg_table(P->g[k1], P->direction_weights, G1);
     for (int n = 0; n < NDIR; ++n) {
         S1->count[n] = S0->count[n] = 0;
         S1->e[n] = (orc_entry *)malloc(sizeof(orc_entry) * cap);
@@ -414,6 +439,7 @@ static int build_two_step(const orc_problem *P, int k1, int k2, orc_stencil *S1,
             double grow[NDIR], gsum = 0.0;
             for (int m = 0; m < NDIR; ++m) {
                 grow[m] = hg(P->g[k2], D[0] * DIRS[m][0] + D[1] * DIRS[m][1] + D[2] * DIRS[m][2]);
+                if (P->direction_weights == 1) grow[m] *= direction_weight(1, m);
                 gsum += grow[m];
             }
             for (int m = 0; m < NDIR; ++m) grow[m] /= gsum;

@@ -202,6 +202,8 @@ drts_status validate(const drts_problem *p)
         return fail(nullptr, DRTS_EUNSUPPORTED, "the tensor-core batched step runs FP32 problems");
     if (p->interface != DRTS_INTERFACE_FIRST_ORDER && p->interface != DRTS_INTERFACE_TWO_STEP)
         return fail(nullptr, DRTS_EINVAL, "bad interface");
+    if (p->direction_weights != DRTS_HG_EQUAL && p->direction_weights != DRTS_HG_QUADRATURE)
+        return fail(nullptr, DRTS_EINVAL, "bad direction_weights");
     if (p->interface == DRTS_INTERFACE_TWO_STEP) {
         // planar interfaces normal to z: one medium per z layer
         const int64_t layer = int64_t(p->nx) * p->ny;

@@ -152,10 +152,27 @@ void column_exit(const double *Wn, const double *r_edge, int mask, int det_face,
     }
 }
 
+// Share of the sphere of lattice direction m in the discrete kernel
+// (DRTS_HG_QUADRATURE): the weights of the degree-7 rule on the 26
+// directions, fixed by the octahedral moments 1, x^4, x^2 y^2 and x^2 y^2 z^2
+// (sphere averages 1, 1/5, 1/15, 1/105): 6 a + 12 b + 8 c = 1,
+// 2 a + 2 b + 8 c / 9 = 1/5, b + 8 c / 9 = 1/15, 8 c / 27 = 1/105, so
+// a = 1/21 (axes), b = 4/105 (face diagonals), c = 9/280 (body diagonals).
+double direction_share(int mode, int m)
+{
+    if (mode != DRTS_HG_QUADRATURE) return 1.0;
+    switch (dirs().nnzc[m]) {
+    case 1: return 1.0 / 21.0;
+    case 2: return 4.0 / 105.0;
+    default: return 9.0 / 280.0;
+    }
+}
+
 // Henyey-Greenstein weights of the 26 lattice directions for scattering out
 // of the unit vector u, normalised over the lattice (the discrete kernel of
-// Section 5, here also for a direction that is not a lattice one).
-void phase_row(double g, const double u[3], double out[kDirs])
+// Section 5, here also for a direction that is not a lattice one); with
+// DRTS_HG_QUADRATURE each direction also carries its share of the sphere.
+void phase_row(double g, int mode, const double u[3], double out[kDirs])
 {
     const Directions &D = dirs();
     double sum = 0.0;
@@ -163,6 +180,7 @@ void phase_row(double g, const double u[3], double out[kDirs])
         const double mu = u[0] * D.u[m][0] + u[1] * D.u[m][1] + u[2] * D.u[m][2];
         const double den = 1.0 + g * g - 2.0 * g * mu;
         out[m] = (1.0 - g * g) / (den * std::sqrt(den));
+        if (mode == DRTS_HG_QUADRATURE) out[m] *= direction_share(mode, m);
         sum += out[m];
     }
     for (int m = 0; m < kDirs; ++m) out[m] /= sum;
@@ -240,7 +258,7 @@ bool two_step_column(const drts_problem &p, double nmin, int k1, int k2, int n, 
 
     // scattered before the plane
     double ph1[kDirs];
-    phase_row(m1.g, D.u[n], ph1);
+    phase_row(m1.g, p.direction_weights, D.u[n], ph1);
     const double p_scat = (1.0 - std::exp(-m1.mu_s * tc * lam1 * h)) * std::exp(-m1.mu_a * lam1 * h);
     if (p_scat > 0.0)
         for (int m = 0; m < kDirs; ++m) {
@@ -256,7 +274,7 @@ bool two_step_column(const drts_problem &p, double nmin, int k1, int k2, int n, 
     const double R = fresnel(ci, m1.n, m2.n);
     const int nr = D.index_of[offset_index(D.v[n][0], D.v[n][1], -D.v[n][2])];
     double phr[kDirs];
-    phase_row(m1.g, D.u[nr], phr);
+    phase_row(m1.g, p.direction_weights, D.u[nr], phr);
     const double one = 1.0;
     flight(Wn, C, D.u[nr], (1.0 - tc) * lam1, h, m1, phr, &nr, &one, 1, p_keep * R);
     if (R < 1.0) {
@@ -284,7 +302,7 @@ bool two_step_column(const drts_problem &p, double nmin, int k1, int k2, int n, 
             ns = 2;
         }
         double ph2[kDirs];
-        phase_row(m2.g, u, ph2);
+        phase_row(m2.g, p.direction_weights, u, ph2);
         flight(Wn, C, u, (1.0 - tc) * lam2, h, m2, ph2, states, share, ns, p_keep * (1.0 - R));
     }
     return true;
@@ -407,11 +425,13 @@ std::string build_host_tables(const drts_problem &p, HostTables &t, double path_
         double *Wk = &t.W[size_t(k) * kDirs * kOffs * kDirs];
         for (int n = 0; n < kDirs; ++n) {
             // discrete Henyey-Greenstein kernel from S_n, normalised over m
+            // (each m weighted by its share of the sphere with DRTS_HG_QUADRATURE)
             double phase[kDirs], psum = 0.0;
             for (int m = 0; m < kDirs; ++m) {
                 double mu = D.u[n][0] * D.u[m][0] + D.u[n][1] * D.u[m][1] + D.u[n][2] * D.u[m][2];
                 double den = 1.0 + md.g * md.g - 2.0 * md.g * mu;
                 phase[m] = (1.0 - md.g * md.g) / (den * std::sqrt(den));
+                if (p.direction_weights == DRTS_HG_QUADRATURE) phase[m] *= direction_share(p.direction_weights, m);
                 psum += phase[m];
             }
             const double B[3] = {lam * D.u[n][0], lam * D.u[n][1], lam * D.u[n][2]};

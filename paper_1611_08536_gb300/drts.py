@@ -37,6 +37,10 @@ class Medium(ctypes.Structure):
                 ("g", ctypes.c_double), ("n", ctypes.c_double)]
 
 
+# weights of the outgoing directions in the discrete HG kernel (drts.h)
+HG_EQUAL, HG_QUADRATURE = 0, 1
+
+
 class ProblemC(ctypes.Structure):
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
@@ -53,6 +57,7 @@ class ProblemC(ctypes.Structure):
         ("max_steps", ctypes.c_int64),
         ("batched_kernel", ctypes.c_int32),
         ("interface", ctypes.c_int32),
+        ("direction_weights", ctypes.c_int32),
     ]
 
 
@@ -345,7 +350,7 @@ def problem_struct(prob, max_steps=0):
                  float(prob.n_outside), int(prob.boundary), int(prob.precision),
                  int(prob.n_rhs), int(prob.det_face), int(prob.det_nu),
                  int(prob.det_nv), int(max_steps), int(getattr(prob, "batched_kernel", 0)),
-                 int(getattr(prob, "interface", 0)))
+                 int(getattr(prob, "interface", 0)), int(getattr(prob, "direction_weights", 0)))
     s._keep = (media, mov)
     return s
 

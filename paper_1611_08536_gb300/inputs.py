@@ -47,6 +47,10 @@ def direction_vector(d: int):
     return (q % 3 - 1, (q // 3) % 3 - 1, q // 9 - 1)
 
 
+# weights of the outgoing directions in the discrete Henyey-Greenstein
+# kernel: every lattice direction alike, or each by its quadrature weight
+HG_EQUAL, HG_QUADRATURE = 0, 1
+
 # interface treatment (Section 4.2): per-contribution first-order folding, or
 # the two-step crossing of planar interfaces (layered media only)
 INTERFACE_FIRST_ORDER, INTERFACE_TWO_STEP = 0, 1
@@ -68,6 +72,7 @@ class Problem:
     name: str = ""
     batched_kernel: int = 0        # 0 CUDA cores, 1 tensor cores (n_rhs > 1)
     interface: int = 0             # INTERFACE_FIRST_ORDER or INTERFACE_TWO_STEP (layered media)
+    direction_weights: int = 0     # HG_EQUAL or HG_QUADRATURE (weights of the HG kernel's directions)
 
     @property
     def n_voxels(self) -> int:

@@ -70,6 +70,14 @@ def small_cases():
     out.append(("min_2x2x2_fp32", p))
     p, _ = I.three_layers(12, precision=I.FP16_ROWSCALE)
     out.append(("layers12_fp16", p))
+    # the HG kernel's directions weighted by their quadrature shares
+    p, _ = I.three_layers(10, precision=I.FP64)
+    p.direction_weights = I.HG_QUADRATURE
+    out.append(("layers10_quadrature_fp64", p))
+    p = I.Problem((5, 6, 7), 0.05, [(3.0, 0.2, 0.8, 1.33), (9.0, 0.02, 0.9, 1.5)], mov, 1.0,
+                  I.FRESNEL, I.FP32, 1, I.FACE_MX, 3, 2, "ragged_quadrature",
+                  direction_weights=I.HG_QUADRATURE)
+    out.append(("ragged_5x6x7_quadrature_fp32", p))
     return out
 
 
@@ -105,6 +113,17 @@ def _run_both(gpu, oracle_mod, prob, src, steps, x0=None):
         x = ctx.read_state()
         det, led = ctx.read_detectors()
     return (x, det, led), (xo, deto, ledo)
+
+
+def test_quadrature_weighted_kernel_fp64_steps(gpu, oracle_mod):
+    """A run with the quadrature-weighted HG kernel follows the oracle's
+    (FP64, three layers, Fresnel edges, 60 steps)."""
+    prob, src = I.three_layers(10, precision=I.FP64)
+    prob.direction_weights = I.HG_QUADRATURE
+    (x, det, led), (xo, deto, ledo) = _run_both(gpu, oracle_mod, prob, src, 60)
+    assert rel_l1(x, xo) < 1e-12
+    assert rel_l1(det, deto) < 1e-12
+    assert np.allclose(led, ledo, rtol=1e-11)
 
 
 def test_fresnel_cube16_fp64_300_steps(gpu, oracle_mod):

@@ -1,7 +1,8 @@
 """The product's host-built tables (drts_host_tables: no device needed)
 against the FP64 oracle on CPU: the stencil W_k[n][o][m] of Eq. 18-21 for
 every medium, the exit fractions by face mask against the oracle's per-state
-column functionals (Section 4.2, Eq. 27), and the FP16 row scales."""
+column functionals (Section 4.2, Eq. 27), and the FP16 row scales; with the
+kernel's directions weighted alike and by their quadrature shares."""
 import numpy as np
 import pytest
 
@@ -18,8 +19,15 @@ def _problems():
     mov[:, 3:, :] = 1
     p5 = I.Problem((5, 6, 7), 0.05, [(3.0, 0.2, 0.8, 1.33), (9.0, 0.02, 0.9, 1.5)], mov, 1.0,
                    I.MIRROR, I.FP64, 1, I.FACE_MX, 3, 2, "ragged_mirror")
+    # the kernel weighting each direction by its quadrature share (R7 variant)
+    q2, _ = I.three_layers(12, precision=I.FP32)
+    q2.direction_weights = I.HG_QUADRATURE
+    q5 = I.Problem((5, 6, 7), 0.05, [(3.0, 0.2, 0.8, 1.33), (9.0, 0.02, 0.9, 1.5)], mov, 1.0,
+                   I.FRESNEL, I.FP16_ROWSCALE, 1, I.FACE_MX, 3, 2, "ragged_quadrature",
+                   direction_weights=I.HG_QUADRATURE)
     return [("fresnel8", p1), ("layers12", p2), ("inclusions10_open_fp16", p3),
-            ("ellipsoids13", p4), ("ragged_mirror", p5)]
+            ("ellipsoids13", p4), ("ragged_mirror", p5), ("layers12_quadrature", q2),
+            ("ragged_quadrature_fp16", q5)]
 
 
 @pytest.fixture(scope="module")
@@ -83,3 +91,30 @@ def test_bad_medium_is_rejected(lib):
         drts.host_tables(prob, 1)
     assert e.value.status == drts.EINVAL
     assert "medium out of range" in str(e.value)
+
+
+def test_quadrature_weighting_changes_the_kernel(lib):
+    """The option is not inert: with g = 0 the equal kernel sends 1/26 of the
+    scattered mass to every direction, the quadrature kernel 1/21, 4/105 and
+    9/280 to axis, face-diagonal and body-diagonal directions."""
+    prob = I.Problem((4, 4, 4), 0.1, [(5.0, 0.0, 0.0, 1.0)], np.zeros((4, 4, 4), np.uint8), 1.0,
+                     I.MIRROR, I.FP64, 1, I.FACE_PZ, 2, 2, "g0")
+    We, _, _, _ = drts.host_tables(prob, 0)
+    prob.direction_weights = I.HG_QUADRATURE
+    Wq, _, _, _ = drts.host_tables(prob, 0)
+    unsc = np.exp(-0.5)
+    n = I.direction_index(0, 0, 1)
+    for W, expect in ((We, lambda m: 1.0 / 26.0),
+                      (Wq, lambda m: {1: 1 / 21, 2: 4 / 105, 3: 9 / 280}[int(np.count_nonzero(I.direction_vector(m)))])):
+        share = W[n].sum(axis=0)
+        share[n] -= unsc
+        for m in range(26):
+            assert share[m] == pytest.approx(expect(m) * (1.0 - unsc), rel=1e-13)
+
+
+def test_bad_direction_weights_rejected(lib):
+    prob, _ = I.fresnel_cube(4, precision=I.FP32)
+    prob.direction_weights = 2
+    with pytest.raises(drts.DrtsError) as e:
+        drts.host_tables(prob, 0)
+    assert e.value.status == drts.EINVAL

@@ -28,7 +28,10 @@ def _problems():
                  boundary=I.OPEN)
     p4 = _layers([0, 0, 1, 2, 2], [(8.0, 0.01, 0.8, 1.4), (12.0, 0.2, 0.7, 1.5), (5.0, 0.05, 0.95, 1.3)],
                  "thin_middle", boundary=I.MIRROR)
-    return [("layers12", p1), ("contrast", p2), ("ballistic_isotropic", p3), ("thin_middle", p4)]
+    p5 = _layers([0, 0, 0, 1, 1, 1], [(10.0, 0.05, 0.9, 1.0), (10.0, 0.05, 0.9, 1.5)], "contrast_quadrature")
+    p5.direction_weights = I.HG_QUADRATURE      # the refracted piece's kernel weighted too
+    return [("layers12", p1), ("contrast", p2), ("ballistic_isotropic", p3), ("thin_middle", p4),
+            ("contrast_quadrature", p5)]
 
 
 def _pairs(prob):

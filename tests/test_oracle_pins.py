@@ -142,10 +142,12 @@ def test_hg_forward_bias_monotone(oracle_mod):
             assert s[a + 1] > s[a]
 
 
-def _scattered_shares(oracle_mod, g, mu_s=5.0, h=0.1):
+def _scattered_shares(oracle_mod, g, mu_s=5.0, h=0.1, weights=I.HG_EQUAL):
     """share[n][m]: the scattered part of W[n] summed over targets, per
     outgoing direction m (no absorption), normalised to sum 1 per n."""
-    W = oracle_mod.raw_stencil(_prob(4, [(mu_s, 0.0, g, 1.0)], h=h), 0)
+    prob = _prob(4, [(mu_s, 0.0, g, 1.0)], h=h)
+    prob.direction_weights = weights
+    W = oracle_mod.raw_stencil(prob, 0)
     out = np.zeros((26, 26))
     for n in range(26):
         sh = W[n].sum(axis=0)
@@ -185,6 +187,47 @@ def test_hg_mean_cosine_slope_is_one(oracle_mod):
         un = _unit(n)
         mean_cos = sum(share[n, m] * float(un @ _unit(m)) for m in range(26))
         assert mean_cos / g == pytest.approx(1.0, abs=1e-4), (n, mean_cos / g)
+
+
+def test_quadrature_shares_integrate_degree_seven(oracle_mod):
+    """With the quadrature weighting (reading R7, variant) and g = 0 the
+    kernel is the weights themselves.  As the weights of a rule on the
+    sphere they must reproduce the sphere averages of monomials (the
+    average of x^a y^b z^c over the unit sphere, a, b, c even, is
+    (a-1)!!(b-1)!!(c-1)!! / (a+b+c+1)!!) up to degree 7 -- including x^4,
+    x^6 and x^4 y^2, which the three equations fixing the weights do not
+    use -- and fail at degree 8, the first the 26 points cannot carry."""
+    w = _scattered_shares(oracle_mod, 0.0, weights=I.HG_QUADRATURE)
+    U = np.array([_unit(m) for m in range(26)])
+
+    def dfact(k):
+        return 1 if k <= 0 else k * dfact(k - 2)
+
+    def sphere_avg(a, b, c):
+        return dfact(a - 1) * dfact(b - 1) * dfact(c - 1) / dfact(a + b + c + 1)
+
+    for n in range(26):
+        assert np.allclose(w[n], w[0], rtol=0, atol=1e-15)           # the same for every n
+    for a, b, c in [(0, 0, 0), (2, 0, 0), (4, 0, 0), (2, 2, 0), (6, 0, 0), (4, 2, 0), (2, 2, 2),
+                    (0, 4, 2), (0, 0, 6), (1, 0, 0), (3, 2, 1), (1, 1, 5)]:
+        got = float(np.sum(w[0] * U[:, 0] ** a * U[:, 1] ** b * U[:, 2] ** c))
+        expect = sphere_avg(a, b, c) if a % 2 == 0 and b % 2 == 0 and c % 2 == 0 else 0.0
+        assert got == pytest.approx(expect, abs=1e-15), (a, b, c)
+    deg8 = float(np.sum(w[0] * U[:, 0] ** 8))
+    assert abs(deg8 - sphere_avg(8, 0, 0)) > 1e-3
+
+
+def test_quadrature_kernel_mean_cosine(oracle_mod):
+    """HG's mean cosine is g.  The quadrature-weighted kernel integrates
+    the Legendre terms of degree <= 6 of p and of p times cos exactly, so its
+    discrete mean cosine misses g only by the terms of degree 7 and above
+    (at g = 0.3: below 1e-3 for every incoming direction); the
+    equal-weight kernel misses it already at degree 3 (4.6e-3 at g = 0.3)."""
+    g = 0.3
+    for weights, lo, hi in ((I.HG_QUADRATURE, 0.0, 1e-3), (I.HG_EQUAL, 2e-3, 1e-2)):
+        share = _scattered_shares(oracle_mod, g, weights=weights)
+        dev = [abs(sum(share[n, m] * float(_unit(n) @ _unit(m)) for m in range(26)) - g) for n in range(26)]
+        assert lo <= max(dev) < hi, (weights, max(dev))
 
 
 def test_hg_forward_limit(oracle_mod):

@@ -83,6 +83,18 @@ def test_homogeneous_cube_has_the_48_symmetries(oracle_mod, boundary):
         _check_invariant(A, _state_permutation(prob.shape, P))
 
 
+def test_quadrature_kernel_keeps_the_48_symmetries(oracle_mod):
+    """The quadrature shares are equal within each class of directions the
+    cube's symmetries permute, so the weighted kernel keeps all 48."""
+    n = 4
+    prob = I.Problem((n, n, n), 0.1, [(10.0, 0.05, 0.8, 1.4)], np.zeros((n, n, n), np.uint8), 1.0,
+                     I.FRESNEL, I.FP64, 1, I.FACE_PZ, 1, 1, "cube4_quadrature",
+                     direction_weights=I.HG_QUADRATURE)
+    A = _matrix(oracle_mod, prob)
+    for P in _signed_permutations():
+        _check_invariant(A, _state_permutation(prob.shape, P))
+
+
 @pytest.mark.parametrize("boundary", [I.FRESNEL, I.MIRROR])
 def test_layered_medium_has_the_square_symmetries(oracle_mod, boundary):
     nxy, nz = 4, 7
