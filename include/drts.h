@@ -476,6 +476,14 @@ drts_status drts_autotune(drts_ctx *ctx, int32_t trial_steps, drts_tune_result *
                                        arrives at the first grid barrier */
 drts_status drts_set_fault(drts_ctx *ctx, int32_t kind, int64_t arg);
 
+/* Host-side allocator fault for tests (process-wide, all threads): after
+ * `n_ok` further device allocations of context buffers succeed, the next one
+ * fails as if the device were out of memory, without calling the allocator;
+ * later ones succeed again.  The failing call returns DRTS_ENOMEM and frees
+ * what it allocated (drts_assemble frees the partial context and sets *out
+ * to NULL).  A negative n_ok disarms the fault.  Always DRTS_OK. */
+drts_status drts_set_alloc_fault(int64_t n_ok);
+
 /*
  * Sum of x(t) of right-hand side rhs (the "sum of x" term of the ledger that
  * drts_read_detectors returns), written to out_device: one FP64 value in
@@ -547,6 +555,7 @@ typedef struct drts_server_config {
 #define DRTS_REQ_RUNNING 1
 #define DRTS_REQ_DONE 2
 #define DRTS_REQ_FAILED 3
+#define DRTS_REQ_CANCELLED 4
 
 typedef struct drts_request_info {
     int32_t state;                   /* DRTS_REQ_* */
@@ -569,6 +578,7 @@ typedef struct drts_server_stats {
      * ticks, and the part of it in the ticks that instantiated */
     int64_t graph_updates, graph_instantiations;
     double host_graph_s, host_instantiate_s;
+    int64_t cancelled;               /* requests withdrawn by drts_server_cancel */
 } drts_server_stats;
 
 /* Create a server on the current device (cfg is copied; *out owns its
@@ -608,8 +618,18 @@ drts_status drts_server_result(drts_server *srv, int64_t request_id, int32_t rhs
  * unknown id, rhs or a NULL buffer. */
 drts_status drts_server_result_state(drts_server *srv, int64_t request_id, int32_t rhs,
                                      double *state_out);
-/* Forget a finished or failed request and its results (DRTS_ESTATE while it
- * is queued or running, DRTS_EINVAL for an unknown id). */
+/* Withdraw a queued or running request.  A queued one leaves the queue; a
+ * running one is stopped between ticks: the call waits for the server's
+ * streams (nothing of the simulation is then in flight), frees its device
+ * memory and returns its footprint to the budget.  The request ends in
+ * DRTS_REQ_CANCELLED with no results (drts_server_result reports
+ * DRTS_ESTATE) until it is released.  DRTS_ESTATE for a request that has
+ * already finished, failed or been cancelled, DRTS_EINVAL for an unknown id,
+ * DRTS_ECUDA if waiting for the device fails. */
+drts_status drts_server_cancel(drts_server *srv, int64_t request_id);
+/* Forget a finished, failed or cancelled request and its results
+ * (DRTS_ESTATE while it is queued or running, DRTS_EINVAL for an unknown
+ * id). */
 drts_status drts_server_release(drts_server *srv, int64_t request_id);
 drts_status drts_server_get_stats(const drts_server *srv, drts_server_stats *out);
 /* Text of the server's last error ("" for NULL); valid until the next call. */

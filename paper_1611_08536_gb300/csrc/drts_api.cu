@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -128,10 +129,26 @@ drts_status cuda_fail(drts_ctx *c, cudaError_t e, const char *where)
     return fail(c, e == cudaErrorMemoryAllocation ? DRTS_ENOMEM : DRTS_ECUDA, m);
 }
 
+// Allocator fault for tests (drts_set_alloc_fault): successful context
+// allocations left before one fails; negative = disarmed.
+std::atomic<int64_t> g_alloc_fault{-1};
+
+bool alloc_fault_fires()
+{
+    int64_t n = g_alloc_fault.load();
+    while (n >= 0) {
+        // n > 0: one more allocation may succeed; n == 0: this one fails and
+        // the fault disarms itself
+        if (g_alloc_fault.compare_exchange_weak(n, n > 0 ? n - 1 : -1)) return n == 0;
+    }
+    return false;
+}
+
 template <class T>
 cudaError_t dalloc(drts_ctx *c, T **p, size_t bytes)
 {
     void *q = nullptr;
+    if (alloc_fault_fires()) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
     if (e == cudaSuccess) {
         c->allocs.push_back(q);
@@ -1327,6 +1344,12 @@ try {
     }
 } catch (...) {
     return caught(c, "drts_set_fault");
+}
+
+drts_status drts_set_alloc_fault(int64_t n_ok)
+{
+    g_alloc_fault.store(n_ok < 0 ? -1 : n_ok);
+    return DRTS_OK;
 }
 
 drts_status drts_state_sum_noalloc(drts_ctx *c, int32_t rhs, double *out_device)

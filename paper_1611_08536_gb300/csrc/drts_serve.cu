@@ -430,6 +430,36 @@ try {
     return scaught(s, "drts_server_result_state");
 }
 
+drts_status drts_server_cancel(drts_server *s, int64_t id)
+try {
+    if (!s) return DRTS_EINVAL;
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end()) return sfail(s, DRTS_EINVAL, "unknown request");
+    Request &r = *it->second;
+    if (r.state == DRTS_REQ_QUEUED) {
+        s->queue.erase(std::find(s->queue.begin(), s->queue.end(), id));
+    } else if (r.state == DRTS_REQ_RUNNING) {
+        // between ticks; the tick graph joins every side stream back into
+        // the main stream, so these two waits leave nothing in flight
+        cudaError_t e = cudaStreamSynchronize(s->main);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->admit);
+        if (e != cudaSuccess) return sfail(s, DRTS_ECUDA, std::string("cancel: ") + cudaGetErrorString(e));
+        drts_destroy(r.ctx);
+        r.ctx = nullptr;
+        s->used -= r.footprint;
+        s->resident.erase(std::find(s->resident.begin(), s->resident.end(), id));
+    } else {
+        return sfail(s, DRTS_ESTATE, "request already finished, failed or cancelled");
+    }
+    r.state = DRTS_REQ_CANCELLED;
+    r.error = "request cancelled";
+    r.t_done = Clock::now();
+    s->stats.cancelled++;
+    return DRTS_OK;
+} catch (...) {
+    return scaught(s, "drts_server_cancel");
+}
+
 drts_status drts_server_release(drts_server *s, int64_t id)
 try {
     if (!s) return DRTS_EINVAL;

@@ -97,7 +97,8 @@ class ServerStats(ctypes.Structure):
                 ("resident", ctypes.c_int32), ("queued", ctypes.c_int32),
                 ("used_bytes", ctypes.c_int64), ("budget_bytes", ctypes.c_int64),
                 ("graph_updates", ctypes.c_int64), ("graph_instantiations", ctypes.c_int64),
-                ("host_graph_s", ctypes.c_double), ("host_instantiate_s", ctypes.c_double)]
+                ("host_graph_s", ctypes.c_double), ("host_instantiate_s", ctypes.c_double),
+                ("cancelled", ctypes.c_int64)]
 
     def as_dict(self):
         return {f[0]: getattr(self, f[0]) for f in self._fields_}
@@ -118,10 +119,10 @@ class Info(ctypes.Structure):
 SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_detectors",
            "drts_read_state", "drts_write_state", "drts_run_host", "drts_export_rows",
            "drts_column_info", "drts_get_info", "drts_host_tables", "drts_two_step_tables", "drts_set_launch", "drts_destroy",
-           "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_autotune",
+           "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_set_alloc_fault", "drts_autotune",
            "drts_set_step_mode", "drts_server_create", "drts_server_submit", "drts_server_tick",
            "drts_server_poll", "drts_server_result", "drts_server_result_state",
-           "drts_server_release",
+           "drts_server_cancel", "drts_server_release",
            "drts_server_get_stats", "drts_server_last_error", "drts_server_destroy",
            "drts_checkpoint_size", "drts_checkpoint_save", "drts_checkpoint_load",
            "drts_set_point_detectors", "drts_read_point_detectors", "drts_sensor_response",
@@ -184,6 +185,8 @@ def load(path: str = LIB_PATH):
     lib.drts_server_poll.argtypes = [vp, i64, ctypes.POINTER(RequestInfo)]
     lib.drts_server_result.argtypes = [vp, i64, i32, vp, vp]
     lib.drts_server_result_state.argtypes = [vp, i64, i32, vp]
+    lib.drts_server_cancel.argtypes = [vp, i64]
+    lib.drts_set_alloc_fault.argtypes = [i64]
     lib.drts_server_release.argtypes = [vp, i64]
     lib.drts_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     lib.drts_server_last_error.argtypes = [vp]
@@ -202,6 +205,12 @@ def load(path: str = LIB_PATH):
 
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def set_alloc_fault(n_ok):
+    """After n_ok further device allocations of context buffers, the next one
+    fails as out of memory (drts_set_alloc_fault); negative disarms."""
+    load().drts_set_alloc_fault(int(n_ok))
 
 
 def host_tables(prob, medium):
@@ -559,7 +568,7 @@ class Context:
                                               int(rhs_tile), int(variant)))
 
 
-REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 SENSOR_FACE, SENSOR_POINT = 0, 1
 SERVE_FIFO, SERVE_SHORTEST_FIRST = 0, 1
 
@@ -624,6 +633,10 @@ class Server:
         out = np.empty(int(n_states), np.float64)
         self._check(self._lib.drts_server_result_state(self._h, int(rid), int(rhs), _ptr(out)))
         return out
+
+    def cancel(self, rid):
+        """Withdraw a queued or running request (drts_server_cancel)."""
+        self._check(self._lib.drts_server_cancel(self._h, int(rid)))
 
     def release(self, rid):
         self._check(self._lib.drts_server_release(self._h, int(rid)))

@@ -205,3 +205,13 @@ int main(void) {
     W, _, _, _ = drts.host_tables(prob, 0)
     assert int(st) == 0 and float(val) == W[13, 14, 13]
     assert out[1].startswith(f"{drts.EINVAL} ") and "medium out of range" in out[1]
+
+
+def test_alloc_fault_hook_needs_no_device():
+    """The allocator fault is host state: arming and disarming it touches no
+    device and always succeeds."""
+    from paper_1611_08536_gb300 import build, drts
+    build.build()
+    lib = drts.load()
+    assert lib.drts_set_alloc_fault(3) == drts.OK
+    assert lib.drts_set_alloc_fault(-5) == drts.OK

@@ -202,3 +202,51 @@ def test_server_result_state_needs_keep_state(gpu):
         with pytest.raises(gpu.DrtsError) as e:
             srv.result_state(rid, 0, n_states=req.problem.n_states)
         assert e.value.status == gpu.ESTATE
+
+
+def test_server_cancel_queued_and_running(gpu):
+    """A queued request cancelled leaves the queue; a running one is stopped
+    between ticks and its footprint returns to the budget; the others finish
+    with the results they have alone.  Neither cancelled request has
+    results, a finished one cannot be cancelled, and cancelled ones can be
+    released."""
+    reqs = small_stream(3, seed=5)
+    for r in reqs:
+        r.n_steps = 60
+    with gpu.Server(max_resident=2, steps_per_tick=5, n_streams=2) as srv:
+        ids = [srv.submit(r.problem, r.sources, r.n_steps) for r in reqs]
+        srv.tick()                                   # admits the first two
+        srv.tick()                                   # they step
+        assert srv.poll(ids[0]).state == gpu.REQ_RUNNING
+        assert srv.poll(ids[1]).state == gpu.REQ_RUNNING
+        assert srv.poll(ids[2]).state == gpu.REQ_QUEUED
+        used = srv.stats()["used_bytes"]
+        srv.cancel(ids[2])                           # queued
+        assert srv.poll(ids[2]).state == gpu.REQ_CANCELLED
+        assert srv.stats()["queued"] == 0
+        srv.cancel(ids[0])                           # running
+        assert srv.poll(ids[0]).state == gpu.REQ_CANCELLED
+        st = srv.stats()
+        assert st["resident"] == 1 and st["cancelled"] == 2
+        assert st["used_bytes"] == used - srv.poll(ids[0]).footprint_bytes
+        for _ in range(100):
+            srv.tick()
+            if srv.poll(ids[1]).state == gpu.REQ_DONE:
+                break
+        assert srv.poll(ids[1]).state == gpu.REQ_DONE
+        alone = run_alone(gpu, reqs[1])
+        for r in range(len(reqs[1].sources)):
+            det, led = srv.result(ids[1], r)
+            assert rel_l1(det, alone[r][0]) < 1e-12
+            assert np.allclose(led, alone[r][1], rtol=1e-12)
+        for i in (ids[0], ids[2]):
+            with pytest.raises(gpu.DrtsError) as e:
+                srv.result(i)
+            assert e.value.status == gpu.ESTATE
+        with pytest.raises(gpu.DrtsError) as e:
+            srv.cancel(ids[1])                       # already finished
+        assert e.value.status == gpu.ESTATE
+        srv.release(ids[0])
+        srv.release(ids[2])
+        st = srv.stats()
+        assert st["completed"] == 1 and st["failed"] == 0 and st["used_bytes"] == 0

@@ -80,3 +80,42 @@ def test_batched_64_rhs(gpu, oracle_mod):
     for r, x in xs.items():
         xo, _, _ = oracle_mod.run(prob, csr, steps, srcs[r].as_tuple())
         assert np.abs(x - xo).sum() / np.abs(xo).sum() < 1e-5, r
+
+
+@pytest.mark.parametrize("precision", [I.FP32, I.FP16_ROWSCALE])
+def test_assembly_survives_every_failed_allocation(gpu, oracle_mod, precision):
+    """Host-side allocator fault: the k-th device allocation of a context
+    fails, for every k the assembly reaches.  Each failure returns
+    DRTS_ENOMEM with nothing left allocated (repeated failures do not grow the
+    device memory in use), and the first k past the last allocation
+    assembles a context whose step matches the oracle."""
+    import torch
+    prob, src = I.three_layers(8, precision=precision)
+    free = []
+    try:
+        for k in range(200):
+            gpu.set_alloc_fault(k)
+            try:
+                ctx = gpu.Context(prob, max_steps=4)
+            except gpu.DrtsError as e:
+                assert e.status == gpu.ENOMEM, (k, e)
+                torch.cuda.synchronize()
+                free.append(torch.cuda.mem_get_info()[0])
+                continue
+            break
+        else:
+            pytest.fail("the assembly never completed")
+    finally:
+        gpu.set_alloc_fault(-1)
+    assert len(free) >= 5
+    # device memory free after the last failure vs after the fourth
+    assert free[-1] >= free[3] - (8 << 20), (free[3], free[-1])
+    with ctx:
+        rng = np.random.default_rng(2)
+        x0 = rng.random(prob.n_states)
+        ctx.write_state(x0)
+        ctx.step_n(1)
+        x1 = ctx.read_state()
+    y = oracle_mod.spmv(oracle_mod.assemble(prob), x0)
+    tol = 1e-6 if precision == I.FP32 else 2e-3
+    assert np.abs(x1 - y).sum() / np.abs(y).sum() < tol
