@@ -36,6 +36,12 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
 
 def workload(name, precision, rhs=1):
     from paper_1611_08536_gb300 import inputs as I
+    if name.startswith("config:"):
+        # a JSON problem file of the package (configs/<name>.json) or a path
+        c = I.load_config(name[len("config:"):], precision)
+        if c.problem is None:
+            raise SystemExit("a served-stream config is a --serve workload")
+        return (c.problem, c.sources) if c.problem.n_rhs > 1 else (c.problem, c.sources[0])
     prec = {"fp32": I.FP32, "fp64": I.FP64, "fp16": I.FP16_ROWSCALE}[precision]
     if name.startswith("ellipsoids_"):
         n = int(name.split("_")[-1])
@@ -930,7 +936,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="drts", choices=["drts", "reference"])
-    ap.add_argument("--workload", default="three_layers_128")
+    ap.add_argument("--workload", default="three_layers_128",
+                    help="<generator>_<size> or config:<name of a JSON problem file>")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16"])
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--blocks-per-sm", type=int, default=0)

@@ -20,11 +20,16 @@ Workloads (all synthetic; the paper publishes no dataset):
                        inclusions of differing optical properties.
   * ``served_request`` one request of a served stream (side, medium, steps,
                        sources drawn from a seeded generator).
+  * ``load_config``    one of the JSON problem files in ``configs/`` (the five
+                       benchmark configurations: generator, arguments, seeds,
+                       precision, steps).
 """
 from __future__ import annotations
 
 import dataclasses
+import json
 import math
+import os
 
 import numpy as np
 
@@ -298,3 +303,51 @@ def served_stream(n_requests: int = 1000, rate_per_s: float = 50.0, seed: int = 
         r.arrival_s = float(arrivals[i])
         out.append(r)
     return out
+
+
+# ---------------------------------------------------------------------------
+# JSON problem files (paper_1611_08536_gb300/configs/*.json): a named
+# workload = one of the seeded generators above, its arguments, the
+# precision and the step count.  The generators are the only place a
+# workload is built, so a config file and the generator call give the same
+# problem.
+
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs")
+_PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": FP16_ROWSCALE}
+
+
+@dataclasses.dataclass
+class Config:
+    name: str
+    spec: dict                     # the file's content
+    problem: Problem = None        # None for a served stream
+    sources: list = None           # Source per right-hand side
+    requests: list = None          # served stream: Request list
+    steps: int = 0
+
+
+def config_names():
+    """Names of the JSON problem files shipped with the package."""
+    return sorted(f[:-5] for f in os.listdir(CONFIG_DIR) if f.endswith(".json"))
+
+
+def load_config(name_or_path: str, precision: str = None) -> Config:
+    """Build the workload a JSON problem file names (a path, or the name of a
+    file in ``CONFIG_DIR``).  ``precision`` overrides the file's ("fp64",
+    "fp32" or "fp16")."""
+    path = name_or_path if name_or_path.endswith(".json") else os.path.join(CONFIG_DIR, name_or_path + ".json")
+    with open(path) as f:
+        spec = json.load(f)
+    prec_name = precision or spec["precision"]
+    if prec_name not in _PRECISIONS:
+        raise ValueError(f"unknown precision {prec_name!r}")
+    gen, args = spec["generator"], dict(spec.get("args", {}))
+    if gen == "served_stream":
+        return Config(spec["name"], spec, requests=served_stream(**args), steps=0)
+    makers = {"fresnel_cube": fresnel_cube, "three_layers": three_layers,
+              "inclusions": inclusions, "ellipsoids": ellipsoids}
+    if gen not in makers:
+        raise ValueError(f"unknown generator {gen!r}")
+    prob, src = makers[gen](precision=_PRECISIONS[prec_name], **args)
+    srcs = src if isinstance(src, list) else [src]
+    return Config(spec["name"], spec, problem=prob, sources=srcs, steps=int(spec.get("steps", 0)))

@@ -157,3 +157,14 @@ def test_batched_roofline_counts_the_methods_work():
     r1 = bench.batched_roofline(2.0 * info.nnz, bench.batched_bytes(info, "fp32", 1), 5.0, peak,
                                 6787.6, "cuda")
     assert r1["bound"] == "hbm" and r1["unit"] == "GB/s"
+
+
+def test_config_workloads():
+    """``--workload config:<name>`` builds the JSON problem file's workload,
+    the same problem as the generator name it stands for."""
+    import numpy as np
+    p, s = bench.workload("config:plain_fp64_cube16", "fp64")
+    q, t = bench.workload("fresnel_cube_16", "fp64")
+    assert p.shape == q.shape and p.media == q.media and np.array_equal(s.state, t.state)
+    pb, srcs = bench.workload("config:batched_inclusions96x64", "fp32")
+    assert pb.n_rhs == 64 and len(srcs) == 64

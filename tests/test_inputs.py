@@ -2,6 +2,7 @@
 their stated recipes: sizes, media, sources, pulse profiles, arrival process,
 and they are reproducible from their seeds.  CPU only."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -98,3 +99,33 @@ def test_workloads_are_reproducible_from_their_seeds():
     r2 = I.served_request(4, 7)
     assert r1.problem.media == r2.problem.media and r1.n_steps == r2.n_steps
     assert np.array_equal(r1.problem.medium_of_voxel, r2.problem.medium_of_voxel)
+
+
+def test_config_files_build_their_workloads():
+    """Each JSON problem file names a generator, its seeds, a precision and a
+    step count; loading it gives the same problem as calling the generator
+    (sizes, media map, sources), at the configurations' sizes."""
+    names = I.config_names()
+    assert names == ["batched_inclusions96x64", "large_ellipsoids192", "plain_fp32_three_layers128",
+                     "plain_fp64_cube16", "served_stream1000"]
+    c = I.load_config("plain_fp64_cube16")
+    p, s = I.fresnel_cube(16, precision=I.FP64)
+    assert c.problem.n_states == 106496 and c.steps == 300 and c.problem.precision == I.FP64
+    assert np.array_equal(c.sources[0].state, s.state)
+    c = I.load_config("batched_inclusions96x64", precision="fp16")
+    p, srcs = I.inclusions(96, n_rhs=64, seed=3, precision=I.FP16_ROWSCALE)
+    assert c.problem.shape == (96, 96, 96) and c.problem.n_rhs == 64 and len(c.sources) == 64
+    assert c.problem.precision == I.FP16_ROWSCALE and c.steps == 1500
+    assert np.array_equal(c.problem.medium_of_voxel, p.medium_of_voxel)
+    assert all(np.array_equal(a.state, b.state) for a, b in zip(c.sources, srcs))
+    c = I.load_config("plain_fp32_three_layers128")
+    assert c.problem.n_states == 26 * 128 ** 3 and c.steps == 2000
+    assert (c.problem.det_nu, c.problem.det_nv) == (16, 16)
+    c = I.load_config("served_stream1000")
+    assert c.problem is None and len(c.requests) == 1000
+    assert {r.problem.shape[0] for r in c.requests} == {32, 48, 64, 80, 96}
+    assert all(500 <= r.n_steps <= 3000 and 1 <= len(r.sources) <= 16 for r in c.requests)
+    spec = I.load_config(os.path.join(I.CONFIG_DIR, "large_ellipsoids192.json")).spec
+    assert spec["steps"] == 5000 and spec["step_mode"] == "persistent" and spec["args"]["n_ell"] == 12
+    with pytest.raises(ValueError):
+        I.load_config("plain_fp64_cube16", precision="fp8")
