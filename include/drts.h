@@ -476,6 +476,21 @@ drts_status drts_autotune(drts_ctx *ctx, int32_t trial_steps, drts_tune_result *
                                        arrives at the first grid barrier */
 drts_status drts_set_fault(drts_ctx *ctx, int32_t kind, int64_t arg);
 
+/* Device allocator for the buffers of contexts made by drts_assemble
+ * (process-wide, all threads; read at each allocation).  alloc_fn(bytes,
+ * cuda_stream, user) returns device memory of at least `bytes` bytes aligned
+ * to 256 bytes, or NULL when it has none (the call that needed it then
+ * fails with DRTS_ENOMEM); free_fn(ptr, cuda_stream, user) takes it back
+ * after the context's stream has drained.  A buffer is freed with the
+ * functions that allocated it, so the allocator may change while contexts
+ * live.  Both NULL restores cudaMalloc / cudaFree; one NULL is DRTS_EINVAL.
+ * This lets a framework's caching allocator (PyTorch's) own the library's
+ * device memory.  Temporary buffers of single calls and the close-packed
+ * contexts keep the stream-ordered CUDA allocator. */
+typedef void *(*drts_alloc_fn)(size_t bytes, void *cuda_stream, void *user);
+typedef void (*drts_free_fn)(void *ptr, void *cuda_stream, void *user);
+drts_status drts_set_allocator(drts_alloc_fn alloc_fn, drts_free_fn free_fn, void *user);
+
 /* Host-side allocator fault for tests (process-wide, all threads): after
  * `n_ok` further device allocations of context buffers succeed, the next one
  * fails as if the device were out of memory, without calling the allocator;

@@ -21,6 +21,21 @@
 
 using namespace drts;
 
+namespace {
+// The device allocator of context buffers (drts_set_allocator); null
+// functions mean cudaMalloc / cudaFree.
+struct Allocator {
+    drts_alloc_fn alloc = nullptr;
+    drts_free_fn free = nullptr;
+    void *user = nullptr;
+};
+// a context buffer and the allocator that owns it
+struct DevBuffer {
+    void *p = nullptr;
+    Allocator a;
+};
+}  // namespace
+
 struct drts_ctx {
     drts_problem prob{};
     cudaStream_t stream = nullptr;
@@ -36,7 +51,7 @@ struct drts_ctx {
     DevTables T{};
     SlicedMatrix A{};
     // device buffers
-    std::vector<void *> allocs;
+    std::vector<DevBuffer> allocs;
     void *x = nullptr, *y = nullptr;     // state ping-pong
     int64_t x_elems = 0;
     double *ledger = nullptr;            // [R][4]
@@ -144,14 +159,40 @@ bool alloc_fault_fires()
     return false;
 }
 
+std::mutex g_allocator_mu;
+Allocator g_allocator;
+
+Allocator current_allocator()
+{
+    std::lock_guard<std::mutex> lock(g_allocator_mu);
+    return g_allocator;
+}
+
+void free_buffer(const DevBuffer &b, cudaStream_t s)
+{
+    if (b.a.free) b.a.free(b.p, s, b.a.user);
+    else cudaFree(b.p);
+}
+
 template <class T>
 cudaError_t dalloc(drts_ctx *c, T **p, size_t bytes)
 {
     void *q = nullptr;
     if (alloc_fault_fires()) return cudaErrorMemoryAllocation;
-    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    const Allocator a = current_allocator();
+    cudaError_t e = cudaSuccess;
+    if (a.alloc) {
+        q = a.alloc(bytes ? bytes : 16, c->stream, a.user);
+        if (!q) return cudaErrorMemoryAllocation;
+        if (reinterpret_cast<uintptr_t>(q) % 256 != 0) {     // bulk copies and vector loads need it
+            a.free(q, c->stream, a.user);
+            return cudaErrorMisalignedAddress;
+        }
+    } else {
+        e = cudaMalloc(&q, bytes ? bytes : 16);
+    }
     if (e == cudaSuccess) {
-        c->allocs.push_back(q);
+        c->allocs.push_back(DevBuffer{q, a});
         *p = static_cast<T *>(q);
     }
     return e;
@@ -164,10 +205,12 @@ void drelease(drts_ctx *c, T *&p)
 {
     if (!p) return;
     cudaStreamSynchronize(c->stream);
-    auto it = std::find(c->allocs.begin(), c->allocs.end(), static_cast<void *>(p));
+    auto it = std::find_if(c->allocs.begin(), c->allocs.end(),
+                           [&](const DevBuffer &b) { return b.p == static_cast<void *>(p); });
     if (it != c->allocs.end()) {
+        const DevBuffer b = *it;
         c->allocs.erase(it);
-        cudaFree(p);
+        free_buffer(b, c->stream);
     }
     p = nullptr;
 }
@@ -1346,6 +1389,14 @@ try {
     return caught(c, "drts_set_fault");
 }
 
+drts_status drts_set_allocator(drts_alloc_fn alloc_fn, drts_free_fn free_fn, void *user)
+{
+    if (!alloc_fn != !free_fn) return DRTS_EINVAL;
+    std::lock_guard<std::mutex> lock(g_allocator_mu);
+    g_allocator = Allocator{alloc_fn, free_fn, alloc_fn ? user : nullptr};
+    return DRTS_OK;
+}
+
 drts_status drts_set_alloc_fault(int64_t n_ok)
 {
     g_alloc_fault.store(n_ok < 0 ? -1 : n_ok);
@@ -1668,7 +1719,7 @@ void drts_destroy(drts_ctx *c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    for (void *p : c->allocs) cudaFree(p);
+    for (const DevBuffer &b : c->allocs) free_buffer(b, c->stream);
     delete c;
 }
 

@@ -119,7 +119,7 @@ class Info(ctypes.Structure):
 SYMBOLS = ["drts_assemble", "drts_inject_source", "drts_step_n", "drts_read_detectors",
            "drts_read_state", "drts_write_state", "drts_run_host", "drts_export_rows",
            "drts_column_info", "drts_get_info", "drts_host_tables", "drts_two_step_tables", "drts_set_launch", "drts_destroy",
-           "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_set_alloc_fault", "drts_autotune",
+           "drts_last_error", "drts_state_sum_noalloc", "drts_set_fault", "drts_set_alloc_fault", "drts_set_allocator", "drts_autotune",
            "drts_set_step_mode", "drts_server_create", "drts_server_submit", "drts_server_tick",
            "drts_server_poll", "drts_server_result", "drts_server_result_state",
            "drts_server_cancel", "drts_server_release",
@@ -187,6 +187,7 @@ def load(path: str = LIB_PATH):
     lib.drts_server_result_state.argtypes = [vp, i64, i32, vp]
     lib.drts_server_cancel.argtypes = [vp, i64]
     lib.drts_set_alloc_fault.argtypes = [i64]
+    lib.drts_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
     lib.drts_server_release.argtypes = [vp, i64]
     lib.drts_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
     lib.drts_server_last_error.argtypes = [vp]
@@ -205,6 +206,44 @@ def load(path: str = LIB_PATH):
 
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+# drts_alloc_fn / drts_free_fn
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_allocator_refs = None           # the installed callbacks, kept alive while installed
+
+
+def use_torch_allocator():
+    """Let PyTorch's caching allocator supply the device buffers of the
+    contexts made from now on (drts_set_allocator): they count in
+    torch.cuda.memory_allocated() and return to its cache on close."""
+    import torch
+    global _allocator_refs
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      int(stream) if stream else None)
+        except Exception:          # out of memory: the library reports DRTS_ENOMEM
+            return None
+
+    def _free(ptr, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    refs = (ALLOC_FN(_alloc), FREE_FN(_free))
+    st = load().drts_set_allocator(refs[0], refs[1], None)
+    if st != OK:
+        raise DrtsError(st, "drts_set_allocator")
+    _allocator_refs = refs
+
+
+def use_cuda_allocator():
+    """Back to cudaMalloc / cudaFree for contexts made from now on.  Buffers
+    already taken from another allocator still go back to it; keep its
+    callbacks alive until those contexts are closed (this module keeps the
+    last installed pair)."""
+    load().drts_set_allocator(ALLOC_FN(), FREE_FN(), None)
 
 
 def set_alloc_fault(n_ok):

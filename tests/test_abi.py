@@ -151,7 +151,10 @@ def test_binding_signatures_match_header():
                 assert t in (C.c_void_p, C.c_char_p) or issubclass(t, C._Pointer), (name, decl, t)
             else:
                 base = decl.split()[-2] if len(decl.split()) > 1 else decl
-                assert t is scalar[base], (name, decl, t)
+                if base.endswith("_fn"):           # callback typedefs: ctypes function pointers
+                    assert issubclass(t, C._CFuncPtr), (name, decl, t)
+                else:
+                    assert t is scalar[base], (name, decl, t)
         if ret.replace(" ", "") == "constchar*":
             assert fn.restype is C.c_char_p, name
         elif ret == "void":
@@ -215,3 +218,13 @@ def test_alloc_fault_hook_needs_no_device():
     lib = drts.load()
     assert lib.drts_set_alloc_fault(3) == drts.OK
     assert lib.drts_set_alloc_fault(-5) == drts.OK
+
+
+def test_allocator_needs_both_functions():
+    """drts_set_allocator takes both callbacks or neither (host state only)."""
+    from paper_1611_08536_gb300 import build, drts
+    build.build()
+    lib = drts.load()
+    keep = drts.ALLOC_FN(lambda n, s, u: None)
+    assert lib.drts_set_allocator(keep, drts.FREE_FN(), None) == drts.EINVAL
+    assert lib.drts_set_allocator(drts.ALLOC_FN(), drts.FREE_FN(), None) == drts.OK

@@ -119,3 +119,28 @@ def test_assembly_survives_every_failed_allocation(gpu, oracle_mod, precision):
     y = oracle_mod.spmv(oracle_mod.assemble(prob), x0)
     tol = 1e-6 if precision == I.FP32 else 2e-3
     assert np.abs(x1 - y).sum() / np.abs(y).sum() < tol
+
+
+def test_torch_caching_allocator_owns_context_buffers(gpu, oracle_mod):
+    """With drts_set_allocator pointed at PyTorch's caching allocator the
+    context's device buffers are PyTorch's (counted by
+    torch.cuda.memory_allocated, returned on close) and the step is the same."""
+    import torch
+    prob, _ = I.three_layers(10, precision=I.FP32)
+    rng = np.random.default_rng(8)
+    x0 = rng.random(prob.n_states)
+    before = torch.cuda.memory_allocated()
+    try:
+        gpu.use_torch_allocator()
+        with gpu.Context(prob, max_steps=2) as ctx:
+            held = torch.cuda.memory_allocated() - before
+            assert held >= ctx.info().matrix_bytes
+            ctx.write_state(x0)
+            ctx.step_n(1)
+            x1 = ctx.read_state()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == before
+    finally:
+        gpu.use_cuda_allocator()
+    y = oracle_mod.spmv(oracle_mod.assemble(prob), x0)
+    assert np.abs(x1 - y).sum() / np.abs(y).sum() < 1e-6
