@@ -437,7 +437,8 @@ try {
     if (it == s->reqs.end()) return sfail(s, DRTS_EINVAL, "unknown request");
     Request &r = *it->second;
     if (r.state == DRTS_REQ_QUEUED) {
-        s->queue.erase(std::find(s->queue.begin(), s->queue.end(), id));
+        auto q = std::find(s->queue.begin(), s->queue.end(), id);
+        if (q != s->queue.end()) s->queue.erase(q);
     } else if (r.state == DRTS_REQ_RUNNING) {
         // between ticks; the tick graph joins every side stream back into
         // the main stream, so these two waits leave nothing in flight
@@ -447,7 +448,8 @@ try {
         drts_destroy(r.ctx);
         r.ctx = nullptr;
         s->used -= r.footprint;
-        s->resident.erase(std::find(s->resident.begin(), s->resident.end(), id));
+        auto k = std::find(s->resident.begin(), s->resident.end(), id);
+        if (k != s->resident.end()) s->resident.erase(k);
     } else {
         return sfail(s, DRTS_ESTATE, "request already finished, failed or cancelled");
     }
