@@ -10,7 +10,11 @@ contraction); this module only compiles it with gcc and marshals numpy arrays.
 Parity status of each function (pins are in ``tests/test_oracle_pins.py``):
   * ``raw_stencil``   pinned: closed-form weights of Eq. 18/19, HG g=0, Eq. 24
                       column sums; the HG kernel's mean cosine slope (Legendre
-                      expansion), its g -> -g reflection and forward limit.
+                      expansion), its g -> -g reflection and forward limit;
+                      the quadrature-weighted kernel (problem field
+                      ``direction_weights``) by its weights' sphere averages
+                      up to degree 7, its mean cosine and the cube's 48
+                      symmetries.
   * ``assemble``      pinned: column sums, mirror conservation, dense brute
                       force on 4^3, ballistic translation, single-scatter line,
                       irreducibility, invariance under the cube's symmetries
