@@ -90,7 +90,7 @@ def test_assembly_survives_every_failed_allocation(gpu, oracle_mod, precision):
     device memory in use), and the first k past the last allocation
     assembles a context whose step matches the oracle."""
     import torch
-    prob, src = I.three_layers(8, precision=precision)
+    prob, _ = I.three_layers(8, precision=precision)
     free = []
     try:
         for k in range(200):
